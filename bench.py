@@ -1,0 +1,354 @@
+"""Benchmark: implicit MPM Lite time steps per second on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path through the C ABI: mpml_resample
+(sort, P2Q, Q2N), mpml_newton_step (stretch reconstruction, Newton with
+Jacobi-PCG to relative residual 1e-6 and line search), mpml_g2p.
+
+Workload: two Neo-Hookean spheres (E = 1e6 Pa, nu = 0.4, r = 0.15 m, rho =
+1000) approaching at 2 m/s relative velocity on a 168^3 grid with 8
+particles per cell (1,073,088 particles), dt = 2e-3 s, starting at contact so
+that every step solves a nonlinear system; FP32 with FP64 reductions.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (bounded sample, see cpu_baseline).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton steps/s & HVP GB/s at rel resid 1e-6; learned-precond FP32 vs plain PCG"
+WORKLOAD = ("two Neo-Hookean spheres (E=1e6, nu=0.4, r=0.15) colliding at 2 m/s on a 168^3 grid, "
+            "8 particles/cell (1,073,088 particles), dt=2e-3, starting at contact")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=168, help="grid cells per axis")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--check-every", type=int, default=16)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("k_newton.cu", "mpml_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2602_07853_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """dram bytes per HVP launch from the committed ncu summary, if taken on the current kernel."""
+    path = os.path.join(ROOT, "profiles", "hvp_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("kernel_hash") != kernel_hash():
+        return None
+    return d.get("dram_bytes_per_launch_full_size")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_sample(sc, newton_iters_per_step):
+    """Oracle on the full workload, bounded: unload, stretch, ONE Newton iteration
+    (full Jacobi-PCG to 1e-6), load.  Step time = fixed part + newton_iters_per_step
+    x one Newton iteration."""
+    import oracle
+
+    o = oracle.Oracle(oracle.make_scene(sc.n, sc.dx, sc.dt, sc.gravity,
+                                        [(m.model, m.E, m.nu) for m in sc.materials],
+                                        wall_layers=sc.wall_layers, inv_dx=sc.inv_dx))
+    p = sc.particles(np.float32)
+    p = {k: (v.astype(np.float64) if k != "mat" else v) for k, v in p.items()}
+    t0 = time.perf_counter()
+    o.unload(**p)
+    o.stretch()
+    t1 = time.perf_counter()
+    o.newton(oracle.default_solver(newton_max=1))
+    t2 = time.perf_counter()
+    o.load()
+    t3 = time.perf_counter()
+    fixed = (t1 - t0) + (t3 - t2)
+    per_newton = t2 - t1
+    return fixed + newton_iters_per_step * per_newton, fixed, per_newton
+
+
+def oracle_newton_count(n):
+    path = os.path.join(ROOT, "oracle", "bench_workload_counts.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        if str(n) in d:
+            return d[str(n)]["newton_iters_first_step"]
+    return 8
+
+
+def run_reference(args, rank, world):
+    from paper_2602_07853_gb300 import scenes
+
+    if rank != 0:
+        return 0
+    sc = scenes.two_spheres(args.n, gap=1.0 / args.n)
+    nnewton = oracle_newton_count(args.n)
+    for _ in range(args.warmup):
+        oracle_sample(sc, nnewton)
+    times = []
+    for _ in range(args.steps):
+        t, fixed, per_newton = oracle_sample(sc, nnewton)
+        times.append(t)
+    total = float(np.sum(times))
+    value = args.steps / total
+    sample = (f"full workload, per step: unload+stretch+load plus ONE Newton iteration (Jacobi-PCG to 1e-6) "
+              f"timed, step time = fixed + {nnewton} x Newton iteration ({nnewton} = the oracle's own Newton "
+              f"count on this workload's first step); single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": args.n, "precision": "fp64", "preconditioner": "jacobi",
+                       "cg_rtol": 1e-6, "newton_rtol": 1e-6},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_2602_07853_gb300.mpml as m
+    from paper_2602_07853_gb300 import scenes
+
+    torch.cuda.set_device(local_rank)
+    m.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    sc = scenes.two_spheres(args.n, gap=1.0 / args.n)
+    mats = [m.material(mt.model, *m.lame_parameters(mt.E, mt.nu)) for mt in sc.materials]
+    desc = m.scene_desc(sc.n, sc.dx, sc.dt, sc.gravity, m.FP32, sc.wall_layers, sc.plate, sc.inv_dx)
+    stream = torch.cuda.current_stream()
+    ctx = m.mpml_create(desc, mats, stream.cuda_stream)
+    p32 = sc.particles(np.float32)
+    init = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in p32.items()}
+    cur = {k: v.clone() for k, v in init.items()}
+    parts = m.particles_from_tensors(cur["x"], cur["v"], cur["F"], cur["G"], cur["mp"], cur["Vp"], cur["mat"])
+    opts = m.solver_opts(check_every=args.check_every)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def reset():
+        for k in cur:
+            cur[k].copy_(init[k])
+
+    def one_step(t):
+        m.mpml_set_time(ctx, t)
+        m.mpml_resample(ctx, parts)
+        rc, st = m.mpml_newton_step(ctx, opts)
+        m.mpml_g2p(ctx, parts)
+        return st
+
+    # warm-up (each step restarts from the contact state so all steps do equal work)
+    for _ in range(args.warmup):
+        reset()
+        one_step(0.0)
+    barrier()
+    m.mpml_set_profiling(ctx, 1)
+    launches0 = m.mpml_kernel_launches(ctx)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    newton_its, cg_its = [], []
+    barrier()
+    for i in range(args.steps):
+        reset()
+        flush.zero_()  # L2 flush (256 MB > 129 MB L2) outside the timed events
+        ev[i][0].record(stream)
+        st = one_step(0.0)
+        ev[i][1].record(stream)
+        newton_its.append(st.newton_iters)
+        cg_its.append(st.cg_iters_total)
+    barrier()
+    clk = clocks.stop()
+    launches = m.mpml_kernel_launches(ctx) - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    hvp_n, hvp_ms, hvp_bytes = m.mpml_hvp_timing(ctx)
+    m.mpml_set_profiling(ctx, 0)
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        host = {k: v.cpu().pin_memory() for k, v in init.items()}
+        hcur = {k: v.clone().pin_memory() for k, v in host.items()}
+        hparts = m.particles_from_tensors(hcur["x"], hcur["v"], hcur["F"], hcur["G"], hcur["mp"], hcur["Vp"],
+                                          hcur["mat"])
+        for k in hcur:
+            hcur[k].copy_(host[k])
+        m.mpml_resample(ctx, hparts)
+        m.mpml_newton_step(ctx, opts)
+        m.mpml_g2p(ctx, hparts)
+        barrier()
+        t_e2e = 0.0
+        for i in range(args.steps):
+            for k in hcur:
+                hcur[k].copy_(host[k])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m.mpml_set_time(ctx, 0.0)
+            m.mpml_resample(ctx, hparts)
+            m.mpml_newton_step(ctx, opts)
+            m.mpml_g2p(ctx, hparts)  # synchronises after the device-to-host copies
+            t_e2e += time.perf_counter() - t0
+        n = sc.num_particles
+        per = 4 * (3 + 3 + 9 + 9 + 1 + 1) + 4
+        e2e = {"value": world * args.steps / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": n * per,
+               "d2h_bytes_per_step": n * per}
+
+    peaks, peak_kind = measured_peaks()
+    roof = None
+    if hvp_n > 0:
+        mean_ms = hvp_ms / hvp_n
+        achieved = hvp_bytes / (mean_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(),
+                "peak_kind": peak_kind, "kernel": "k_hvp", "launches_timed": hvp_n, "mean_launch_ms": mean_ms,
+                "bytes_per_launch": hvp_bytes}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        nn = float(np.mean(newton_its)) if newton_its else 8.0
+        t_step, fixed, per_newton = oracle_sample(sc, nn)
+        cpu = {"value": 1.0 / t_step, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": (f"full workload: unload+stretch+load ({fixed:.1f} s) plus ONE Newton iteration with "
+                          f"Jacobi-PCG to 1e-6 ({per_newton:.1f} s), scaled to {nn:.1f} Newton iterations per "
+                          "step (the GPU run's mean); single thread")}
+    counts = m.mpml_counts(ctx)
+    m.mpml_destroy(ctx)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": args.n, "particles": int(counts["particles"]),
+                           "active_cells": int(counts["cells"]), "dof_nodes": int(counts["nodes"]),
+                           "precision": "fp32 storage and arithmetic, fp64 reductions",
+                           "preconditioner": "jacobi", "cg_rtol": 1e-6, "newton_rtol": 1e-6,
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "newton_iters_per_step": float(np.mean(newton_its)),
+                "cg_iters_per_step": float(np.mean(cg_its)),
+                "newton_iters_per_s": float(np.sum(newton_its)) / (total_ms / 1e3),
+                "hvp_gbs": roof["achieved"] if roof else None,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/*
+ * mpml.h - C ABI of the GB300 (sm_103a) MPM Lite hot path.
+ *
+ * MPM Lite (arXiv 2602.07853) advances particles by one implicit time step
+ * in three calls that follow Algorithm 1 of the paper:
+ *
+ *   mpml_resample     Algorithm 2 (Unload): particle binning and sort, the
+ *                     trilinear particle-to-centre transfer of mass, APIC
+ *                     momentum, velocity gradient, volume and extensive
+ *                     Kirchhoff stress (Sec. 3.1, 3.2), and the constant
+ *                     weight centre-to-node gather (Sec. 3.3).
+ *   mpml_newton_step  Algorithm 3 (Integrate, implicit): rotation-free stretch
+ *                     reconstruction at every active centre (Sec. 4.2, 4.3)
+ *                     and Newton on the incremental potential of Sec. 4.2,
+ *                     matrix-free Jacobi-PCG (or learned-preconditioner
+ *                     flexible CG) with a backtracking line search.
+ *   mpml_g2p          Algorithm 4 (Load): node-to-centre sampling of v and
+ *                     its gradient (Sec. 3.3), trilinear interpolation to the
+ *                     particles (Sec. 3.1), advection, F update.
+ *
+ * Conventions
+ *   - Plain C types only.  Pointers are either device pointers (MPML_MEM_DEVICE)
+ *     or host pointers (MPML_MEM_HOST, pinned or pageable); the caller owns
+ *     them and the library never frees them.
+ *   - Particle arrays are array-of-structures: x, v are n*3, F, G are n*9
+ *     row-major (F[9p + 3r + c]), mass, volume are n, mat is n int32.  Their
+ *     element type is float in an MPML_FP32 context and double in MPML_FP64.
+ *   - Every call is asynchronous on the context's CUDA stream except where
+ *     it says it synchronises.  A status returned by a call is the status of
+ *     what that call could check; errors detected on the device (particle
+ *     outside the grid, non-finite input, failed stretch inversion) are
+ *     latched and returned by the next synchronising call.
+ *   - The library owns one context's scratch (grid, cell, node and solver
+ *     buffers), allocated with cudaMalloc and grown only inside
+ *     mpml_resample; mpml_destroy frees it.
+ *   - Grid: n[a] cells per axis of size dx, nodes 0..n[a], origin 0.  Cells
+ *     and nodes are grouped in 8x8x8 bricks; "key" below means the
+ *     brick-major index ((bz*NBy + by)*NBx + bx)*512 + (lz*64 + ly*8 + lx)
+ *     with NB_a = (n[a] >> 3) + 1.
+ */
+#ifndef MPML_H
+#define MPML_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPML_MAX_MATS 4
+
+typedef struct mpml_ctx_s* mpml_ctx;
+
+typedef enum {
+  MPML_OK = 0,
+  MPML_WARN_NOT_CONVERGED = 1, /* Newton hit its cap or the line search failed */
+  MPML_ERR_ARG = -1,           /* invalid argument (null pointer, bad size, call order) */
+  MPML_ERR_OUT_OF_DOMAIN = -2, /* a particle's 2x2x2 centre stencil leaves the grid */
+  MPML_ERR_NONFINITE = -3,     /* NaN/Inf in particle input or in the solve */
+  MPML_ERR_STRETCH = -4,       /* stress-to-stretch inversion has no admissible root */
+  MPML_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+  MPML_ERR_CUDA = -6,          /* a CUDA runtime call failed */
+  MPML_ERR_NOMEM = -7          /* device allocation failed */
+} mpml_status;
+
+enum { MPML_FIXED_COROTATED = 0, MPML_NEO_HOOKEAN = 1, MPML_HENCKY = 2 };
+enum { MPML_FP32 = 0, MPML_FP64 = 1 };
+enum { MPML_MEM_DEVICE = 0, MPML_MEM_HOST = 1 };
+enum { MPML_PRECOND_JACOBI = 0, MPML_PRECOND_LEARNED = 1 };
+
+/* Isotropic hyperelastic material with Lame parameters (mu, lambda).
+ * MPML_HENCKY: StVK with Hencky strain (Sec. 4.3.1); MPML_NEO_HOOKEAN: split
+ * Neo-Hookean, kappa = 2/3 mu + lambda (Sec. 4.3.2); MPML_FIXED_COROTATED:
+ * psi = mu sum(s_i - 1)^2 + lambda/2 (J - 1)^2 (its stretch inverse is the
+ * library's, the paper gives the general recipe of Sec. 4.3). */
+typedef struct {
+  int model;
+  double mu, lambda;
+} mpml_material;
+
+/* Scene: grid, time step, gravity (folded into the inertia target
+ * vhat = v^n + dt g), precision, Dirichlet boundary.  Nodes with an index
+ * below wall_layers or above n - wall_layers on any axis are sticky (v = 0);
+ * when has_plate, nodes whose position lies in [plate_lo + t plate_vel,
+ * plate_hi + t plate_vel] (t from mpml_set_time) move with plate_vel. */
+typedef struct {
+  int n[3];
+  double dx;
+  double inv_dx; /* exactly 1/dx as the caller defines it; used for binning */
+  double dt;
+  double gravity[3];
+  int precision; /* MPML_FP32 or MPML_FP64 */
+  int wall_layers;
+  int has_plate;
+  double plate_lo[3], plate_hi[3], plate_vel[3];
+} mpml_scene_desc;
+
+typedef struct {
+  int64_t n;
+  int mem;          /* MPML_MEM_DEVICE or MPML_MEM_HOST */
+  void* x;          /* n*3 */
+  void* v;          /* n*3 */
+  void* F;          /* n*9 */
+  void* G;          /* n*9 */
+  void* mass;       /* n */
+  void* volume;     /* n */
+  int32_t* mat;     /* n, material index < n_mats */
+  int32_t* perm;    /* optional (may be NULL), written by mpml_resample:
+                       perm[s] = index before the call of the s-th sorted particle */
+} mpml_particles;
+
+typedef struct {
+  double cg_rtol;      /* stop CG when ||r|| <= cg_rtol ||r0|| (default 1e-6) */
+  int cg_max;          /* CG iteration cap per Newton iteration */
+  double newton_rtol;  /* stop Newton when ||g|| <= newton_rtol ||g(v0)|| */
+  double newton_atol;  /* ... or when ||g|| <= newton_atol */
+  int newton_max;      /* Newton iteration cap */
+  double ls_c1;        /* Armijo constant */
+  int ls_max;          /* maximal number of step halvings */
+  int precond;         /* MPML_PRECOND_JACOBI or MPML_PRECOND_LEARNED */
+  int check_every;     /* CG iterations between convergence polls (host-driven loop) */
+  int use_graph;       /* 1: run the CG loop as a CUDA graph with a device-side while loop */
+} mpml_solver_opts;
+
+typedef struct {
+  int status;
+  int newton_iters;
+  int cg_iters_total;
+  int cg_iters[64];          /* per Newton iteration (first 64) */
+  double alpha[64];          /* accepted line-search step per Newton iteration */
+  double cg_rel_resid[64];   /* CG recurrence residual ||r||/||r0|| at exit */
+  double g0_norm, g_norm;    /* ||g(v0)||, ||g|| at exit (FP64 sums) */
+  double phi0, phi;          /* incremental potential at v0 and at exit */
+  int64_t n_particles, n_cells, n_nodes, n_bricks;
+} mpml_solve_stats;
+
+/* Lifecycle ----------------------------------------------------------- */
+/* stream: a cudaStream_t (NULL = legacy default stream).  n_mats <= MPML_MAX_MATS.
+ * Returns MPML_ERR_ARG for invalid sizes (n[a] < 2, dx <= 0, dt <= 0, ...). */
+int mpml_create(const mpml_scene_desc* desc, const mpml_material* mats, int n_mats,
+                void* stream, mpml_ctx* out);
+int mpml_destroy(mpml_ctx ctx);
+const char* mpml_status_str(int status);
+/* Sets the time used by the moving Dirichlet box for the next step. */
+int mpml_set_time(mpml_ctx ctx, double t);
+/* Blocks until the context's stream is idle; returns the latched device status. */
+int mpml_sync(mpml_ctx ctx);
+
+/* Algorithm 1 ---------------------------------------------------------- */
+/* Algorithm 2.  Reads the particles, sorts a library-owned copy by the key
+ * of the base centre floor(x/dx - 1/2) (stable), builds the active cells
+ * (centres with a nonzero trilinear weight) and DOF nodes (their corners),
+ * and runs P2Q and Q2N.  Synchronises once (to size the grid).  Returns
+ * MPML_ERR_OUT_OF_DOMAIN / MPML_ERR_NONFINITE for bad particles. */
+int mpml_resample(mpml_ctx ctx, const mpml_particles* p);
+/* Algorithm 3, implicit.  Synchronises (convergence tests); fills stats if
+ * non-NULL.  opts may be NULL (defaults). */
+int mpml_newton_step(mpml_ctx ctx, const mpml_solver_opts* opts, mpml_solve_stats* stats);
+/* Algorithm 4.  Writes x, v, F, G, mass, volume, mat of p (the same arrays
+ * or others of the same size) in the sorted order of the last resample.
+ * Asynchronous for device memory; for MPML_MEM_HOST it synchronises after
+ * the device-to-host copies. */
+int mpml_g2p(mpml_ctx ctx, const mpml_particles* p);
+
+/* Introspection and operator access (host buffers; synchronising) ------ */
+/* out[0..3] = particles, active cells, DOF nodes, bricks of the last resample */
+int mpml_counts(mpml_ctx ctx, int64_t out[4]);
+enum { MPML_KEYS_PARTICLES = 0, MPML_KEYS_CELLS = 1, MPML_KEYS_NODES = 2 };
+/* Sorted particle keys, active-cell keys or DOF-node keys (ascending). */
+int mpml_get_keys(mpml_ctx ctx, int what, int64_t* out);
+enum {
+  MPML_F_CELL_MASS = 0,      /* m_c                       1 per active cell  */
+  MPML_F_CELL_VEL = 1,       /* v_c                       3                  */
+  MPML_F_CELL_VGRAD = 2,     /* G_c                       9 row-major        */
+  MPML_F_CELL_VOL = 3,       /* V_ck                      n_mats             */
+  MPML_F_CELL_TAU = 4,       /* tau_ck                    n_mats*9           */
+  MPML_F_CELL_STRETCH = 5,   /* S_ck (after newton_step)  n_mats*9           */
+  MPML_F_CELL_VEL_NEW = 6,   /* v_c^{n+1} (after g2p)     3                  */
+  MPML_F_CELL_VGRAD_NEW = 7, /* G_c^{n+1} (after g2p)     9                  */
+  MPML_F_NODE_MASS = 10,     /* m_i                       1 per DOF node     */
+  MPML_F_NODE_VEL = 11,      /* v_i^n                     3                  */
+  MPML_F_NODE_VHAT = 12,     /* vhat_i                    3                  */
+  MPML_F_NODE_FIXED = 13,    /* 1.0 on Dirichlet nodes    1                  */
+  MPML_F_NODE_VNEW = 14      /* v_i^{n+1}                 3                  */
+};
+/* Copies a field, in key order of active cells / DOF nodes, as double. */
+int mpml_get_field(mpml_ctx ctx, int field, double* out);
+/* Overrides v^{n+1} at the DOF nodes (n_nodes*3 doubles in key order). */
+int mpml_set_node_velocity(mpml_ctx ctx, const double* v);
+/* Reconstructs the stretches (Algorithm 3 line 9) without solving. */
+int mpml_stretch(mpml_ctx ctx);
+/* Incremental potential and its gradient (masked to free DOFs) at node
+ * velocities v (n_nodes*3, key order).  grad may be NULL. */
+int mpml_eval(mpml_ctx ctx, const double* v, double* phi, double* grad);
+/* Builds the per-cell projected tangent at v (n_nodes*3). */
+int mpml_linearize(mpml_ctx ctx, const double* v);
+/* y = H p with the last linearisation (masked), n_nodes*3 each. */
+int mpml_hvp(mpml_ctx ctx, const double* p, double* y);
+
+/* Profiling: when enabled, the HVP kernel launches of mpml_newton_step are
+ * bracketed by CUDA events on the context stream; mpml_hvp_timing returns
+ * the number of timed launches, their total milliseconds and the bytes one
+ * launch moves by the library's count (K_c, p, q, m per active brick). */
+int mpml_set_profiling(mpml_ctx ctx, int enable);
+int mpml_hvp_timing(mpml_ctx ctx, int64_t* launches, double* total_ms, double* bytes_per_launch);
+/* Runs `iters` back-to-back HVPs on the current linearisation with a
+ * device-resident direction and returns the mean kernel milliseconds
+ * (CUDA events on the context stream).  Synchronising. */
+int mpml_hvp_bench(mpml_ctx ctx, int iters, double* mean_ms);
+/* Number of kernel launches issued on the context stream since creation. */
+int64_t mpml_kernel_launches(mpml_ctx ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1105 @@
+// Algorithm 3 (Integrate, implicit branch) on the voxel hex mesh.
+//
+// Stretch reconstruction (Sec. 4.2, 4.3): per active centre and material,
+//   tau = (V tau)/V, tau = Q diag(t) Q^T, s_i from the principal relation of
+//   the material, S = Q diag(s) Q^T (FP64 on the device); stored as S - I.
+// Incremental potential (Sec. 4.2, Algorithm 3 line 12):
+//   Phi(v) = sum_i 1/2 m_i |v_i - vhat_i|^2 + sum_c sum_k V_ck psi_k(F_ck(v)),
+//   F_ck(v) = (I + dt G_c(v)) S_ck, G_c(v) = sum_i v_i (x) grad w_ic.
+// Newton prep (per Newton iteration): per cell the gradient contribution
+//   dt V P S^T grad w_ic, and the PSD-projected tangent on D = G_c(p):
+//   K_c = dt^2 sum_k V_ck L_S^T A_k^+ L_S, built from the analytic eigensystem
+//   of isotropic energies in the signed-SVD frame (3x3 block of psi's Hessian
+//   in the principal stretches, and the twist/flip pairs), eigenvalues
+//   clamped at 0.  Stored as 45 packed floats per cell.
+// HVP (the hot loop): y = M p + sum_c B_c^T K_c B_c p; one CTA per 8^3 brick,
+//   the 9^3 node block of p staged once in shared memory, K_c streamed
+//   coalesced, per-node sums of the 8 neighbouring cells formed in shared
+//   memory, interior nodes stored once, brick-face nodes added atomically.
+//   p^T H p = sum m |p|^2 + sum_c D^T K D is accumulated on the fly (FP64).
+// Jacobi-PCG with FP64 dot products; scalars updated by the last block of
+// each kernel (no host round trip inside an iteration).
+#include "mpml_internal.cuh"
+
+namespace mpml {
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of N doubles; thread 0 atomically adds them to dst[i]
+template <int N>
+__device__ __forceinline__ void block_add(double (&v)[N], double* const (&dst)[N]) {
+  __shared__ double sh[N][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double s = warp_sum(v[i]);
+    if (lane == 0) sh[i][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = lane < nw ? sh[i][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0 && s != 0.0) atomicAdd(dst[i], s);
+    }
+  }
+}
+
+// true in exactly one block: the last one to arrive (after a fence)
+__device__ __forceinline__ bool arrive_last(int* counter) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = atomicAdd(counter, 1);
+    last = (t == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  return last != 0;
+}
+
+__device__ __forceinline__ double vload(const double* p) { return *(volatile const double*)p; }
+
+enum { CNT_FIN = 0, CNT_HVP = 1, CNT_A = 2, CNT_B = 3, CNT_MISC = 4 };
+
+// ---------------------------------------------------------------------------
+// stretch reconstruction (FP64)
+// ---------------------------------------------------------------------------
+__device__ bool fc_sigma(double mu, double lam, const double t[3], double J, double s[3]) {
+  double c = lam * J * (J - 1);
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double disc = 0.25 + (t[i] - c) / (2 * mu);
+    if (disc < -1e-12) ok = false;
+    s[i] = 0.5 + sqrt(disc > 0 ? disc : 0);
+  }
+  return ok;
+}
+__device__ double fc_h(double mu, double lam, const double t[3], double J) {
+  double s[3];
+  fc_sigma(mu, lam, t, J, s);
+  return s[0] * s[1] * s[2] - J;
+}
+__device__ double cbrt_signed(double z) { return z >= 0 ? cbrt(z) : -cbrt(-z); }
+
+// principal stretches from principal Kirchhoff stresses; false if none admissible
+__device__ bool invert_principal(int model, double mu, double lam, const double t[3], double s[3]) {
+  if (model == MPML_HENCKY) {
+    // Sec. 4.3.1 closed form
+    if (!(mu > 0 && lam > -2 * mu / 3)) return false;
+    double tr = t[0] + t[1] + t[2];
+    double ls = tr / (2 * mu + 3 * lam);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s[i] = exp((t[i] - lam * ls) / (2 * mu));
+    return true;
+  }
+  if (model == MPML_NEO_HOOKEAN) {
+    // Sec. 4.3.2 / App. C; the one-real-root branch of Cardano uses u v = -p/3
+    double kap = 2.0 / 3.0 * mu + lam;
+    double alpha = (t[0] + t[1] + t[2]) / 3;
+    double arg = 1 + 2 * alpha / kap;
+    if (!(arg > 0)) return false;
+    double J = sqrt(arg);
+    double sc = mu * pow(J, -2.0 / 3.0);
+    double dl[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dl[i] = (t[i] - alpha) / sc;
+    double p = dl[0] * dl[1] + dl[1] * dl[2] + dl[2] * dl[0];
+    double q = dl[0] * dl[1] * dl[2] - J * J;
+    double disc = (q / 2) * (q / 2) + (p / 3) * (p / 3) * (p / 3);
+    double m;
+    if (disc >= 0) {
+      double sd = sqrt(disc);
+      double u = cbrt_signed(-q / 2 + (q <= 0 ? sd : -sd));
+      double v = (u != 0) ? -p / (3 * u) : 0;
+      m = u + v;
+    } else {
+      double r = 2 * sqrt(-p / 3);
+      double a = 3 * q / (2 * p) * sqrt(-3 / p);
+      a = a > 1 ? 1 : (a < -1 ? -1 : a);
+      m = r * cos(acos(a) / 3);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      double beta = m + dl[i];
+      if (!(beta > 0)) return false;
+      s[i] = sqrt(beta);
+    }
+    return true;
+  }
+  if (model == MPML_FIXED_COROTATED) {
+    // library's inverse: unique root of prod_i s_i(J) = J on J >= 1/2 (bisection)
+    if (!(mu > 0) || lam < 0) return false;
+    if (lam == 0) return fc_sigma(mu, lam, t, 1.0, s);
+    double tmin = fmin(t[0], fmin(t[1], t[2]));
+    double d = 0.25 + (tmin + 0.5 * mu) / lam;
+    if (d < 0) return false;
+    double lo = 0.5, hi = 0.5 + sqrt(d);
+    if (fc_h(mu, lam, t, lo) < 0 || fc_h(mu, lam, t, hi) > 0) return false;
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (fc_h(mu, lam, t, mid) > 0) lo = mid; else hi = mid;
+    }
+    return fc_sigma(mu, lam, t, 0.5 * (lo + hi), s);
+  }
+  return false;
+}
+
+struct SolveInfo {
+  double dt, dx;
+  int nm, nf;
+  MatParams<double> mat[MPML_MAX_MATS];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_stretch(const int* __restrict__ cblist, const uint8_t* __restrict__ cflag,
+                                                 const T* __restrict__ acc, SolveInfo si, T* __restrict__ cs,
+                                                 int* status) {
+  const int id = cblist[blockIdx.x];
+  for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+    if (!cflag[(int64_t)id * BV + l]) continue;
+    for (int k = 0; k < si.nm; ++k) {
+      T* so = cs + ((int64_t)id * si.nm + k) * 6 * BV + l;
+      const T* a = acc + (int64_t)id * si.nf * BV + l;
+      const double V = (double)a[acc_V(k) * BV];
+      if (V == 0.0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) so[q * BV] = T(0);
+        continue;
+      }
+      double tau[9];
+      const int ra[6] = {0, 1, 2, 0, 0, 1}, rb[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        double tq = (double)a[(acc_tau(k) + q) * BV] / V;
+        tau[3 * ra[q] + rb[q]] = tau[3 * rb[q] + ra[q]] = tq;
+      }
+      double ev[3], Q[9], s[3];
+      jacobi3<double>(tau, ev, Q);
+      if (!invert_principal(si.mat[k].model, si.mat[k].mu, si.mat[k].lam, ev, s)) {
+        atomicOr(status, ST_STRETCH);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) so[q * BV] = T(0);
+        continue;
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        double acc2 = 0;
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) acc2 += Q[3 * ra[q] + kk] * (s[kk] - 1.0) * Q[3 * rb[q] + kk];
+        so[q * BV] = (T)acc2;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// node-block staging: the 9^3 nodes of a cell brick (own 8^3 + upper halo)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void stage_nodes(int id, const int* __restrict__ nbr, const T* __restrict__ a,
+                                            const T* __restrict__ b, T beta, T (*sv)[729]) {
+  // sv[r][i] = a + beta * b (b may be null)
+  for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+    const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+    const int t = (nx < 8 && ny < 8 && nz < 8) ? id : __ldg(&nbr[id * NBR + nbr_index(nx >> 3, ny >> 3, nz >> 3)]);
+    const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      T val = T(0);
+      if (t >= 0) {
+        const int64_t o = (int64_t)t * 3 * BV + r * BV + l;
+        val = a[o];
+        if (b) val += beta * b[o];
+      }
+      sv[r][i] = val;
+    }
+  }
+}
+
+__device__ __forceinline__ int node_of(int l, int o) {
+  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+  return ((lz + ((o >> 2) & 1)) * 9 + (ly + ((o >> 1) & 1))) * 9 + (lx + (o & 1));
+}
+
+// D' = sum_o p_o (x) sgn_o (the 1/(4 dx) scale is folded into K)
+template <typename T>
+__device__ __forceinline__ void gather_D(int l, const T (*sv)[729], T D[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) D[q] = T(0);
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int i = node_of(l, o);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T pa = sv[a][i];
+      D[3 * a + 0] += (o & 1) ? pa : -pa;
+      D[3 * a + 1] += (o & 2) ? pa : -pa;
+      D[3 * a + 2] += (o & 4) ? pa : -pa;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-cell constitutive kernel: energy, gradient Q, projected K (D-space)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CellOut {
+  T Q[9];   // dt V P S^T / (4 dx)   (gradient, node contribution = Q sgn)
+  T K[45];  // dt^2 V L^T A+ L / (16 dx^2)
+  double psi;
+  bool ok;
+};
+
+template <typename T>
+__device__ void cell_material(const MatParams<T>& M, T V, const T Gd[9] /* dt*G */, const T s6[6], T kq, T kk,
+                              bool want_k, CellOut<T>& out) {
+  // S = I + s;  H = F - I = dt G + s + dt G s
+  T sm[9] = {s6[0], s6[3], s6[4], s6[3], s6[1], s6[5], s6[4], s6[5], s6[2]};
+  T H[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T acc = Gd[3 * a + b] + sm[3 * a + b];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += Gd[3 * a + k] * sm[3 * k + b];
+      H[3 * a + b] = acc;
+    }
+  T U[9], s[3], e[3], Vv[9], Jm1;
+  svd_from_h(H, U, s, e, Vv, Jm1);
+  Spec<T> sp;
+  if (!spectral(M, s, e, Jm1, sp)) {
+    out.ok = false;
+    return;
+  }
+  out.psi += (double)V * (double)sp.psi;
+  // W = S V = V + s V
+  T W[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T acc = Vv[3 * a + b];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += sm[3 * a + k] * Vv[3 * k + b];
+      W[3 * a + b] = acc;
+    }
+  // Q += kq V U diag(d1) W^T   (P S^T = U diag(d1) V^T S = U diag(d1) W^T)
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += U[3 * a + k] * sp.d1[k] * W[3 * b + k];
+      out.Q[3 * a + b] += kq * V * acc;
+    }
+  if (!want_k) return;
+  const T kv = kk * V;
+  // diagonal block: eigen-decomposition of d2, clamp
+  T ev[3], Qd[9];
+  jacobi3<T>(sp.d2, ev, Qd);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    if (!(ev[m] > T(0))) continue;
+    T d[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        T acc = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc += Qd[3 * i + m] * U[3 * a + i] * W[3 * b + i];
+        d[3 * a + b] = acc;
+      }
+    const T lam = kv * ev[m];
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+      for (int cc = r; cc < 9; ++cc) out.K[k45(r, cc)] += lam * d[r] * d[cc];
+  }
+  // twist (pm, E_ij - E_ji) and flip (pp, E_ij + E_ji) pairs
+  const T rs2 = T(0.70710678118654752440);
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int i = pair_i(p), j = pair_j(p);
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      const T lamv = sg == 0 ? sp.pp[p] : sp.pm[p];
+      if (!(lamv > T(0))) continue;
+      const T sgn = sg == 0 ? T(1) : T(-1);
+      T d[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) d[3 * a + b] = rs2 * (U[3 * a + i] * W[3 * b + j] + sgn * U[3 * a + j] * W[3 * b + i]);
+      const T lam = kv * lamv;
+#pragma unroll
+      for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int cc = r; cc < 9; ++cc) out.K[k45(r, cc)] += lam * d[r] * d[cc];
+    }
+  }
+}
+
+// node init: g = m (v - vhat), diag = m, inertia energy (all bricks, 512 thr)
+template <typename T>
+__global__ void __launch_bounds__(512) k_node_init(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
+                                                   const T* __restrict__ v, const T* __restrict__ vhat, T* g, T* diag,
+                                                   DevScalars* sc) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  const int64_t slot = (int64_t)id * BV + l;
+  const bool dof = nflag[slot] & NF_DOF;
+  double ein = 0;
+  const T mi = dof ? m[slot] : T(0);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int64_t o = (int64_t)id * 3 * BV + r * BV + l;
+    T d = dof ? v[o] - vhat[o] : T(0);
+    g[o] = mi * d;
+    diag[o] = mi;
+    ein += 0.5 * (double)mi * (double)d * (double)d;
+  }
+  double vals[1] = {ein};
+  double* const dst[1] = {&sc->phi_in};
+  block_add<1>(vals, dst);
+}
+
+// atomic add to a node slot addressed from a cell brick (local node 0..8 per axis)
+template <typename T>
+__device__ __forceinline__ T* node_ptr(T* base, int id, const int* __restrict__ nbr, int nx, int ny, int nz, int r) {
+  const int t = (nx < 8 && ny < 8 && nz < 8) ? id : __ldg(&nbr[id * NBR + nbr_index(nx >> 3, ny >> 3, nz >> 3)]);
+  if (t < 0) return nullptr;
+  return base + (int64_t)t * 3 * BV + r * BV + (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+}
+
+// Newton prep over cell bricks (256 threads, 2 cells each).
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                                 const uint8_t* __restrict__ cflag, const T* __restrict__ acc,
+                                                 const T* __restrict__ cs, const T* __restrict__ v, SolveInfo si,
+                                                 int want_k, T* __restrict__ K, T* g, T* diag, DevScalars* sc,
+                                                 int* status) {
+  __shared__ T sv[3][729];
+  const int id = cblist[blockIdx.x];
+  stage_nodes<T>(id, nbr, v, nullptr, T(0), sv);
+  __syncthreads();
+  const T gw = (T)(0.25 / si.dx);
+  const T kq = (T)(si.dt * 0.25 / si.dx);
+  const T kk = (T)(si.dt * si.dt / (16.0 * si.dx * si.dx));
+  double esum = 0;
+  int bad = 0;
+  MatParams<T> mats[MPML_MAX_MATS];
+#pragma unroll
+  for (int k = 0; k < MPML_MAX_MATS; ++k) {
+    mats[k].model = si.mat[k].model;
+    mats[k].mu = (T)si.mat[k].mu;
+    mats[k].lam = (T)si.mat[k].lam;
+  }
+  for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+    if (!cflag[(int64_t)id * BV + l]) continue;
+    T D[9];
+    gather_D<T>(l, sv, D);
+    T Gd[9];
+    const T sgd = (T)si.dt * gw;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Gd[q] = sgd * D[q];
+    CellOut<T> co;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) co.Q[q] = T(0);
+#pragma unroll
+    for (int q = 0; q < 45; ++q) co.K[q] = T(0);
+    co.psi = 0;
+    co.ok = true;
+    for (int k = 0; k < si.nm; ++k) {
+      const T V = acc[((int64_t)id * si.nf + acc_V(k)) * BV + l];
+      if (V == T(0)) continue;
+      T s6[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) s6[q] = cs[(((int64_t)id * si.nm + k) * 6 + q) * BV + l];
+      cell_material<T>(mats[k], V, Gd, s6, kq, kk, want_k != 0, co);
+    }
+    if (!co.ok) {
+      bad = 1;
+      continue;
+    }
+    esum += co.psi;
+    if (want_k) {
+      T* Kd = K + (int64_t)id * 45 * BV + l;
+#pragma unroll
+      for (int q = 0; q < 45; ++q) Kd[q * BV] = co.K[q];
+    }
+    // scatter gradient and Jacobi diagonal to the 8 corners
+    const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const T sg[3] = {(o & 1) ? T(1) : T(-1), (o & 2) ? T(1) : T(-1), (o & 4) ? T(1) : T(-1)};
+      const int nx = lx + (o & 1), ny = ly + ((o >> 1) & 1), nz = lz + ((o >> 2) & 1);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        T* gp = node_ptr(g, id, nbr, nx, ny, nz, a);
+        if (!gp) continue;
+        T gv = co.Q[3 * a] * sg[0] + co.Q[3 * a + 1] * sg[1] + co.Q[3 * a + 2] * sg[2];
+        atomicAdd(gp, gv);
+        if (want_k) {
+          T dv = 0;
+#pragma unroll
+          for (int b = 0; b < 3; ++b)
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) {
+              const int r = 3 * a + b, cc = 3 * a + bb;
+              dv += co.K[r <= cc ? k45(r, cc) : k45(cc, r)] * sg[b] * sg[bb];
+            }
+          atomicAdd(node_ptr(diag, id, nbr, nx, ny, nz, a), dv);
+        }
+      }
+    }
+  }
+  if (bad) atomicOr(status, ST_NONFINITE);
+  double vals[1] = {esum};
+  double* const dst[1] = {&sc->phi_el};
+  block_add<1>(vals, dst);
+}
+
+// finalize the gradient (mask), Jacobi inverse, |g|^2 and the CG start:
+// x = 0, r = -g, z = D^-1 r, p = z, q(face) = 0.
+template <typename T>
+__global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nflag, const T* __restrict__ m, T* g,
+                                                  T* diag_dinv, T* x, T* r, T* p, T* q, int init_cg, double rtol2,
+                                                  int cg_max, DevScalars* sc) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  const int64_t slot = (int64_t)id * BV + l;
+  const uint8_t f = nflag[slot];
+  const bool free_ = (f & NF_DOF) && !(f & NF_FIXED);
+  const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
+  double gg = 0, rz = 0, rr = 0, pmp = 0;
+  const T mi = free_ ? m[slot] : T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+    T gv = free_ ? g[o] : T(0);
+    g[o] = gv;
+    T di = free_ ? T(1) / diag_dinv[o] : T(0);
+    diag_dinv[o] = di;
+    gg += (double)gv * (double)gv;
+    if (init_cg) {
+      T rv = -gv, zv = di * rv;
+      x[o] = T(0);
+      r[o] = rv;
+      p[o] = zv;
+      if (face) q[o] = T(0);
+      rz += (double)rv * (double)zv;
+      rr += (double)rv * (double)rv;
+      pmp += (double)mi * (double)zv * (double)zv;
+    }
+  }
+  double vals[4] = {gg, rz, rr, pmp};
+  double* const dst[4] = {&sc->gg, &sc->rz, &sc->rr0, &sc->pMp};
+  block_add<4>(vals, dst);
+  if (arrive_last(&sc->counter[CNT_FIN]) && threadIdx.x == 0) {
+    double rr0 = vload(&sc->rr0);
+    sc->tol2 = rtol2 * rr0;
+    sc->done = (rr0 == 0.0) ? 1 : 0;
+    sc->iters = 0;
+    sc->cg_max = cg_max;
+    sc->rr = 0;
+    sc->rr_last = rr0;
+    sc->rz_new = 0;
+    sc->pKp = 0;
+    sc->counter[CNT_FIN] = 0;
+  }
+}
+
+// HVP over cell bricks: q = M p + sum_c B^T K B p (faces atomically).
+template <typename T>
+__global__ void __launch_bounds__(256) k_hvp(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                             const uint8_t* __restrict__ cflag, const T* __restrict__ K,
+                                             const T* __restrict__ p, const T* __restrict__ m, T* q,
+                                             DevScalars* sc, int finalize) {
+  if (finalize && *(volatile int*)&sc->done) return;
+  extern __shared__ __align__(16) unsigned char hvp_smem[];
+  T (*sv)[729] = reinterpret_cast<T (*)[729]>(hvp_smem);
+  T (*skd)[BV] = reinterpret_cast<T (*)[BV]>(hvp_smem + sizeof(T) * 3 * 729 + (16 - (sizeof(T) * 3 * 729) % 16) % 16);
+  const int id = cblist[blockIdx.x];
+  stage_nodes<T>(id, nbr, p, nullptr, T(0), sv);
+  __syncthreads();
+  double pkp = 0;
+  for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+    T KD[9];
+    if (cflag[(int64_t)id * BV + l]) {
+      T D[9];
+      gather_D<T>(l, sv, D);
+      const T* Kc = K + (int64_t)id * 45 * BV + l;
+      T Kv[45];
+#pragma unroll
+      for (int j = 0; j < 45; ++j) Kv[j] = __ldg(&Kc[j * BV]);
+#pragma unroll
+      for (int r = 0; r < 9; ++r) KD[r] = T(0);
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        KD[r] += Kv[k45(r, r)] * D[r];
+#pragma unroll
+        for (int cc = r + 1; cc < 9; ++cc) {
+          KD[r] += Kv[k45(r, cc)] * D[cc];
+          KD[cc] += Kv[k45(r, cc)] * D[r];
+        }
+      }
+      T dkd = 0;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) dkd += D[r] * KD[r];
+      pkp += (double)dkd;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 9; ++r) KD[r] = T(0);
+    }
+#pragma unroll
+    for (int r = 0; r < 9; ++r) skd[r][l] = KD[r];
+  }
+  __syncthreads();
+  // node sums over the 9^3 block
+  for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+    const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+    T y[3] = {0, 0, 0};
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int cx = nx - (o & 1), cy = ny - ((o >> 1) & 1), cz = nz - ((o >> 2) & 1);
+      if (cx < 0 || cy < 0 || cz < 0 || cx > 7 || cy > 7 || cz > 7) continue;
+      const int c = (cz * 8 + cy) * 8 + cx;
+      const T s0 = (o & 1) ? T(1) : T(-1), s1 = (o & 2) ? T(1) : T(-1), s2 = (o & 4) ? T(1) : T(-1);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) y[a] += skd[3 * a][c] * s0 + skd[3 * a + 1][c] * s1 + skd[3 * a + 2][c] * s2;
+    }
+    const bool own = nx < 8 && ny < 8 && nz < 8;
+    const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
+    if (own) {
+      const int l = nz * 64 + ny * 8 + nx;
+      const T mi = m[(int64_t)id * BV + l];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        T val = y[a] + mi * sv[a][i];
+        T* dst = q + (int64_t)id * 3 * BV + a * BV + l;
+        if (excl) *dst = val;
+        else if (val != T(0)) atomicAdd(dst, val);
+      }
+    } else {
+      const int t = __ldg(&nbr[id * NBR + nbr_index(nx >> 3, ny >> 3, nz >> 3)]);
+      if (t < 0) continue;
+      const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (y[a] != T(0)) atomicAdd(q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
+    }
+  }
+  double vals[1] = {pkp};
+  double* const dst[1] = {&sc->pKp};
+  block_add<1>(vals, dst);
+  if (finalize && arrive_last(&sc->counter[CNT_HVP]) && threadIdx.x == 0) {
+    double pq = vload(&sc->pMp) + vload(&sc->pKp);
+    if (!(pq > 0.0)) {
+      sc->done = 1;  // breakdown (zero direction)
+      sc->alpha = 0;
+    } else {
+      sc->alpha = vload(&sc->rz) / pq;
+    }
+    sc->pKp = 0;
+    sc->counter[CNT_HVP] = 0;
+  }
+}
+
+// CG update A: x += alpha p, r -= alpha q, z = D^-1 r, r^T z, r^T r; the last
+// block tests convergence and forms beta.
+template <typename T>
+__global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ dinv, const T* __restrict__ p,
+                                              const T* __restrict__ q, T* x, T* r, DevScalars* sc) {
+  if (*(volatile int*)&sc->done) return;
+  const int id = blockIdx.x, l = threadIdx.x;
+  const double alpha = vload(&sc->alpha);
+  const T al = (T)alpha;
+  double rz = 0, rr = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+    const T di = dinv[o];
+    if (di > T(0)) {
+      T xv = x[o] + al * p[o];
+      T rv = r[o] - al * q[o];
+      x[o] = xv;
+      r[o] = rv;
+      rz += (double)rv * (double)(di * rv);
+      rr += (double)rv * (double)rv;
+    }
+  }
+  double vals[2] = {rz, rr};
+  double* const dst[2] = {&sc->rz_new, &sc->rr};
+  block_add<2>(vals, dst);
+  if (arrive_last(&sc->counter[CNT_A]) && threadIdx.x == 0) {
+    const double rzn = vload(&sc->rz_new), rrv = vload(&sc->rr);
+    const int it = sc->iters + 1;
+    sc->iters = it;
+    sc->rr_last = rrv;
+    if (rrv <= sc->tol2 || it >= sc->cg_max || !(rrv == rrv)) sc->done = 1;
+    sc->beta = rzn / vload(&sc->rz);
+    sc->rz = rzn;
+    sc->rz_new = 0;
+    sc->rr = 0;
+    sc->pMp = 0;
+    sc->counter[CNT_A] = 0;
+  }
+}
+
+// CG update B: p = D^-1 r + beta p, q(face) = 0, sum m |p|^2
+template <typename T>
+__global__ void __launch_bounds__(512) k_cg_b(const T* __restrict__ dinv, const T* __restrict__ m,
+                                              const T* __restrict__ r, T* p, T* q, DevScalars* sc) {
+  if (*(volatile int*)&sc->done) return;
+  const int id = blockIdx.x, l = threadIdx.x;
+  const T be = (T)vload(&sc->beta);
+  const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
+  const T mi = m[(int64_t)id * BV + l];
+  double pmp = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+    const T di = dinv[o];
+    T pv = T(0);
+    if (di > T(0)) pv = di * r[o] + be * p[o];
+    p[o] = pv;
+    if (face) q[o] = T(0);
+    pmp += (double)mi * (double)pv * (double)pv;
+  }
+  double vals[1] = {pmp};
+  double* const dst[1] = {&sc->pMp};
+  block_add<1>(vals, dst);
+}
+
+// g^T x over free DOFs
+template <typename T>
+__global__ void __launch_bounds__(512) k_dot(const T* __restrict__ a, const T* __restrict__ b, double* out) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  double s = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int64_t o = (int64_t)id * 3 * BV + c * BV + l;
+    s += (double)a[o] * (double)b[o];
+  }
+  double vals[1] = {s};
+  double* const dst[1] = {out};
+  block_add<1>(vals, dst);
+}
+
+// line-search energy at v + alpha x: inertia over all bricks
+template <typename T>
+__global__ void __launch_bounds__(512) k_energy_nodes(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
+                                                      const T* __restrict__ v, const T* __restrict__ x,
+                                                      const T* __restrict__ vhat, T alpha, DevScalars* sc) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  const int64_t slot = (int64_t)id * BV + l;
+  double e = 0;
+  if (nflag[slot] & NF_DOF) {
+    const T mi = m[slot];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+      const T d = v[o] + alpha * x[o] - vhat[o];
+      e += 0.5 * (double)mi * (double)d * (double)d;
+    }
+  }
+  double vals[1] = {e};
+  double* const dst[1] = {&sc->phi_in};
+  block_add<1>(vals, dst);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_energy_cells(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                                      const uint8_t* __restrict__ cflag, const T* __restrict__ acc,
+                                                      const T* __restrict__ cs, const T* __restrict__ v,
+                                                      const T* __restrict__ x, T alpha, SolveInfo si, DevScalars* sc) {
+  __shared__ T sv[3][729];
+  const int id = cblist[blockIdx.x];
+  stage_nodes<T>(id, nbr, v, x, alpha, sv);
+  __syncthreads();
+  const T gw = (T)(0.25 / si.dx);
+  double esum = 0;
+  int bad = 0;
+  MatParams<T> mats[MPML_MAX_MATS];
+#pragma unroll
+  for (int k = 0; k < MPML_MAX_MATS; ++k) {
+    mats[k].model = si.mat[k].model;
+    mats[k].mu = (T)si.mat[k].mu;
+    mats[k].lam = (T)si.mat[k].lam;
+  }
+  for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+    if (!cflag[(int64_t)id * BV + l]) continue;
+    T D[9];
+    gather_D<T>(l, sv, D);
+    T Gd[9];
+    const T sgd = (T)si.dt * gw;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Gd[q] = sgd * D[q];
+    for (int k = 0; k < si.nm; ++k) {
+      const T V = acc[((int64_t)id * si.nf + acc_V(k)) * BV + l];
+      if (V == T(0)) continue;
+      T sm6[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) sm6[q] = cs[(((int64_t)id * si.nm + k) * 6 + q) * BV + l];
+      T sm[9] = {sm6[0], sm6[3], sm6[4], sm6[3], sm6[1], sm6[5], sm6[4], sm6[5], sm6[2]};
+      T H[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          T s2 = Gd[3 * a + b] + sm[3 * a + b];
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) s2 += Gd[3 * a + kk] * sm[3 * kk + b];
+          H[3 * a + b] = s2;
+        }
+      T U[9], s[3], e[3], Vv[9], Jm1;
+      svd_from_h(H, U, s, e, Vv, Jm1);
+      Spec<T> sp;
+      if (!spectral(mats[k], s, e, Jm1, sp)) {
+        bad = 1;
+        continue;
+      }
+      esum += (double)V * (double)sp.psi;
+    }
+  }
+  if (bad) atomicAdd(&sc->infeasible, 1);
+  double vals[1] = {esum};
+  double* const dst[1] = {&sc->phi_el};
+  block_add<1>(vals, dst);
+}
+
+// v += alpha x on free DOFs
+template <typename T>
+__global__ void __launch_bounds__(512) k_axpy(const T* __restrict__ dinv, const T* __restrict__ x, T alpha, T* v) {
+  const int id = blockIdx.x, l = threadIdx.x;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+    if (dinv[o] > T(0)) v[o] += alpha * x[o];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static SolveInfo solve_info(mpml_ctx_s* c) {
+  SolveInfo si;
+  si.dt = c->d.dt;
+  si.dx = c->d.dx;
+  si.nm = c->nm;
+  si.nf = acc_fields(c->nm);
+  for (int k = 0; k < MPML_MAX_MATS; ++k) {
+    const mpml_material& m = c->mats[k < c->nm ? k : 0];
+    si.mat[k].model = m.model;
+    si.mat[k].mu = m.mu;
+    si.mat[k].lam = m.lambda;
+  }
+  return si;
+}
+
+template <typename T>
+static int alloc_solver(mpml_ctx_s* c) {
+  const int64_t ns = c->nb * BV;
+  const size_t es = sizeof(T);
+  int rc;
+  if ((rc = ensure(c->cs, es * 6 * c->nm * ns)) || (rc = ensure(c->cK, es * 45 * ns)) ||
+      (rc = ensure(c->ng, es * 3 * ns)) || (rc = ensure(c->ndinv, es * 3 * ns)) || (rc = ensure(c->nx, es * 3 * ns)) ||
+      (rc = ensure(c->nr, es * 3 * ns)) || (rc = ensure(c->np, es * 3 * ns)) || (rc = ensure(c->nq, es * 3 * ns)))
+    return rc;
+  return MPML_OK;
+}
+
+template <typename T>
+static int stretch_t(mpml_ctx_s* c) {
+  int rc = alloc_solver<T>(c);
+  if (rc) return rc;
+  SolveInfo si = solve_info(c);
+  if (c->ncb > 0) {
+    k_stretch<T><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const uint8_t*)c->cflag.p,
+                                                    (const T*)c->cacc.p, si, (T*)c->cs.p, (int*)c->status.p);
+    c->launches++;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+int stretch_all(mpml_ctx_s* c) { return c->fp64 ? stretch_t<double>(c) : stretch_t<float>(c); }
+
+static DevScalars* dscal(mpml_ctx_s* c) { return (DevScalars*)c->scal.p; }
+
+static int read_scalars(mpml_ctx_s* c) {
+  cudaMemcpyAsync(c->hscal, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s);
+  cudaMemcpyAsync(c->hstatus, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+  return cuda_status(cudaStreamSynchronize(c->s));
+}
+
+// prep at the current iterate (c->nvnew): gradient, energy, K (optional), CG start
+template <typename T>
+static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg_max) {
+  SolveInfo si = solve_info(c);
+  cudaMemsetAsync(c->scal.p, 0, sizeof(DevScalars), c->s);
+  const unsigned nb = (unsigned)c->nb, ncb = (unsigned)c->ncb;
+  if (nb == 0) return MPML_OK;
+  k_node_init<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (const T*)c->nvnew.p,
+                                     (const T*)c->nvhat.p, (T*)c->ng.p, (T*)c->ndinv.p, dscal(c));
+  if (ncb > 0)
+    k_prep<T><<<ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p,
+                                    (const T*)c->cacc.p, (const T*)c->cs.p, (const T*)c->nvnew.p, si, want_k,
+                                    (T*)c->cK.p, (T*)c->ng.p, (T*)c->ndinv.p, dscal(c), (int*)c->status.p);
+  k_finalize<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (T*)c->ng.p,
+                                    (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p, (T*)c->np.p, (T*)c->nq.p, init_cg,
+                                    cg_rtol * cg_rtol, cg_max, dscal(c));
+  c->launches += ncb > 0 ? 3 : 2;
+  return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+constexpr size_t hvp_smem_bytes() {
+  return sizeof(T) * 3 * 729 + (16 - (sizeof(T) * 3 * 729) % 16) % 16 + sizeof(T) * 9 * BV;
+}
+
+template <typename T>
+static void launch_hvp(mpml_ctx_s* c, const T* p, T* q, int finalize) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_hvp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hvp_smem_bytes<T>());
+    attr = true;
+  }
+  k_hvp<T><<<(unsigned)c->ncb, 256, hvp_smem_bytes<T>(), c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
+                                              (const uint8_t*)c->cflag.p, (const T*)c->cK.p, p,
+                                              (const T*)c->nmass.p, q, dscal(c), finalize);
+  c->launches++;
+}
+
+template <typename T>
+static void cg_iteration(mpml_ctx_s* c) {
+  const unsigned nb = (unsigned)c->nb;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profiling) {
+    if (c->ev_used + 2 > (int)c->ev_pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+      }
+    }
+    e0 = c->ev_pool[c->ev_used++];
+    e1 = c->ev_pool[c->ev_used++];
+    cudaEventRecord(e0, c->s);
+  }
+  launch_hvp<T>(c, (const T*)c->np.p, (T*)c->nq.p, 1);
+  if (c->profiling) cudaEventRecord(e1, c->s);
+  k_cg_a<T><<<nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->np.p, (const T*)c->nq.p, (T*)c->nx.p,
+                                (T*)c->nr.p, dscal(c));
+  k_cg_b<T><<<nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nmass.p, (const T*)c->nr.p, (T*)c->np.p,
+                                (T*)c->nq.p, dscal(c));
+  c->launches += 2;
+}
+
+static void harvest_events(mpml_ctx_s* c) {
+  for (int i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
+      c->hvp_ms_total += ms;
+      c->hvp_launches_timed++;
+    }
+  }
+  c->ev_used = 0;
+}
+
+template <typename T>
+static int pcg_t(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, double* rel) {
+  int rc;
+  const int every = o->check_every > 0 ? o->check_every : 16;
+  int launched = 0;
+  if ((rc = read_scalars(c))) return rc;
+  while (!c->hscal->done && launched < o->cg_max) {
+    for (int j = 0; j < every && launched < o->cg_max; ++j, ++launched) cg_iteration<T>(c);
+    if ((rc = cuda_status(cudaGetLastError()))) return rc;
+    if ((rc = read_scalars(c))) return rc;
+    if (c->profiling) harvest_events(c);
+  }
+  *iters = c->hscal->iters;
+  const double rr0 = c->hscal->rr0;
+  *rel = rr0 > 0 ? sqrt(c->hscal->rr_last / rr0) : 0.0;
+  return MPML_OK;
+}
+
+template <typename T>
+static int energy_t(mpml_ctx_s* c, double alpha, double* phi, int* infeasible) {
+  SolveInfo si = solve_info(c);
+  DevScalars* d = dscal(c);
+  cudaMemsetAsync(&d->phi_in, 0, sizeof(double), c->s);
+  cudaMemsetAsync(&d->phi_el, 0, sizeof(double), c->s);
+  cudaMemsetAsync(&d->infeasible, 0, sizeof(int), c->s);
+  k_energy_nodes<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
+                                                     (const T*)c->nvnew.p, (const T*)c->nx.p, (const T*)c->nvhat.p,
+                                                     (T)alpha, d);
+  if (c->ncb > 0)
+    k_energy_cells<T><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
+                                                         (const uint8_t*)c->cflag.p, (const T*)c->cacc.p,
+                                                         (const T*)c->cs.p, (const T*)c->nvnew.p,
+                                                         (const T*)c->nx.p, (T)alpha, si, d);
+  c->launches += 2;
+  int rc = read_scalars(c);
+  if (rc) return rc;
+  *infeasible = c->hscal->infeasible;
+  *phi = c->hscal->phi_in + c->hscal->phi_el;
+  return MPML_OK;
+}
+
+template <typename T>
+static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st) {
+  int rc = alloc_solver<T>(c);
+  if (rc) return rc;
+  if (c->nb == 0) {
+    st->status = MPML_OK;
+    return MPML_OK;
+  }
+  if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max)) || (rc = read_scalars(c))) return rc;
+  if (*c->hstatus & ST_NONFINITE) return MPML_ERR_NONFINITE;
+  double g0 = sqrt(c->hscal->gg), gn = g0;
+  double phi = c->hscal->phi_in + c->hscal->phi_el;
+  st->g0_norm = g0;
+  st->phi0 = phi;
+  int status = MPML_OK, it = 0;
+  while (true) {
+    if (gn <= o->newton_rtol * g0 || gn <= o->newton_atol) break;
+    if (it >= o->newton_max) {
+      status = MPML_WARN_NOT_CONVERGED;
+      break;
+    }
+    int cgit = 0;
+    double rel = 0;
+    if ((rc = pcg_t<T>(c, o, &cgit, &rel))) return rc;
+    if (it < 64) {
+      st->cg_iters[it] = cgit;
+      st->cg_rel_resid[it] = rel;
+    }
+    st->cg_iters_total += cgit;
+    // slope g^T dx
+    DevScalars* d = dscal(c);
+    cudaMemsetAsync(&d->slope, 0, sizeof(double), c->s);
+    k_dot<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->ng.p, (const T*)c->nx.p, &d->slope);
+    c->launches++;
+    if ((rc = read_scalars(c))) return rc;
+    const double slope = c->hscal->slope;
+    double alpha = 1.0, phit = 0;
+    bool accepted = false;
+    for (int ls = 0; ls <= o->ls_max; ++ls) {
+      int inf = 0;
+      if ((rc = energy_t<T>(c, alpha, &phit, &inf))) return rc;
+      if (inf == 0 && phit <= phi + o->ls_c1 * alpha * slope) {
+        accepted = true;
+        break;
+      }
+      alpha *= 0.5;
+    }
+    if (it < 64) st->alpha[it] = accepted ? alpha : 0.0;
+    ++it;
+    if (!accepted) {
+      status = MPML_WARN_NOT_CONVERGED;
+      break;
+    }
+    k_axpy<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nx.p, (T)alpha, (T*)c->nvnew.p);
+    c->launches++;
+    if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max)) || (rc = read_scalars(c))) return rc;
+    gn = sqrt(c->hscal->gg);
+    phi = c->hscal->phi_in + c->hscal->phi_el;
+  }
+  st->newton_iters = it;
+  st->g_norm = gn;
+  st->phi = phi;
+  st->status = status;
+  return status;
+}
+
+int newton_solve(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st) {
+  return c->fp64 ? newton_t<double>(c, o, st) : newton_t<float>(c, o, st);
+}
+
+// ---- operator-level helpers (introspection API) -----------------------------
+template <typename T>
+static int eval_t(mpml_ctx_s* c, const void* v, double* phi, void* grad) {
+  int rc = alloc_solver<T>(c);
+  if (rc) return rc;
+  cudaMemcpyAsync(c->nvnew.p, v, sizeof(T) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
+  if ((rc = prep_t<T>(c, 1, 0, 1e-6, 1)) || (rc = read_scalars(c))) return rc;
+  *phi = c->hscal->phi_in + c->hscal->phi_el;
+  if (grad) cudaMemcpyAsync(grad, c->ng.p, sizeof(T) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
+  return cuda_status(cudaStreamSynchronize(c->s));
+}
+
+int eval_device(mpml_ctx_s* c, const void* v, double* phi, void* grad) {
+  return c->fp64 ? eval_t<double>(c, v, phi, grad) : eval_t<float>(c, v, phi, grad);
+}
+
+int linearize_device(mpml_ctx_s* c, const void* v) {
+  double phi;
+  return eval_device(c, v, &phi, nullptr);
+}
+
+template <typename T>
+__global__ void k_zero_faces(T* q) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
+  if (face)
+    for (int a = 0; a < 3; ++a) q[(int64_t)id * 3 * BV + a * BV + l] = T(0);
+}
+
+template <typename T>
+static int hvp_t(mpml_ctx_s* c, const void* p, void* y) {
+  cudaMemcpyAsync(c->np.p, p, sizeof(T) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
+  cudaMemsetAsync(c->nq.p, 0, sizeof(T) * 3 * c->nb * BV, c->s);
+  if (c->ncb > 0) launch_hvp<T>(c, (const T*)c->np.p, (T*)c->nq.p, 0);
+  cudaMemcpyAsync(y, c->nq.p, sizeof(T) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
+  return cuda_status(cudaStreamSynchronize(c->s));
+}
+
+int hvp_device(mpml_ctx_s* c, const void* p, void* y) {
+  return c->fp64 ? hvp_t<double>(c, p, y) : hvp_t<float>(c, p, y);
+}
+
+template <typename T>
+static int hvp_bench_t(mpml_ctx_s* c, int iters, double* mean_ms) {
+  if (c->ncb == 0 || iters <= 0) {
+    *mean_ms = 0;
+    return MPML_OK;
+  }
+  // direction: the current p (left by the last solve) is fine; q faces zeroed per launch
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  double tot = 0;
+  for (int i = 0; i < iters; ++i) {
+    k_zero_faces<T><<<(unsigned)c->nb, BV, 0, c->s>>>((T*)c->nq.p);
+    cudaEventRecord(a, c->s);
+    launch_hvp<T>(c, (const T*)c->np.p, (T*)c->nq.p, 0);
+    cudaEventRecord(b, c->s);
+    cudaEventSynchronize(b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    tot += ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *mean_ms = tot / iters;
+  return cuda_status(cudaGetLastError());
+}
+
+int hvp_bench(mpml_ctx_s* c, int iters, double* mean_ms) {
+  return c->fp64 ? hvp_bench_t<double>(c, iters, mean_ms) : hvp_bench_t<float>(c, iters, mean_ms);
+}
+
+}  // namespace mpml

@@ -1,0 +1,528 @@
+// C ABI of the library (declared in include/mpml.h): context lifecycle, the
+// three calls of one MPM Lite time step (Algorithm 1: Unload, Integrate,
+// Load), and the synchronising introspection / operator entry points.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
+#include "mpml_internal.cuh"
+
+using namespace mpml;
+
+namespace {
+
+bool bad_desc(const mpml_scene_desc* d, const mpml_material* mats, int n_mats) {
+  if (!d || !mats || n_mats < 1 || n_mats > MPML_MAX_MATS) return true;
+  for (int a = 0; a < 3; ++a)
+    if (d->n[a] < 2 || d->n[a] > (1 << 16)) return true;
+  if (!(d->dx > 0) || !(d->inv_dx > 0) || !(d->dt > 0)) return true;
+  if (d->precision != MPML_FP32 && d->precision != MPML_FP64) return true;
+  if (d->wall_layers < 0) return true;
+  for (int k = 0; k < n_mats; ++k) {
+    if (mats[k].model < 0 || mats[k].model > 2) return true;
+    if (!(mats[k].mu > 0)) return true;
+  }
+  // P2Q shared-memory accumulators: 729 centres x (13 + 7 n_mats) fields
+  const size_t es = d->precision == MPML_FP64 ? 8 : 4;
+  if (729 * (size_t)(13 + 7 * n_mats) * es > 227 * 1024) return true;
+  return false;
+}
+
+int latched(mpml_ctx_s* c) {
+  int st = *c->hstatus;
+  if (st & ST_NONFINITE) return MPML_ERR_NONFINITE;
+  if (st & ST_OUT_OF_DOMAIN) return MPML_ERR_OUT_OF_DOMAIN;
+  if (st & ST_STRETCH) return MPML_ERR_STRETCH;
+  if (st & ST_BADMAT) return MPML_ERR_ARG;
+  if (st & ST_TIMEOUT) return MPML_ERR_TIMEOUT;
+  return MPML_OK;
+}
+
+int sync_status(mpml_ctx_s* c) {
+  cudaMemcpyAsync(c->hstatus, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+  int rc = cuda_status(cudaStreamSynchronize(c->s));
+  if (rc) return rc;
+  return latched(c);
+}
+
+bool bad_particles(const mpml_particles* p) {
+  if (!p || p->n < 0 || p->n > (int64_t)INT32_MAX - 1) return true;
+  if (p->n > 0 && (!p->x || !p->v || !p->F || !p->G || !p->mass || !p->volume || !p->mat)) return true;
+  return p->mem != MPML_MEM_DEVICE && p->mem != MPML_MEM_HOST;
+}
+
+// host-side compaction: copy a brick-layout array and keep the slots whose
+// flag is set, in brick-list (= key) order.
+template <typename T>
+int export_slots(mpml_ctx_s* c, const void* dev, int width, const mpml::Buf& flag, uint8_t mask, double* out) {
+  const int64_t ns = c->nb * BV;
+  std::vector<T> h((size_t)ns * width);
+  std::vector<uint8_t> f((size_t)ns);
+  if (ns == 0) return MPML_OK;
+  cudaMemcpyAsync(h.data(), dev, sizeof(T) * ns * width, cudaMemcpyDeviceToHost, c->s);
+  cudaMemcpyAsync(f.data(), flag.p, ns, cudaMemcpyDeviceToHost, c->s);
+  int rc = cuda_status(cudaStreamSynchronize(c->s));
+  if (rc) return rc;
+  int64_t q = 0;
+  for (int64_t b = 0; b < c->nb; ++b)
+    for (int l = 0; l < BV; ++l) {
+      if (!(f[b * BV + l] & mask)) continue;
+      for (int w = 0; w < width; ++w) out[q * width + w] = (double)h[(b * width + w) * BV + l];
+      ++q;
+    }
+  return MPML_OK;
+}
+
+// host-side scatter of a DOF-ordered node vector (n*3 doubles) into the brick layout
+template <typename T>
+int import_nodes(mpml_ctx_s* c, const double* in, void* dev) {
+  const int64_t ns = c->nb * BV;
+  std::vector<T> h((size_t)ns * 3, T(0));
+  std::vector<uint8_t> f((size_t)ns);
+  if (ns == 0) return MPML_OK;
+  cudaMemcpyAsync(f.data(), c->nflag.p, ns, cudaMemcpyDeviceToHost, c->s);
+  int rc = cuda_status(cudaStreamSynchronize(c->s));
+  if (rc) return rc;
+  int64_t q = 0;
+  for (int64_t b = 0; b < c->nb; ++b)
+    for (int l = 0; l < BV; ++l) {
+      if (!(f[b * BV + l] & NF_DOF)) continue;
+      for (int a = 0; a < 3; ++a) h[(b * 3 + a) * BV + l] = (T)in[q * 3 + a];
+      ++q;
+    }
+  cudaMemcpyAsync(dev, h.data(), sizeof(T) * ns * 3, cudaMemcpyHostToDevice, c->s);
+  return cuda_status(cudaStreamSynchronize(c->s));
+}
+
+template <typename T>
+int get_field_t(mpml_ctx_s* c, int field, double* out) {
+  const int nm = c->nm, nf = acc_fields(nm);
+  const int64_t ns = c->nb * BV;
+  switch (field) {
+    case MPML_F_CELL_MASS:
+    case MPML_F_CELL_VEL:
+    case MPML_F_CELL_VGRAD:
+    case MPML_F_CELL_VOL:
+    case MPML_F_CELL_TAU: {
+      std::vector<double> a((size_t)c->nb * 0 + 1);
+      int64_t ncell = 0;
+      // export all accumulator fields, then normalise on the host
+      std::vector<uint8_t> f((size_t)ns);
+      cudaMemcpyAsync(f.data(), c->cflag.p, ns ? ns : 1, cudaMemcpyDeviceToHost, c->s);
+      int rc = cuda_status(cudaStreamSynchronize(c->s));
+      if (rc) return rc;
+      for (auto v : f) ncell += v ? 1 : 0;
+      std::vector<double> acc((size_t)ncell * nf);
+      if ((rc = export_slots<T>(c, c->cacc.p, nf, c->cflag, 1, acc.data()))) return rc;
+      for (int64_t i = 0; i < ncell; ++i) {
+        const double* r = &acc[i * nf];
+        const double m = r[0];
+        if (field == MPML_F_CELL_MASS) out[i] = m;
+        if (field == MPML_F_CELL_VEL)
+          for (int a2 = 0; a2 < 3; ++a2) out[i * 3 + a2] = m != 0 ? r[1 + a2] / m : 0;
+        if (field == MPML_F_CELL_VGRAD)
+          for (int q = 0; q < 9; ++q) out[i * 9 + q] = m != 0 ? r[4 + q] / m : 0;
+        if (field == MPML_F_CELL_VOL)
+          for (int k = 0; k < nm; ++k) out[i * nm + k] = r[acc_V(k)];
+        if (field == MPML_F_CELL_TAU)
+          for (int k = 0; k < nm; ++k) {
+            const double V = r[acc_V(k)];
+            const int ra[6] = {0, 1, 2, 0, 0, 1}, rb[6] = {0, 1, 2, 1, 2, 2};
+            for (int q = 0; q < 6; ++q) {
+              double t = V != 0 ? r[acc_tau(k) + q] / V : 0;
+              out[(i * nm + k) * 9 + 3 * ra[q] + rb[q]] = t;
+              out[(i * nm + k) * 9 + 3 * rb[q] + ra[q]] = t;
+            }
+          }
+      }
+      return MPML_OK;
+    }
+    case MPML_F_CELL_STRETCH: {
+      std::vector<uint8_t> f((size_t)ns);
+      cudaMemcpyAsync(f.data(), c->cflag.p, ns ? ns : 1, cudaMemcpyDeviceToHost, c->s);
+      int rc = cuda_status(cudaStreamSynchronize(c->s));
+      if (rc) return rc;
+      int64_t ncell = 0;
+      for (auto v : f) ncell += v ? 1 : 0;
+      std::vector<double> s6((size_t)ncell * 6 * nm);
+      if ((rc = export_slots<T>(c, c->cs.p, 6 * nm, c->cflag, 1, s6.data()))) return rc;
+      const int ra[6] = {0, 1, 2, 0, 0, 1}, rb[6] = {0, 1, 2, 1, 2, 2};
+      for (int64_t i = 0; i < ncell; ++i)
+        for (int k = 0; k < nm; ++k)
+          for (int q = 0; q < 6; ++q) {
+            double v = s6[i * 6 * nm + k * 6 + q] + (q < 3 ? 1.0 : 0.0);
+            out[(i * nm + k) * 9 + 3 * ra[q] + rb[q]] = v;
+            out[(i * nm + k) * 9 + 3 * rb[q] + ra[q]] = v;
+          }
+      return MPML_OK;
+    }
+    case MPML_F_CELL_VEL_NEW:
+    case MPML_F_CELL_VGRAD_NEW: {
+      std::vector<uint8_t> f((size_t)ns);
+      cudaMemcpyAsync(f.data(), c->cflag.p, ns ? ns : 1, cudaMemcpyDeviceToHost, c->s);
+      int rc = cuda_status(cudaStreamSynchronize(c->s));
+      if (rc) return rc;
+      int64_t ncell = 0;
+      for (auto v : f) ncell += v ? 1 : 0;
+      std::vector<double> a12((size_t)ncell * 12);
+      if ((rc = export_slots<T>(c, c->cnew.p, 12, c->cflag, 1, a12.data()))) return rc;
+      for (int64_t i = 0; i < ncell; ++i) {
+        if (field == MPML_F_CELL_VEL_NEW)
+          for (int a2 = 0; a2 < 3; ++a2) out[i * 3 + a2] = a12[i * 12 + a2];
+        else
+          for (int q = 0; q < 9; ++q) out[i * 9 + q] = a12[i * 12 + 3 + q];
+      }
+      return MPML_OK;
+    }
+    case MPML_F_NODE_MASS: return export_slots<T>(c, c->nmass.p, 1, c->nflag, NF_DOF, out);
+    case MPML_F_NODE_VEL: return export_slots<T>(c, c->nv.p, 3, c->nflag, NF_DOF, out);
+    case MPML_F_NODE_VHAT: return export_slots<T>(c, c->nvhat.p, 3, c->nflag, NF_DOF, out);
+    case MPML_F_NODE_VNEW: return export_slots<T>(c, c->nvnew.p, 3, c->nflag, NF_DOF, out);
+    case MPML_F_NODE_FIXED: {
+      std::vector<uint8_t> f((size_t)ns);
+      cudaMemcpyAsync(f.data(), c->nflag.p, ns ? ns : 1, cudaMemcpyDeviceToHost, c->s);
+      int rc = cuda_status(cudaStreamSynchronize(c->s));
+      if (rc) return rc;
+      int64_t q = 0;
+      for (int64_t i = 0; i < ns; ++i)
+        if (f[i] & NF_DOF) out[q++] = (f[i] & NF_FIXED) ? 1.0 : 0.0;
+      return MPML_OK;
+    }
+    default: return MPML_ERR_ARG;
+  }
+}
+
+template <typename T>
+int node_vector_op(mpml_ctx_s* c, int op, const double* in, double* phi, double* out) {
+  // op 0: eval (in = v, out = grad); 1: linearize (in = v); 2: hvp (in = p, out = y)
+  const int64_t ns = c->nb * BV;
+  mpml::Buf tmp_in, tmp_out;
+  int rc;
+  if ((rc = ensure(tmp_in, sizeof(T) * 3 * (ns ? ns : 1))) || (rc = ensure(tmp_out, sizeof(T) * 3 * (ns ? ns : 1)))) {
+    free_buf(tmp_in);
+    free_buf(tmp_out);
+    return rc;
+  }
+  rc = import_nodes<T>(c, in, tmp_in.p);
+  if (!rc) {
+    if (op == 0) rc = eval_device(c, tmp_in.p, phi, out ? tmp_out.p : nullptr);
+    if (op == 1) rc = linearize_device(c, tmp_in.p);
+    if (op == 2) rc = hvp_device(c, tmp_in.p, tmp_out.p);
+  }
+  if (!rc && out) {
+    rc = export_slots<T>(c, tmp_out.p, 3, c->nflag, NF_DOF, out);
+    if (!rc && op == 2) {
+      // mask rows of fixed DOFs
+      std::vector<double> fixed((size_t)c->nb * BV);
+      std::vector<uint8_t> f((size_t)ns);
+      cudaMemcpy(f.data(), c->nflag.p, ns, cudaMemcpyDeviceToHost);
+      int64_t q = 0;
+      for (int64_t i = 0; i < ns; ++i)
+        if (f[i] & NF_DOF) {
+          if (f[i] & NF_FIXED) out[3 * q] = out[3 * q + 1] = out[3 * q + 2] = 0;
+          ++q;
+        }
+    }
+  }
+  cudaStreamSynchronize(c->s);
+  free_buf(tmp_in);
+  free_buf(tmp_out);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpml_create(const mpml_scene_desc* desc, const mpml_material* mats, int n_mats, void* stream, mpml_ctx* out) {
+  if (!out) return MPML_ERR_ARG;
+  *out = nullptr;
+  if (bad_desc(desc, mats, n_mats)) return MPML_ERR_ARG;
+  mpml_ctx_s* c = new mpml_ctx_s();
+  c->d = *desc;
+  for (int k = 0; k < n_mats; ++k) c->mats[k] = mats[k];
+  c->nm = n_mats;
+  c->s = (cudaStream_t)stream;
+  c->fp64 = desc->precision == MPML_FP64;
+  c->esz = c->fp64 ? 8 : 4;
+  for (int a = 0; a < 3; ++a) c->NB[a] = (desc->n[a] >> 3) + 1;
+  c->NBT = (int64_t)c->NB[0] * c->NB[1] * c->NB[2];
+  cudaGetDevice(&c->device);
+  int rc;
+  if ((rc = ensure(c->scal, sizeof(DevScalars))) || (rc = ensure(c->status, sizeof(int)))) {
+    mpml_destroy(c);
+    return rc;
+  }
+  if (cudaMallocHost(&c->hscal, sizeof(DevScalars)) != cudaSuccess ||
+      cudaMallocHost(&c->hstatus, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    mpml_destroy(c);
+    return MPML_ERR_NOMEM;
+  }
+  memset(c->hscal, 0, sizeof(DevScalars));
+  *c->hstatus = 0;
+  cudaMemsetAsync(c->scal.p, 0, sizeof(DevScalars), c->s);
+  cudaMemsetAsync(c->status.p, 0, sizeof(int), c->s);
+  if ((rc = cuda_status(cudaStreamSynchronize(c->s)))) {
+    mpml_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MPML_OK;
+}
+
+int mpml_destroy(mpml_ctx c) {
+  if (!c) return MPML_ERR_ARG;
+  if (c->s || true) cudaStreamSynchronize(c->s);
+  Buf* bufs[] = {&c->bflag_c, &c->bflag_n, &c->bmap, &c->blist, &c->cblist, &c->nbr, &c->px, &c->pv, &c->pF,
+                 &c->pG, &c->pm, &c->pV, &c->pmat, &c->pperm, &c->pkey, &c->prank, &c->pbase, &c->ux, &c->uv,
+                 &c->uF, &c->uG, &c->um, &c->uV, &c->umat, &c->cnt, &c->start, &c->scan_tmp, &c->cflag,
+                 &c->cacc, &c->cs, &c->cK, &c->cnew, &c->nflag, &c->nmass, &c->nv, &c->nvhat, &c->nvfix,
+                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->scal, &c->status};
+  for (Buf* b : bufs) free_buf(*b);
+  if (c->hscal) cudaFreeHost(c->hscal);
+  if (c->hstatus) cudaFreeHost(c->hstatus);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+  return MPML_OK;
+}
+
+const char* mpml_status_str(int s) {
+  switch (s) {
+    case MPML_OK: return "ok";
+    case MPML_WARN_NOT_CONVERGED: return "warning: Newton did not converge";
+    case MPML_ERR_ARG: return "invalid argument";
+    case MPML_ERR_OUT_OF_DOMAIN: return "particle stencil outside the grid";
+    case MPML_ERR_NONFINITE: return "non-finite value";
+    case MPML_ERR_STRETCH: return "stress-to-stretch inversion failed";
+    case MPML_ERR_TIMEOUT: return "bounded device wait timed out";
+    case MPML_ERR_CUDA: return "CUDA runtime error";
+    case MPML_ERR_NOMEM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+int mpml_set_time(mpml_ctx c, double t) {
+  if (!c) return MPML_ERR_ARG;
+  c->time = t;
+  return MPML_OK;
+}
+
+int mpml_sync(mpml_ctx c) {
+  if (!c) return MPML_ERR_ARG;
+  return sync_status(c);
+}
+
+int mpml_resample(mpml_ctx c, const mpml_particles* p) {
+  if (!c || bad_particles(p)) return MPML_ERR_ARG;
+  cudaMemsetAsync(c->status.p, 0, sizeof(int), c->s);
+  c->np_count = p->n;
+  const void *x = p->x, *v = p->v, *F = p->F, *G = p->G, *m = p->mass, *V = p->volume;
+  const int32_t* mat = p->mat;
+  int32_t* perm = p->perm;
+  const int64_t n = p->n;
+  const size_t es = c->esz;
+  int rc;
+  Buf perm_stage;
+  if (p->mem == MPML_MEM_HOST) {
+    if ((rc = ensure(c->ux, es * 3 * n)) || (rc = ensure(c->uv, es * 3 * n)) || (rc = ensure(c->uF, es * 9 * n)) ||
+        (rc = ensure(c->uG, es * 9 * n)) || (rc = ensure(c->um, es * n)) || (rc = ensure(c->uV, es * n)) ||
+        (rc = ensure(c->umat, sizeof(int32_t) * n)))
+      return rc;
+    cudaMemcpyAsync(c->ux.p, x, es * 3 * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(c->uv.p, v, es * 3 * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(c->uF.p, F, es * 9 * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(c->uG.p, G, es * 9 * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(c->um.p, m, es * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(c->uV.p, V, es * n, cudaMemcpyHostToDevice, c->s);
+    cudaMemcpyAsync(c->umat.p, mat, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->s);
+    x = c->ux.p; v = c->uv.p; F = c->uF.p; G = c->uG.p; m = c->um.p; V = c->uV.p;
+    mat = (const int32_t*)c->umat.p;
+    if (perm) {
+      if ((rc = ensure(perm_stage, sizeof(int32_t) * n))) return rc;
+    }
+  }
+  int32_t* perm_dev = (p->mem == MPML_MEM_HOST) ? (perm ? (int32_t*)perm_stage.p : nullptr) : perm;
+  rc = resample_device(c, x, v, F, G, m, V, mat, perm_dev);
+  if (!rc) rc = p2q_q2n(c);
+  if (!rc && p->mem == MPML_MEM_HOST && perm)
+    cudaMemcpyAsync(perm, perm_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->s);
+  if (perm_stage.p) {
+    cudaStreamSynchronize(c->s);
+    free_buf(perm_stage);
+  }
+  if (rc) return rc;
+  c->stage = 1;
+  c->have_lin = 0;
+  return MPML_OK;
+}
+
+int mpml_stretch(mpml_ctx c) {
+  if (!c || c->stage < 1) return MPML_ERR_ARG;
+  int rc = stretch_all(c);
+  if (rc) return rc;
+  rc = sync_status(c);
+  if (rc) return rc;
+  c->stage = 2;
+  return MPML_OK;
+}
+
+int mpml_newton_step(mpml_ctx c, const mpml_solver_opts* o, mpml_solve_stats* st) {
+  if (!c || c->stage < 1) return MPML_ERR_ARG;
+  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 0};
+  if (!o) o = &def;
+  mpml_solve_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  int rc = stretch_all(c);
+  if (rc) return rc;
+  if ((rc = sync_status(c))) return rc;
+  rc = newton_solve(c, o, st);
+  st->n_particles = c->np_count;
+  st->n_bricks = c->nb;
+  if (rc < 0) return rc;
+  c->have_lin = 1;
+  int rc2 = sync_status(c);
+  if (rc2) return rc2;
+  c->stage = 3;
+  return rc;
+}
+
+int mpml_g2p(mpml_ctx c, const mpml_particles* p) {
+  if (!c || bad_particles(p) || c->stage < 1 || p->n != c->np_count) return MPML_ERR_ARG;
+  const int64_t n = p->n;
+  const size_t es = c->esz;
+  int rc;
+  if (p->mem == MPML_MEM_DEVICE) {
+    rc = g2p_device(c, p->x, p->v, p->F, p->G, p->mass, p->volume, p->mat);
+    if (rc) return rc;
+  } else {
+    if ((rc = ensure(c->ux, es * 3 * n)) || (rc = ensure(c->uv, es * 3 * n)) || (rc = ensure(c->uF, es * 9 * n)) ||
+        (rc = ensure(c->uG, es * 9 * n)) || (rc = ensure(c->um, es * n)) || (rc = ensure(c->uV, es * n)) ||
+        (rc = ensure(c->umat, sizeof(int32_t) * n)))
+      return rc;
+    rc = g2p_device(c, c->ux.p, c->uv.p, c->uF.p, c->uG.p, c->um.p, c->uV.p, (int32_t*)c->umat.p);
+    if (rc) return rc;
+    cudaMemcpyAsync(p->x, c->ux.p, es * 3 * n, cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(p->v, c->uv.p, es * 3 * n, cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(p->F, c->uF.p, es * 9 * n, cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(p->G, c->uG.p, es * 9 * n, cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(p->mass, c->um.p, es * n, cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(p->volume, c->uV.p, es * n, cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(p->mat, c->umat.p, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->s);
+    if ((rc = sync_status(c))) return rc;
+  }
+  c->stage = 4;
+  return MPML_OK;
+}
+
+int mpml_counts(mpml_ctx c, int64_t out[4]) {
+  if (!c || !out) return MPML_ERR_ARG;
+  const int64_t ns = c->nb * BV;
+  std::vector<uint8_t> cf((size_t)ns), nf((size_t)ns);
+  if (ns) {
+    cudaMemcpyAsync(cf.data(), c->cflag.p, ns, cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(nf.data(), c->nflag.p, ns, cudaMemcpyDeviceToHost, c->s);
+  }
+  int rc = cuda_status(cudaStreamSynchronize(c->s));
+  if (rc) return rc;
+  int64_t ncell = 0, nnode = 0;
+  for (int64_t i = 0; i < ns; ++i) {
+    ncell += cf[i] ? 1 : 0;
+    nnode += (nf[i] & NF_DOF) ? 1 : 0;
+  }
+  out[0] = c->np_count;
+  out[1] = ncell;
+  out[2] = nnode;
+  out[3] = c->nb;
+  return MPML_OK;
+}
+
+int mpml_get_keys(mpml_ctx c, int what, int64_t* out) {
+  if (!c || !out) return MPML_ERR_ARG;
+  if (what == MPML_KEYS_PARTICLES) {
+    // compact key -> brick-major key via the brick list
+    std::vector<int> k((size_t)c->np_count), bl((size_t)c->nb);
+    if (c->np_count) cudaMemcpyAsync(k.data(), c->pkey.p, sizeof(int) * c->np_count, cudaMemcpyDeviceToHost, c->s);
+    if (c->nb) cudaMemcpyAsync(bl.data(), c->blist.p, sizeof(int) * c->nb, cudaMemcpyDeviceToHost, c->s);
+    int rc = cuda_status(cudaStreamSynchronize(c->s));
+    if (rc) return rc;
+    for (int64_t i = 0; i < c->np_count; ++i) out[i] = (int64_t)bl[k[i] / BV] * BV + (k[i] % BV);
+    return MPML_OK;
+  }
+  if (what != MPML_KEYS_CELLS && what != MPML_KEYS_NODES) return MPML_ERR_ARG;
+  const int64_t ns = c->nb * BV;
+  std::vector<uint8_t> f((size_t)ns);
+  std::vector<int> bl((size_t)c->nb);
+  if (ns) {
+    cudaMemcpyAsync(f.data(), what == MPML_KEYS_CELLS ? c->cflag.p : c->nflag.p, ns, cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(bl.data(), c->blist.p, sizeof(int) * c->nb, cudaMemcpyDeviceToHost, c->s);
+  }
+  int rc = cuda_status(cudaStreamSynchronize(c->s));
+  if (rc) return rc;
+  int64_t q = 0;
+  const uint8_t mask = what == MPML_KEYS_CELLS ? 1 : NF_DOF;
+  for (int64_t b = 0; b < c->nb; ++b)
+    for (int l = 0; l < BV; ++l)
+      if (f[b * BV + l] & mask) out[q++] = (int64_t)bl[b] * BV + l;
+  return MPML_OK;
+}
+
+int mpml_get_field(mpml_ctx c, int field, double* out) {
+  if (!c || !out || c->stage < 1) return MPML_ERR_ARG;
+  return c->fp64 ? get_field_t<double>(c, field, out) : get_field_t<float>(c, field, out);
+}
+
+int mpml_set_node_velocity(mpml_ctx c, const double* v) {
+  if (!c || !v || c->stage < 1) return MPML_ERR_ARG;
+  return c->fp64 ? import_nodes<double>(c, v, c->nvnew.p) : import_nodes<float>(c, v, c->nvnew.p);
+}
+
+int mpml_eval(mpml_ctx c, const double* v, double* phi, double* grad) {
+  if (!c || !v || !phi || c->stage < 2) return MPML_ERR_ARG;
+  int rc = c->fp64 ? node_vector_op<double>(c, 0, v, phi, grad) : node_vector_op<float>(c, 0, v, phi, grad);
+  if (!rc) c->have_lin = 1;
+  return rc;
+}
+
+int mpml_linearize(mpml_ctx c, const double* v) {
+  if (!c || !v || c->stage < 2) return MPML_ERR_ARG;
+  int rc = c->fp64 ? node_vector_op<double>(c, 1, v, nullptr, nullptr) : node_vector_op<float>(c, 1, v, nullptr, nullptr);
+  if (!rc) c->have_lin = 1;
+  return rc;
+}
+
+int mpml_hvp(mpml_ctx c, const double* p, double* y) {
+  if (!c || !p || !y || !c->have_lin) return MPML_ERR_ARG;
+  return c->fp64 ? node_vector_op<double>(c, 2, p, nullptr, y) : node_vector_op<float>(c, 2, p, nullptr, y);
+}
+
+int mpml_set_profiling(mpml_ctx c, int enable) {
+  if (!c) return MPML_ERR_ARG;
+  c->profiling = enable ? 1 : 0;
+  c->hvp_launches_timed = 0;
+  c->hvp_ms_total = 0;
+  c->ev_used = 0;
+  return MPML_OK;
+}
+
+int mpml_hvp_timing(mpml_ctx c, int64_t* launches, double* total_ms, double* bytes_per_launch) {
+  if (!c) return MPML_ERR_ARG;
+  if (launches) *launches = c->hvp_launches_timed;
+  if (total_ms) *total_ms = c->hvp_ms_total;
+  if (bytes_per_launch) {
+    // per cell brick: K (45/cell) read, p (3/node) read, m read, q (3/node) written
+    const double e = (double)c->esz;
+    *bytes_per_launch = (double)c->ncb * BV * (45 * e + 3 * e + e + 3 * e);
+  }
+  return MPML_OK;
+}
+
+int mpml_hvp_bench(mpml_ctx c, int iters, double* mean_ms) {
+  if (!c || !mean_ms || !c->have_lin) return MPML_ERR_ARG;
+  return hvp_bench(c, iters, mean_ms);
+}
+
+int64_t mpml_kernel_launches(mpml_ctx c) { return c ? c->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,451 @@
+// Internal declarations of the sm_103a MPM Lite library: the context, the
+// brick layout, device status bits, and the per-cell constitutive math
+// shared by the kernels (stretch reconstruction, Newton prep, line search).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "mpml.h"
+
+namespace mpml {
+
+// ---------------------------------------------------------------------------
+// Brick layout: 8x8x8 cells (or nodes) per brick, brick-major keys.
+// Cell data is stored per brick as [brick][field][512] so that the 512
+// threads of a brick read each field coalesced; node vectors as
+// [brick][component][512].
+// ---------------------------------------------------------------------------
+constexpr int BR = 8;
+constexpr int BV = 512;
+constexpr int NBR = 27;  // neighbour table entries per brick (offsets -1..1)
+
+__host__ __device__ inline int nbr_index(int dx, int dy, int dz) {
+  return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
+}
+
+// device status bits (latched, OR-ed)
+enum : int {
+  ST_OUT_OF_DOMAIN = 1,
+  ST_NONFINITE = 2,
+  ST_STRETCH = 4,
+  ST_TIMEOUT = 8,
+  ST_BADMAT = 16,
+};
+
+// node flags
+enum : uint8_t { NF_DOF = 1, NF_FIXED = 2 };
+
+// Per-cell accumulators of the unload (Algorithm 2), per brick-field plane:
+//   0: m   1-3: m v   4-12: m G   then per material k: V_k, (V tau)_k (6 sym)
+__host__ __device__ inline int acc_fields(int nm) { return 13 + 7 * nm; }
+__host__ __device__ inline int acc_V(int k) { return 13 + 7 * k; }
+__host__ __device__ inline int acc_tau(int k) { return 14 + 7 * k; }
+
+// symmetric 3x3 packing: xx yy zz xy xz yz
+__host__ __device__ inline int sym_idx(int a, int b) {
+  if (a == b) return a;
+  int lo = a < b ? a : b, hi = a < b ? b : a;
+  return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+
+// symmetric 9x9 packed upper triangle, row-major: index of (r, c), r <= c
+__host__ __device__ inline int k45(int r, int c) { return r * 9 - r * (r - 1) / 2 + (c - r); }
+
+// Device-side solver scalars (one struct per context, in device memory).
+struct DevScalars {
+  double pMp;      // sum m |p|^2 of the current direction (update kernel)
+  double pKp;      // sum_c D^T K D (HVP kernel)
+  double rz;       // r^T z
+  double rz_new;
+  double rr;       // r^T r
+  double rr0;
+  double alpha, beta;
+  double gg;       // |g|^2
+  double phi_el;   // elastic energy sum
+  double phi_in;   // inertia sum
+  double slope;    // g^T dx
+  double tol2;     // (cg_rtol)^2 rr0
+  double rr_last;  // r^T r at the last CG update
+  int infeasible;  // cells where the energy is undefined (line search)
+  int done;
+  int iters;
+  int cg_max;
+  int counter[8];  // last-block tickets per kernel kind
+  int pad;
+};
+
+template <typename T>
+struct MatParams {
+  int model;
+  T mu, lam;
+};
+
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace mpml
+
+struct mpml_ctx_s {
+  mpml_scene_desc d;
+  mpml_material mats[MPML_MAX_MATS];
+  int nm = 1;
+  cudaStream_t s = nullptr;
+  int fp64 = 0;
+  size_t esz = 4;
+  int NB[3] = {0, 0, 0};
+  int64_t NBT = 0;
+  double time = 0;
+  int device = 0;
+
+  // brick bookkeeping
+  mpml::Buf bflag_c, bflag_n, bmap, blist, cblist, nbr;
+  // particles (sorted library copies and temporaries)
+  mpml::Buf px, pv, pF, pG, pm, pV, pmat, pperm, pkey, prank, pbase;
+  // staging of unsorted input (host mode)
+  mpml::Buf ux, uv, uF, uG, um, uV, umat;
+  // counting sort
+  mpml::Buf cnt, start, scan_tmp;
+  // cells
+  mpml::Buf cflag, cacc, cs, cK, cnew;
+  // nodes
+  mpml::Buf nflag, nmass, nv, nvhat, nvfix, nvnew, ng, ndinv, nx, nr, np, nq;
+  // scalars and status
+  mpml::Buf scal, status;
+  mpml::DevScalars* hscal = nullptr;  // pinned mirror
+  int* hstatus = nullptr;             // pinned
+
+  int64_t np_count = 0, nb = 0, ncb = 0;
+  int stage = 0;  // 0 nothing, 1 unloaded, 2 stretched, 3 solved, 4 loaded
+  int have_lin = 0;
+
+  // profiling of HVP launches
+  int profiling = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  int ev_used = 0;
+  int64_t hvp_launches_timed = 0;
+  double hvp_ms_total = 0;
+  int64_t launches = 0;
+};
+
+namespace mpml {
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+int ensure(Buf& b, size_t bytes);
+void free_buf(Buf& b);
+int cuda_status(cudaError_t e);
+
+int resample_device(mpml_ctx_s* c, const void* x, const void* v, const void* F, const void* G,
+                    const void* m, const void* V, const int32_t* mat, int32_t* perm_out);
+int p2q_q2n(mpml_ctx_s* c);
+int stretch_all(mpml_ctx_s* c);
+int newton_solve(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st);
+int g2p_device(mpml_ctx_s* c, void* x, void* v, void* F, void* G, void* m, void* V, int32_t* mat);
+
+// operator-level helpers used by the introspection API
+int eval_device(mpml_ctx_s* c, const void* v_nodes, double* phi, void* grad_nodes);
+int linearize_device(mpml_ctx_s* c, const void* v_nodes);
+int hvp_device(mpml_ctx_s* c, const void* p_nodes, void* y_nodes);
+int hvp_bench(mpml_ctx_s* c, int iters, double* mean_ms);
+int n2q_device(mpml_ctx_s* c);
+
+inline unsigned div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Device math
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T dsqrt(T x);
+template <>
+__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T eps_of();
+template <>
+__device__ __forceinline__ float eps_of<float>() { return 1.1920929e-7f; }
+template <>
+__device__ __forceinline__ double eps_of<double>() { return 2.220446049250313e-16; }
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 (row-major A);
+// eigenvectors in the columns of Q.
+template <typename T>
+__device__ void jacobi3(const T Ain[9], T ev[3], T Q[9]) {
+  T A[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) A[i] = Ain[i];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Q[i] = (i % 4 == 0) ? T(1) : T(0);
+  T fro = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fro += A[i] * A[i];
+  const T tol = eps_of<T>() * eps_of<T>() * fro * T(1e-2);
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    T off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    if (!(off > tol)) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      T apq = A[3 * p + q];
+      if (apq == T(0)) continue;
+      T theta = (A[3 * q + q] - A[3 * p + p]) / (T(2) * apq);
+      T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + dsqrt(theta * theta + T(1)));
+      T cc = T(1) / dsqrt(t * t + T(1)), ss = t * cc;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T akp = A[3 * k + p], akq = A[3 * k + q];
+        A[3 * k + p] = cc * akp - ss * akq;
+        A[3 * k + q] = ss * akp + cc * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T apk = A[3 * p + k], aqk = A[3 * q + k];
+        A[3 * p + k] = cc * apk - ss * aqk;
+        A[3 * q + k] = ss * apk + cc * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        T vkp = Q[3 * k + p], vkq = Q[3 * k + q];
+        Q[3 * k + p] = cc * vkp - ss * vkq;
+        Q[3 * k + q] = ss * vkp + cc * vkq;
+      }
+    }
+  }
+  ev[0] = A[0];
+  ev[1] = A[4];
+  ev[2] = A[8];
+}
+
+// Signed SVD of F = I + H from the eigen-decomposition of F^T F - I =
+// H + H^T + H^T H, returning s = singular values (s0 >= s1 >= |s2|, s2 < 0
+// when det F < 0), e = s - 1 computed without cancellation, J - 1 likewise.
+template <typename T>
+__device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1) {
+  T E[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T acc = H[3 * a + b] + H[3 * b + a];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += H[3 * k + a] * H[3 * k + b];
+      E[3 * a + b] = acc;
+    }
+  T lam[3], W[9];
+  jacobi3(E, lam, W);
+  int i0 = 0, i1 = 1, i2 = 2;
+  if (lam[i1] > lam[i0]) { int t = i0; i0 = i1; i1 = t; }
+  if (lam[i2] > lam[i0]) { int t = i0; i0 = i2; i2 = t; }
+  if (lam[i2] > lam[i1]) { int t = i1; i1 = i2; i2 = t; }
+  const int id[3] = {i0, i1, i2};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) V[3 * r + c] = W[3 * r + id[c]];
+  T detV = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
+           V[2] * (V[3] * V[7] - V[4] * V[6]);
+  if (detV < T(0)) {
+    V[2] = -V[2];
+    V[5] = -V[5];
+    V[8] = -V[8];
+  }
+  T l[3] = {lam[i0], lam[i1], lam[i2]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T li = l[i] > T(-1) ? l[i] : T(-1);
+    s[i] = dsqrt(T(1) + li);
+    e[i] = li / (T(1) + s[i]);
+  }
+  // b_j = F v_j
+  T b[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      T acc = V[3 * r + j];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += H[3 * r + k] * V[3 * k + j];
+      b[j][r] = acc;
+    }
+  T u0[3], u1[3], u2[3];
+  T n0 = dsqrt(b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2]);
+  if (n0 > T(1e-30)) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) u0[r] = b[0][r] / n0;
+  } else {
+    u0[0] = 1; u0[1] = 0; u0[2] = 0;
+  }
+  T dd = u0[0] * b[1][0] + u0[1] * b[1][1] + u0[2] * b[1][2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) u1[r] = b[1][r] - dd * u0[r];
+  T n1 = dsqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+  if (n1 > T(1e-30)) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) u1[r] /= n1;
+  } else {
+    T a0 = fabs(u0[0]) > T(0.9) ? T(0) : T(1), a1 = fabs(u0[0]) > T(0.9) ? T(1) : T(0);
+    T ee = a0 * u0[0] + a1 * u0[1];
+    u1[0] = a0 - ee * u0[0];
+    u1[1] = a1 - ee * u0[1];
+    u1[2] = -ee * u0[2];
+    T nn = dsqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) u1[r] /= nn;
+  }
+  u2[0] = u0[1] * u1[2] - u0[2] * u1[1];
+  u2[1] = u0[2] * u1[0] - u0[0] * u1[2];
+  u2[2] = u0[0] * u1[1] - u0[1] * u1[0];
+  T d2 = u2[0] * b[2][0] + u2[1] * b[2][1] + u2[2] * b[2][2];
+  if (d2 < T(0)) {
+    s[2] = -s[2];
+    e[2] = s[2] - T(1);
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    U[3 * r + 0] = u0[r];
+    U[3 * r + 1] = u1[r];
+    U[3 * r + 2] = u2[r];
+  }
+  Jm1 = e[0] + e[1] + e[2] + e[0] * e[1] + e[0] * e[2] + e[1] * e[2] + e[0] * e[1] * e[2];
+}
+
+// Spectral data of an isotropic energy at principal stretches s (e = s - 1,
+// Jm1 = J - 1 given accurately): psi, d1 = dpsi/ds, d2 = Hessian in s, and
+// per pair (0,1),(0,2),(1,2): pp = (d1_i - d1_j)/(s_i - s_j),
+// pm = (d1_i + d1_j)/(s_i + s_j), in closed forms finite at s_i = s_j.
+template <typename T>
+struct Spec {
+  T psi, d1[3], d2[9], pp[3], pm[3];
+};
+
+template <typename T>
+__device__ __forceinline__ T log1p_t(T x);
+template <>
+__device__ __forceinline__ float log1p_t<float>(float x) { return log1pf(x); }
+template <>
+__device__ __forceinline__ double log1p_t<double>(double x) { return log1p(x); }
+template <typename T>
+__device__ __forceinline__ T expm1_t(T x);
+template <>
+__device__ __forceinline__ float expm1_t<float>(float x) { return expm1f(x); }
+template <>
+__device__ __forceinline__ double expm1_t<double>(double x) { return expm1(x); }
+template <typename T>
+__device__ __forceinline__ T exp_t(T x);
+template <>
+__device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+
+// x - log(1 + x) without cancellation near 0
+template <typename T>
+__device__ __forceinline__ T x_minus_log1p(T x) {
+  if (fabs(x) < T(0.05)) {
+    // alternating series x^2/2 - x^3/3 + ... (12 terms: error < 0.05^13)
+    T acc = 0, pw = x * x;
+#pragma unroll
+    for (int k = 2; k < 14; ++k) {
+      acc += ((k & 1) ? -pw : pw) / T(k);
+      pw *= x;
+    }
+    return acc;
+  }
+  return x - log1p_t(x);
+}
+
+__device__ __forceinline__ int pair_i(int p) { return p == 2 ? 1 : 0; }
+__device__ __forceinline__ int pair_j(int p) { return p == 0 ? 1 : 2; }
+__device__ __forceinline__ int pair_k(int p) { return 2 - p; }
+
+// returns false where the energy is undefined (J <= 0 for NH / Hencky)
+template <typename T>
+__device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm1, Spec<T>& o) {
+  const T mu = M.mu, lam = M.lam;
+  const T J = T(1) + Jm1;
+  if (M.model == MPML_FIXED_COROTATED) {
+    o.psi = mu * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) + T(0.5) * lam * Jm1 * Jm1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int j = (i + 1) % 3, k = (i + 2) % 3;
+      o.d1[i] = T(2) * mu * e[i] + lam * Jm1 * s[j] * s[k];
+      o.d2[4 * i] = T(2) * mu + lam * (s[j] * s[k]) * (s[j] * s[k]);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int i = pair_i(p), j = pair_j(p), k = pair_k(p);
+      o.d2[3 * i + j] = o.d2[3 * j + i] = lam * s[k] * (T(2) * J - T(1));
+      o.pp[p] = T(2) * mu - lam * Jm1 * s[k];
+      o.pm[p] = T(2) * mu * (e[i] + e[j]) / (s[i] + s[j]) + lam * Jm1 * s[k];
+    }
+    return true;
+  }
+  if (M.model == MPML_NEO_HOOKEAN) {
+    if (!(J > T(0))) return false;
+    const T kap = T(2) / T(3) * mu + lam;
+    const T lJ = log1p_t(Jm1);
+    const T cm1 = expm1_t(T(-2) / T(3) * lJ);  // J^{-2/3} - 1
+    const T c = T(1) + cm1;
+    const T I1m3 = e[0] * (T(2) + e[0]) + e[1] * (T(2) + e[1]) + e[2] * (T(2) + e[2]);
+    const T I1 = T(3) + I1m3;
+    const T J2m1 = Jm1 * (T(2) + Jm1);
+    o.psi = T(0.5) * mu * (c * I1m3 + T(3) * cm1) +
+            T(0.25) * kap * (T(2) * x_minus_log1p(Jm1) + Jm1 * Jm1);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int j = (i + 1) % 3, k = (i + 2) % 3;
+      // s_i - I1/(3 s_i) = ((s_i^2 - s_j^2) + (s_i^2 - s_k^2)) / (3 s_i)
+      const T dij = (e[i] - e[j]) * (T(2) + e[i] + e[j]);
+      const T dik = (e[i] - e[k]) * (T(2) + e[i] + e[k]);
+      o.d1[i] = mu * c * (dij + dik) / (T(3) * s[i]) + T(0.5) * kap * J2m1 / s[i];
+      o.d2[4 * i] = mu * c * (T(-1) / T(3) + T(5) * I1 / (T(9) * s[i] * s[i])) +
+                    T(0.5) * kap * (J * J + T(1)) / (s[i] * s[i]);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int i = pair_i(p), j = pair_j(p);
+      const T sij = s[i] * s[j];
+      o.d2[3 * i + j] = o.d2[3 * j + i] =
+          mu * c / sij * (T(-2) / T(3) * s[i] * s[i] - T(2) / T(3) * s[j] * s[j] + T(2) / T(9) * I1) +
+          kap * J * J / sij;
+      o.pp[p] = mu * c * (T(1) + I1 / (T(3) * sij)) - T(0.5) * kap * J2m1 / sij;
+      o.pm[p] = mu * c * (T(1) - I1 / (T(3) * sij)) + T(0.5) * kap * J2m1 / sij;
+    }
+    return true;
+  }
+  if (M.model == MPML_HENCKY) {
+    if (!(s[0] > T(0) && s[1] > T(0) && s[2] > T(0))) return false;
+    const T l[3] = {log1p_t(e[0]), log1p_t(e[1]), log1p_t(e[2])};
+    const T tr = l[0] + l[1] + l[2];
+    o.psi = mu * (l[0] * l[0] + l[1] * l[1] + l[2] * l[2]) + T(0.5) * lam * tr * tr;
+    T t[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t[i] = T(2) * mu * l[i] + lam * tr;
+      o.d1[i] = t[i] / s[i];
+      o.d2[4 * i] = (T(2) * mu + lam - t[i]) / (s[i] * s[i]);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int i = pair_i(p), j = pair_j(p);
+      o.d2[3 * i + j] = o.d2[3 * j + i] = lam / (s[i] * s[j]);
+      const T z = (s[i] - s[j]) / s[j];
+      const T L = fabs(z) < T(1e-4) ? T(1) - T(0.5) * z + z * z / T(3) : log1p_t(z) / z;
+      o.pp[p] = (T(2) * mu * (L - l[j]) - lam * tr) / (s[i] * s[j]);
+      o.pm[p] = (t[i] * s[j] + t[j] * s[i]) / (s[i] * s[j] * (s[i] + s[j]));
+    }
+    return true;
+  }
+  return false;
+}
+
+}  // namespace mpml
