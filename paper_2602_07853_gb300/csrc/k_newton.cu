@@ -163,18 +163,18 @@ struct SolveInfo {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_stretch(const int* __restrict__ cblist, const uint8_t* __restrict__ cflag,
-                                                 const T* __restrict__ acc, SolveInfo si, T* __restrict__ cs,
+                                                 const T* __restrict__ acc, SolveInfo si, double* __restrict__ cs,
                                                  int* status) {
   const int id = cblist[blockIdx.x];
   for (int l = threadIdx.x; l < BV; l += blockDim.x) {
     if (!cflag[(int64_t)id * BV + l]) continue;
     for (int k = 0; k < si.nm; ++k) {
-      T* so = cs + ((int64_t)id * si.nm + k) * 6 * BV + l;
+      double* so = cs + ((int64_t)id * si.nm + k) * 6 * BV + l;
       const T* a = acc + (int64_t)id * si.nf * BV + l;
       const double V = (double)a[acc_V(k) * BV];
       if (V == 0.0) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) so[q * BV] = T(0);
+        for (int q = 0; q < 6; ++q) so[q * BV] = 0.0;
         continue;
       }
       double tau[9];
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_stretch(const int* __restrict__ cblist,
       if (!invert_principal(si.mat[k].model, si.mat[k].mu, si.mat[k].lam, ev, s)) {
         atomicOr(status, ST_STRETCH);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) so[q * BV] = T(0);
+        for (int q = 0; q < 6; ++q) so[q * BV] = 0.0;
         continue;
       }
 #pragma unroll
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(256) k_stretch(const int* __restrict__ cblist,
         double acc2 = 0;
 #pragma unroll
         for (int kk = 0; kk < 3; ++kk) acc2 += Q[3 * ra[q] + kk] * (s[kk] - 1.0) * Q[3 * rb[q] + kk];
-        so[q * BV] = (T)acc2;
+        so[q * BV] = acc2;
       }
     }
   }
@@ -206,9 +206,9 @@ __global__ void __launch_bounds__(256) k_stretch(const int* __restrict__ cblist,
 // ---------------------------------------------------------------------------
 // node-block staging: the 9^3 nodes of a cell brick (own 8^3 + upper halo)
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void stage_nodes(int id, const int* __restrict__ nbr, const T* __restrict__ a,
-                                            const T* __restrict__ b, T beta, T (*sv)[729]) {
+template <typename S, typename A, typename B>
+__device__ __forceinline__ void stage_nodes(int id, const int* __restrict__ nbr, const A* __restrict__ a,
+                                            const B* __restrict__ b, double beta, S (*sv)[729]) {
   // sv[r][i] = a + beta * b (b may be null)
   for (int i = threadIdx.x; i < 729; i += blockDim.x) {
     const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
@@ -216,11 +216,11 @@ __device__ __forceinline__ void stage_nodes(int id, const int* __restrict__ nbr,
     const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      T val = T(0);
+      S val = S(0);
       if (t >= 0) {
         const int64_t o = (int64_t)t * 3 * BV + r * BV + l;
-        val = a[o];
-        if (b) val += beta * b[o];
+        val = (S)a[o];
+        if (b) val += (S)(beta * (double)b[o]);
       }
       sv[r][i] = val;
     }
@@ -251,46 +251,55 @@ __device__ __forceinline__ void gather_D(int l, const T (*sv)[729], T D[9]) {
 }
 
 // ---------------------------------------------------------------------------
-// per-cell constitutive kernel: energy, gradient Q, projected K (D-space)
+// Per-cell constitutive work.  The stress, gradient and energy are formed in
+// FP64 (they decide where Newton stops and whether the line search accepts);
+// the projected tangent K only sets the CG convergence rate and is built in
+// the storage precision T from the FP64 decomposition.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct CellOut {
-  T Q[9];   // dt V P S^T / (4 dx)   (gradient, node contribution = Q sgn)
-  T K[45];  // dt^2 V L^T A+ L / (16 dx^2)
+  double Q[9];  // dt V P S^T / (4 dx)   (gradient, node contribution = Q sgn)
+  T K[45];      // dt^2 V L^T A+ L / (16 dx^2)
   double psi;
   bool ok;
 };
 
-template <typename T>
-__device__ void cell_material(const MatParams<T>& M, T V, const T Gd[9] /* dt*G */, const T s6[6], T kq, T kk,
-                              bool want_k, CellOut<T>& out) {
-  // S = I + s;  H = F - I = dt G + s + dt G s
-  T sm[9] = {s6[0], s6[3], s6[4], s6[3], s6[1], s6[5], s6[4], s6[5], s6[2]};
-  T H[9];
+// F - I = dt G + s + dt G s with S = I + s (symmetric, packed xx yy zz xy xz yz)
+__device__ __forceinline__ void trial_h(const double Gd[9], const double s6[6], double sm[9], double H[9]) {
+  sm[0] = s6[0]; sm[1] = s6[3]; sm[2] = s6[4];
+  sm[3] = s6[3]; sm[4] = s6[1]; sm[5] = s6[5];
+  sm[6] = s6[4]; sm[7] = s6[5]; sm[8] = s6[2];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      T acc = Gd[3 * a + b] + sm[3 * a + b];
+      double acc = Gd[3 * a + b] + sm[3 * a + b];
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc += Gd[3 * a + k] * sm[3 * k + b];
       H[3 * a + b] = acc;
     }
-  T U[9], s[3], e[3], Vv[9], Jm1;
-  svd_from_h(H, U, s, e, Vv, Jm1);
-  Spec<T> sp;
-  if (!spectral(M, s, e, Jm1, sp)) {
+}
+
+template <typename T>
+__device__ void cell_material(const MatParams<double>& M, double V, const double Gd[9] /* dt*G */,
+                              const double s6[6], double kq, double kk, bool want_k, CellOut<T>& out) {
+  double sm[9], H[9];
+  trial_h(Gd, s6, sm, H);
+  double U[9], s[3], e[3], Vv[9], Jm1;
+  svd_from_h<double>(H, U, s, e, Vv, Jm1);
+  Spec<double> sp;
+  if (!spectral<double>(M, s, e, Jm1, sp)) {
     out.ok = false;
     return;
   }
-  out.psi += (double)V * (double)sp.psi;
+  out.psi += V * sp.psi;
   // W = S V = V + s V
-  T W[9];
+  double W[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      T acc = Vv[3 * a + b];
+      double acc = Vv[3 * a + b];
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc += sm[3 * a + k] * Vv[3 * k + b];
       W[3 * a + b] = acc;
@@ -300,16 +309,23 @@ __device__ void cell_material(const MatParams<T>& M, T V, const T Gd[9] /* dt*G 
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      T acc = 0;
+      double acc = 0;
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc += U[3 * a + k] * sp.d1[k] * W[3 * b + k];
       out.Q[3 * a + b] += kq * V * acc;
     }
   if (!want_k) return;
-  const T kv = kk * V;
+  T Ut[9], Wt[9], d2[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    Ut[i] = (T)U[i];
+    Wt[i] = (T)W[i];
+    d2[i] = (T)sp.d2[i];
+  }
+  const T kv = (T)(kk * V);
   // diagonal block: eigen-decomposition of d2, clamp
   T ev[3], Qd[9];
-  jacobi3<T>(sp.d2, ev, Qd);
+  jacobi3<T>(d2, ev, Qd);
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     if (!(ev[m] > T(0))) continue;
@@ -320,7 +336,7 @@ __device__ void cell_material(const MatParams<T>& M, T V, const T Gd[9] /* dt*G 
       for (int b = 0; b < 3; ++b) {
         T acc = 0;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) acc += Qd[3 * i + m] * U[3 * a + i] * W[3 * b + i];
+        for (int i = 0; i < 3; ++i) acc += Qd[3 * i + m] * Ut[3 * a + i] * Wt[3 * b + i];
         d[3 * a + b] = acc;
       }
     const T lam = kv * ev[m];
@@ -336,14 +352,15 @@ __device__ void cell_material(const MatParams<T>& M, T V, const T Gd[9] /* dt*G 
     const int i = pair_i(p), j = pair_j(p);
 #pragma unroll
     for (int sg = 0; sg < 2; ++sg) {
-      const T lamv = sg == 0 ? sp.pp[p] : sp.pm[p];
+      const T lamv = (T)(sg == 0 ? sp.pp[p] : sp.pm[p]);
       if (!(lamv > T(0))) continue;
       const T sgn = sg == 0 ? T(1) : T(-1);
       T d[9];
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) d[3 * a + b] = rs2 * (U[3 * a + i] * W[3 * b + j] + sgn * U[3 * a + j] * W[3 * b + i]);
+        for (int b = 0; b < 3; ++b)
+          d[3 * a + b] = rs2 * (Ut[3 * a + i] * Wt[3 * b + j] + sgn * Ut[3 * a + j] * Wt[3 * b + i]);
       const T lam = kv * lamv;
 #pragma unroll
       for (int r = 0; r < 9; ++r)
@@ -353,30 +370,30 @@ __device__ void cell_material(const MatParams<T>& M, T V, const T Gd[9] /* dt*G 
   }
 }
 
-// node init: g = m (v - vhat), diag = m, inertia energy (all bricks, 512 thr)
+// node init: g = m (v - vhat) (FP64), diag = m, inertia energy (all bricks, 512 thr)
 template <typename T>
 __global__ void __launch_bounds__(512) k_node_init(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
-                                                   const T* __restrict__ v, const T* __restrict__ vhat, T* g, T* diag,
-                                                   DevScalars* sc) {
+                                                   const double* __restrict__ v, const double* __restrict__ vhat,
+                                                   double* g, T* diag, DevScalars* sc) {
   const int id = blockIdx.x, l = threadIdx.x;
   const int64_t slot = (int64_t)id * BV + l;
   const bool dof = nflag[slot] & NF_DOF;
   double ein = 0;
-  const T mi = dof ? m[slot] : T(0);
+  const double mi = dof ? (double)m[slot] : 0.0;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const int64_t o = (int64_t)id * 3 * BV + r * BV + l;
-    T d = dof ? v[o] - vhat[o] : T(0);
+    double d = dof ? v[o] - vhat[o] : 0.0;
     g[o] = mi * d;
-    diag[o] = mi;
-    ein += 0.5 * (double)mi * (double)d * (double)d;
+    diag[o] = (T)mi;
+    ein += 0.5 * mi * d * d;
   }
   double vals[1] = {ein};
   double* const dst[1] = {&sc->phi_in};
   block_add<1>(vals, dst);
 }
 
-// atomic add to a node slot addressed from a cell brick (local node 0..8 per axis)
+// pointer to a node slot addressed from a cell brick (local node 0..8 per axis)
 template <typename T>
 __device__ __forceinline__ T* node_ptr(T* base, int id, const int* __restrict__ nbr, int nx, int ny, int nz, int r) {
   const int t = (nx < 8 && ny < 8 && nz < 8) ? id : __ldg(&nbr[id * NBR + nbr_index(nx >> 3, ny >> 3, nz >> 3)]);
@@ -388,47 +405,40 @@ __device__ __forceinline__ T* node_ptr(T* base, int id, const int* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist, const int* __restrict__ nbr,
                                                  const uint8_t* __restrict__ cflag, const T* __restrict__ acc,
-                                                 const T* __restrict__ cs, const T* __restrict__ v, SolveInfo si,
-                                                 int want_k, T* __restrict__ K, T* g, T* diag, DevScalars* sc,
-                                                 int* status) {
-  __shared__ T sv[3][729];
+                                                 const double* __restrict__ cs, const double* __restrict__ v,
+                                                 SolveInfo si, int want_k, T* __restrict__ K, double* g, T* diag,
+                                                 DevScalars* sc, int* status) {
+  __shared__ double sv[3][729];
   const int id = cblist[blockIdx.x];
-  stage_nodes<T>(id, nbr, v, nullptr, T(0), sv);
+  stage_nodes<double, double, double>(id, nbr, v, nullptr, 0.0, sv);
   __syncthreads();
-  const T gw = (T)(0.25 / si.dx);
-  const T kq = (T)(si.dt * 0.25 / si.dx);
-  const T kk = (T)(si.dt * si.dt / (16.0 * si.dx * si.dx));
+  const double gw = 0.25 / si.dx;
+  const double kq = si.dt * 0.25 / si.dx;
+  const double kk = si.dt * si.dt / (16.0 * si.dx * si.dx);
   double esum = 0;
   int bad = 0;
-  MatParams<T> mats[MPML_MAX_MATS];
-#pragma unroll
-  for (int k = 0; k < MPML_MAX_MATS; ++k) {
-    mats[k].model = si.mat[k].model;
-    mats[k].mu = (T)si.mat[k].mu;
-    mats[k].lam = (T)si.mat[k].lam;
-  }
   for (int l = threadIdx.x; l < BV; l += blockDim.x) {
     if (!cflag[(int64_t)id * BV + l]) continue;
-    T D[9];
-    gather_D<T>(l, sv, D);
-    T Gd[9];
-    const T sgd = (T)si.dt * gw;
+    double D[9];
+    gather_D<double>(l, sv, D);
+    double Gd[9];
+    const double sgd = si.dt * gw;
 #pragma unroll
     for (int q = 0; q < 9; ++q) Gd[q] = sgd * D[q];
     CellOut<T> co;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) co.Q[q] = T(0);
+    for (int q = 0; q < 9; ++q) co.Q[q] = 0.0;
 #pragma unroll
     for (int q = 0; q < 45; ++q) co.K[q] = T(0);
     co.psi = 0;
     co.ok = true;
     for (int k = 0; k < si.nm; ++k) {
-      const T V = acc[((int64_t)id * si.nf + acc_V(k)) * BV + l];
-      if (V == T(0)) continue;
-      T s6[6];
+      const double V = (double)acc[((int64_t)id * si.nf + acc_V(k)) * BV + l];
+      if (V == 0.0) continue;
+      double s6[6];
 #pragma unroll
       for (int q = 0; q < 6; ++q) s6[q] = cs[(((int64_t)id * si.nm + k) * 6 + q) * BV + l];
-      cell_material<T>(mats[k], V, Gd, s6, kq, kk, want_k != 0, co);
+      cell_material<T>(si.mat[k], V, Gd, s6, kq, kk, want_k != 0, co);
     }
     if (!co.ok) {
       bad = 1;
@@ -440,17 +450,17 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
 #pragma unroll
       for (int q = 0; q < 45; ++q) Kd[q * BV] = co.K[q];
     }
-    // scatter gradient and Jacobi diagonal to the 8 corners
+    // scatter gradient (FP64) and Jacobi diagonal to the 8 corners
     const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-      const T sg[3] = {(o & 1) ? T(1) : T(-1), (o & 2) ? T(1) : T(-1), (o & 4) ? T(1) : T(-1)};
+      const double sg[3] = {(o & 1) ? 1.0 : -1.0, (o & 2) ? 1.0 : -1.0, (o & 4) ? 1.0 : -1.0};
       const int nx = lx + (o & 1), ny = ly + ((o >> 1) & 1), nz = lz + ((o >> 2) & 1);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        T* gp = node_ptr(g, id, nbr, nx, ny, nz, a);
+        double* gp = node_ptr(g, id, nbr, nx, ny, nz, a);
         if (!gp) continue;
-        T gv = co.Q[3 * a] * sg[0] + co.Q[3 * a + 1] * sg[1] + co.Q[3 * a + 2] * sg[2];
+        double gv = co.Q[3 * a] * sg[0] + co.Q[3 * a + 1] * sg[1] + co.Q[3 * a + 2] * sg[2];
         atomicAdd(gp, gv);
         if (want_k) {
           T dv = 0;
@@ -459,7 +469,7 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
 #pragma unroll
             for (int bb = 0; bb < 3; ++bb) {
               const int r = 3 * a + b, cc = 3 * a + bb;
-              dv += co.K[r <= cc ? k45(r, cc) : k45(cc, r)] * sg[b] * sg[bb];
+              dv += co.K[r <= cc ? k45(r, cc) : k45(cc, r)] * (T)sg[b] * (T)sg[bb];
             }
           atomicAdd(node_ptr(diag, id, nbr, nx, ny, nz, a), dv);
         }
@@ -475,9 +485,9 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
 // finalize the gradient (mask), Jacobi inverse, |g|^2 and the CG start:
 // x = 0, r = -g, z = D^-1 r, p = z, q(face) = 0.
 template <typename T>
-__global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nflag, const T* __restrict__ m, T* g,
-                                                  T* diag_dinv, T* x, T* r, T* p, T* q, int init_cg, double rtol2,
-                                                  int cg_max, DevScalars* sc) {
+__global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
+                                                  double* g, T* diag_dinv, T* x, T* r, T* p, T* q, int init_cg,
+                                                  double rtol2, int cg_max, DevScalars* sc) {
   const int id = blockIdx.x, l = threadIdx.x;
   const int64_t slot = (int64_t)id * BV + l;
   const uint8_t f = nflag[slot];
@@ -488,17 +498,17 @@ __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nf
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
-    T gv = free_ ? g[o] : T(0);
+    double gv = free_ ? g[o] : 0.0;
     g[o] = gv;
     T di = free_ ? T(1) / diag_dinv[o] : T(0);
     diag_dinv[o] = di;
-    gg += (double)gv * (double)gv;
+    gg += gv * gv;
     if (init_cg) {
-      T rv = -gv, zv = di * rv;
+      T rv = (T)(-gv), zv = di * rv;
       x[o] = T(0);
       r[o] = rv;
       p[o] = zv;
-      if (face) q[o] = T(0);
+      if (face) q[o] = mi * zv;  // mass term of brick-face nodes (HVP adds the rest)
       rz += (double)rv * (double)zv;
       rr += (double)rv * (double)rv;
       pmp += (double)mi * (double)zv * (double)zv;
@@ -532,7 +542,7 @@ __global__ void __launch_bounds__(256) k_hvp(const int* __restrict__ cblist, con
   T (*sv)[729] = reinterpret_cast<T (*)[729]>(hvp_smem);
   T (*skd)[BV] = reinterpret_cast<T (*)[BV]>(hvp_smem + sizeof(T) * 3 * 729 + (16 - (sizeof(T) * 3 * 729) % 16) % 16);
   const int id = cblist[blockIdx.x];
-  stage_nodes<T>(id, nbr, p, nullptr, T(0), sv);
+  stage_nodes<T, T, T>(id, nbr, p, (const T*)nullptr, 0.0, sv);
   __syncthreads();
   double pkp = 0;
   for (int l = threadIdx.x; l < BV; l += blockDim.x) {
@@ -583,14 +593,14 @@ __global__ void __launch_bounds__(256) k_hvp(const int* __restrict__ cblist, con
     const bool own = nx < 8 && ny < 8 && nz < 8;
     const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
     if (own) {
+      // brick-face nodes arrive here with q = m p already (set by the kernel
+      // that produced p, for every brick including those without cells)
       const int l = nz * 64 + ny * 8 + nx;
-      const T mi = m[(int64_t)id * BV + l];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        T val = y[a] + mi * sv[a][i];
         T* dst = q + (int64_t)id * 3 * BV + a * BV + l;
-        if (excl) *dst = val;
-        else if (val != T(0)) atomicAdd(dst, val);
+        if (excl) *dst = y[a] + m[(int64_t)id * BV + l] * sv[a][i];
+        else if (y[a] != T(0)) atomicAdd(dst, y[a]);
       }
     } else {
       const int t = __ldg(&nbr[id * NBR + nbr_index(nx >> 3, ny >> 3, nz >> 3)]);
@@ -675,7 +685,7 @@ __global__ void __launch_bounds__(512) k_cg_b(const T* __restrict__ dinv, const 
     T pv = T(0);
     if (di > T(0)) pv = di * r[o] + be * p[o];
     p[o] = pv;
-    if (face) q[o] = T(0);
+    if (face) q[o] = mi * pv;  // mass term of brick-face nodes (HVP adds the rest)
     pmp += (double)mi * (double)pv * (double)pv;
   }
   double vals[1] = {pmp};
@@ -685,13 +695,13 @@ __global__ void __launch_bounds__(512) k_cg_b(const T* __restrict__ dinv, const 
 
 // g^T x over free DOFs
 template <typename T>
-__global__ void __launch_bounds__(512) k_dot(const T* __restrict__ a, const T* __restrict__ b, double* out) {
+__global__ void __launch_bounds__(512) k_dot(const double* __restrict__ a, const T* __restrict__ b, double* out) {
   const int id = blockIdx.x, l = threadIdx.x;
   double s = 0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int64_t o = (int64_t)id * 3 * BV + c * BV + l;
-    s += (double)a[o] * (double)b[o];
+    s += a[o] * (double)b[o];
   }
   double vals[1] = {s};
   double* const dst[1] = {out};
@@ -701,18 +711,18 @@ __global__ void __launch_bounds__(512) k_dot(const T* __restrict__ a, const T* _
 // line-search energy at v + alpha x: inertia over all bricks
 template <typename T>
 __global__ void __launch_bounds__(512) k_energy_nodes(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
-                                                      const T* __restrict__ v, const T* __restrict__ x,
-                                                      const T* __restrict__ vhat, T alpha, DevScalars* sc) {
+                                                      const double* __restrict__ v, const T* __restrict__ x,
+                                                      const double* __restrict__ vhat, double alpha, DevScalars* sc) {
   const int id = blockIdx.x, l = threadIdx.x;
   const int64_t slot = (int64_t)id * BV + l;
   double e = 0;
   if (nflag[slot] & NF_DOF) {
-    const T mi = m[slot];
+    const double mi = (double)m[slot];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
-      const T d = v[o] + alpha * x[o] - vhat[o];
-      e += 0.5 * (double)mi * (double)d * (double)d;
+      const double d = v[o] + alpha * (double)x[o] - vhat[o];
+      e += 0.5 * mi * d * d;
     }
   }
   double vals[1] = {e};
@@ -723,55 +733,39 @@ __global__ void __launch_bounds__(512) k_energy_nodes(const uint8_t* __restrict_
 template <typename T>
 __global__ void __launch_bounds__(256) k_energy_cells(const int* __restrict__ cblist, const int* __restrict__ nbr,
                                                       const uint8_t* __restrict__ cflag, const T* __restrict__ acc,
-                                                      const T* __restrict__ cs, const T* __restrict__ v,
-                                                      const T* __restrict__ x, T alpha, SolveInfo si, DevScalars* sc) {
-  __shared__ T sv[3][729];
+                                                      const double* __restrict__ cs, const double* __restrict__ v,
+                                                      const T* __restrict__ x, double alpha, SolveInfo si,
+                                                      DevScalars* sc) {
+  __shared__ double sv[3][729];
   const int id = cblist[blockIdx.x];
-  stage_nodes<T>(id, nbr, v, x, alpha, sv);
+  stage_nodes<double, double, T>(id, nbr, v, x, alpha, sv);
   __syncthreads();
-  const T gw = (T)(0.25 / si.dx);
+  const double gw = 0.25 / si.dx;
   double esum = 0;
   int bad = 0;
-  MatParams<T> mats[MPML_MAX_MATS];
-#pragma unroll
-  for (int k = 0; k < MPML_MAX_MATS; ++k) {
-    mats[k].model = si.mat[k].model;
-    mats[k].mu = (T)si.mat[k].mu;
-    mats[k].lam = (T)si.mat[k].lam;
-  }
   for (int l = threadIdx.x; l < BV; l += blockDim.x) {
     if (!cflag[(int64_t)id * BV + l]) continue;
-    T D[9];
-    gather_D<T>(l, sv, D);
-    T Gd[9];
-    const T sgd = (T)si.dt * gw;
+    double D[9];
+    gather_D<double>(l, sv, D);
+    double Gd[9];
+    const double sgd = si.dt * gw;
 #pragma unroll
     for (int q = 0; q < 9; ++q) Gd[q] = sgd * D[q];
     for (int k = 0; k < si.nm; ++k) {
-      const T V = acc[((int64_t)id * si.nf + acc_V(k)) * BV + l];
-      if (V == T(0)) continue;
-      T sm6[6];
+      const double V = (double)acc[((int64_t)id * si.nf + acc_V(k)) * BV + l];
+      if (V == 0.0) continue;
+      double s6[6], sm[9], H[9];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) sm6[q] = cs[(((int64_t)id * si.nm + k) * 6 + q) * BV + l];
-      T sm[9] = {sm6[0], sm6[3], sm6[4], sm6[3], sm6[1], sm6[5], sm6[4], sm6[5], sm6[2]};
-      T H[9];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          T s2 = Gd[3 * a + b] + sm[3 * a + b];
-#pragma unroll
-          for (int kk = 0; kk < 3; ++kk) s2 += Gd[3 * a + kk] * sm[3 * kk + b];
-          H[3 * a + b] = s2;
-        }
-      T U[9], s[3], e[3], Vv[9], Jm1;
-      svd_from_h(H, U, s, e, Vv, Jm1);
-      Spec<T> sp;
-      if (!spectral(mats[k], s, e, Jm1, sp)) {
+      for (int q = 0; q < 6; ++q) s6[q] = cs[(((int64_t)id * si.nm + k) * 6 + q) * BV + l];
+      trial_h(Gd, s6, sm, H);
+      double U[9], s[3], e[3], Vv[9], Jm1;
+      svd_from_h<double>(H, U, s, e, Vv, Jm1);
+      Spec<double> sp;
+      if (!spectral<double>(si.mat[k], s, e, Jm1, sp)) {
         bad = 1;
         continue;
       }
-      esum += (double)V * (double)sp.psi;
+      esum += V * sp.psi;
     }
   }
   if (bad) atomicAdd(&sc->infeasible, 1);
@@ -782,12 +776,13 @@ __global__ void __launch_bounds__(256) k_energy_cells(const int* __restrict__ cb
 
 // v += alpha x on free DOFs
 template <typename T>
-__global__ void __launch_bounds__(512) k_axpy(const T* __restrict__ dinv, const T* __restrict__ x, T alpha, T* v) {
+__global__ void __launch_bounds__(512) k_axpy(const T* __restrict__ dinv, const T* __restrict__ x, double alpha,
+                                              double* v) {
   const int id = blockIdx.x, l = threadIdx.x;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
-    if (dinv[o] > T(0)) v[o] += alpha * x[o];
+    if (dinv[o] > T(0)) v[o] += alpha * (double)x[o];
   }
 }
 
@@ -814,8 +809,8 @@ static int alloc_solver(mpml_ctx_s* c) {
   const int64_t ns = c->nb * BV;
   const size_t es = sizeof(T);
   int rc;
-  if ((rc = ensure(c->cs, es * 6 * c->nm * ns)) || (rc = ensure(c->cK, es * 45 * ns)) ||
-      (rc = ensure(c->ng, es * 3 * ns)) || (rc = ensure(c->ndinv, es * 3 * ns)) || (rc = ensure(c->nx, es * 3 * ns)) ||
+  if ((rc = ensure(c->cs, sizeof(double) * 6 * c->nm * ns)) || (rc = ensure(c->cK, es * 45 * ns)) ||
+      (rc = ensure(c->ng, sizeof(double) * 3 * ns)) || (rc = ensure(c->ndinv, es * 3 * ns)) || (rc = ensure(c->nx, es * 3 * ns)) ||
       (rc = ensure(c->nr, es * 3 * ns)) || (rc = ensure(c->np, es * 3 * ns)) || (rc = ensure(c->nq, es * 3 * ns)))
     return rc;
   return MPML_OK;
@@ -828,7 +823,7 @@ static int stretch_t(mpml_ctx_s* c) {
   SolveInfo si = solve_info(c);
   if (c->ncb > 0) {
     k_stretch<T><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const uint8_t*)c->cflag.p,
-                                                    (const T*)c->cacc.p, si, (T*)c->cs.p, (int*)c->status.p);
+                                                    (const T*)c->cacc.p, si, (double*)c->cs.p, (int*)c->status.p);
     c->launches++;
   }
   return cuda_status(cudaGetLastError());
@@ -851,13 +846,14 @@ static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg
   cudaMemsetAsync(c->scal.p, 0, sizeof(DevScalars), c->s);
   const unsigned nb = (unsigned)c->nb, ncb = (unsigned)c->ncb;
   if (nb == 0) return MPML_OK;
-  k_node_init<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (const T*)c->nvnew.p,
-                                     (const T*)c->nvhat.p, (T*)c->ng.p, (T*)c->ndinv.p, dscal(c));
+  k_node_init<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (const double*)c->nvnew.p,
+                                     (const double*)c->nvhat.p, (double*)c->ng.p, (T*)c->ndinv.p, dscal(c));
   if (ncb > 0)
     k_prep<T><<<ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p,
-                                    (const T*)c->cacc.p, (const T*)c->cs.p, (const T*)c->nvnew.p, si, want_k,
-                                    (T*)c->cK.p, (T*)c->ng.p, (T*)c->ndinv.p, dscal(c), (int*)c->status.p);
-  k_finalize<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (T*)c->ng.p,
+                                    (const T*)c->cacc.p, (const double*)c->cs.p, (const double*)c->nvnew.p, si,
+                                    want_k, (T*)c->cK.p, (double*)c->ng.p, (T*)c->ndinv.p, dscal(c),
+                                    (int*)c->status.p);
+  k_finalize<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (double*)c->ng.p,
                                     (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p, (T*)c->np.p, (T*)c->nq.p, init_cg,
                                     cg_rtol * cg_rtol, cg_max, dscal(c));
   c->launches += ncb > 0 ? 3 : 2;
@@ -944,13 +940,13 @@ static int energy_t(mpml_ctx_s* c, double alpha, double* phi, int* infeasible) {
   cudaMemsetAsync(&d->phi_el, 0, sizeof(double), c->s);
   cudaMemsetAsync(&d->infeasible, 0, sizeof(int), c->s);
   k_energy_nodes<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
-                                                     (const T*)c->nvnew.p, (const T*)c->nx.p, (const T*)c->nvhat.p,
-                                                     (T)alpha, d);
+                                                     (const double*)c->nvnew.p, (const T*)c->nx.p,
+                                                     (const double*)c->nvhat.p, alpha, d);
   if (c->ncb > 0)
     k_energy_cells<T><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
                                                          (const uint8_t*)c->cflag.p, (const T*)c->cacc.p,
-                                                         (const T*)c->cs.p, (const T*)c->nvnew.p,
-                                                         (const T*)c->nx.p, (T)alpha, si, d);
+                                                         (const double*)c->cs.p, (const double*)c->nvnew.p,
+                                                         (const T*)c->nx.p, alpha, si, d);
   c->launches += 2;
   int rc = read_scalars(c);
   if (rc) return rc;
@@ -991,7 +987,7 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     // slope g^T dx
     DevScalars* d = dscal(c);
     cudaMemsetAsync(&d->slope, 0, sizeof(double), c->s);
-    k_dot<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->ng.p, (const T*)c->nx.p, &d->slope);
+    k_dot<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const double*)c->ng.p, (const T*)c->nx.p, &d->slope);
     c->launches++;
     if ((rc = read_scalars(c))) return rc;
     const double slope = c->hscal->slope;
@@ -1012,7 +1008,7 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
       status = MPML_WARN_NOT_CONVERGED;
       break;
     }
-    k_axpy<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nx.p, (T)alpha, (T*)c->nvnew.p);
+    k_axpy<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nx.p, alpha, (double*)c->nvnew.p);
     c->launches++;
     if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max)) || (rc = read_scalars(c))) return rc;
     gn = sqrt(c->hscal->gg);
@@ -1034,10 +1030,10 @@ template <typename T>
 static int eval_t(mpml_ctx_s* c, const void* v, double* phi, void* grad) {
   int rc = alloc_solver<T>(c);
   if (rc) return rc;
-  cudaMemcpyAsync(c->nvnew.p, v, sizeof(T) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
+  cudaMemcpyAsync(c->nvnew.p, v, sizeof(double) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
   if ((rc = prep_t<T>(c, 1, 0, 1e-6, 1)) || (rc = read_scalars(c))) return rc;
   *phi = c->hscal->phi_in + c->hscal->phi_el;
-  if (grad) cudaMemcpyAsync(grad, c->ng.p, sizeof(T) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
+  if (grad) cudaMemcpyAsync(grad, c->ng.p, sizeof(double) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
   return cuda_status(cudaStreamSynchronize(c->s));
 }
 
@@ -1050,18 +1046,23 @@ int linearize_device(mpml_ctx_s* c, const void* v) {
   return eval_device(c, v, &phi, nullptr);
 }
 
+// q = m p on brick-face node slots (the HVP adds the elastic part there)
 template <typename T>
-__global__ void k_zero_faces(T* q) {
+__global__ void k_init_faces(const T* __restrict__ p, const T* __restrict__ m, T* q) {
   const int id = blockIdx.x, l = threadIdx.x;
   const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
-  if (face)
-    for (int a = 0; a < 3; ++a) q[(int64_t)id * 3 * BV + a * BV + l] = T(0);
+  if (face) {
+    const T mi = m[(int64_t)id * BV + l];
+    for (int a = 0; a < 3; ++a) q[(int64_t)id * 3 * BV + a * BV + l] = mi * p[(int64_t)id * 3 * BV + a * BV + l];
+  }
 }
 
 template <typename T>
 static int hvp_t(mpml_ctx_s* c, const void* p, void* y) {
   cudaMemcpyAsync(c->np.p, p, sizeof(T) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
   cudaMemsetAsync(c->nq.p, 0, sizeof(T) * 3 * c->nb * BV, c->s);
+  if (c->nb > 0)
+    k_init_faces<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->np.p, (const T*)c->nmass.p, (T*)c->nq.p);
   if (c->ncb > 0) launch_hvp<T>(c, (const T*)c->np.p, (T*)c->nq.p, 0);
   cudaMemcpyAsync(y, c->nq.p, sizeof(T) * 3 * c->nb * BV, cudaMemcpyDeviceToDevice, c->s);
   return cuda_status(cudaStreamSynchronize(c->s));
@@ -1083,7 +1084,7 @@ static int hvp_bench_t(mpml_ctx_s* c, int iters, double* mean_ms) {
   cudaEventCreate(&b);
   double tot = 0;
   for (int i = 0; i < iters; ++i) {
-    k_zero_faces<T><<<(unsigned)c->nb, BV, 0, c->s>>>((T*)c->nq.p);
+    k_init_faces<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->np.p, (const T*)c->nmass.p, (T*)c->nq.p);
     cudaEventRecord(a, c->s);
     launch_hvp<T>(c, (const T*)c->np.p, (T*)c->nq.p, 0);
     cudaEventRecord(b, c->s);

@@ -347,14 +347,13 @@ struct BoundaryInfo {
 };
 
 // Dirichlet rule: sticky outer wall layers, then the moving box.
-template <typename T>
-__global__ void k_node_setup(const int* blist, GridInfo g, BoundaryInfo bi, uint8_t* nflag, T* vfix) {
+__global__ void k_node_setup(const int* blist, GridInfo g, BoundaryInfo bi, uint8_t* nflag, double* vfix) {
   int id = blockIdx.x;
   int l = threadIdx.x;
   int64_t slot = (int64_t)id * BV + l;
   uint8_t f = nflag[slot];
-  T* vf = vfix + (int64_t)id * 3 * BV + l;
-  vf[0] = vf[BV] = vf[2 * BV] = T(0);
+  double* vf = vfix + (int64_t)id * 3 * BV + l;
+  vf[0] = vf[BV] = vf[2 * BV] = 0.0;
   if (!(f & NF_DOF)) return;
   int64_t d = blist[id];
   int bx = (int)(d % g.NB[0]), by = (int)((d / g.NB[0]) % g.NB[1]), bz = (int)(d / ((int64_t)g.NB[0] * g.NB[1]));
@@ -372,9 +371,9 @@ __global__ void k_node_setup(const int* blist, GridInfo g, BoundaryInfo bi, uint
     }
     if (in) {
       fixed = true;
-      vf[0] = (T)bi.vel[0];
-      vf[BV] = (T)bi.vel[1];
-      vf[2 * BV] = (T)bi.vel[2];
+      vf[0] = bi.vel[0];
+      vf[BV] = bi.vel[1];
+      vf[2 * BV] = bi.vel[2];
     }
   }
   if (fixed) nflag[slot] = f | NF_FIXED;
@@ -466,7 +465,7 @@ static int resample_t(mpml_ctx_s* c, const void* x_, const void* v_, const void*
                                                  (const uint8_t*)c->cflag.p, (uint8_t*)c->nflag.p);
     c->launches++;
   }
-  if ((rc = ensure(c->nvfix, es * 3 * nslots))) return rc;
+  if ((rc = ensure(c->nvfix, sizeof(double) * 3 * nslots))) return rc;
   BoundaryInfo bi;
   for (int a = 0; a < 3; ++a) {
     bi.n[a] = c->d.n[a];
@@ -479,7 +478,7 @@ static int resample_t(mpml_ctx_s* c, const void* x_, const void* v_, const void*
   bi.dx = c->d.dx;
   bi.t = c->time;
   if (nb > 0) {
-    k_node_setup<T><<<(unsigned)nb, BV, 0, s>>>((const int*)c->blist.p, g, bi, (uint8_t*)c->nflag.p, (T*)c->nvfix.p);
+    k_node_setup<<<(unsigned)nb, BV, 0, s>>>((const int*)c->blist.p, g, bi, (uint8_t*)c->nflag.p, (double*)c->nvfix.p);
     c->launches++;
   }
   return cuda_status(cudaGetLastError());

@@ -192,18 +192,19 @@ __global__ void __launch_bounds__(256) k_p2q(const int* __restrict__ cblist, con
 template <typename T>
 __global__ void __launch_bounds__(512) k_q2n(const int* __restrict__ nbr, const uint8_t* __restrict__ nflag,
                                              const uint8_t* __restrict__ cflag, const T* __restrict__ acc,
-                                             const T* __restrict__ vfix, XferInfo xi, T* __restrict__ nmass,
-                                             T* __restrict__ nv, T* __restrict__ nvhat, T* __restrict__ vcur) {
+                                             const double* __restrict__ vfix, XferInfo xi, T* __restrict__ nmass,
+                                             double* __restrict__ nv, double* __restrict__ nvhat,
+                                             double* __restrict__ vcur) {
   const int id = blockIdx.x, l = threadIdx.x;
   const int64_t slot = (int64_t)id * BV + l;
   const uint8_t fl = nflag[slot];
-  T* vo = nv + (int64_t)id * 3 * BV + l;
-  T* vh = nvhat + (int64_t)id * 3 * BV + l;
-  T* vc = vcur + (int64_t)id * 3 * BV + l;
+  double* vo = nv + (int64_t)id * 3 * BV + l;
+  double* vh = nvhat + (int64_t)id * 3 * BV + l;
+  double* vc = vcur + (int64_t)id * 3 * BV + l;
   if (!(fl & NF_DOF)) {
     nmass[slot] = T(0);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) vo[r * BV] = vh[r * BV] = vc[r * BV] = T(0);
+    for (int r = 0; r < 3; ++r) vo[r * BV] = vh[r * BV] = vc[r * BV] = 0.0;
     return;
   }
   const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
@@ -235,8 +236,8 @@ __global__ void __launch_bounds__(512) k_q2n(const int* __restrict__ nbr, const 
   const bool fixed = fl & NF_FIXED;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    T vi = mi != T(0) ? mv[r] / mi : T(0);
-    T vhat = vi + (T)(xi.dt * xi.grav[r]);
+    double vi = mi != T(0) ? (double)mv[r] / (double)mi : 0.0;
+    double vhat = vi + xi.dt * xi.grav[r];
     vo[r * BV] = vi;
     vh[r * BV] = vhat;
     vc[r * BV] = fixed ? vfix[(int64_t)id * 3 * BV + r * BV + l] : vhat;
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(512) k_q2n(const int* __restrict__ nbr, const 
 // N2Q: v_c and G_c at active centres (cell-brick CTAs, 512 threads).
 template <typename T>
 __global__ void __launch_bounds__(512) k_n2q(const int* __restrict__ cblist, const int* __restrict__ nbr,
-                                             const uint8_t* __restrict__ cflag, const T* __restrict__ vn,
+                                             const uint8_t* __restrict__ cflag, const double* __restrict__ vn,
                                              XferInfo xi, T* __restrict__ cnew) {
   __shared__ T sv[3][729];
   const int id = cblist[blockIdx.x];
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(512) k_n2q(const int* __restrict__ cblist, con
     const int t = (nx < 8 && ny < 8 && nz < 8) ? id : nbr[id * NBR + nbr_index(nx >> 3, ny >> 3, nz >> 3)];
     const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) sv[r][i] = t >= 0 ? vn[(int64_t)t * 3 * BV + r * BV + l] : T(0);
+    for (int r = 0; r < 3; ++r) sv[r][i] = t >= 0 ? (T)vn[(int64_t)t * 3 * BV + r * BV + l] : T(0);
   }
   __syncthreads();
   const int l = threadIdx.x;
@@ -364,9 +365,10 @@ static int p2q_q2n_t(mpml_ctx_s* c) {
   XferInfo xi = xfer_info(c);
   const size_t es = sizeof(T);
   int rc;
+  const size_t ds = sizeof(double);
   if ((rc = ensure(c->cacc, es * xi.nf * nslots)) || (rc = ensure(c->nmass, es * nslots)) ||
-      (rc = ensure(c->nv, es * 3 * nslots)) || (rc = ensure(c->nvhat, es * 3 * nslots)) ||
-      (rc = ensure(c->nvnew, es * 3 * nslots)))
+      (rc = ensure(c->nv, ds * 3 * nslots)) || (rc = ensure(c->nvhat, ds * 3 * nslots)) ||
+      (rc = ensure(c->nvnew, ds * 3 * nslots)))
     return rc;
   if (nslots > 0) cudaMemsetAsync(c->cacc.p, 0, es * xi.nf * nslots, c->s);
   if (c->ncb > 0) {
@@ -381,8 +383,8 @@ static int p2q_q2n_t(mpml_ctx_s* c) {
   if (c->nb > 0) {
     k_q2n<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const int*)c->nbr.p, (const uint8_t*)c->nflag.p,
                                                (const uint8_t*)c->cflag.p, (const T*)c->cacc.p,
-                                               (const T*)c->nvfix.p, xi, (T*)c->nmass.p, (T*)c->nv.p,
-                                               (T*)c->nvhat.p, (T*)c->nvnew.p);
+                                               (const double*)c->nvfix.p, xi, (T*)c->nmass.p, (double*)c->nv.p,
+                                               (double*)c->nvhat.p, (double*)c->nvnew.p);
     c->launches++;
   }
   return cuda_status(cudaGetLastError());
@@ -397,7 +399,7 @@ static int n2q_t(mpml_ctx_s* c) {
   XferInfo xi = xfer_info(c);
   if (c->ncb > 0) {
     k_n2q<T><<<(unsigned)c->ncb, BV, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
-                                                (const uint8_t*)c->cflag.p, (const T*)c->nvnew.p, xi,
+                                                (const uint8_t*)c->cflag.p, (const double*)c->nvnew.p, xi,
                                                 (T*)c->cnew.p);
     c->launches++;
   }

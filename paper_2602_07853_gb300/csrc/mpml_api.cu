@@ -145,7 +145,7 @@ int get_field_t(mpml_ctx_s* c, int field, double* out) {
       int64_t ncell = 0;
       for (auto v : f) ncell += v ? 1 : 0;
       std::vector<double> s6((size_t)ncell * 6 * nm);
-      if ((rc = export_slots<T>(c, c->cs.p, 6 * nm, c->cflag, 1, s6.data()))) return rc;
+      if ((rc = export_slots<double>(c, c->cs.p, 6 * nm, c->cflag, 1, s6.data()))) return rc;
       const int ra[6] = {0, 1, 2, 0, 0, 1}, rb[6] = {0, 1, 2, 1, 2, 2};
       for (int64_t i = 0; i < ncell; ++i)
         for (int k = 0; k < nm; ++k)
@@ -175,9 +175,9 @@ int get_field_t(mpml_ctx_s* c, int field, double* out) {
       return MPML_OK;
     }
     case MPML_F_NODE_MASS: return export_slots<T>(c, c->nmass.p, 1, c->nflag, NF_DOF, out);
-    case MPML_F_NODE_VEL: return export_slots<T>(c, c->nv.p, 3, c->nflag, NF_DOF, out);
-    case MPML_F_NODE_VHAT: return export_slots<T>(c, c->nvhat.p, 3, c->nflag, NF_DOF, out);
-    case MPML_F_NODE_VNEW: return export_slots<T>(c, c->nvnew.p, 3, c->nflag, NF_DOF, out);
+    case MPML_F_NODE_VEL: return export_slots<double>(c, c->nv.p, 3, c->nflag, NF_DOF, out);
+    case MPML_F_NODE_VHAT: return export_slots<double>(c, c->nvhat.p, 3, c->nflag, NF_DOF, out);
+    case MPML_F_NODE_VNEW: return export_slots<double>(c, c->nvnew.p, 3, c->nflag, NF_DOF, out);
     case MPML_F_NODE_FIXED: {
       std::vector<uint8_t> f((size_t)ns);
       cudaMemcpyAsync(f.data(), c->nflag.p, ns ? ns : 1, cudaMemcpyDeviceToHost, c->s);
@@ -475,19 +475,19 @@ int mpml_get_field(mpml_ctx c, int field, double* out) {
 
 int mpml_set_node_velocity(mpml_ctx c, const double* v) {
   if (!c || !v || c->stage < 1) return MPML_ERR_ARG;
-  return c->fp64 ? import_nodes<double>(c, v, c->nvnew.p) : import_nodes<float>(c, v, c->nvnew.p);
+  return import_nodes<double>(c, v, c->nvnew.p);
 }
 
 int mpml_eval(mpml_ctx c, const double* v, double* phi, double* grad) {
   if (!c || !v || !phi || c->stage < 2) return MPML_ERR_ARG;
-  int rc = c->fp64 ? node_vector_op<double>(c, 0, v, phi, grad) : node_vector_op<float>(c, 0, v, phi, grad);
+  int rc = node_vector_op<double>(c, 0, v, phi, grad);  // the Newton iterate and gradient are FP64
   if (!rc) c->have_lin = 1;
   return rc;
 }
 
 int mpml_linearize(mpml_ctx c, const double* v) {
   if (!c || !v || c->stage < 2) return MPML_ERR_ARG;
-  int rc = c->fp64 ? node_vector_op<double>(c, 1, v, nullptr, nullptr) : node_vector_op<float>(c, 1, v, nullptr, nullptr);
+  int rc = node_vector_op<double>(c, 1, v, nullptr, nullptr);
   if (!rc) c->have_lin = 1;
   return rc;
 }
