@@ -120,7 +120,8 @@ typedef struct {
   int ls_max;          /* maximal number of step halvings */
   int precond;         /* MPML_PRECOND_JACOBI or MPML_PRECOND_LEARNED */
   int check_every;     /* CG iterations between convergence polls (host-driven loop) */
-  int use_graph;       /* 1: run the CG loop as a CUDA graph with a device-side while loop */
+  int use_graph;       /* 1 (default when opts is NULL): the whole CG solve is one CUDA graph
+                          launch with a device-side conditional WHILE loop; 0: host-driven loop */
 } mpml_solver_opts;
 
 typedef struct {
@@ -198,10 +199,12 @@ int mpml_linearize(mpml_ctx ctx, const double* v);
 /* y = H p with the last linearisation (masked), n_nodes*3 each. */
 int mpml_hvp(mpml_ctx ctx, const double* p, double* y);
 
-/* Profiling: when enabled, the HVP kernel launches of mpml_newton_step are
- * bracketed by CUDA events on the context stream; mpml_hvp_timing returns
+/* Profiling: when enabled, every HVP kernel launch (also inside the
+ * graph-driven CG loop) is timed on the device from the earliest block start
+ * to the last block end with the GPU global timer; mpml_hvp_timing returns
  * the number of timed launches, their total milliseconds and the bytes one
- * launch moves by the library's count (K_c, p, q, m per active brick). */
+ * launch moves by the library's count (K_c, p, q, m per active brick).
+ * Enabling (or re-enabling) resets the counters.  Synchronising. */
 int mpml_set_profiling(mpml_ctx ctx, int enable);
 int mpml_hvp_timing(mpml_ctx ctx, int64_t* launches, double* total_ms, double* bytes_per_launch);
 /* Runs `iters` back-to-back HVPs on the current linearisation with a

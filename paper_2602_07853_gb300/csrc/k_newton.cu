@@ -54,16 +54,66 @@ __device__ __forceinline__ void block_add(double (&v)[N], double* const (&dst)[N
 }
 
 // true in exactly one block: the last one to arrive (after a fence)
+// (what must be visible before the ticket is written by thread 0 only)
 __device__ __forceinline__ bool arrive_last(int* counter) {
   __shared__ int last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     int t = atomicAdd(counter, 1);
     last = (t == (int)gridDim.x - 1);
   }
   __syncthreads();
   return last != 0;
+}
+
+// block-wide sums of N doubles stored by thread 0 to part[blockIdx.x * N + i]
+template <int N>
+__device__ __forceinline__ void block_store(double (&v)[N], double* part) {
+  __shared__ double sh[N][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double s = warp_sum(v[i]);
+    if (lane == 0) sh[i][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = lane < nw ? sh[i][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0) part[(int64_t)blockIdx.x * N + i] = s;
+    }
+  }
+}
+
+// sums of the per-block partials in a fixed order (deterministic); result in
+// thread 0.  Called by every thread of the last block.
+template <int N>
+__device__ __forceinline__ void block_sum_parts(const double* part, int nblk, double (&out)[N]) {
+  __shared__ double sh[N][32];
+  double acc[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) acc[i] = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] += __ldcg(&part[(int64_t)b * N + i]);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    double s = warp_sum(acc[i]);
+    if (lane == 0) sh[i][wid] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[i][w];
+      out[i] = s;
+    }
+  }
 }
 
 __device__ __forceinline__ double vload(const double* p) { return *(volatile const double*)p; }
@@ -487,7 +537,7 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
 template <typename T>
 __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
                                                   double* g, T* diag_dinv, T* x, T* r, T* p, T* q, int init_cg,
-                                                  double rtol2, int cg_max, DevScalars* sc) {
+                                                  double rtol2, int cg_max, DevScalars* sc, double* part) {
   const int id = blockIdx.x, l = threadIdx.x;
   const int64_t slot = (int64_t)id * BV + l;
   const uint8_t f = nflag[slot];
@@ -515,10 +565,16 @@ __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nf
     }
   }
   double vals[4] = {gg, rz, rr, pmp};
-  double* const dst[4] = {&sc->gg, &sc->rz, &sc->rr0, &sc->pMp};
-  block_add<4>(vals, dst);
-  if (arrive_last(&sc->counter[CNT_FIN]) && threadIdx.x == 0) {
-    double rr0 = vload(&sc->rr0);
+  block_store<4>(vals, part);
+  if (arrive_last(&sc->counter[CNT_FIN])) {
+    double tot[4];
+    block_sum_parts<4>(part, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    sc->gg = tot[0];
+    sc->rz = tot[1];
+    sc->rr0 = tot[2];
+    sc->pMp = tot[3];
+    double rr0 = tot[2];
     sc->tol2 = rtol2 * rr0;
     sc->done = (rr0 == 0.0) ? 1 : 0;
     sc->iters = 0;
@@ -531,13 +587,196 @@ __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nf
   }
 }
 
+// ---------------------------------------------------------------------------
+// device-side launch timing (globaltimer): first block start .. last block end
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void prof_begin(DevProf* pf) {
+  if (pf && threadIdx.x == 0) atomicMin(&pf->t0, gtimer());
+}
+__device__ __forceinline__ void prof_end(DevProf* pf) {
+  if (!pf) return;
+  if (arrive_last(&pf->counter) && threadIdx.x == 0) {
+    const unsigned long long t1 = gtimer(), t0 = *(volatile unsigned long long*)&pf->t0;
+    pf->ns += t1 - t0;
+    pf->count += 1;
+    pf->t0 = ~0ull;
+    pf->counter = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy + mbarrier helpers (sm_90+ PTX, used on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// 1D bulk copy global -> shared, completion counted on the mbarrier (16-byte
+// aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on timeout (the caller flags ST_TIMEOUT)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+  for (int i = 0; i < (1 << 24); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// FP32 HVP with the brick's K block (45 x 512 floats = 92160 B) brought into
+// shared memory by one TMA bulk copy issued before the p halo is staged; the
+// K region is reused for the per-cell K D' results, so two CTAs fit per SM.
+constexpr unsigned HVP_K_BYTES = 45u * BV * 4u;
+constexpr size_t HVP_TMA_SMEM = HVP_K_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
+
+__global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                                    const uint8_t* __restrict__ cflag, const float* __restrict__ K,
+                                                    const float* __restrict__ p, const float* __restrict__ m,
+                                                    float* q, DevScalars* sc, int finalize, DevProf* pf,
+                                                    int* status, double* part) {
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_done = finalize ? sc->done : 0;
+  __syncthreads();
+  if (s_done) return;
+  prof_begin(pf);
+  extern __shared__ __align__(128) unsigned char hsm[];
+  float* Ks = reinterpret_cast<float*>(hsm);  // [45][512], later [9][512] K D'
+  float (*sv)[729] = reinterpret_cast<float (*)[729]>(hsm + HVP_K_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(hsm + HVP_K_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  const int id = cblist[blockIdx.x];
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, HVP_K_BYTES);
+    tma_load_1d(Ks, K + (int64_t)id * 45 * BV, HVP_K_BYTES, bar);
+  }
+  stage_nodes<float, float, float>(id, nbr, p, (const float*)nullptr, 0.0, sv);
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+  double pkp = 0;
+  float KD[2][9];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int l = threadIdx.x + h * 256;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) KD[h][r] = 0.f;
+    if (ok && cflag[(int64_t)id * BV + l]) {
+      float D[9];
+      gather_D<float>(l, sv, D);
+#pragma unroll
+      for (int r = 0; r < 9; ++r) {
+        KD[h][r] += Ks[k45(r, r) * BV + l] * D[r];
+#pragma unroll
+        for (int cc = r + 1; cc < 9; ++cc) {
+          const float kv = Ks[k45(r, cc) * BV + l];
+          KD[h][r] += kv * D[cc];
+          KD[h][cc] += kv * D[r];
+        }
+      }
+      float dkd = 0.f;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) dkd += D[r] * KD[h][r];
+      pkp += (double)dkd;
+    }
+  }
+  __syncthreads();  // every thread is done reading K: reuse the region for K D'
+  float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(Ks);
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int r = 0; r < 9; ++r) skd[r][threadIdx.x + h * 256] = KD[h][r];
+  __syncthreads();
+  for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+    const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+    float y[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int cx = nx - (o & 1), cy = ny - ((o >> 1) & 1), cz = nz - ((o >> 2) & 1);
+      if (cx < 0 || cy < 0 || cz < 0 || cx > 7 || cy > 7 || cz > 7) continue;
+      const int c = (cz * 8 + cy) * 8 + cx;
+      const float s0 = (o & 1) ? 1.f : -1.f, s1 = (o & 2) ? 1.f : -1.f, s2 = (o & 4) ? 1.f : -1.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) y[a] += skd[3 * a][c] * s0 + skd[3 * a + 1][c] * s1 + skd[3 * a + 2][c] * s2;
+    }
+    const bool own = nx < 8 && ny < 8 && nz < 8;
+    const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
+    if (own) {
+      const int l = nz * 64 + ny * 8 + nx;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        float* dst = q + (int64_t)id * 3 * BV + a * BV + l;
+        if (excl) *dst = y[a] + m[(int64_t)id * BV + l] * sv[a][i];
+        else if (y[a] != 0.f) atomicAdd(dst, y[a]);
+      }
+    } else {
+      const int t = __ldg(&nbr[id * NBR + nbr_index(nx >> 3, ny >> 3, nz >> 3)]);
+      if (t < 0) continue;
+      const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (y[a] != 0.f) atomicAdd(q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
+    }
+  }
+  double vals[1] = {pkp};
+  block_store<1>(vals, part);
+  if (finalize && arrive_last(&sc->counter[CNT_HVP])) {
+    double tot[1];
+    block_sum_parts<1>(part, gridDim.x, tot);
+    double pq = sc->pMp + tot[0];
+    if (threadIdx.x != 0) {
+      // only thread 0 updates the scalars
+    } else if (!(pq > 0.0)) {
+      sc->done = 1;
+      sc->alpha = 0;
+    } else {
+      sc->alpha = sc->rz / pq;
+    }
+    sc->counter[CNT_HVP] = 0;
+  }
+  prof_end(pf);
+}
+
 // HVP over cell bricks: q = M p + sum_c B^T K B p (faces atomically).
 template <typename T>
 __global__ void __launch_bounds__(256) k_hvp(const int* __restrict__ cblist, const int* __restrict__ nbr,
                                              const uint8_t* __restrict__ cflag, const T* __restrict__ K,
                                              const T* __restrict__ p, const T* __restrict__ m, T* q,
-                                             DevScalars* sc, int finalize) {
-  if (finalize && *(volatile int*)&sc->done) return;
+                                             DevScalars* sc, int finalize, DevProf* pf, double* part) {
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_done = finalize ? sc->done : 0;
+  __syncthreads();
+  if (s_done) return;
+  prof_begin(pf);
   extern __shared__ __align__(16) unsigned char hvp_smem[];
   T (*sv)[729] = reinterpret_cast<T (*)[729]>(hvp_smem);
   T (*skd)[BV] = reinterpret_cast<T (*)[BV]>(hvp_smem + sizeof(T) * 3 * 729 + (16 - (sizeof(T) * 3 * 729) % 16) % 16);
@@ -612,30 +851,39 @@ __global__ void __launch_bounds__(256) k_hvp(const int* __restrict__ cblist, con
     }
   }
   double vals[1] = {pkp};
-  double* const dst[1] = {&sc->pKp};
-  block_add<1>(vals, dst);
-  if (finalize && arrive_last(&sc->counter[CNT_HVP]) && threadIdx.x == 0) {
-    double pq = vload(&sc->pMp) + vload(&sc->pKp);
-    if (!(pq > 0.0)) {
+  block_store<1>(vals, part);
+  if (finalize && arrive_last(&sc->counter[CNT_HVP])) {
+    double tot[1];
+    block_sum_parts<1>(part, gridDim.x, tot);
+    double pq = sc->pMp + tot[0];
+    if (threadIdx.x != 0) {
+      // only thread 0 updates the scalars
+    } else if (!(pq > 0.0)) {
       sc->done = 1;  // breakdown (zero direction)
       sc->alpha = 0;
     } else {
-      sc->alpha = vload(&sc->rz) / pq;
+      sc->alpha = sc->rz / pq;
     }
-    sc->pKp = 0;
     sc->counter[CNT_HVP] = 0;
   }
+  prof_end(pf);
 }
 
 // CG update A: x += alpha p, r -= alpha q, z = D^-1 r, r^T z, r^T r; the last
-// block tests convergence and forms beta.
+// block tests convergence and forms beta.  Generic version (any T).
 template <typename T>
 __global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ dinv, const T* __restrict__ p,
-                                              const T* __restrict__ q, T* x, T* r, DevScalars* sc) {
-  if (*(volatile int*)&sc->done) return;
+                                              const T* __restrict__ q, T* x, T* r, DevScalars* sc, double* part) {
+  __shared__ int s_done;
+  __shared__ double s_alpha;
+  if (threadIdx.x == 0) {
+    s_done = sc->done;
+    s_alpha = sc->alpha;
+  }
+  __syncthreads();
+  if (s_done) return;
   const int id = blockIdx.x, l = threadIdx.x;
-  const double alpha = vload(&sc->alpha);
-  const T al = (T)alpha;
+  const T al = (T)s_alpha;
   double rz = 0, rr = 0;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -651,30 +899,93 @@ __global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ dinv, const 
     }
   }
   double vals[2] = {rz, rr};
-  double* const dst[2] = {&sc->rz_new, &sc->rr};
-  block_add<2>(vals, dst);
-  if (arrive_last(&sc->counter[CNT_A]) && threadIdx.x == 0) {
-    const double rzn = vload(&sc->rz_new), rrv = vload(&sc->rr);
+  block_store<2>(vals, part);
+  if (arrive_last(&sc->counter[CNT_A])) {
+    double tot[2];
+    block_sum_parts<2>(part, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    const double rzn = tot[0], rrv = tot[1];
     const int it = sc->iters + 1;
     sc->iters = it;
     sc->rr_last = rrv;
     if (rrv <= sc->tol2 || it >= sc->cg_max || !(rrv == rrv)) sc->done = 1;
-    sc->beta = rzn / vload(&sc->rz);
+    sc->beta = rzn / sc->rz;
     sc->rz = rzn;
-    sc->rz_new = 0;
-    sc->rr = 0;
-    sc->pMp = 0;
     sc->counter[CNT_A] = 0;
   }
 }
 
-// CG update B: p = D^-1 r + beta p, q(face) = 0, sum m |p|^2
+// FP32 version: 128 threads per brick, 4 consecutive slots per thread with
+// 16-byte loads; products and per-thread sums in FP32, accumulation across
+// threads and blocks in FP64 (FP64 arithmetic is scarce on this GPU).
+__global__ void __launch_bounds__(128) k_cg_a4(const float* __restrict__ dinv, const float* __restrict__ p,
+                                               const float* __restrict__ q, float* x, float* r, DevScalars* sc,
+                                               double* part) {
+  __shared__ int s_done;
+  __shared__ float s_alpha;
+  if (threadIdx.x == 0) {
+    s_done = sc->done;
+    s_alpha = (float)sc->alpha;
+  }
+  __syncthreads();
+  if (s_done) return;
+  const float al = s_alpha;
+  double rz = 0, rr = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = ((int64_t)blockIdx.x * 3 + a) * BV + 4 * threadIdx.x;
+    const float4 d4 = *reinterpret_cast<const float4*>(dinv + o);
+    const float4 p4 = *reinterpret_cast<const float4*>(p + o);
+    const float4 q4 = *reinterpret_cast<const float4*>(q + o);
+    float4 x4 = *reinterpret_cast<const float4*>(x + o);
+    float4 r4 = *reinterpret_cast<const float4*>(r + o);
+    const float dd[4] = {d4.x, d4.y, d4.z, d4.w}, pp[4] = {p4.x, p4.y, p4.z, p4.w}, qq[4] = {q4.x, q4.y, q4.z, q4.w};
+    float xx[4] = {x4.x, x4.y, x4.z, x4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
+    float srz = 0.f, srr = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool f = dd[j] > 0.f;
+      xx[j] = f ? xx[j] + al * pp[j] : xx[j];
+      rv[j] = f ? rv[j] - al * qq[j] : rv[j];
+      srz += f ? rv[j] * dd[j] * rv[j] : 0.f;
+      srr += f ? rv[j] * rv[j] : 0.f;
+    }
+    *reinterpret_cast<float4*>(x + o) = make_float4(xx[0], xx[1], xx[2], xx[3]);
+    *reinterpret_cast<float4*>(r + o) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+    rz += (double)srz;
+    rr += (double)srr;
+  }
+  double vals[2] = {rz, rr};
+  block_store<2>(vals, part);
+  if (arrive_last(&sc->counter[CNT_A])) {
+    double tot[2];
+    block_sum_parts<2>(part, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    const double rzn = tot[0], rrv = tot[1];
+    const int it = sc->iters + 1;
+    sc->iters = it;
+    sc->rr_last = rrv;
+    if (rrv <= sc->tol2 || it >= sc->cg_max || !(rrv == rrv)) sc->done = 1;
+    sc->beta = rzn / sc->rz;
+    sc->rz = rzn;
+    sc->counter[CNT_A] = 0;
+  }
+}
+
+// CG update B: p = D^-1 r + beta p, q(face) = m p, sum m |p|^2
 template <typename T>
 __global__ void __launch_bounds__(512) k_cg_b(const T* __restrict__ dinv, const T* __restrict__ m,
-                                              const T* __restrict__ r, T* p, T* q, DevScalars* sc) {
-  if (*(volatile int*)&sc->done) return;
+                                              const T* __restrict__ r, T* p, T* q, DevScalars* sc, double* part) {
+  __shared__ int s_done;
+  __shared__ double s_beta;
+  if (threadIdx.x == 0) {
+    s_done = sc->done;
+    s_beta = sc->beta;
+  }
+  __syncthreads();
+  if (s_done) return;
   const int id = blockIdx.x, l = threadIdx.x;
-  const T be = (T)vload(&sc->beta);
+  const T be = (T)s_beta;
   const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
   const T mi = m[(int64_t)id * BV + l];
   double pmp = 0;
@@ -689,8 +1000,65 @@ __global__ void __launch_bounds__(512) k_cg_b(const T* __restrict__ dinv, const 
     pmp += (double)mi * (double)pv * (double)pv;
   }
   double vals[1] = {pmp};
-  double* const dst[1] = {&sc->pMp};
-  block_add<1>(vals, dst);
+  block_store<1>(vals, part);
+  if (arrive_last(&sc->counter[CNT_B])) {
+    double tot[1];
+    block_sum_parts<1>(part, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    sc->pMp = tot[0];
+    sc->counter[CNT_B] = 0;
+  }
+}
+
+// FP32 version of B (4 slots per thread, 16-byte accesses)
+__global__ void __launch_bounds__(128) k_cg_b4(const float* __restrict__ dinv, const float* __restrict__ m,
+                                               const float* __restrict__ r, float* p, float* q, DevScalars* sc,
+                                               double* part) {
+  __shared__ int s_done;
+  __shared__ float s_beta;
+  if (threadIdx.x == 0) {
+    s_done = sc->done;
+    s_beta = (float)sc->beta;
+  }
+  __syncthreads();
+  if (s_done) return;
+  const float be = s_beta;
+  const int l0 = 4 * threadIdx.x;
+  // slots l0..l0+3 share (ly, lz); lx = l0 & 7 is 0 or 4
+  const bool face_yz = ((l0 >> 3) & 7) == 0 || (l0 >> 6) == 0;
+  const bool face0 = face_yz || (l0 & 7) == 0;
+  const float4 m4 = *reinterpret_cast<const float4*>(m + (int64_t)blockIdx.x * BV + l0);
+  const float mm[4] = {m4.x, m4.y, m4.z, m4.w};
+  float spmp = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = ((int64_t)blockIdx.x * 3 + a) * BV + l0;
+    const float4 d4 = *reinterpret_cast<const float4*>(dinv + o);
+    const float4 r4 = *reinterpret_cast<const float4*>(r + o);
+    const float4 p4 = *reinterpret_cast<const float4*>(p + o);
+    const float dd[4] = {d4.x, d4.y, d4.z, d4.w}, rr4[4] = {r4.x, r4.y, r4.z, r4.w}, po[4] = {p4.x, p4.y, p4.z, p4.w};
+    float pv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      pv[j] = dd[j] > 0.f ? dd[j] * rr4[j] + be * po[j] : 0.f;
+      spmp += mm[j] * pv[j] * pv[j];
+    }
+    *reinterpret_cast<float4*>(p + o) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+    if (face_yz) {
+      *reinterpret_cast<float4*>(q + o) = make_float4(mm[0] * pv[0], mm[1] * pv[1], mm[2] * pv[2], mm[3] * pv[3]);
+    } else if (face0) {
+      q[o] = mm[0] * pv[0];
+    }
+  }
+  double vals[1] = {(double)spmp};
+  block_store<1>(vals, part);
+  if (arrive_last(&sc->counter[CNT_B])) {
+    double tot[1];
+    block_sum_parts<1>(part, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    sc->pMp = tot[0];
+    sc->counter[CNT_B] = 0;
+  }
 }
 
 // g^T x over free DOFs
@@ -811,7 +1179,8 @@ static int alloc_solver(mpml_ctx_s* c) {
   int rc;
   if ((rc = ensure(c->cs, sizeof(double) * 6 * c->nm * ns)) || (rc = ensure(c->cK, es * 45 * ns)) ||
       (rc = ensure(c->ng, sizeof(double) * 3 * ns)) || (rc = ensure(c->ndinv, es * 3 * ns)) || (rc = ensure(c->nx, es * 3 * ns)) ||
-      (rc = ensure(c->nr, es * 3 * ns)) || (rc = ensure(c->np, es * 3 * ns)) || (rc = ensure(c->nq, es * 3 * ns)))
+      (rc = ensure(c->nr, es * 3 * ns)) || (rc = ensure(c->np, es * 3 * ns)) || (rc = ensure(c->nq, es * 3 * ns)) ||
+      (rc = ensure(c->part, sizeof(double) * 8 * (c->nb ? c->nb : 1))))
     return rc;
   return MPML_OK;
 }
@@ -832,6 +1201,11 @@ static int stretch_t(mpml_ctx_s* c) {
 int stretch_all(mpml_ctx_s* c) { return c->fp64 ? stretch_t<double>(c) : stretch_t<float>(c); }
 
 static DevScalars* dscal(mpml_ctx_s* c) { return (DevScalars*)c->scal.p; }
+// per-block partial sums of the reductions (8 doubles per brick)
+static double* part_fin(mpml_ctx_s* c) { return (double*)c->part.p; }
+static double* part_hvp(mpml_ctx_s* c) { return (double*)c->part.p + 4 * c->nb; }
+static double* part_a(mpml_ctx_s* c) { return (double*)c->part.p + 5 * c->nb; }
+static double* part_b(mpml_ctx_s* c) { return (double*)c->part.p + 7 * c->nb; }
 
 static int read_scalars(mpml_ctx_s* c) {
   cudaMemcpyAsync(c->hscal, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s);
@@ -855,7 +1229,7 @@ static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg
                                     (int*)c->status.p);
   k_finalize<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (double*)c->ng.p,
                                     (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p, (T*)c->np.p, (T*)c->nq.p, init_cg,
-                                    cg_rtol * cg_rtol, cg_max, dscal(c));
+                                    cg_rtol * cg_rtol, cg_max, dscal(c), part_fin(c));
   c->launches += ncb > 0 ? 3 : 2;
   return cuda_status(cudaGetLastError());
 }
@@ -867,64 +1241,133 @@ constexpr size_t hvp_smem_bytes() {
 
 template <typename T>
 static void launch_hvp(mpml_ctx_s* c, const T* p, T* q, int finalize) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_hvp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hvp_smem_bytes<T>());
-    attr = true;
+  DevProf* pf = c->profiling ? (DevProf*)c->prof.p : nullptr;
+  if (sizeof(T) == 4) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_hvp_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_TMA_SMEM);
+      attr = true;
+    }
+    k_hvp_tma<<<(unsigned)c->ncb, 256, HVP_TMA_SMEM, c->s>>>(
+        (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
+        (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
+        part_hvp(c));
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_hvp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hvp_smem_bytes<T>());
+      attr = true;
+    }
+    k_hvp<T><<<(unsigned)c->ncb, 256, hvp_smem_bytes<T>(), c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
+                                                                 (const uint8_t*)c->cflag.p, (const T*)c->cK.p, p,
+                                                                 (const T*)c->nmass.p, q, dscal(c), finalize, pf,
+                                                                 part_hvp(c));
   }
-  k_hvp<T><<<(unsigned)c->ncb, 256, hvp_smem_bytes<T>(), c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
-                                              (const uint8_t*)c->cflag.p, (const T*)c->cK.p, p,
-                                              (const T*)c->nmass.p, q, dscal(c), finalize);
   c->launches++;
 }
 
 template <typename T>
 static void cg_iteration(mpml_ctx_s* c) {
   const unsigned nb = (unsigned)c->nb;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (c->profiling) {
-    if (c->ev_used + 2 > (int)c->ev_pool.size()) {
-      for (int i = 0; i < 64; ++i) {
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        c->ev_pool.push_back(e);
-      }
-    }
-    e0 = c->ev_pool[c->ev_used++];
-    e1 = c->ev_pool[c->ev_used++];
-    cudaEventRecord(e0, c->s);
-  }
   launch_hvp<T>(c, (const T*)c->np.p, (T*)c->nq.p, 1);
-  if (c->profiling) cudaEventRecord(e1, c->s);
-  k_cg_a<T><<<nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->np.p, (const T*)c->nq.p, (T*)c->nx.p,
-                                (T*)c->nr.p, dscal(c));
-  k_cg_b<T><<<nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nmass.p, (const T*)c->nr.p, (T*)c->np.p,
-                                (T*)c->nq.p, dscal(c));
+  if (sizeof(T) == 4) {
+    k_cg_a4<<<nb, 128, 0, c->s>>>((const float*)c->ndinv.p, (const float*)c->np.p, (const float*)c->nq.p,
+                                  (float*)c->nx.p, (float*)c->nr.p, dscal(c), part_a(c));
+    k_cg_b4<<<nb, 128, 0, c->s>>>((const float*)c->ndinv.p, (const float*)c->nmass.p, (const float*)c->nr.p,
+                                  (float*)c->np.p, (float*)c->nq.p, dscal(c), part_b(c));
+  } else {
+    k_cg_a<T><<<nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->np.p, (const T*)c->nq.p, (T*)c->nx.p,
+                                  (T*)c->nr.p, dscal(c), part_a(c));
+    k_cg_b<T><<<nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nmass.p, (const T*)c->nr.p, (T*)c->np.p,
+                                  (T*)c->nq.p, dscal(c), part_b(c));
+  }
   c->launches += 2;
 }
 
-static void harvest_events(mpml_ctx_s* c) {
-  for (int i = 0; i + 1 < c->ev_used; i += 2) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, c->ev_pool[i], c->ev_pool[i + 1]) == cudaSuccess) {
-      c->hvp_ms_total += ms;
-      c->hvp_launches_timed++;
-    }
+// Condition of the graph-driven CG loop: continue while not converged, under
+// the iteration cap, and under a hard cap on loop bodies (always terminates).
+__global__ void k_cg_cond(DevScalars* sc, cudaGraphConditionalHandle h, int max_bodies) {
+  const int b = sc->bodies + 1;
+  sc->bodies = b;
+  const int go = !(*(volatile int*)&sc->done) && sc->iters < sc->cg_max && b < max_bodies;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+constexpr int CG_UNROLL = 4;
+
+template <typename T>
+static int ensure_cg_graph(mpml_ctx_s* c, int cg_max) {
+  const uintptr_t key[16] = {(uintptr_t)c->nb, (uintptr_t)c->ncb, (uintptr_t)c->np.p, (uintptr_t)c->nq.p,
+                             (uintptr_t)c->nx.p, (uintptr_t)c->nr.p, (uintptr_t)c->ndinv.p, (uintptr_t)c->nmass.p,
+                             (uintptr_t)c->cK.p, (uintptr_t)c->scal.p, (uintptr_t)c->profiling,
+                             (uintptr_t)c->cblist.p, (uintptr_t)c->nbr.p, (uintptr_t)c->cflag.p,
+                             (uintptr_t)cg_max, (uintptr_t)c->prof.p};
+  if (c->cg_exec && memcmp(key, c->cg_key, sizeof key) == 0) return MPML_OK;
+  if (c->cg_exec) {
+    cudaGraphExecDestroy(c->cg_exec);
+    c->cg_exec = nullptr;
   }
-  c->ev_used = 0;
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return MPML_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  int rc = MPML_OK;
+  cudaGraphConditionalHandle h;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t node;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return MPML_ERR_CUDA;
+  if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) rc = MPML_ERR_CUDA;
+  if (!rc) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess) rc = MPML_ERR_CUDA;
+  }
+  if (!rc) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t user = c->s;
+    c->s = c->cap_stream;  // the kernels below are recorded into the loop body
+    if (cudaStreamBeginCaptureToGraph(c->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      rc = MPML_ERR_CUDA;
+    } else {
+      const int64_t before = c->launches;
+      for (int u = 0; u < CG_UNROLL; ++u) cg_iteration<T>(c);
+      k_cg_cond<<<1, 1, 0, c->s>>>(dscal(c), h, cg_max / CG_UNROLL + 2);
+      c->launches = before;  // recorded, not launched
+      cudaGraph_t out = nullptr;
+      if (cudaStreamEndCapture(c->s, &out) != cudaSuccess) rc = MPML_ERR_CUDA;
+    }
+    c->s = user;
+  }
+  if (!rc && cudaGraphInstantiate(&c->cg_exec, g, 0) != cudaSuccess) {
+    c->cg_exec = nullptr;
+    rc = MPML_ERR_CUDA;
+  }
+  cudaGraphDestroy(g);
+  if (rc) {
+    cudaGetLastError();
+    return rc;
+  }
+  memcpy(c->cg_key, key, sizeof key);
+  return MPML_OK;
 }
 
 template <typename T>
 static int pcg_t(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, double* rel) {
   int rc;
-  const int every = o->check_every > 0 ? o->check_every : 16;
-  int launched = 0;
-  if ((rc = read_scalars(c))) return rc;
-  while (!c->hscal->done && launched < o->cg_max) {
-    for (int j = 0; j < every && launched < o->cg_max; ++j, ++launched) cg_iteration<T>(c);
-    if ((rc = cuda_status(cudaGetLastError()))) return rc;
+  if (o->use_graph && c->ncb > 0 && ensure_cg_graph<T>(c, o->cg_max) == MPML_OK) {
+    if ((rc = cuda_status(cudaGraphLaunch(c->cg_exec, c->s)))) return rc;
     if ((rc = read_scalars(c))) return rc;
-    if (c->profiling) harvest_events(c);
+    c->launches += (int64_t)c->hscal->bodies * (3 * CG_UNROLL + 1);
+  } else {
+    const int every = o->check_every > 0 ? o->check_every : 16;
+    int launched = 0;
+    if ((rc = read_scalars(c))) return rc;
+    while (!c->hscal->done && launched < o->cg_max) {
+      for (int j = 0; j < every && launched < o->cg_max; ++j, ++launched) cg_iteration<T>(c);
+      if ((rc = cuda_status(cudaGetLastError()))) return rc;
+      if ((rc = read_scalars(c))) return rc;
+    }
   }
   *iters = c->hscal->iters;
   const double rr0 = c->hscal->rr0;

@@ -278,11 +278,12 @@ int mpml_destroy(mpml_ctx c) {
                  &c->pG, &c->pm, &c->pV, &c->pmat, &c->pperm, &c->pkey, &c->prank, &c->pbase, &c->ux, &c->uv,
                  &c->uF, &c->uG, &c->um, &c->uV, &c->umat, &c->cnt, &c->start, &c->scan_tmp, &c->cflag,
                  &c->cacc, &c->cs, &c->cK, &c->cnew, &c->nflag, &c->nmass, &c->nv, &c->nvhat, &c->nvfix,
-                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->scal, &c->status};
+                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->scal, &c->status, &c->prof, &c->part};
   for (Buf* b : bufs) free_buf(*b);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hstatus) cudaFreeHost(c->hstatus);
-  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return MPML_OK;
 }
@@ -369,7 +370,7 @@ int mpml_stretch(mpml_ctx c) {
 
 int mpml_newton_step(mpml_ctx c, const mpml_solver_opts* o, mpml_solve_stats* st) {
   if (!c || c->stage < 1) return MPML_ERR_ARG;
-  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 0};
+  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 1};
   if (!o) o = &def;
   mpml_solve_stats local;
   if (!st) st = &local;
@@ -499,17 +500,26 @@ int mpml_hvp(mpml_ctx c, const double* p, double* y) {
 
 int mpml_set_profiling(mpml_ctx c, int enable) {
   if (!c) return MPML_ERR_ARG;
+  int rc = ensure(c->prof, sizeof(DevProf));
+  if (rc) return rc;
+  DevProf init = {~0ull, 0ull, 0ull, 0, 0};
+  cudaMemcpyAsync(c->prof.p, &init, sizeof init, cudaMemcpyHostToDevice, c->s);
+  rc = cuda_status(cudaStreamSynchronize(c->s));
+  if (rc) return rc;
   c->profiling = enable ? 1 : 0;
-  c->hvp_launches_timed = 0;
-  c->hvp_ms_total = 0;
-  c->ev_used = 0;
   return MPML_OK;
 }
 
 int mpml_hvp_timing(mpml_ctx c, int64_t* launches, double* total_ms, double* bytes_per_launch) {
   if (!c) return MPML_ERR_ARG;
-  if (launches) *launches = c->hvp_launches_timed;
-  if (total_ms) *total_ms = c->hvp_ms_total;
+  DevProf pf = {~0ull, 0ull, 0ull, 0, 0};
+  if (c->prof.p) {
+    cudaMemcpyAsync(&pf, c->prof.p, sizeof pf, cudaMemcpyDeviceToHost, c->s);
+    int rc = cuda_status(cudaStreamSynchronize(c->s));
+    if (rc) return rc;
+  }
+  if (launches) *launches = (int64_t)pf.count;
+  if (total_ms) *total_ms = (double)pf.ns * 1e-6;
   if (bytes_per_launch) {
     // per cell brick: K (45/cell) read, p (3/node) read, m read, q (3/node) written
     const double e = (double)c->esz;

@@ -75,7 +75,17 @@ struct DevScalars {
   int done;
   int iters;
   int cg_max;
+  int bodies;      // executed bodies of the graph-driven CG loop
   int counter[8];  // last-block tickets per kernel kind
+  int pad;
+};
+
+// Device-side launch timing of the HVP (globaltimer ns), enabled by profiling.
+struct DevProf {
+  unsigned long long t0;     // earliest block start of the running launch
+  unsigned long long ns;     // accumulated launch durations
+  unsigned long long count;  // timed launches
+  int counter;               // last-block ticket
   int pad;
 };
 
@@ -117,7 +127,7 @@ struct mpml_ctx_s {
   // nodes
   mpml::Buf nflag, nmass, nv, nvhat, nvfix, nvnew, ng, ndinv, nx, nr, np, nq;
   // scalars and status
-  mpml::Buf scal, status;
+  mpml::Buf scal, status, prof, part;
   mpml::DevScalars* hscal = nullptr;  // pinned mirror
   int* hstatus = nullptr;             // pinned
 
@@ -125,12 +135,13 @@ struct mpml_ctx_s {
   int stage = 0;  // 0 nothing, 1 unloaded, 2 stretched, 3 solved, 4 loaded
   int have_lin = 0;
 
+  // graph-driven CG loop (conditional WHILE node), rebuilt when its key changes
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t cg_exec = nullptr;
+  uintptr_t cg_key[16] = {};
+
   // profiling of HVP launches
   int profiling = 0;
-  std::vector<cudaEvent_t> ev_pool;
-  int ev_used = 0;
-  int64_t hvp_launches_timed = 0;
-  double hvp_ms_total = 0;
   int64_t launches = 0;
 };
 
