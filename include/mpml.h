@@ -120,8 +120,10 @@ typedef struct {
   int ls_max;          /* maximal number of step halvings */
   int precond;         /* MPML_PRECOND_JACOBI or MPML_PRECOND_LEARNED */
   int check_every;     /* CG iterations between convergence polls (host-driven loop) */
-  int use_graph;       /* 1 (default when opts is NULL): the whole CG solve is one CUDA graph
-                          launch with a device-side conditional WHILE loop; 0: host-driven loop */
+  int use_graph;       /* how the CG loop runs: 0 host-driven launches; 1 one CUDA graph launch
+                          with a device-side conditional WHILE loop; 2 (default when opts is
+                          NULL) one persistent cooperative kernel with bounded grid barriers
+                          (FP32 single-material contexts; others use 1) */
 } mpml_solver_opts;
 
 typedef struct {

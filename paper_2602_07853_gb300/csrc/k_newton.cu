@@ -277,6 +277,26 @@ __device__ __forceinline__ void stage_nodes(int id, const int* __restrict__ nbr,
   }
 }
 
+// same, with the brick's 27-entry neighbour row already in shared memory
+template <typename S, typename A>
+__device__ __forceinline__ void stage_nodes_sn(int id, const int* s_nbr, const A* __restrict__ a, S (*sv)[729]) {
+  for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+    const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+    const int t = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+    const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+    S v0 = S(0), v1 = S(0), v2 = S(0);
+    if (t >= 0) {
+      const int64_t o = (int64_t)t * 3 * BV + l;
+      v0 = (S)a[o];
+      v1 = (S)a[o + BV];
+      v2 = (S)a[o + 2 * BV];
+    }
+    sv[0][i] = v0;
+    sv[1][i] = v1;
+    sv[2][i] = v2;
+  }
+}
+
 __device__ __forceinline__ int node_of(int l, int o) {
   const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
   return ((lz + ((o >> 2) & 1)) * 9 + (ly + ((o >> 1) & 1))) * 9 + (lx + (o & 1));
@@ -310,9 +330,60 @@ template <typename T>
 struct CellOut {
   double Q[9];  // dt V P S^T / (4 dx)   (gradient, node contribution = Q sgn)
   T K[45];      // dt^2 V L^T A+ L / (16 dx^2)
+  // the same tangent as 27 numbers (single material): quaternions of U, V and
+  // of the eigenbasis of the 3x3 block, S - I (6), and the clamped, scaled
+  // eigenvalues of the block (3), flip (3) and twist (3) modes
+  T C[27];
   double psi;
   bool ok;
 };
+
+// unit quaternion (w, x, y, z) of a rotation matrix (row-major), Shepperd's method
+__device__ __forceinline__ void rot_to_quat(const double R[9], double q[4]) {
+  const double tr = R[0] + R[4] + R[8];
+  if (tr > 0) {
+    const double s = 2.0 * sqrt(tr + 1.0);
+    q[0] = 0.25 * s;
+    q[1] = (R[7] - R[5]) / s;
+    q[2] = (R[2] - R[6]) / s;
+    q[3] = (R[3] - R[1]) / s;
+  } else if (R[0] > R[4] && R[0] > R[8]) {
+    const double s = 2.0 * sqrt(1.0 + R[0] - R[4] - R[8]);
+    q[0] = (R[7] - R[5]) / s;
+    q[1] = 0.25 * s;
+    q[2] = (R[1] + R[3]) / s;
+    q[3] = (R[2] + R[6]) / s;
+  } else if (R[4] > R[8]) {
+    const double s = 2.0 * sqrt(1.0 + R[4] - R[0] - R[8]);
+    q[0] = (R[2] - R[6]) / s;
+    q[1] = (R[1] + R[3]) / s;
+    q[2] = 0.25 * s;
+    q[3] = (R[5] + R[7]) / s;
+  } else {
+    const double s = 2.0 * sqrt(1.0 + R[8] - R[0] - R[4]);
+    q[0] = (R[3] - R[1]) / s;
+    q[1] = (R[2] + R[6]) / s;
+    q[2] = (R[5] + R[7]) / s;
+    q[3] = 0.25 * s;
+  }
+  const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) q[i] /= n;
+}
+
+// rotation matrix (row-major) of a unit quaternion (w, x, y, z)
+template <typename T>
+__device__ __forceinline__ void quat_to_rot(T w, T x, T y, T z, T R[9]) {
+  R[0] = T(1) - T(2) * (y * y + z * z);
+  R[1] = T(2) * (x * y - z * w);
+  R[2] = T(2) * (x * z + y * w);
+  R[3] = T(2) * (x * y + z * w);
+  R[4] = T(1) - T(2) * (x * x + z * z);
+  R[5] = T(2) * (y * z - x * w);
+  R[6] = T(2) * (x * z - y * w);
+  R[7] = T(2) * (y * z + x * w);
+  R[8] = T(1) - T(2) * (x * x + y * y);
+}
 
 // F - I = dt G + s + dt G s with S = I + s (symmetric, packed xx yy zz xy xz yz)
 __device__ __forceinline__ void trial_h(const double Gd[9], const double s6[6], double sm[9], double H[9]) {
@@ -376,6 +447,37 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
   // diagonal block: eigen-decomposition of d2, clamp
   T ev[3], Qd[9];
   jacobi3<T>(d2, ev, Qd);
+  {
+    // compressed record (valid for single-material cells)
+    double Qq[9], q[4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Qq[i] = (double)Qd[i];
+    const double det = Qq[0] * (Qq[4] * Qq[8] - Qq[5] * Qq[7]) - Qq[1] * (Qq[3] * Qq[8] - Qq[5] * Qq[6]) +
+                       Qq[2] * (Qq[3] * Qq[7] - Qq[4] * Qq[6]);
+    if (det < 0) {
+      Qq[2] = -Qq[2];
+      Qq[5] = -Qq[5];
+      Qq[8] = -Qq[8];
+    }
+    rot_to_quat(U, q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out.C[i] = (T)q[i];
+    rot_to_quat(Vv, q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out.C[4 + i] = (T)q[i];
+    rot_to_quat(Qq, q);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out.C[8 + i] = (T)q[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out.C[12 + i] = (T)s6[i];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) out.C[18 + m] = ev[m] > T(0) ? kv * ev[m] : T(0);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      out.C[21 + p] = sp.pp[p] > 0 ? kv * (T)sp.pp[p] : T(0);
+      out.C[24 + p] = sp.pm[p] > 0 ? kv * (T)sp.pm[p] : T(0);
+    }
+  }
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     if (!(ev[m] > T(0))) continue;
@@ -480,6 +582,8 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
     for (int q = 0; q < 9; ++q) co.Q[q] = 0.0;
 #pragma unroll
     for (int q = 0; q < 45; ++q) co.K[q] = T(0);
+#pragma unroll
+    for (int q = 0; q < 27; ++q) co.C[q] = T(0);
     co.psi = 0;
     co.ok = true;
     for (int k = 0; k < si.nm; ++k) {
@@ -495,7 +599,11 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
       continue;
     }
     esum += co.psi;
-    if (want_k) {
+    if (want_k == 2) {  // compressed tangent (single material, FP32)
+      T* Kd = K + (int64_t)id * 27 * BV + l;
+#pragma unroll
+      for (int q = 0; q < 27; ++q) Kd[q * BV] = co.C[q];
+    } else if (want_k) {
       T* Kd = K + (int64_t)id * 45 * BV + l;
 #pragma unroll
       for (int q = 0; q < 45; ++q) Kd[q * BV] = co.K[q];
@@ -669,17 +777,19 @@ __global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cbli
   float* Ks = reinterpret_cast<float*>(hsm);  // [45][512], later [9][512] K D'
   float (*sv)[729] = reinterpret_cast<float (*)[729]>(hsm + HVP_K_BYTES);
   uint64_t* bar = reinterpret_cast<uint64_t*>(hsm + HVP_K_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  __shared__ int s_nbr[NBR];
   const int id = cblist[blockIdx.x];
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
+  if (threadIdx.x < NBR) s_nbr[threadIdx.x] = nbr[id * NBR + threadIdx.x];
   __syncthreads();
   if (threadIdx.x == 0) {
     mbar_arrive_expect_tx(bar, HVP_K_BYTES);
     tma_load_1d(Ks, K + (int64_t)id * 45 * BV, HVP_K_BYTES, bar);
   }
-  stage_nodes<float, float, float>(id, nbr, p, (const float*)nullptr, 0.0, sv);
+  stage_nodes_sn<float, float>(id, s_nbr, p, sv);
   __syncthreads();
   const bool ok = mbar_wait_bounded(bar, 0);
   if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
@@ -739,7 +849,7 @@ __global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cbli
         else if (y[a] != 0.f) atomicAdd(dst, y[a]);
       }
     } else {
-      const int t = __ldg(&nbr[id * NBR + nbr_index(nx >> 3, ny >> 3, nz >> 3)]);
+      const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
       if (t < 0) continue;
       const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
 #pragma unroll
@@ -762,6 +872,169 @@ __global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cbli
       sc->alpha = sc->rz / pq;
     }
     sc->counter[CNT_HVP] = 0;
+  }
+  prof_end(pf);
+}
+
+// FP32 HVP on the compressed tangent (27 floats per cell, single material):
+// K D' = U Mt W^T with M = U^T D' W, W = S V, and Mt the clamped eigen-modes of
+// the isotropic tangent applied to M (3x3 block in the eigenbasis Qd on the
+// diagonal of M, flip / twist modes on its off-diagonal pairs).
+constexpr unsigned HVP_C_BYTES = 27u * BV * 4u;
+constexpr size_t HVP_C_SMEM = HVP_C_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
+
+__device__ __forceinline__ void apply_compressed(const float* __restrict__ Cs, int l, const float D[9], float KD[9]) {
+  float c[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) c[q] = Cs[q * BV + l];
+  float U[9], V[9], Qd[9];
+  quat_to_rot<float>(c[0], c[1], c[2], c[3], U);
+  quat_to_rot<float>(c[4], c[5], c[6], c[7], V);
+  quat_to_rot<float>(c[8], c[9], c[10], c[11], Qd);
+  const float sm[9] = {c[12], c[15], c[16], c[15], c[13], c[17], c[16], c[17], c[14]};
+  float W[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) W[3 * a + b] = V[3 * a + b] + sm[3 * a] * V[b] + sm[3 * a + 1] * V[3 + b] + sm[3 * a + 2] * V[6 + b];
+  // M = U^T D W
+  float T1[9], M[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) T1[3 * i + b] = U[i] * D[b] + U[3 + i] * D[3 + b] + U[6 + i] * D[6 + b];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * i + j] = T1[3 * i] * W[j] + T1[3 * i + 1] * W[3 + j] + T1[3 * i + 2] * W[6 + j];
+  float Mt[9];
+  // diagonal block
+  float y[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) y[k] = c[18 + k] * (Qd[k] * M[0] + Qd[3 + k] * M[4] + Qd[6 + k] * M[8]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Mt[4 * i] = Qd[3 * i] * y[0] + Qd[3 * i + 1] * y[1] + Qd[3 * i + 2] * y[2];
+  // pairs (0,1), (0,2), (1,2): flip (M_ij + M_ji)/sqrt2, twist (M_ij - M_ji)/sqrt2
+  const int PI[3] = {0, 0, 1}, PJ[3] = {1, 2, 2};
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int i = PI[p], j = PJ[p];
+    const float f = 0.5f * c[21 + p] * (M[3 * i + j] + M[3 * j + i]);
+    const float t = 0.5f * c[24 + p] * (M[3 * i + j] - M[3 * j + i]);
+    Mt[3 * i + j] = f + t;
+    Mt[3 * j + i] = f - t;
+  }
+  // K D' = U Mt W^T
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) T1[3 * a + j] = U[3 * a] * Mt[j] + U[3 * a + 1] * Mt[3 + j] + U[3 * a + 2] * Mt[6 + j];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) KD[3 * a + b] = T1[3 * a] * W[3 * b] + T1[3 * a + 1] * W[3 * b + 1] + T1[3 * a + 2] * W[3 * b + 2];
+}
+
+__global__ void __launch_bounds__(256, 3) k_hvp_c27(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                                    const uint8_t* __restrict__ cflag, const float* __restrict__ K,
+                                                    const float* __restrict__ p, const float* __restrict__ m,
+                                                    float* q, DevScalars* sc, int finalize, DevProf* pf,
+                                                    int* status, double* part) {
+  __shared__ int s_done;
+  if (threadIdx.x == 0) s_done = finalize ? sc->done : 0;
+  __syncthreads();
+  if (s_done) return;
+  prof_begin(pf);
+  extern __shared__ __align__(128) unsigned char csm[];
+  float* Cs = reinterpret_cast<float*>(csm);  // [27][512], later [9][512] K D'
+  float (*sv)[729] = reinterpret_cast<float (*)[729]>(csm + HVP_C_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(csm + HVP_C_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  __shared__ int s_nbr[NBR];
+  const int id = cblist[blockIdx.x];
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  if (threadIdx.x < NBR) s_nbr[threadIdx.x] = nbr[id * NBR + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(bar, HVP_C_BYTES);
+    tma_load_1d(Cs, K + (int64_t)id * 27 * BV, HVP_C_BYTES, bar);
+  }
+  stage_nodes_sn<float, float>(id, s_nbr, p, sv);
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+  double pkp = 0;
+  float KD[2][9];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int l = threadIdx.x + h * 256;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) KD[h][r] = 0.f;
+    if (ok && cflag[(int64_t)id * BV + l]) {
+      float D[9];
+      gather_D<float>(l, sv, D);
+      apply_compressed(Cs, l, D, KD[h]);
+      float dkd = 0.f;
+#pragma unroll
+      for (int r = 0; r < 9; ++r) dkd += D[r] * KD[h][r];
+      pkp += (double)dkd;
+    }
+  }
+  __syncthreads();  // all reads of the tangent done: reuse the region for K D'
+  float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(Cs);
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int r = 0; r < 9; ++r) skd[r][threadIdx.x + h * 256] = KD[h][r];
+  __syncthreads();
+  for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+    const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+    float y[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int cx = nx - (o & 1), cy = ny - ((o >> 1) & 1), cz = nz - ((o >> 2) & 1);
+      if (cx < 0 || cy < 0 || cz < 0 || cx > 7 || cy > 7 || cz > 7) continue;
+      const int cc = (cz * 8 + cy) * 8 + cx;
+      const float s0 = (o & 1) ? 1.f : -1.f, s1 = (o & 2) ? 1.f : -1.f, s2 = (o & 4) ? 1.f : -1.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) y[a] += skd[3 * a][cc] * s0 + skd[3 * a + 1][cc] * s1 + skd[3 * a + 2][cc] * s2;
+    }
+    const bool own = nx < 8 && ny < 8 && nz < 8;
+    const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
+    if (own) {
+      const int l = nz * 64 + ny * 8 + nx;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        float* dst = q + (int64_t)id * 3 * BV + a * BV + l;
+        if (excl) *dst = y[a] + m[(int64_t)id * BV + l] * sv[a][i];
+        else if (y[a] != 0.f) atomicAdd(dst, y[a]);
+      }
+    } else {
+      const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+      if (t < 0) continue;
+      const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (y[a] != 0.f) atomicAdd(q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
+    }
+  }
+  double vals[1] = {pkp};
+  block_store<1>(vals, part);
+  if (finalize && arrive_last(&sc->counter[CNT_HVP])) {
+    double tot[1];
+    block_sum_parts<1>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      const double pq = sc->pMp + tot[0];
+      if (!(pq > 0.0)) {
+        sc->done = 1;
+        sc->alpha = 0;
+      } else {
+        sc->alpha = sc->rz / pq;
+      }
+      sc->counter[CNT_HVP] = 0;
+    }
   }
   prof_end(pf);
 }
@@ -1225,7 +1498,8 @@ static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg
   if (ncb > 0)
     k_prep<T><<<ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p,
                                     (const T*)c->cacc.p, (const double*)c->cs.p, (const double*)c->nvnew.p, si,
-                                    want_k, (T*)c->cK.p, (double*)c->ng.p, (T*)c->ndinv.p, dscal(c),
+                                    want_k ? (c->compressed ? 2 : 1) : 0, (T*)c->cK.p, (double*)c->ng.p,
+                                    (T*)c->ndinv.p, dscal(c),
                                     (int*)c->status.p);
   k_finalize<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (double*)c->ng.p,
                                     (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p, (T*)c->np.p, (T*)c->nq.p, init_cg,
@@ -1242,7 +1516,17 @@ constexpr size_t hvp_smem_bytes() {
 template <typename T>
 static void launch_hvp(mpml_ctx_s* c, const T* p, T* q, int finalize) {
   DevProf* pf = c->profiling ? (DevProf*)c->prof.p : nullptr;
-  if (sizeof(T) == 4) {
+  if (sizeof(T) == 4 && c->compressed) {
+    static bool attr_c = false;
+    if (!attr_c) {
+      cudaFuncSetAttribute(k_hvp_c27, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_C_SMEM);
+      attr_c = true;
+    }
+    k_hvp_c27<<<(unsigned)c->ncb, 256, HVP_C_SMEM, c->s>>>(
+        (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
+        (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
+        part_hvp(c));
+  } else if (sizeof(T) == 4) {
     static bool attr = false;
     if (!attr) {
       cudaFuncSetAttribute(k_hvp_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_TMA_SMEM);
@@ -1352,9 +1636,416 @@ static int ensure_cg_graph(mpml_ctx_s* c, int cg_max) {
   return MPML_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent Jacobi-PCG (FP32, compressed tangent): the whole CG solve in one
+// cooperative launch.  Each iteration has two phases separated by grid
+// barriers:
+//   H: for every cell brick of this CTA, stage p_new = D^-1 r + beta p_old on
+//      the 9^3 node block (the update of p fused into the halo staging; the
+//      owner writes p_new to the other p buffer), apply K (TMA-staged tangent)
+//      and scatter q; bricks holding only DOF nodes get p_new and the mass
+//      term.  Partials: p^T M p, p^T K p.
+//   A: x += alpha p_new, r -= alpha q, q = 0, partials r^T D^-1 r, r^T r.
+// Every CTA sums the per-CTA partials in the same order, so all take the same
+// decisions (alpha, beta, convergence) without another barrier.  Barrier
+// waits are bounded; a timeout sets ST_TIMEOUT and ends the solve.
+// ---------------------------------------------------------------------------
+struct PcgArgs {
+  const int* cblist;
+  const int* nolist;
+  const int* nbr;
+  const uint8_t* cflag;
+  const float* C;
+  const float* m;
+  const float* dinv;
+  float* x;
+  float* r;
+  float* pa;
+  float* pb;
+  float* q;
+  DevScalars* sc;
+  double* acc;    // [4][2] rotating accumulators of the phase sums
+  unsigned* gbar; // {arrivals, generation}
+  int ncb, nnob, nb, cg_max;
+  int* status;
+  DevProf* pf;
+};
+
+// bounded grid barrier (all CTAs co-resident: cooperative launch)
+__device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gbar + 1;
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
+      gbar[0] = 0;
+      __threadfence();
+      atomicAdd(gbar + 1, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*vgen == g) {
+        if (++spins > (1u << 25)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// block sums of 2 values added atomically to acc[0..1] (thread 0)
+__device__ __forceinline__ void block_atomic2(double a, double b, double* acc) {
+  __shared__ double red2[2][32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red2[0][wid] = a;
+    red2[1][wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += red2[0][w];
+      sb += red2[1][w];
+    }
+    atomicAdd(acc, sa);
+    atomicAdd(acc + 1, sb);
+  }
+}
+
+// every CTA: sums of the 2 partials of all CTAs (fixed order) -> s_out[2]
+__device__ __forceinline__ void sum_partials2(const double* part, double* s_out) {
+  __shared__ double red[2][32];
+  double a = 0, b = 0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+    a += __ldcg(&part[2 * k]);
+    b += __ldcg(&part[2 * k + 1]);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += red[0][w];
+      sb += red[1][w];
+    }
+    s_out[0] = sa;
+    s_out[1] = sb;
+  }
+  __syncthreads();
+}
+
+// p_new at one node slot of brick t (0 where not a free DOF)
+__device__ __forceinline__ float pnew_at(const PcgArgs& A, int64_t o, float beta, const float* pold) {
+  const float di = A.dinv[o];
+  return di > 0.f ? di * A.r[o] + beta * pold[o] : 0.f;
+}
+
+__global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
+  extern __shared__ __align__(128) unsigned char psm[];
+  float* Cs = reinterpret_cast<float*>(psm);
+  float (*sv)[729] = reinterpret_cast<float (*)[729]>(psm + HVP_C_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(psm + HVP_C_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  __shared__ int s_nbr[NBR];
+  __shared__ int s_flag;
+  __shared__ double s_sum[2];
+  DevScalars* sc = A.sc;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  unsigned tma_phase = 0;
+  double rz = sc->rz;
+  const double tol2 = sc->tol2;
+  int done = sc->done;
+  int it = 0;
+  double rr_last = sc->rr_last;
+  float beta = 0.f;
+  float* pold = A.pa;
+  float* pnext = A.pb;
+  const int G = gridDim.x;
+  bool alive = true;
+  while (!done && alive) {
+    const unsigned long long t_h0 = (A.pf && blockIdx.x == 0 && threadIdx.x == 0) ? gtimer() : 0ull;
+    // ---------------- phase H ----------------
+    double pmp = 0, pkp = 0;
+    for (int jc = blockIdx.x; jc < A.ncb; jc += G) {
+      const int id = A.cblist[jc];
+      if (threadIdx.x < NBR) s_nbr[threadIdx.x] = A.nbr[id * NBR + threadIdx.x];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        // order the previous brick's generic accesses to Cs before the async copy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, HVP_C_BYTES);
+        tma_load_1d(Cs, A.C + (int64_t)id * 27 * BV, HVP_C_BYTES, bar);
+      }
+      for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+        const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+        const int t = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+        const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+        if (t >= 0) {
+          const int64_t o = (int64_t)t * 3 * BV + l;
+          v0 = pnew_at(A, o, beta, pold);
+          v1 = pnew_at(A, o + BV, beta, pold);
+          v2 = pnew_at(A, o + 2 * BV, beta, pold);
+          if (t == id) {  // owner: store p_new and count its mass energy
+            pnext[o] = v0;
+            pnext[o + BV] = v1;
+            pnext[o + 2 * BV] = v2;
+            pmp += (double)(A.m[(int64_t)id * BV + l] * (v0 * v0 + v1 * v1 + v2 * v2));
+          }
+        }
+        sv[0][i] = v0;
+        sv[1][i] = v1;
+        sv[2][i] = v2;
+      }
+      __syncthreads();
+      const bool ok = mbar_wait_bounded(bar, tma_phase);
+      tma_phase ^= 1u;
+      if (!ok && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+      float KD[2][9];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int l = threadIdx.x + h * 256;
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr) KD[h][rr] = 0.f;
+        if (ok && A.cflag[(int64_t)id * BV + l]) {
+          float D[9];
+          gather_D<float>(l, sv, D);
+          apply_compressed(Cs, l, D, KD[h]);
+          float dkd = 0.f;
+#pragma unroll
+          for (int rr = 0; rr < 9; ++rr) dkd += D[rr] * KD[h][rr];
+          pkp += (double)dkd;
+        }
+      }
+      __syncthreads();
+      float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(Cs);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr) skd[rr][threadIdx.x + h * 256] = KD[h][rr];
+      __syncthreads();
+      for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+        const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+        float y[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          const int cx = nx - (o & 1), cy = ny - ((o >> 1) & 1), cz = nz - ((o >> 2) & 1);
+          if (cx < 0 || cy < 0 || cz < 0 || cx > 7 || cy > 7 || cz > 7) continue;
+          const int cc = (cz * 8 + cy) * 8 + cx;
+          const float s0 = (o & 1) ? 1.f : -1.f, s1 = (o & 2) ? 1.f : -1.f, s2 = (o & 4) ? 1.f : -1.f;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) y[a] += skd[3 * a][cc] * s0 + skd[3 * a + 1][cc] * s1 + skd[3 * a + 2][cc] * s2;
+        }
+        const bool own = nx < 8 && ny < 8 && nz < 8;
+        const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
+        if (own) {
+          const int l = nz * 64 + ny * 8 + nx;
+          const float mi = A.m[(int64_t)id * BV + l];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            float* dst = A.q + (int64_t)id * 3 * BV + a * BV + l;
+            const float val = y[a] + mi * sv[a][i];
+            if (excl) *dst = val;
+            else if (val != 0.f) atomicAdd(dst, val);
+          }
+        } else {
+          const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+          if (t < 0) continue;
+          const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (y[a] != 0.f) atomicAdd(A.q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
+        }
+      }
+      __syncthreads();  // Cs / sv / s_nbr are reused by the next brick
+    }
+    // bricks with DOF nodes but no cells: p_new and the mass term
+    for (int jn = blockIdx.x; jn < A.nnob; jn += G) {
+      const int id = A.nolist[jn];
+      for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+        const int64_t o = (int64_t)id * 3 * BV + l;
+        const float v0 = pnew_at(A, o, beta, pold), v1 = pnew_at(A, o + BV, beta, pold),
+                    v2 = pnew_at(A, o + 2 * BV, beta, pold);
+        pnext[o] = v0;
+        pnext[o + BV] = v1;
+        pnext[o + 2 * BV] = v2;
+        const float mi = A.m[(int64_t)id * BV + l];
+        pmp += (double)(mi * (v0 * v0 + v1 * v1 + v2 * v2));
+        if (v0 != 0.f) atomicAdd(A.q + o, mi * v0);
+        if (v1 != 0.f) atomicAdd(A.q + o + BV, mi * v1);
+        if (v2 != 0.f) atomicAdd(A.q + o + 2 * BV, mi * v2);
+      }
+    }
+    // phase sums go to slot k = (2 it) % 4; CTA 0 clears slot k + 2, last read
+    // two barriers ago and next written two barriers later
+    double* accH = A.acc + 2 * ((2 * it) & 3);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double* z = A.acc + 2 * ((2 * it + 2) & 3);
+      z[0] = 0.0;
+      z[1] = 0.0;
+    }
+    block_atomic2(pmp, pkp, accH);
+    if (!grid_barrier(A.gbar, &s_flag)) {
+      alive = false;
+      break;
+    }
+    if (threadIdx.x == 0) {
+      s_sum[0] = __ldcg(accH);
+      s_sum[1] = __ldcg(accH + 1);
+    }
+    __syncthreads();
+    const double pq = s_sum[0] + s_sum[1];
+    if (A.pf && blockIdx.x == 0 && threadIdx.x == 0) {
+      A.pf->ns += gtimer() - t_h0;
+      A.pf->count += 1;
+    }
+    if (!(pq > 0.0)) {
+      done = 1;  // breakdown
+      break;
+    }
+    const float alpha = (float)(rz / pq);
+    // ---------------- phase A ----------------
+    double rzl = 0, rrl = 0;
+    for (int jb = blockIdx.x; jb < A.nb; jb += G) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
+        const float2 d2 = *reinterpret_cast<const float2*>(A.dinv + o);
+        const float2 p2 = *reinterpret_cast<const float2*>(pnext + o);
+        const float2 q2 = *reinterpret_cast<const float2*>(A.q + o);
+        float2 x2 = *reinterpret_cast<const float2*>(A.x + o);
+        float2 r2 = *reinterpret_cast<const float2*>(A.r + o);
+        if (d2.x > 0.f) {
+          x2.x += alpha * p2.x;
+          r2.x -= alpha * q2.x;
+        }
+        if (d2.y > 0.f) {
+          x2.y += alpha * p2.y;
+          r2.y -= alpha * q2.y;
+        }
+        *reinterpret_cast<float2*>(A.x + o) = x2;
+        *reinterpret_cast<float2*>(A.r + o) = r2;
+        *reinterpret_cast<float2*>(A.q + o) = make_float2(0.f, 0.f);
+        const float srz = (d2.x > 0.f ? r2.x * d2.x * r2.x : 0.f) + (d2.y > 0.f ? r2.y * d2.y * r2.y : 0.f);
+        const float srr = (d2.x > 0.f ? r2.x * r2.x : 0.f) + (d2.y > 0.f ? r2.y * r2.y : 0.f);
+        rzl += (double)srz;
+        rrl += (double)srr;
+      }
+    }
+    double* accA = A.acc + 2 * ((2 * it + 1) & 3);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double* z = A.acc + 2 * ((2 * it + 3) & 3);
+      z[0] = 0.0;
+      z[1] = 0.0;
+    }
+    block_atomic2(rzl, rrl, accA);
+    if (!grid_barrier(A.gbar, &s_flag)) {
+      alive = false;
+      break;
+    }
+    if (threadIdx.x == 0) {
+      s_sum[0] = __ldcg(accA);
+      s_sum[1] = __ldcg(accA + 1);
+    }
+    __syncthreads();
+    const double rzn = s_sum[0], rrn = s_sum[1];
+    ++it;
+    rr_last = rrn;
+    if (rrn <= tol2 || it >= A.cg_max || !(rrn == rrn)) done = 1;
+    beta = (float)(rzn / rz);
+    rz = rzn;
+    float* tmp = pold;
+    pold = pnext;
+    pnext = tmp;
+  }
+  if (!alive && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->iters = it;
+    sc->rr_last = rr_last;
+    sc->rz = rz;
+    sc->done = 1;
+  }
+}
+
+static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
+  static int max_blocks = -1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_pcg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_C_SMEM);
+    attr = true;
+  }
+  if (max_blocks < 0) {
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, 256, HVP_C_SMEM) != cudaSuccess)
+      per_sm = 0;
+    max_blocks = per_sm * nsm;
+  }
+  if (max_blocks <= 0) return MPML_ERR_CUDA;
+  int G = max_blocks;
+  int rc;
+  // barrier words (2 unsigned) followed by the 4 x 2 rotating accumulators
+  if ((rc = ensure(c->gbar, 16 + 8 * sizeof(double))) || (rc = ensure(c->np2, sizeof(float) * 3 * c->nb * BV)))
+    return rc;
+  cudaMemsetAsync(c->gbar.p, 0, 16 + 8 * sizeof(double), c->s);
+  PcgArgs a;
+  a.cblist = (const int*)c->cblist.p;
+  a.nolist = (const int*)c->nolist.p;
+  a.nbr = (const int*)c->nbr.p;
+  a.cflag = (const uint8_t*)c->cflag.p;
+  a.C = (const float*)c->cK.p;
+  a.m = (const float*)c->nmass.p;
+  a.dinv = (const float*)c->ndinv.p;
+  a.x = (float*)c->nx.p;
+  a.r = (float*)c->nr.p;
+  a.pa = (float*)c->np.p;
+  a.pb = (float*)c->np2.p;
+  a.q = (float*)c->nq.p;
+  a.sc = dscal(c);
+  a.acc = (double*)((char*)c->gbar.p + 16);
+  a.gbar = (unsigned*)c->gbar.p;
+  a.ncb = (int)c->ncb;
+  a.nnob = (int)c->nnob;
+  a.nb = (int)c->nb;
+  a.cg_max = o->cg_max;
+  a.status = (int*)c->status.p;
+  a.pf = c->profiling ? (DevProf*)c->prof.p : nullptr;
+  // q starts at zero (the phase-A kernel zeroes it after each use)
+  cudaMemsetAsync(c->nq.p, 0, sizeof(float) * 3 * c->nb * BV, c->s);
+  void* args[] = {&a};
+  rc = cuda_status(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent, dim3(G), dim3(256), args, HVP_C_SMEM,
+                                               c->s));
+  c->launches++;
+  return rc;
+}
+
 template <typename T>
 static int pcg_t(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, double* rel) {
   int rc;
+  if (sizeof(T) == 4 && c->compressed && o->use_graph == 2) {
+    if ((rc = pcg_persistent(c, o))) return rc;
+    if ((rc = read_scalars(c))) return rc;
+  } else
   if (o->use_graph && c->ncb > 0 && ensure_cg_graph<T>(c, o->cg_max) == MPML_OK) {
     if ((rc = cuda_status(cudaGraphLaunch(c->cg_exec, c->s)))) return rc;
     if ((rc = read_scalars(c))) return rc;

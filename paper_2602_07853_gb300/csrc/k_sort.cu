@@ -95,10 +95,10 @@ __global__ void k_bin_mark(int64_t np, const T* __restrict__ x, GridInfo g, uint
 
 // Single-block ordered compaction of the dense brick flags.
 __global__ void k_compact_bricks(int64_t NBT, const uint8_t* bflag_c, const uint8_t* bflag_n, int* bmap,
-                                 int* blist, int* cblist, int* counts) {
-  __shared__ int warp_tot[2][32];
-  __shared__ int carry[2];
-  if (threadIdx.x == 0) carry[0] = carry[1] = 0;
+                                 int* blist, int* cblist, int* nolist, int* counts) {
+  __shared__ int warp_tot[3][32];
+  __shared__ int carry[3];
+  if (threadIdx.x == 0) carry[0] = carry[1] = carry[2] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t base = 0; base < NBT; base += blockDim.x) {
@@ -108,17 +108,22 @@ __global__ void k_compact_bricks(int64_t NBT, const uint8_t* bflag_c, const uint
       fc = bflag_c[i] ? 1 : 0;
       fa = (fc || bflag_n[i]) ? 1 : 0;
     }
-    unsigned ma = __ballot_sync(0xffffffffu, fa), mc = __ballot_sync(0xffffffffu, fc);
-    int pa = __popc(ma & ((1u << lane) - 1)), pc = __popc(mc & ((1u << lane) - 1));
+    const int fo = fa && !fc;  // bricks holding DOF nodes but no active cell
+    unsigned ma = __ballot_sync(0xffffffffu, fa), mc = __ballot_sync(0xffffffffu, fc),
+             mo = __ballot_sync(0xffffffffu, fo);
+    int pa = __popc(ma & ((1u << lane) - 1)), pc = __popc(mc & ((1u << lane) - 1)),
+        po = __popc(mo & ((1u << lane) - 1));
     if (lane == 0) {
       warp_tot[0][wid] = __popc(ma);
       warp_tot[1][wid] = __popc(mc);
+      warp_tot[2][wid] = __popc(mo);
     }
     __syncthreads();
-    int offa = carry[0], offc = carry[1];
+    int offa = carry[0], offc = carry[1], offo = carry[2];
     for (int w = 0; w < wid; ++w) {
       offa += warp_tot[0][w];
       offc += warp_tot[1][w];
+      offo += warp_tot[2][w];
     }
     if (i < NBT) {
       if (fa) {
@@ -126,6 +131,7 @@ __global__ void k_compact_bricks(int64_t NBT, const uint8_t* bflag_c, const uint
         bmap[i] = id;
         blist[id] = (int)i;
         if (fc) cblist[offc + pc] = id;
+        if (fo) nolist[offo + po] = id;
       } else {
         bmap[i] = -1;
       }
@@ -135,6 +141,7 @@ __global__ void k_compact_bricks(int64_t NBT, const uint8_t* bflag_c, const uint
       for (int w = 0; w < nw; ++w) {
         carry[0] += warp_tot[0][w];
         carry[1] += warp_tot[1][w];
+        carry[2] += warp_tot[2][w];
       }
     }
     __syncthreads();
@@ -142,6 +149,7 @@ __global__ void k_compact_bricks(int64_t NBT, const uint8_t* bflag_c, const uint
   if (threadIdx.x == 0) {
     counts[0] = carry[0];
     counts[1] = carry[1];
+    counts[2] = carry[2];
   }
 }
 
@@ -401,7 +409,7 @@ static int resample_t(mpml_ctx_s* c, const void* x_, const void* v_, const void*
   // brick flags
   if ((rc = ensure(c->bflag_c, c->NBT)) || (rc = ensure(c->bflag_n, c->NBT)) ||
       (rc = ensure(c->bmap, sizeof(int) * c->NBT)) || (rc = ensure(c->blist, sizeof(int) * c->NBT)) ||
-      (rc = ensure(c->cblist, sizeof(int) * c->NBT)))
+      (rc = ensure(c->cblist, sizeof(int) * c->NBT)) || (rc = ensure(c->nolist, sizeof(int) * c->NBT)))
     return rc;
   cudaMemsetAsync(c->bflag_c.p, 0, c->NBT, s);
   cudaMemsetAsync(c->bflag_n.p, 0, c->NBT, s);
@@ -410,8 +418,8 @@ static int resample_t(mpml_ctx_s* c, const void* x_, const void* v_, const void*
     c->launches++;
   }
   k_compact_bricks<<<1, 1024, 0, s>>>(c->NBT, (const uint8_t*)c->bflag_c.p, (const uint8_t*)c->bflag_n.p,
-                                      (int*)c->bmap.p, (int*)c->blist.p, (int*)c->cblist.p,
-                                      (int*)&((DevScalars*)c->scal.p)->counter[6]);
+                                      (int*)c->bmap.p, (int*)c->blist.p, (int*)c->cblist.p, (int*)c->nolist.p,
+                                      (int*)&((DevScalars*)c->scal.p)->counter[5]);
   c->launches++;
   // counts (and the status word) to the host: one synchronisation per resample
   cudaMemcpyAsync(c->hscal, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, s);
@@ -419,8 +427,9 @@ static int resample_t(mpml_ctx_s* c, const void* x_, const void* v_, const void*
   if ((rc = cuda_status(cudaStreamSynchronize(s)))) return rc;
   if (*c->hstatus & ST_NONFINITE) return MPML_ERR_NONFINITE;
   if (*c->hstatus & ST_OUT_OF_DOMAIN) return MPML_ERR_OUT_OF_DOMAIN;
-  c->nb = c->hscal->counter[6];
-  c->ncb = c->hscal->counter[7];
+  c->nb = c->hscal->counter[5];
+  c->ncb = c->hscal->counter[6];
+  c->nnob = c->hscal->counter[7];
   const int64_t nb = c->nb, nslots = nb * BV;
   // neighbour table
   if ((rc = ensure(c->nbr, sizeof(int) * NBR * (nb ? nb : 1)))) return rc;

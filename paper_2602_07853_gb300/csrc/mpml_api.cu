@@ -245,6 +245,7 @@ int mpml_create(const mpml_scene_desc* desc, const mpml_material* mats, int n_ma
   c->s = (cudaStream_t)stream;
   c->fp64 = desc->precision == MPML_FP64;
   c->esz = c->fp64 ? 8 : 4;
+  c->compressed = (!c->fp64 && n_mats == 1) ? 1 : 0;
   for (int a = 0; a < 3; ++a) c->NB[a] = (desc->n[a] >> 3) + 1;
   c->NBT = (int64_t)c->NB[0] * c->NB[1] * c->NB[2];
   cudaGetDevice(&c->device);
@@ -278,7 +279,7 @@ int mpml_destroy(mpml_ctx c) {
                  &c->pG, &c->pm, &c->pV, &c->pmat, &c->pperm, &c->pkey, &c->prank, &c->pbase, &c->ux, &c->uv,
                  &c->uF, &c->uG, &c->um, &c->uV, &c->umat, &c->cnt, &c->start, &c->scan_tmp, &c->cflag,
                  &c->cacc, &c->cs, &c->cK, &c->cnew, &c->nflag, &c->nmass, &c->nv, &c->nvhat, &c->nvfix,
-                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->scal, &c->status, &c->prof, &c->part};
+                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->nolist};
   for (Buf* b : bufs) free_buf(*b);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hstatus) cudaFreeHost(c->hstatus);
@@ -370,7 +371,7 @@ int mpml_stretch(mpml_ctx c) {
 
 int mpml_newton_step(mpml_ctx c, const mpml_solver_opts* o, mpml_solve_stats* st) {
   if (!c || c->stage < 1) return MPML_ERR_ARG;
-  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 1};
+  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 2};
   if (!o) o = &def;
   mpml_solve_stats local;
   if (!st) st = &local;
@@ -523,7 +524,8 @@ int mpml_hvp_timing(mpml_ctx c, int64_t* launches, double* total_ms, double* byt
   if (bytes_per_launch) {
     // per cell brick: K (45/cell) read, p (3/node) read, m read, q (3/node) written
     const double e = (double)c->esz;
-    *bytes_per_launch = (double)c->ncb * BV * (45 * e + 3 * e + e + 3 * e);
+    const double kf = c->compressed ? 27.0 : 45.0;  // tangent numbers per cell
+    *bytes_per_launch = (double)c->ncb * BV * (kf * e + 3 * e + e + 3 * e);
   }
   return MPML_OK;
 }

@@ -108,6 +108,7 @@ struct mpml_ctx_s {
   int nm = 1;
   cudaStream_t s = nullptr;
   int fp64 = 0;
+  int compressed = 0;  // FP32, single material: HVP on the 27-number tangent
   size_t esz = 4;
   int NB[3] = {0, 0, 0};
   int64_t NBT = 0;
@@ -115,7 +116,7 @@ struct mpml_ctx_s {
   int device = 0;
 
   // brick bookkeeping
-  mpml::Buf bflag_c, bflag_n, bmap, blist, cblist, nbr;
+  mpml::Buf bflag_c, bflag_n, bmap, blist, cblist, nolist, nbr;
   // particles (sorted library copies and temporaries)
   mpml::Buf px, pv, pF, pG, pm, pV, pmat, pperm, pkey, prank, pbase;
   // staging of unsorted input (host mode)
@@ -125,13 +126,13 @@ struct mpml_ctx_s {
   // cells
   mpml::Buf cflag, cacc, cs, cK, cnew;
   // nodes
-  mpml::Buf nflag, nmass, nv, nvhat, nvfix, nvnew, ng, ndinv, nx, nr, np, nq;
+  mpml::Buf nflag, nmass, nv, nvhat, nvfix, nvnew, ng, ndinv, nx, nr, np, np2, nq;
   // scalars and status
-  mpml::Buf scal, status, prof, part;
+  mpml::Buf scal, status, prof, part, gbar;
   mpml::DevScalars* hscal = nullptr;  // pinned mirror
   int* hstatus = nullptr;             // pinned
 
-  int64_t np_count = 0, nb = 0, ncb = 0;
+  int64_t np_count = 0, nb = 0, ncb = 0, nnob = 0;  // bricks: all, with cells, node-only
   int stage = 0;  // 0 nothing, 1 unloaded, 2 stretched, 3 solved, 4 loaded
   int have_lin = 0;
 

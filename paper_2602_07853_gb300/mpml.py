@@ -272,7 +272,7 @@ def material(model, mu, lam):
 
 
 def solver_opts(cg_rtol=1e-6, cg_max=10000, newton_rtol=1e-6, newton_atol=0.0, newton_max=50, ls_c1=1e-4,
-                ls_max=30, precond=PRECOND_JACOBI, check_every=16, use_graph=1):
+                ls_max=30, precond=PRECOND_JACOBI, check_every=16, use_graph=2):
     o = mpml_solver_opts()
     o.cg_rtol, o.cg_max, o.newton_rtol, o.newton_atol, o.newton_max = cg_rtol, cg_max, newton_rtol, newton_atol, newton_max
     o.ls_c1, o.ls_max, o.precond, o.check_every, o.use_graph = ls_c1, ls_max, precond, check_every, use_graph
