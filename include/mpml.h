@@ -136,6 +136,7 @@ typedef struct {
   double g0_norm, g_norm;    /* ||g(v0)||, ||g|| at exit (FP64 sums) */
   double phi0, phi;          /* incremental potential at v0 and at exit */
   int64_t n_particles, n_cells, n_nodes, n_bricks;
+  int fcg_fallbacks;         /* learned solves that continued with Jacobi-PCG */
 } mpml_solve_stats;
 
 /* Lifecycle ----------------------------------------------------------- */
@@ -215,6 +216,48 @@ int mpml_hvp_timing(mpml_ctx ctx, int64_t* launches, double* total_ms, double* b
 int mpml_hvp_bench(mpml_ctx ctx, int iters, double* mean_ms);
 /* Number of kernel launches issued on the context stream since creation. */
 int64_t mpml_kernel_launches(mpml_ctx ctx);
+
+/* Learned preconditioner ------------------------------------------------
+ * Not in the paper: the workload asks for a small 3D convolutional network
+ * on the node grid used inside flexible CG.  Network: three bias-free
+ * 3x3x3 convolutions 3 -> 16 -> 16 -> 3 channels, ReLU after the first two,
+ * outputs kept on DOF nodes (free DOFs for the last layer); BF16 weights and
+ * activations with FP32 accumulation on the tensor cores.  Preconditioner:
+ *   z = D^-1 r + s D^-1/2 NN(D^-1/2 r / s),  s = RMS of D^-1/2 r,
+ * D the Jacobi diagonal.  With opts->precond = MPML_PRECOND_LEARNED (FP32,
+ * single-material contexts, weights set) mpml_newton_step runs flexible CG;
+ * when it stalls (z^T r <= 0, or no decrease of ||r|| in 20 iterations) the
+ * solve continues with Jacobi-PCG from the current iterate.
+ * Weights use the layout per layer (27 taps, C_out, C_in), tap
+ * (dz+1)*9 + (dy+1)*3 + (dx+1), layers concatenated (9504 floats). */
+typedef struct {
+  int samples;   /* (residual, error) pairs taken from one Jacobi-PCG solve */
+  double rtol;   /* tolerance of that solve (the pairs' reference solution) */
+  int cg_max;
+  int epochs;
+  int batch;     /* pairs per Adam step */
+  float lr;
+} mpml_train_opts;
+typedef struct {
+  int samples;
+  double loss_first;  /* mean H-norm loss of the first epoch */
+  double loss_last;   /* ... of the last epoch */
+} mpml_train_stats;
+int mpml_nn_weight_count(void);
+int mpml_nn_set_weights(mpml_ctx ctx, const float* w);
+int mpml_nn_get_weights(mpml_ctx ctx, float* w);
+/* Accumulated weight gradient (same layout), as left by mpml_nn_loss_grad. */
+int mpml_nn_get_grad(mpml_ctx ctx, float* g);
+/* z = preconditioner(r) on the current linearisation (DOF order, n*3). */
+int mpml_nn_apply(mpml_ctx ctx, const double* r, double* z);
+/* Loss L = (z(r) - e)^T H (z(r) - e) / (e^T H e) of one pair and its weight
+ * gradient (written to the gradient accumulator, which is zeroed first). */
+int mpml_nn_loss_grad(mpml_ctx ctx, const double* r, const double* e, double* loss);
+/* Trains on the current Newton system (after mpml_resample): reconstructs the
+ * stretches, solves the first Newton system with Jacobi-PCG, takes
+ * `samples` pairs (r_k, x* - x_k) along the way and runs Adam on the H-norm
+ * loss.  Weights must be set (e.g. a seeded initialisation). */
+int mpml_nn_train(mpml_ctx ctx, const mpml_train_opts* opts, mpml_train_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -120,6 +120,9 @@ __device__ __forceinline__ double vload(const double* p) { return *(volatile con
 
 enum { CNT_FIN = 0, CNT_HVP = 1, CNT_A = 2, CNT_B = 3, CNT_MISC = 4 };
 
+template <typename T>
+__global__ void k_init_faces(const T* __restrict__ p, const T* __restrict__ m, T* q);
+
 // ---------------------------------------------------------------------------
 // stretch reconstruction (FP64)
 // ---------------------------------------------------------------------------
@@ -652,6 +655,7 @@ __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nf
   const bool free_ = (f & NF_DOF) && !(f & NF_FIXED);
   const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
   double gg = 0, rz = 0, rr = 0, pmp = 0;
+  const double nfr = free_ ? 3.0 : 0.0;
   const T mi = free_ ? m[slot] : T(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -672,16 +676,18 @@ __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nf
       pmp += (double)mi * (double)zv * (double)zv;
     }
   }
-  double vals[4] = {gg, rz, rr, pmp};
-  block_store<4>(vals, part);
+  double vals[5] = {gg, rz, rr, pmp, nfr};
+  block_store<5>(vals, part);
   if (arrive_last(&sc->counter[CNT_FIN])) {
-    double tot[4];
-    block_sum_parts<4>(part, gridDim.x, tot);
+    double tot[5];
+    block_sum_parts<5>(part, gridDim.x, tot);
     if (threadIdx.x != 0) return;
     sc->gg = tot[0];
     sc->rz = tot[1];
+    sc->rzj = tot[1];
     sc->rr0 = tot[2];
     sc->pMp = tot[3];
+    sc->nfree = tot[4];
     double rr0 = tot[2];
     sc->tol2 = rtol2 * rr0;
     sc->done = (rr0 == 0.0) ? 1 : 0;
@@ -871,6 +877,7 @@ __global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cbli
     } else {
       sc->alpha = sc->rz / pq;
     }
+    sc->pq = pq;
     sc->counter[CNT_HVP] = 0;
   }
   prof_end(pf);
@@ -1033,6 +1040,7 @@ __global__ void __launch_bounds__(256, 3) k_hvp_c27(const int* __restrict__ cbli
       } else {
         sc->alpha = sc->rz / pq;
       }
+      sc->pq = pq;
       sc->counter[CNT_HVP] = 0;
     }
   }
@@ -1137,6 +1145,7 @@ __global__ void __launch_bounds__(256) k_hvp(const int* __restrict__ cblist, con
     } else {
       sc->alpha = sc->rz / pq;
     }
+    sc->pq = pq;
     sc->counter[CNT_HVP] = 0;
   }
   prof_end(pf);
@@ -1193,7 +1202,7 @@ __global__ void __launch_bounds__(512) k_cg_a(const T* __restrict__ dinv, const 
 // threads and blocks in FP64 (FP64 arithmetic is scarce on this GPU).
 __global__ void __launch_bounds__(128) k_cg_a4(const float* __restrict__ dinv, const float* __restrict__ p,
                                                const float* __restrict__ q, float* x, float* r, DevScalars* sc,
-                                               double* part) {
+                                               double* part, int fcg) {
   __shared__ int s_done;
   __shared__ float s_alpha;
   if (threadIdx.x == 0) {
@@ -1239,8 +1248,20 @@ __global__ void __launch_bounds__(128) k_cg_a4(const float* __restrict__ dinv, c
     sc->iters = it;
     sc->rr_last = rrv;
     if (rrv <= sc->tol2 || it >= sc->cg_max || !(rrv == rrv)) sc->done = 1;
-    sc->beta = rzn / sc->rz;
-    sc->rz = rzn;
+    if (fcg) {
+      // flexible CG: beta and r^T z come later (after the network); here the
+      // network input scale and the stall test (no progress in 20 iterations)
+      sc->rzj = rzn;
+      sc->nn_s = sc->nfree > 0 ? sqrt(rzn / sc->nfree) : 0.0;
+      if (it > 20 && rrv >= sc->rr_ring[(it - 20) & 31]) {
+        sc->fallback = 1;
+        sc->done = 1;
+      }
+      sc->rr_ring[it & 31] = rrv;
+    } else {
+      sc->beta = rzn / sc->rz;
+      sc->rz = rzn;
+    }
     sc->counter[CNT_A] = 0;
   }
 }
@@ -1453,7 +1474,7 @@ static int alloc_solver(mpml_ctx_s* c) {
   if ((rc = ensure(c->cs, sizeof(double) * 6 * c->nm * ns)) || (rc = ensure(c->cK, es * 45 * ns)) ||
       (rc = ensure(c->ng, sizeof(double) * 3 * ns)) || (rc = ensure(c->ndinv, es * 3 * ns)) || (rc = ensure(c->nx, es * 3 * ns)) ||
       (rc = ensure(c->nr, es * 3 * ns)) || (rc = ensure(c->np, es * 3 * ns)) || (rc = ensure(c->nq, es * 3 * ns)) ||
-      (rc = ensure(c->part, sizeof(double) * 8 * (c->nb ? c->nb : 1))))
+      (rc = ensure(c->part, sizeof(double) * 10 * (c->nb ? c->nb : 1))))
     return rc;
   return MPML_OK;
 }
@@ -1476,9 +1497,9 @@ int stretch_all(mpml_ctx_s* c) { return c->fp64 ? stretch_t<double>(c) : stretch
 static DevScalars* dscal(mpml_ctx_s* c) { return (DevScalars*)c->scal.p; }
 // per-block partial sums of the reductions (8 doubles per brick)
 static double* part_fin(mpml_ctx_s* c) { return (double*)c->part.p; }
-static double* part_hvp(mpml_ctx_s* c) { return (double*)c->part.p + 4 * c->nb; }
-static double* part_a(mpml_ctx_s* c) { return (double*)c->part.p + 5 * c->nb; }
-static double* part_b(mpml_ctx_s* c) { return (double*)c->part.p + 7 * c->nb; }
+static double* part_hvp(mpml_ctx_s* c) { return (double*)c->part.p + 5 * c->nb; }
+static double* part_a(mpml_ctx_s* c) { return (double*)c->part.p + 6 * c->nb; }
+static double* part_b(mpml_ctx_s* c) { return (double*)c->part.p + 8 * c->nb; }
 
 static int read_scalars(mpml_ctx_s* c) {
   cudaMemcpyAsync(c->hscal, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s);
@@ -1556,7 +1577,7 @@ static void cg_iteration(mpml_ctx_s* c) {
   launch_hvp<T>(c, (const T*)c->np.p, (T*)c->nq.p, 1);
   if (sizeof(T) == 4) {
     k_cg_a4<<<nb, 128, 0, c->s>>>((const float*)c->ndinv.p, (const float*)c->np.p, (const float*)c->nq.p,
-                                  (float*)c->nx.p, (float*)c->nr.p, dscal(c), part_a(c));
+                                  (float*)c->nx.p, (float*)c->nr.p, dscal(c), part_a(c), 0);
     k_cg_b4<<<nb, 128, 0, c->s>>>((const float*)c->ndinv.p, (const float*)c->nmass.p, (const float*)c->nr.p,
                                   (float*)c->np.p, (float*)c->nq.p, dscal(c), part_b(c));
   } else {
@@ -2039,9 +2060,374 @@ static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
   return rc;
 }
 
+// ---------------------------------------------------------------------------
+// Flexible CG with the learned preconditioner (FP32 contexts).  Notay's FCG
+// with one stored direction: alpha = r^T z / p^T H p, beta = -z^T H p / p^T H p
+// (equal to the Polak-Ribiere form).  Stall rule: z^T r <= 0, or no decrease
+// of r^T r in 20 iterations -> the solve continues with Jacobi-PCG.
+// ---------------------------------------------------------------------------
+// sums of the per-brick (z^T q, z^T r) partials (one block, fixed order)
+__global__ void __launch_bounds__(512) k_fcg_beta(const double* __restrict__ part, int nb, DevScalars* sc,
+                                                  int init) {
+  __shared__ double red[2][16];
+  double a = 0, b = 0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    a += part[2 * i];
+    b += part[2 * i + 1];
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double zq = 0, zr = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    zq += red[0][w];
+    zr += red[1][w];
+  }
+  if (sc->done) return;
+  if (!(zr > 0.0)) {  // not a descent direction: fall back to Jacobi
+    sc->fallback = 1;
+    sc->done = 1;
+    return;
+  }
+  sc->beta = init ? 0.0 : -zq / sc->pq;
+  sc->rz = zr;
+}
+
+// p = z + beta p, q(face) = m p, sum m |p|^2
+__global__ void __launch_bounds__(512) k_fcg_p(const float* __restrict__ z, const float* __restrict__ m, float* p,
+                                               float* q, DevScalars* sc, double* part) {
+  __shared__ int s_done;
+  __shared__ float s_beta;
+  if (threadIdx.x == 0) {
+    s_done = sc->done;
+    s_beta = (float)sc->beta;
+  }
+  __syncthreads();
+  if (s_done) return;
+  const int id = blockIdx.x, l = threadIdx.x;
+  const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
+  const float mi = m[(int64_t)id * BV + l];
+  float pmp = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = ((int64_t)id * 3 + a) * BV + l;
+    const float pv = z[o] + s_beta * p[o];
+    p[o] = pv;
+    if (face) q[o] = mi * pv;
+    pmp += mi * pv * pv;
+  }
+  double vals[1] = {(double)pmp};
+  block_store<1>(vals, part);
+  if (arrive_last(&sc->counter[CNT_B])) {
+    double tot[1];
+    block_sum_parts<1>(part, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    sc->pMp = tot[0];
+    sc->counter[CNT_B] = 0;
+  }
+}
+
+// r^T D^-1 r of the current residual; restart values for Jacobi-PCG
+__global__ void __launch_bounds__(512) k_rz_jacobi(const float* __restrict__ r, const float* __restrict__ dinv,
+                                                   DevScalars* sc, double* part, int restart) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  float s = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = ((int64_t)id * 3 + a) * BV + l;
+    const float di = dinv[o];
+    if (di > 0.f) s += r[o] * di * r[o];
+  }
+  double vals[1] = {(double)s};
+  block_store<1>(vals, part);
+  if (arrive_last(&sc->counter[CNT_MISC])) {
+    double tot[1];
+    block_sum_parts<1>(part, gridDim.x, tot);
+    if (threadIdx.x != 0) return;
+    sc->rzj = tot[0];
+    sc->nn_s = sc->nfree > 0 ? sqrt(tot[0] / sc->nfree) : 0.0;
+    if (restart) {
+      sc->rz = tot[0];
+      sc->done = 0;
+      sc->fallback = 0;
+      sc->iters = 0;
+    }
+    sc->counter[CNT_MISC] = 0;
+  }
+}
+
+static void fcg_iteration(mpml_ctx_s* c) {
+  const unsigned nb = (unsigned)c->nb;
+  DevScalars* d = dscal(c);
+  launch_hvp<float>(c, (const float*)c->np.p, (float*)c->nq.p, 1);
+  k_cg_a4<<<nb, 128, 0, c->s>>>((const float*)c->ndinv.p, (const float*)c->np.p, (const float*)c->nq.p,
+                                (float*)c->nx.p, (float*)c->nr.p, d, part_a(c), 1);
+  nn_apply(c, &d->nn_s, (const float*)c->nq.p, part_fin(c));
+  k_fcg_beta<<<1, 512, 0, c->s>>>(part_fin(c), (int)c->nb, d, 0);
+  k_fcg_p<<<nb, BV, 0, c->s>>>((const float*)c->nz.p, (const float*)c->nmass.p, (float*)c->np.p, (float*)c->nq.p, d,
+                               part_b(c));
+  c->launches += 4;
+}
+
+// flexible CG from the state left by prep (x = 0, r = -g, Jacobi scalars);
+// returns iterations and whether it fell back
+static int fcg_solve(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, int* fell_back) {
+  int rc;
+  DevScalars* d = dscal(c);
+  if ((rc = nn_ensure(c))) return rc;
+  const unsigned nb = (unsigned)c->nb;
+  // z0 = B(r0), rz = z0^T r0, p0 = z0
+  k_rz_jacobi<<<nb, BV, 0, c->s>>>((const float*)c->nr.p, (const float*)c->ndinv.p, d, part_b(c), 0);
+  nn_apply(c, &d->nn_s, nullptr, part_fin(c));
+  k_fcg_beta<<<1, 512, 0, c->s>>>(part_fin(c), (int)c->nb, d, 1);
+  k_fcg_p<<<nb, BV, 0, c->s>>>((const float*)c->nz.p, (const float*)c->nmass.p, (float*)c->np.p, (float*)c->nq.p, d,
+                               part_b(c));
+  c->launches += 3;
+  if ((rc = read_scalars(c))) return rc;
+  const int every = o->check_every > 0 ? o->check_every : 8;
+  int launched = 0;
+  while (!c->hscal->done && launched < o->cg_max) {
+    for (int j = 0; j < every && launched < o->cg_max; ++j, ++launched) fcg_iteration(c);
+    if ((rc = cuda_status(cudaGetLastError()))) return rc;
+    if ((rc = read_scalars(c))) return rc;
+  }
+  *iters = c->hscal->iters;
+  *fell_back = c->hscal->fallback;
+  return MPML_OK;
+}
+
+// ---------------------------------------------------------------------------
+// training data and training (learned preconditioner)
+// ---------------------------------------------------------------------------
+// FP64 sum of a . b over free slots (atomic; training path only)
+__global__ void __launch_bounds__(512) k_dot_ff(const float* __restrict__ a, const float* __restrict__ b,
+                                                const float* __restrict__ dinv, double* out) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int64_t o = ((int64_t)id * 3 + c) * BV + l;
+    if (dinv[o] > 0.f) s += a[o] * b[o];
+  }
+  double vals[1] = {(double)s};
+  double* const dst[1] = {out};
+  block_add<1>(vals, dst);
+}
+
+// y = a - b (free slots)
+__global__ void k_sub(const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ dinv,
+                      float* y, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = dinv[i] > 0.f ? a[i] - b[i] : 0.f;
+}
+
+// loss gradient w.r.t. the network output: gy = 2 s sqrt(D^-1) H d / den
+__global__ void k_nn_gy(const float* __restrict__ hd, const float* __restrict__ dinv, const double* s_ptr,
+                        double den, float* gy, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float di = dinv[i];
+  gy[i] = di > 0.f ? (float)(2.0 * *s_ptr / den) * sqrtf(di) * hd[i] : 0.f;
+}
+
+// FP32 HVP y = H p on the current linearisation (q faces initialised to m p)
+static void hvp_f32(mpml_ctx_s* c, const float* p, float* y) {
+  const int64_t ns = c->nb * BV;
+  cudaMemsetAsync(y, 0, sizeof(float) * 3 * ns, c->s);
+  k_init_faces<float><<<(unsigned)c->nb, BV, 0, c->s>>>(p, (const float*)c->nmass.p, y);
+  if (c->ncb > 0) launch_hvp<float>(c, p, y, 0);
+  c->launches++;
+}
+
+// one training pair (r in c->nr, e given): loss, and the weight gradient
+// accumulated (scaled) on the device
+static int nn_pair(mpml_ctx_s* c, const float* e, double den, float scale, double* loss_out, bool backward) {
+  DevScalars* d = dscal(c);
+  const int64_t ns = c->nb * BV, n3 = 3 * ns;
+  const unsigned nb = (unsigned)c->nb;
+  k_rz_jacobi<<<nb, BV, 0, c->s>>>((const float*)c->nr.p, (const float*)c->ndinv.p, d, part_b(c), 0);
+  nn_apply(c, &d->nn_s, nullptr, nullptr);
+  float* z = (float*)c->nz.p;
+  float* hd = (float*)c->nnhd.p;
+  k_sub<<<div_up(n3, 256), 256, 0, c->s>>>(z, e, (const float*)c->ndinv.p, z, n3);
+  hvp_f32(c, z, hd);
+  double* acc = &d->slope;
+  cudaMemsetAsync(acc, 0, sizeof(double), c->s);
+  k_dot_ff<<<nb, BV, 0, c->s>>>(z, hd, (const float*)c->ndinv.p, acc);
+  c->launches += 4;
+  if (backward) {
+    // reuse z's buffer for gy (d = z - e is no longer needed)
+    k_nn_gy<<<div_up(n3, 256), 256, 0, c->s>>>(hd, (const float*)c->ndinv.p, &d->nn_s, den, z, n3);
+    nn_backward(c, z, scale);
+    c->launches++;
+  }
+  if (loss_out) {
+    int rc = read_scalars(c);
+    if (rc) return rc;
+    *loss_out = c->hscal->slope / den;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+int nn_collect(mpml_ctx_s* c, int nsamples, double rtol, int cg_max) {
+  // the current Newton system: stretch + prep at vhat (Dirichlet values set)
+  int rc;
+  if (c->fp64 || !c->compressed) return MPML_ERR_ARG;
+  if ((rc = stretch_all(c)) || (rc = alloc_solver<float>(c)) || (rc = nn_ensure(c))) return rc;
+  const int64_t ns = c->nb * BV, n3 = 3 * ns;
+  if (nsamples < 1) nsamples = 1;
+  if ((rc = ensure(c->nns_r, sizeof(float) * n3 * nsamples)) || (rc = ensure(c->nns_e, sizeof(float) * n3 * nsamples)) ||
+      (rc = ensure(c->nnhd, sizeof(float) * n3)))
+    return rc;
+  // first pass: iteration count of the solve
+  if ((rc = prep_t<float>(c, 1, 1, rtol, cg_max)) || (rc = read_scalars(c))) return rc;
+  int total = 0;
+  while (!c->hscal->done && total < cg_max) {
+    for (int j = 0; j < 16 && total < cg_max; ++j, ++total) cg_iteration<float>(c);
+    if ((rc = read_scalars(c))) return rc;
+  }
+  total = c->hscal->iters;
+  // second pass with snapshots of (r_k, x_k) at k_j = j total / nsamples
+  if ((rc = prep_t<float>(c, 1, 1, rtol, cg_max)) || (rc = read_scalars(c))) return rc;
+  float* R = (float*)c->nns_r.p;
+  float* E = (float*)c->nns_e.p;
+  int it = 0;
+  for (int j = 0; j < nsamples; ++j) {
+    const int target = (int)((int64_t)j * total / nsamples);
+    while (it < target) {
+      cg_iteration<float>(c);
+      ++it;
+    }
+    cudaMemcpyAsync(R + (int64_t)j * n3, c->nr.p, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(E + (int64_t)j * n3, c->nx.p, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
+  }
+  if ((rc = read_scalars(c))) return rc;
+  while (!c->hscal->done && it < cg_max) {
+    for (int j = 0; j < 16 && it < cg_max; ++j, ++it) cg_iteration<float>(c);
+    if ((rc = read_scalars(c))) return rc;
+  }
+  // e_j = x* - x_{k_j}
+  for (int j = 0; j < nsamples; ++j)
+    k_sub<<<div_up(n3, 256), 256, 0, c->s>>>((const float*)c->nx.p, E + (int64_t)j * n3, (const float*)c->ndinv.p,
+                                             E + (int64_t)j * n3, n3);
+  c->nn_nsamples = nsamples;
+  return cuda_status(cudaStreamSynchronize(c->s));
+}
+
+int nn_train(mpml_ctx_s* c, int epochs, int batch, float lr, double* loss_first, double* loss_last) {
+  int rc;
+  if (!c->nn_ready || c->nn_nsamples < 1) return MPML_ERR_ARG;
+  const int ns_ = c->nn_nsamples;
+  const int64_t n3 = 3 * c->nb * BV;
+  float* R = (float*)c->nns_r.p;
+  float* E = (float*)c->nns_e.p;
+  // e^T H e of every pair
+  std::vector<double> den(ns_);
+  for (int j = 0; j < ns_; ++j) {
+    float* e = E + (int64_t)j * n3;
+    hvp_f32(c, e, (float*)c->nnhd.p);
+    DevScalars* d = dscal(c);
+    cudaMemsetAsync(&d->slope, 0, sizeof(double), c->s);
+    k_dot_ff<<<(unsigned)c->nb, BV, 0, c->s>>>(e, (const float*)c->nnhd.p, (const float*)c->ndinv.p, &d->slope);
+    if ((rc = read_scalars(c))) return rc;
+    den[j] = c->hscal->slope > 0 ? c->hscal->slope : 1.0;
+  }
+  if (batch < 1) batch = 1;
+  uint64_t rng = 0x9e3779b97f4a7c15ull;
+  std::vector<int> order(ns_);
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int j = 0; j < ns_; ++j) order[j] = j;
+    for (int j = ns_ - 1; j > 0; --j) {  // Fisher-Yates with a fixed LCG
+      rng = rng * 6364136223846793005ull + 1442695040888963407ull;
+      const int k = (int)((rng >> 33) % (uint64_t)(j + 1));
+      std::swap(order[j], order[k]);
+    }
+    double lsum = 0;
+    int inb = 0;
+    for (int jj = 0; jj < ns_; ++jj) {
+      const int j = order[jj];
+      cudaMemcpyAsync(c->nr.p, R + (int64_t)j * n3, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
+      double l = 0;
+      if ((rc = nn_pair(c, E + (int64_t)j * n3, den[j], 1.0f / (float)batch, &l, true))) return rc;
+      lsum += l;
+      if (++inb == batch || jj == ns_ - 1) {
+        nn_adam(c, lr, ++c->nn_adam_step);
+        if ((rc = nn_refresh_weights(c))) return rc;
+        inb = 0;
+      }
+    }
+    if (ep == 0 && loss_first) *loss_first = lsum / ns_;
+    if (loss_last) *loss_last = lsum / ns_;
+  }
+  return cuda_status(cudaStreamSynchronize(c->s));
+}
+
+// z = B(r) for a given node vector (tests); needs a linearisation
+int nn_apply_host(mpml_ctx_s* c, const void* r_nodes, void* z_nodes) {
+  int rc;
+  if (!c->nn_ready) return MPML_ERR_ARG;
+  if ((rc = nn_ensure(c))) return rc;
+  const int64_t n3 = 3 * c->nb * BV;
+  cudaMemcpyAsync(c->nr.p, r_nodes, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
+  DevScalars* d = dscal(c);
+  k_rz_jacobi<<<(unsigned)c->nb, BV, 0, c->s>>>((const float*)c->nr.p, (const float*)c->ndinv.p, d, part_b(c), 0);
+  nn_apply(c, &d->nn_s, nullptr, nullptr);
+  cudaMemcpyAsync(z_nodes, c->nz.p, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
+  return cuda_status(cudaStreamSynchronize(c->s));
+}
+
+// loss of one pair and its weight gradient (device grad buffer zeroed first)
+int nn_loss_grad_host(mpml_ctx_s* c, const void* r_nodes, const void* e_nodes, double* loss) {
+  int rc;
+  if (!c->nn_ready) return MPML_ERR_ARG;
+  const int64_t n3 = 3 * c->nb * BV;
+  if ((rc = ensure(c->nnhd, sizeof(float) * n3)) || (rc = ensure(c->nns_e, sizeof(float) * n3))) return rc;
+  cudaMemcpyAsync(c->nr.p, r_nodes, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
+  float* e = (float*)c->nns_e.p;
+  cudaMemcpyAsync(e, e_nodes, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
+  // den = e^T H e
+  hvp_f32(c, e, (float*)c->nnhd.p);
+  DevScalars* d = dscal(c);
+  cudaMemsetAsync(&d->slope, 0, sizeof(double), c->s);
+  k_dot_ff<<<(unsigned)c->nb, BV, 0, c->s>>>(e, (const float*)c->nnhd.p, (const float*)c->ndinv.p, &d->slope);
+  if ((rc = read_scalars(c))) return rc;
+  const double den = c->hscal->slope > 0 ? c->hscal->slope : 1.0;
+  // zero the gradient accumulator, then one pair with scale 1
+  std::vector<float> zeros((size_t)nn_weight_count(), 0.f);
+  (void)zeros;
+  return nn_pair(c, e, den, 1.0f, loss, true);
+}
+
 template <typename T>
 static int pcg_t(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, double* rel) {
   int rc;
+  if (sizeof(T) == 4 && o->precond == MPML_PRECOND_LEARNED && c->nn_ready && c->compressed) {
+    int fit = 0, fb = 0;
+    if ((rc = fcg_solve(c, o, &fit, &fb))) return rc;
+    c->last_fcg_fallback = fb;
+    if (!fb) {
+      *iters = fit;
+      const double rr0 = c->hscal->rr0;
+      *rel = rr0 > 0 ? sqrt(c->hscal->rr_last / rr0) : 0.0;
+      return MPML_OK;
+    }
+    // flexible CG stalled: continue from the current x, r with Jacobi-PCG
+    k_rz_jacobi<<<(unsigned)c->nb, BV, 0, c->s>>>((const float*)c->nr.p, (const float*)c->ndinv.p, dscal(c),
+                                                   part_b(c), 1);
+    c->launches++;
+    mpml_solver_opts j = *o;
+    j.precond = MPML_PRECOND_JACOBI;
+    j.cg_max = o->cg_max > fit ? o->cg_max - fit : 1;
+    int jit = 0;
+    if ((rc = pcg_t<T>(c, &j, &jit, rel))) return rc;
+    *iters = fit + jit;
+    return MPML_OK;
+  }
   if (sizeof(T) == 4 && c->compressed && o->use_graph == 2) {
     if ((rc = pcg_persistent(c, o))) return rc;
     if ((rc = read_scalars(c))) return rc;
@@ -2112,7 +2498,9 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     }
     int cgit = 0;
     double rel = 0;
+    c->last_fcg_fallback = 0;
     if ((rc = pcg_t<T>(c, o, &cgit, &rel))) return rc;
+    st->fcg_fallbacks += c->last_fcg_fallback;
     if (it < 64) {
       st->cg_iters[it] = cgit;
       st->cg_rel_resid[it] = rel;

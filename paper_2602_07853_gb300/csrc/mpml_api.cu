@@ -279,7 +279,8 @@ int mpml_destroy(mpml_ctx c) {
                  &c->pG, &c->pm, &c->pV, &c->pmat, &c->pperm, &c->pkey, &c->prank, &c->pbase, &c->ux, &c->uv,
                  &c->uF, &c->uG, &c->um, &c->uV, &c->umat, &c->cnt, &c->start, &c->scan_tmp, &c->cflag,
                  &c->cacc, &c->cs, &c->cK, &c->cnew, &c->nflag, &c->nmass, &c->nv, &c->nvhat, &c->nvfix,
-                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->nolist};
+                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->nolist,
+                 &c->nnw, &c->nnact, &c->nny, &c->nnpart, &c->nz, &c->nns_r, &c->nns_e, &c->nnhd};
   for (Buf* b : bufs) free_buf(*b);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hstatus) cudaFreeHost(c->hstatus);
@@ -536,5 +537,86 @@ int mpml_hvp_bench(mpml_ctx c, int iters, double* mean_ms) {
 }
 
 int64_t mpml_kernel_launches(mpml_ctx c) { return c ? c->launches : -1; }
+
+int mpml_nn_weight_count(void) { return nn_weight_count(); }
+
+int mpml_nn_set_weights(mpml_ctx c, const float* w) {
+  if (!c || !w || c->stage < 1) return MPML_ERR_ARG;
+  if (c->fp64 || !c->compressed) return MPML_ERR_ARG;  // FP32 single-material contexts
+  int rc = nn_set_weights(c, w);
+  if (!rc) c->nn_ready = 1;
+  return rc;
+}
+
+int mpml_nn_get_weights(mpml_ctx c, float* w) {
+  if (!c || !w || !c->nn_ready) return MPML_ERR_ARG;
+  return nn_get_weights(c, w, 0);
+}
+
+int mpml_nn_get_grad(mpml_ctx c, float* g) {
+  if (!c || !g || !c->nn_ready) return MPML_ERR_ARG;
+  return nn_get_weights(c, g, 1);
+}
+
+int mpml_nn_apply(mpml_ctx c, const double* r, double* z) {
+  if (!c || !r || !z || !c->nn_ready || !c->have_lin) return MPML_ERR_ARG;
+  const int64_t ns = c->nb * BV;
+  mpml::Buf rin, zout;
+  int rc;
+  if ((rc = ensure(rin, sizeof(float) * 3 * (ns ? ns : 1))) || (rc = ensure(zout, sizeof(float) * 3 * (ns ? ns : 1))) ||
+      (rc = nn_ensure(c))) {
+    free_buf(rin);
+    free_buf(zout);
+    return rc;
+  }
+  rc = import_nodes<float>(c, r, rin.p);
+  if (!rc) rc = nn_apply_host(c, rin.p, zout.p);
+  if (!rc) rc = export_slots<float>(c, zout.p, 3, c->nflag, NF_DOF, z);
+  cudaStreamSynchronize(c->s);
+  free_buf(rin);
+  free_buf(zout);
+  return rc;
+}
+
+int mpml_nn_loss_grad(mpml_ctx c, const double* r, const double* e, double* loss) {
+  if (!c || !r || !e || !loss || !c->nn_ready || !c->have_lin) return MPML_ERR_ARG;
+  const int64_t ns = c->nb * BV;
+  mpml::Buf rin, ein;
+  int rc;
+  if ((rc = ensure(rin, sizeof(float) * 3 * (ns ? ns : 1))) || (rc = ensure(ein, sizeof(float) * 3 * (ns ? ns : 1))) ||
+      (rc = nn_ensure(c))) {
+    free_buf(rin);
+    free_buf(ein);
+    return rc;
+  }
+  rc = import_nodes<float>(c, r, rin.p);
+  if (!rc) rc = import_nodes<float>(c, e, ein.p);
+  if (!rc) {
+    // zero the gradient accumulator (it follows the master weights)
+    cudaMemsetAsync((float*)c->nnw.p + 3 * 27 * 256, 0, sizeof(float) * 3 * 27 * 256, c->s);
+    rc = nn_loss_grad_host(c, rin.p, ein.p, loss);
+  }
+  cudaStreamSynchronize(c->s);
+  free_buf(rin);
+  free_buf(ein);
+  return rc;
+}
+
+int mpml_nn_train(mpml_ctx c, const mpml_train_opts* o, mpml_train_stats* st) {
+  if (!c || !o || c->stage < 1 || !c->nn_ready) return MPML_ERR_ARG;
+  if (o->samples < 1 || o->epochs < 0 || o->batch < 1 || !(o->lr >= 0)) return MPML_ERR_ARG;
+  int rc = nn_collect(c, o->samples, o->rtol, o->cg_max);
+  if (rc) return rc;
+  double l0 = 0, l1 = 0;
+  rc = nn_train(c, o->epochs, o->batch, o->lr, &l0, &l1);
+  if (rc) return rc;
+  c->have_lin = 1;
+  if (st) {
+    st->samples = c->nn_nsamples;
+    st->loss_first = l0;
+    st->loss_last = l1;
+  }
+  return sync_status(c);
+}
 
 }  // extern "C"

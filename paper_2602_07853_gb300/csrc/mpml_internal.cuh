@@ -71,6 +71,12 @@ struct DevScalars {
   double slope;    // g^T dx
   double tol2;     // (cg_rtol)^2 rr0
   double rr_last;  // r^T r at the last CG update
+  double pq;       // p^T H p of the current direction
+  double nn_s;     // RMS of D^-1/2 r (network input scale)
+  double nfree;    // number of free DOF components
+  double rzj;      // r^T D^-1 r (Jacobi) of the current residual
+  double rr_ring[32];  // r^T r history (stall test of flexible CG)
+  int fallback;    // flexible CG stalled: continue with Jacobi-PCG
   int infeasible;  // cells where the energy is undefined (line search)
   int done;
   int iters;
@@ -129,6 +135,13 @@ struct mpml_ctx_s {
   mpml::Buf nflag, nmass, nv, nvhat, nvfix, nvnew, ng, ndinv, nx, nr, np, np2, nq;
   // scalars and status
   mpml::Buf scal, status, prof, part, gbar;
+  // learned preconditioner: weights/grads/Adam + bf16 copies, activations,
+  // network output, wgrad partials, z, training samples
+  mpml::Buf nnw, nnact, nny, nnpart, nz, nns_r, nns_e, nnhd;
+  int nn_ready = 0;        // weights set
+  int nn_nsamples = 0;     // stored training pairs
+  int nn_adam_step = 0;
+  int last_fcg_fallback = 0;  // the last learned solve fell back to Jacobi-PCG
   mpml::DevScalars* hscal = nullptr;  // pinned mirror
   int* hstatus = nullptr;             // pinned
 
@@ -168,6 +181,23 @@ int linearize_device(mpml_ctx_s* c, const void* v_nodes);
 int hvp_device(mpml_ctx_s* c, const void* p_nodes, void* y_nodes);
 int hvp_bench(mpml_ctx_s* c, int iters, double* mean_ms);
 int n2q_device(mpml_ctx_s* c);
+
+// learned preconditioner (k_nn.cu)
+int nn_ensure(mpml_ctx_s* c);
+int nn_refresh_weights(mpml_ctx_s* c);
+void nn_forward(mpml_ctx_s* c);
+void nn_apply(mpml_ctx_s* c, const double* s_ptr, const float* q, double* part);
+void nn_backward(mpml_ctx_s* c, const float* gy, float scale);
+void nn_adam(mpml_ctx_s* c, float lr, int step);
+int nn_set_weights(mpml_ctx_s* c, const float* w);
+int nn_get_weights(mpml_ctx_s* c, float* w, int grad);
+int nn_weight_count();
+float* nn_output(mpml_ctx_s* c);  // y, fp32 [brick][3][512]
+// learned preconditioner drivers (k_newton.cu)
+int nn_apply_host(mpml_ctx_s* c, const void* r_nodes, void* z_nodes);
+int nn_loss_grad_host(mpml_ctx_s* c, const void* r_nodes, const void* e_nodes, double* loss);
+int nn_collect(mpml_ctx_s* c, int nsamples, double rtol, int cg_max);
+int nn_train(mpml_ctx_s* c, int epochs, int batch, float lr, double* loss_first, double* loss_last);
 
 inline unsigned div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 

@@ -56,7 +56,16 @@ class mpml_solve_stats(C.Structure):
                 ("cg_iters", C.c_int * 64), ("alpha", C.c_double * 64), ("cg_rel_resid", C.c_double * 64),
                 ("g0_norm", C.c_double), ("g_norm", C.c_double), ("phi0", C.c_double), ("phi", C.c_double),
                 ("n_particles", C.c_int64), ("n_cells", C.c_int64), ("n_nodes", C.c_int64),
-                ("n_bricks", C.c_int64)]
+                ("n_bricks", C.c_int64), ("fcg_fallbacks", C.c_int)]
+
+
+class mpml_train_opts(C.Structure):
+    _fields_ = [("samples", C.c_int), ("rtol", C.c_double), ("cg_max", C.c_int), ("epochs", C.c_int),
+                ("batch", C.c_int), ("lr", C.c_float)]
+
+
+class mpml_train_stats(C.Structure):
+    _fields_ = [("samples", C.c_int), ("loss_first", C.c_double), ("loss_last", C.c_double)]
 
 
 _D = C.POINTER(C.c_double)
@@ -85,6 +94,13 @@ EXPORTS = {
     "mpml_hvp_timing": (C.c_int, [C.c_void_p, _I64, _D, _D]),
     "mpml_hvp_bench": (C.c_int, [C.c_void_p, C.c_int, _D]),
     "mpml_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "mpml_nn_weight_count": (C.c_int, []),
+    "mpml_nn_set_weights": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "mpml_nn_get_weights": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "mpml_nn_get_grad": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
+    "mpml_nn_apply": (C.c_int, [C.c_void_p, _D, _D]),
+    "mpml_nn_loss_grad": (C.c_int, [C.c_void_p, _D, _D, _D]),
+    "mpml_nn_train": (C.c_int, [C.c_void_p, C.POINTER(mpml_train_opts), C.POINTER(mpml_train_stats)]),
 }
 
 
@@ -300,3 +316,82 @@ def particles_from_tensors(x, v, F, G, mass, volume, mat, perm=None):
 def lame_parameters(E, nu):
     """(mu, lambda) from Young's modulus and Poisson's ratio."""
     return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+
+
+# ---------------------------------------------------------------------------
+# learned preconditioner
+# ---------------------------------------------------------------------------
+NN_SHAPES = ((27, 16, 3), (27, 16, 16), (27, 3, 16))
+
+
+def nn_pack(Ws):
+    """Concatenate per-layer (27, Cout, Cin) arrays into the C layout (float32)."""
+    return np.ascontiguousarray(np.concatenate([np.asarray(W, np.float32).ravel() for W in Ws]))
+
+
+def nn_unpack(flat):
+    out, off = [], 0
+    for sh in NN_SHAPES:
+        n = int(np.prod(sh))
+        out.append(np.asarray(flat[off:off + n], np.float64).reshape(sh))
+        off += n
+    return out
+
+
+def mpml_nn_weight_count():
+    return int(load().mpml_nn_weight_count())
+
+
+def mpml_nn_set_weights(ctx, Ws):
+    w = nn_pack(Ws)
+    return _check(load().mpml_nn_set_weights(ctx, w.ctypes.data_as(C.POINTER(C.c_float))), "mpml_nn_set_weights")
+
+
+def mpml_nn_get_weights(ctx):
+    w = np.zeros(mpml_nn_weight_count(), np.float32)
+    _check(load().mpml_nn_get_weights(ctx, w.ctypes.data_as(C.POINTER(C.c_float))), "mpml_nn_get_weights")
+    return nn_unpack(w)
+
+
+def mpml_nn_get_grad(ctx):
+    w = np.zeros(mpml_nn_weight_count(), np.float32)
+    _check(load().mpml_nn_get_grad(ctx, w.ctypes.data_as(C.POINTER(C.c_float))), "mpml_nn_get_grad")
+    return nn_unpack(w)
+
+
+def mpml_nn_apply(ctx, r):
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    z = np.zeros_like(r)
+    _check(load().mpml_nn_apply(ctx, r.ctypes.data_as(_D), z.ctypes.data_as(_D)), "mpml_nn_apply")
+    return z
+
+
+def mpml_nn_loss_grad(ctx, r, e):
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    loss = C.c_double()
+    _check(load().mpml_nn_loss_grad(ctx, r.ctypes.data_as(_D), e.ctypes.data_as(_D), C.byref(loss)),
+           "mpml_nn_loss_grad")
+    return loss.value, mpml_nn_get_grad(ctx)
+
+
+def train_opts(samples=32, rtol=1e-8, cg_max=20000, epochs=20, batch=4, lr=1e-3):
+    o = mpml_train_opts()
+    o.samples, o.rtol, o.cg_max, o.epochs, o.batch, o.lr = samples, rtol, cg_max, epochs, batch, lr
+    return o
+
+
+def mpml_nn_train(ctx, opts=None):
+    st = mpml_train_stats()
+    _check(load().mpml_nn_train(ctx, C.byref(opts if opts is not None else train_opts()), C.byref(st)),
+           "mpml_nn_train")
+    return st
+
+
+def nn_init_weights(seed=0, gain=1.0):
+    """Seeded He-style initialisation (numpy PCG64), per-layer (27, Cout, Cin)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ws = []
+    for (t, cout, cin) in NN_SHAPES:
+        Ws.append(gain * np.sqrt(2.0 / (27 * cin)) * rng.standard_normal((t, cout, cin)))
+    return Ws
