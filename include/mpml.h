@@ -61,7 +61,8 @@ typedef enum {
   MPML_ERR_STRETCH = -4,       /* stress-to-stretch inversion has no admissible root */
   MPML_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
   MPML_ERR_CUDA = -6,          /* a CUDA runtime call failed */
-  MPML_ERR_NOMEM = -7          /* device allocation failed */
+  MPML_ERR_NOMEM = -7,         /* device allocation failed */
+  MPML_ERR_TOO_LARGE = -8      /* size above a fixed capacity (mpml_sort_particles_noalloc) */
 } mpml_status;
 
 enum { MPML_FIXED_COROTATED = 0, MPML_NEO_HOOKEAN = 1, MPML_HENCKY = 2 };
@@ -258,6 +259,37 @@ int mpml_nn_loss_grad(mpml_ctx ctx, const double* r, const double* e, double* lo
  * `samples` pairs (r_k, x* - x_k) along the way and runs Adam on the H-norm
  * loss.  Weights must be set (e.g. a seeded initialisation). */
 int mpml_nn_train(mpml_ctx ctx, const mpml_train_opts* opts, mpml_train_stats* stats);
+
+/* Allocation-free particle sort ----------------------------------------
+ * No counterpart in the paper: a service for callers that must not allocate
+ * device memory when they sort, e.g. an application whose own arena owns all
+ * device memory, or a time-critical loop that cannot take cudaMalloc's
+ * implicit device-wide synchronisation.  It needs no context and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Computes the order mpml_resample gives the particles: ascending brick-major
+ * key of the base centre floor(x/dx - 1/2), ties by input index.
+ *   n, inv_dx   the grid of an mpml_scene_desc (n[a] >= 2, inv_dx > 0)
+ *   precision   MPML_FP32 (x is float) or MPML_FP64 (double)
+ *   x           device pointer, n_particles*3 positions (read only)
+ *   perm        device pointer, n_particles int32: perm[s] = input index of
+ *               the s-th particle in sorted order (written)
+ *   keys        device pointer, n_particles int64 keys of the sorted
+ *               particles (written), or NULL
+ *   stream      a cudaStream_t (NULL = legacy default stream)
+ * Its scratch is one fixed array in device memory (about 16 MiB, which every
+ * GPU that loads this library holds until the process exits): a grid with
+ * NB_x*NB_y*NB_z*512 > MPML_NOALLOC_MAX_SLOTS (e.g. more than 127 cells per
+ * axis of a cube) is rejected with MPML_ERR_TOO_LARGE, n_particles above
+ * INT32_MAX with MPML_ERR_ARG.  The first call on a device looks up the
+ * array's device address (the device must be current); make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race.  Synchronises
+ * the stream; returns MPML_ERR_OUT_OF_DOMAIN / MPML_ERR_NONFINITE for bad
+ * particles (perm is then incomplete). */
+#define MPML_NOALLOC_MAX_SLOTS (1 << 21)
+int mpml_sort_particles_noalloc(const int n[3], double inv_dx, int precision, const void* x,
+                                int64_t n_particles, int32_t* perm, int64_t* keys, void* stream);
 
 #ifdef __cplusplus
 }

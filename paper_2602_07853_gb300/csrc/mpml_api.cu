@@ -301,6 +301,7 @@ const char* mpml_status_str(int s) {
     case MPML_ERR_TIMEOUT: return "bounded device wait timed out";
     case MPML_ERR_CUDA: return "CUDA runtime error";
     case MPML_ERR_NOMEM: return "out of device memory";
+    case MPML_ERR_TOO_LARGE: return "size above the fixed scratch capacity";
     default: return "unknown status";
   }
 }

@@ -18,6 +18,8 @@ from . import build as _build
 MAX_MATS = 4
 OK, WARN_NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_OUT_OF_DOMAIN, ERR_NONFINITE, ERR_STRETCH, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = -1, -2, -3, -4, -5, -6, -7
+ERR_TOO_LARGE = -8
+NOALLOC_MAX_SLOTS = 1 << 21
 FIXED_COROTATED, NEO_HOOKEAN, HENCKY = 0, 1, 2
 FP32, FP64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
@@ -101,6 +103,8 @@ EXPORTS = {
     "mpml_nn_apply": (C.c_int, [C.c_void_p, _D, _D]),
     "mpml_nn_loss_grad": (C.c_int, [C.c_void_p, _D, _D, _D]),
     "mpml_nn_train": (C.c_int, [C.c_void_p, C.POINTER(mpml_train_opts), C.POINTER(mpml_train_stats)]),
+    "mpml_sort_particles_noalloc": (C.c_int, [C.POINTER(C.c_int), C.c_double, C.c_int, C.c_void_p, C.c_int64,
+                                              C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -395,3 +399,18 @@ def nn_init_weights(seed=0, gain=1.0):
     for (t, cout, cin) in NN_SHAPES:
         Ws.append(gain * np.sqrt(2.0 / (27 * cin)) * rng.standard_normal((t, cout, cin)))
     return Ws
+
+
+def mpml_sort_particles_noalloc(n, inv_dx, precision, x, perm, keys=None, stream=None):
+    """Allocation-free sort of the particles at x (a CUDA tensor, n_particles x 3, float32 for FP32 or
+    float64 for FP64) into perm (int32 CUDA tensor) and optionally keys (int64 CUDA tensor).
+    stream: a torch.cuda.Stream or a raw cudaStream_t (None = legacy default stream).
+    Returns the status code (raises on errors)."""
+    nn = (C.c_int * 3)(*[int(a) for a in n])
+    np_ = int(x.shape[0]) if x is not None else 0
+    s = getattr(stream, "cuda_stream", stream)
+    rc = load().mpml_sort_particles_noalloc(nn, float(inv_dx), int(precision),
+                                            x.data_ptr() if x is not None else None, np_,
+                                            perm.data_ptr() if perm is not None else None,
+                                            keys.data_ptr() if keys is not None else None, s)
+    return _check(rc, "mpml_sort_particles_noalloc")

@@ -76,3 +76,21 @@ int main(void){
                                                  m.mpml_solver_opts, m.mpml_solve_stats)]
     assert offs == [m.mpml_scene_desc.plate_vel.offset, m.mpml_particles.perm.offset,
                     m.mpml_solve_stats.g0_norm.offset, m.mpml_solve_stats.n_bricks.offset]
+
+
+def test_noalloc_sort_rejects_on_the_host(lib_path):
+    """Argument and capacity checks of mpml_sort_particles_noalloc run before any CUDA call."""
+    import paper_2602_07853_gb300.mpml as m
+    lib = m.load()
+    f = lib.mpml_sort_particles_noalloc
+    dummy = ctypes.c_void_p(256)  # never dereferenced: every case below returns before any launch
+    n_ok, n_big = (ctypes.c_int * 3)(127, 127, 127), (ctypes.c_int * 3)(128, 127, 127)
+    assert f(n_big, 128.0, m.FP32, dummy, 10, dummy, None, None) == m.ERR_TOO_LARGE
+    assert f(n_ok, 128.0, m.FP32, dummy, 0, None, None, None) == m.OK
+    assert f(n_ok, 128.0, m.FP32, None, 10, dummy, None, None) == m.ERR_ARG
+    assert f(n_ok, 128.0, m.FP32, dummy, 10, None, None, None) == m.ERR_ARG
+    assert f(n_ok, 128.0, 7, dummy, 10, dummy, None, None) == m.ERR_ARG
+    assert f(n_ok, 0.0, m.FP32, dummy, 10, dummy, None, None) == m.ERR_ARG
+    assert f(n_ok, 128.0, m.FP32, dummy, 1 << 31, dummy, None, None) == m.ERR_ARG
+    assert f((ctypes.c_int * 3)(1, 8, 8), 128.0, m.FP32, dummy, 10, dummy, None, None) == m.ERR_ARG
+    assert lib.mpml_status_str(m.ERR_TOO_LARGE).decode().startswith("size above")
