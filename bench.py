@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--check-every", type=int, default=16)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner comparison")
     return ap.parse_args()
 
 
@@ -115,15 +116,24 @@ def kernel_hash():
 
 
 def ncu_traffic():
-    """dram bytes per HVP launch from the committed ncu summary, if taken on the current kernel."""
-    path = os.path.join(ROOT, "profiles", "hvp_traffic.json")
+    """DRAM bytes of one persistent-PCG launch from the committed ncu capture (cold cache; the CG
+    working set then stays in L2), or None when the capture was taken on another version of the
+    kernel."""
+    path = os.path.join(ROOT, "profiles", "pcg_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
     if d.get("kernel_hash") != kernel_hash():
         return None
-    return d.get("dram_bytes_per_launch_full_size")
+    return d["dram_bytes_per_launch"]
+
+
+def pcg_bytes_per_iter(n_cells, n_nodes):
+    """Algorithmic bytes of one CG iteration (FP32): the HVP reads the 27-number compressed tangent
+    of every active cell (108 B) and per DOF node p, m and writes q (28 B); the CG update makes
+    about ten 12-byte vector passes per DOF node (x, r, p, q, D^-1 reads and writes)."""
+    return 108.0 * n_cells + (28.0 + 120.0) * n_nodes
 
 
 # ---------------------------------------------------------------------------
@@ -195,6 +205,49 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def learned_comparison(m, ctx, parts, reset, one_step, args, stream, flush):
+    """Trains the learned preconditioner on the workload's first Newton system (untimed), then
+    times the same steps with flexible CG (CUDA events, L2 flushed as for the main number)."""
+    import torch
+
+    reset()
+    m.mpml_set_time(ctx, 0.0)
+    m.mpml_resample(ctx, parts)
+    m.mpml_nn_set_weights(ctx, m.nn_init_weights(0, gain=0.1))
+    t0 = time.perf_counter()
+    tr = m.mpml_nn_train(ctx, m.train_opts())
+    train_s = time.perf_counter() - t0
+    opts = m.solver_opts(precond=m.PRECOND_LEARNED)
+    for _ in range(max(1, args.warmup)):
+        reset()
+        m.mpml_set_time(ctx, 0.0)
+        m.mpml_resample(ctx, parts)
+        m.mpml_newton_step(ctx, opts)
+        m.mpml_g2p(ctx, parts)
+    torch.cuda.synchronize()
+    ms, cg, fb, nw = [], [], [], []
+    for _ in range(args.steps):
+        reset()
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.mpml_set_time(ctx, 0.0)
+        m.mpml_resample(ctx, parts)
+        rc, st = m.mpml_newton_step(ctx, opts)
+        m.mpml_g2p(ctx, parts)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        cg.append(st.cg_iters_total)
+        fb.append(st.fcg_fallbacks)
+        nw.append(st.newton_iters)
+    return {"steps_per_s": 1e3 * len(ms) / float(np.sum(ms)), "ms_per_step": float(np.mean(ms)),
+            "cg_iters_per_step": float(np.mean(cg)), "newton_iters_per_step": float(np.mean(nw)),
+            "fcg_fallbacks_per_step": float(np.mean(fb)), "train_s": train_s, "train_samples": tr.samples,
+            "loss_first": tr.loss_first, "loss_last": tr.loss_last,
+            "solver": "flexible CG with the trained 3-layer 16-channel BF16 network, Jacobi-PCG fallback"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -246,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    newton_its, cg_its = [], []
+    newton_its, cg_its, last_cg = [], [], []
     barrier()
     for i in range(args.steps):
         reset()
@@ -256,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
         ev[i][1].record(stream)
         newton_its.append(st.newton_iters)
         cg_its.append(st.cg_iters_total)
+        last_cg = [int(st.cg_iters[k]) for k in range(min(st.newton_iters, 64))]
     barrier()
     clk = clocks.stop()
     launches = m.mpml_kernel_launches(ctx) - launches0
@@ -266,7 +320,9 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     hvp_n, hvp_ms, hvp_bytes = m.mpml_hvp_timing(ctx)
+    pcg_n, pcg_iters, pcg_ms = m.mpml_pcg_timing(ctx)
     m.mpml_set_profiling(ctx, 0)
+    counts = m.mpml_counts(ctx)
     value = world * args.steps / (total_ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
@@ -300,13 +356,28 @@ def run_ours(args, rank, world, local_rank):
 
     peaks, peak_kind = measured_peaks()
     roof = None
-    if hvp_n > 0:
-        mean_ms = hvp_ms / hvp_n
-        achieved = hvp_bytes / (mean_ms / 1e3) / 1e9
+    if pcg_n > 0:
+        # the dominant kernel: one persistent cooperative launch runs a whole Jacobi-PCG solve
+        per_iter = pcg_bytes_per_iter(counts["cells"], counts["nodes"])
+        mean_ms = pcg_ms / pcg_n
+        iters_per_launch = pcg_iters / pcg_n
+        achieved = per_iter * iters_per_launch / (mean_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic(),
-                "peak_kind": peak_kind, "kernel": "k_hvp", "launches_timed": hvp_n, "mean_launch_ms": mean_ms,
-                "bytes_per_launch": hvp_bytes}
+                "peak_kind": peak_kind, "kernel": "k_pcg_persistent", "launches_timed": pcg_n,
+                "mean_launch_ms": mean_ms, "cg_iters_per_launch": iters_per_launch,
+                "bytes_per_cg_iter": per_iter, "us_per_cg_iter": 1e3 * pcg_ms / max(pcg_iters, 1),
+                "timing": "CUDA events around each launch on the context stream"}
+    hvp = None
+    if hvp_n > 0:
+        hvp_mean = hvp_ms / hvp_n
+        hvp = {"gbs": hvp_bytes / (hvp_mean / 1e3) / 1e9, "frac": hvp_bytes / (hvp_mean / 1e3) / 1e9 / peaks["hbm_gbs"],
+               "mean_us": 1e3 * hvp_mean, "phases_timed": hvp_n, "bytes_per_hvp": hvp_bytes,
+               "timing": "device global timer, HVP phase of the persistent kernel (first block start to barrier)"}
+
+    learned = None
+    if not args.no_learned:
+        learned = learned_comparison(m, ctx, parts, reset, one_step, args, stream, flush)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -316,7 +387,6 @@ def run_ours(args, rank, world, local_rank):
                "sample": (f"full workload: unload+stretch+load ({fixed:.1f} s) plus ONE Newton iteration with "
                           f"Jacobi-PCG to 1e-6 ({per_newton:.1f} s), scaled to {nn:.1f} Newton iterations per "
                           "step (the GPU run's mean); single thread")}
-    counts = m.mpml_counts(ctx)
     m.mpml_destroy(ctx)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -331,7 +401,8 @@ def run_ours(args, rank, world, local_rank):
                 "newton_iters_per_step": float(np.mean(newton_its)),
                 "cg_iters_per_step": float(np.mean(cg_its)),
                 "newton_iters_per_s": float(np.sum(newton_its)) / (total_ms / 1e3),
-                "hvp_gbs": roof["achieved"] if roof else None,
+                "cg_iters_last_step": last_cg,
+                "hvp_gbs": hvp["gbs"] if hvp else None, "hvp": hvp, "learned_precond": learned,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)

@@ -215,6 +215,11 @@ int mpml_hvp_timing(mpml_ctx ctx, int64_t* launches, double* total_ms, double* b
  * device-resident direction and returns the mean kernel milliseconds
  * (CUDA events on the context stream).  Synchronising. */
 int mpml_hvp_bench(mpml_ctx ctx, int iters, double* mean_ms);
+/* With profiling enabled: the persistent cooperative PCG kernel (use_graph = 2)
+ * is bracketed by CUDA events on the context stream; returns its launches
+ * since profiling was enabled, the CG iterations they ran and their total
+ * milliseconds.  Host-side only (no synchronisation). */
+int mpml_pcg_timing(mpml_ctx ctx, int64_t* launches, int64_t* cg_iters, double* total_ms);
 /* Number of kernel launches issued on the context stream since creation. */
 int64_t mpml_kernel_launches(mpml_ctx ctx);
 

@@ -2054,10 +2054,26 @@ static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
   // q starts at zero (the phase-A kernel zeroes it after each use)
   cudaMemsetAsync(c->nq.p, 0, sizeof(float) * 3 * c->nb * BV, c->s);
   void* args[] = {&a};
+  const bool timed = c->profiling && c->pcg_ev[0] && c->pcg_ev[1];
+  if (timed) cudaEventRecord(c->pcg_ev[0], c->s);
   rc = cuda_status(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent, dim3(G), dim3(256), args, HVP_C_SMEM,
                                                c->s));
+  if (timed) cudaEventRecord(c->pcg_ev[1], c->s);
   c->launches++;
   return rc;
+}
+
+// after the solve has been read back: add the launch's event time and iterations
+static void pcg_persistent_account(mpml_ctx_s* c) {
+  if (!(c->profiling && c->pcg_ev[0] && c->pcg_ev[1])) return;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->pcg_ev[0], c->pcg_ev[1]) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  c->pcg_ms += ms;
+  c->pcg_launches += 1;
+  c->pcg_iters += c->hscal->iters;
 }
 
 // ---------------------------------------------------------------------------
@@ -2431,6 +2447,7 @@ static int pcg_t(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, double* r
   if (sizeof(T) == 4 && c->compressed && o->use_graph == 2) {
     if ((rc = pcg_persistent(c, o))) return rc;
     if ((rc = read_scalars(c))) return rc;
+    pcg_persistent_account(c);
   } else
   if (o->use_graph && c->ncb > 0 && ensure_cg_graph<T>(c, o->cg_max) == MPML_OK) {
     if ((rc = cuda_status(cudaGraphLaunch(c->cg_exec, c->s)))) return rc;

@@ -286,6 +286,8 @@ int mpml_destroy(mpml_ctx c) {
   if (c->hstatus) cudaFreeHost(c->hstatus);
   if (c->cg_exec) cudaGraphExecDestroy(c->cg_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  for (cudaEvent_t e : c->pcg_ev)
+    if (e) cudaEventDestroy(e);
   delete c;
   return MPML_OK;
 }
@@ -509,7 +511,19 @@ int mpml_set_profiling(mpml_ctx c, int enable) {
   cudaMemcpyAsync(c->prof.p, &init, sizeof init, cudaMemcpyHostToDevice, c->s);
   rc = cuda_status(cudaStreamSynchronize(c->s));
   if (rc) return rc;
+  for (int k = 0; k < 2; ++k)
+    if (!c->pcg_ev[k] && cudaEventCreate(&c->pcg_ev[k]) != cudaSuccess) return MPML_ERR_CUDA;
+  c->pcg_launches = c->pcg_iters = 0;
+  c->pcg_ms = 0.0;
   c->profiling = enable ? 1 : 0;
+  return MPML_OK;
+}
+
+int mpml_pcg_timing(mpml_ctx c, int64_t* launches, int64_t* cg_iters, double* total_ms) {
+  if (!c) return MPML_ERR_ARG;
+  if (launches) *launches = c->pcg_launches;
+  if (cg_iters) *cg_iters = c->pcg_iters;
+  if (total_ms) *total_ms = c->pcg_ms;
   return MPML_OK;
 }
 

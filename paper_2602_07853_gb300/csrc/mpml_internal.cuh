@@ -157,6 +157,11 @@ struct mpml_ctx_s {
   // profiling of HVP launches
   int profiling = 0;
   int64_t launches = 0;
+  // CUDA-event timing of the persistent PCG kernel (profiling): launches,
+  // their CG iterations and total milliseconds
+  cudaEvent_t pcg_ev[2] = {nullptr, nullptr};
+  int64_t pcg_launches = 0, pcg_iters = 0;
+  double pcg_ms = 0.0;
 };
 
 namespace mpml {

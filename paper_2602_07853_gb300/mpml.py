@@ -96,6 +96,7 @@ EXPORTS = {
     "mpml_hvp_timing": (C.c_int, [C.c_void_p, _I64, _D, _D]),
     "mpml_hvp_bench": (C.c_int, [C.c_void_p, C.c_int, _D]),
     "mpml_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "mpml_pcg_timing": (C.c_int, [C.c_void_p, _I64, _I64, _D]),
     "mpml_nn_weight_count": (C.c_int, []),
     "mpml_nn_set_weights": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "mpml_nn_get_weights": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
@@ -259,6 +260,12 @@ def mpml_hvp_bench(ctx, iters):
     ms = C.c_double()
     _check(load().mpml_hvp_bench(ctx, int(iters), C.byref(ms)), "mpml_hvp_bench")
     return ms.value
+
+
+def mpml_pcg_timing(ctx):
+    n, it, ms = C.c_int64(), C.c_int64(), C.c_double()
+    _check(load().mpml_pcg_timing(ctx, C.byref(n), C.byref(it), C.byref(ms)), "mpml_pcg_timing")
+    return n.value, it.value, ms.value
 
 
 def mpml_kernel_launches(ctx):
