@@ -15,9 +15,11 @@ conv(a, W)[i] = sum_t W[t] @ a[i + d_t], t = (dz+1)*9 + (dy+1)*3 + (dx+1),
 d_t = (dx, dy, dz) in {-1,0,1}^3, zero outside the grid; W has shape
 (27, C_out, C_in).  No biases (the map is positively homogeneous).
 
-Training loss for a residual / error pair (r, e) of one Newton system H:
-  L = (z(r) - e)^T H (z(r) - e) / (e^T H e)
-(the H-norm error of the preconditioned step; H enters as a callable).
+Training loss for a residual / error pair (r, e = H^-1 r) of one Newton system H:
+  L = 1 - z^T H e / sqrt(z^T H z * e^T H e) = 1 - z^T r / sqrt(z^T H z * r^T e)
+one minus the H-cosine between the preconditioned residual z(r) and the error
+(CG is invariant to the scale of the preconditioner, so only the direction of
+z is scored; a z with z^T r <= 0 scores >= 1).  H enters as a callable.
 """
 from __future__ import annotations
 
@@ -99,18 +101,18 @@ def precondition(r, dinv, Ws, dof, free):
 
 
 def loss_and_grad(r, e, dinv, Ws, dof, free, hvp):
-    """H-norm loss of one pair and its gradient w.r.t. the weights.
-    hvp: callable (X,Y,Z,3) -> (X,Y,Z,3), the Newton Hessian (masked)."""
+    """Loss of one pair (one minus the H-cosine of z(r) and e) and its gradient w.r.t. the
+    weights.  hvp: callable (X,Y,Z,3) -> (X,Y,Z,3), the Newton Hessian (masked)."""
     z, aux = precondition(r, dinv, Ws, dof, free)
-    He = hvp(e)
-    den = float(np.sum(e * He))
-    d = z - e
-    Hd = hvp(d)
-    L = float(np.sum(d * Hd)) / den
+    c = float(np.sum(e * hvp(e)))
+    Hz = hvp(z)
+    a = float(np.sum(z * r))
+    b = float(np.sum(z * Hz))
+    L = 1.0 - a / np.sqrt(b * c)
     if aux is None:
         return L, [np.zeros_like(W) for W in Ws]
     cache, s, sq = aux
-    gz = 2.0 * Hd / den
+    gz = -r / np.sqrt(b * c) + a * Hz / (np.sqrt(c) * b ** 1.5)
     gy = s * sq * gz
     gWs, _ = network_backward(cache, gy, Ws, dof, free)
     return L, gWs

@@ -138,3 +138,27 @@ def test_loss_gradient_finite_differences():
             fd = (nn.loss_and_grad(r, e, dinv, Wp, dof, free, hvp)[0] -
                   nn.loss_and_grad(r, e, dinv, Wm, dof, free, hvp)[0]) / (2 * h)
             assert np.isclose(gWs[l][idw], fd, rtol=1e-5, atol=1e-9), (l, idw)
+
+
+def test_loss_is_zero_for_an_exact_preconditioner_and_scale_free():
+    """With H diagonal, Jacobi (zero network) is the exact inverse: the H-cosine is 1.  The loss
+    depends only on the direction of z: positive homogeneity of the network makes it invariant to
+    the scale of r, and it is bounded by [0, 2]."""
+    shape = (4, 3, 3)
+    dof, free = masks(shape, 14)
+    rng = np.random.default_rng(15)
+    hdiag = free[..., None] * rng.uniform(1.0, 3.0, shape + (3,)) + (1 - free[..., None])
+
+    def hvp(v):
+        return free[..., None] * hdiag * v
+
+    dinv = free[..., None] / hdiag
+    r = free[..., None] * rng.standard_normal(shape + (3,))
+    e = dinv * r
+    zero = [np.zeros_like(W) for W in nn.init_weights(0)]
+    L0, _ = nn.loss_and_grad(r, e, dinv, zero, dof, free, hvp)
+    assert abs(L0) < 1e-14
+    Ws = nn.init_weights(16)
+    L1, _ = nn.loss_and_grad(r, e, dinv, Ws, dof, free, hvp)
+    L2, _ = nn.loss_and_grad(5.0 * r, 5.0 * e, dinv, Ws, dof, free, hvp)
+    assert 0.0 < L1 < 2.0 and abs(L1 - L2) < 1e-12
