@@ -246,7 +246,7 @@ typedef struct {
 } mpml_train_opts;
 typedef struct {
   int samples;
-  double loss_first;  /* mean H-norm loss of the first epoch */
+  double loss_first;  /* mean loss of the first epoch */
   double loss_last;   /* ... of the last epoch */
 } mpml_train_stats;
 int mpml_nn_weight_count(void);
@@ -256,13 +256,15 @@ int mpml_nn_get_weights(mpml_ctx ctx, float* w);
 int mpml_nn_get_grad(mpml_ctx ctx, float* g);
 /* z = preconditioner(r) on the current linearisation (DOF order, n*3). */
 int mpml_nn_apply(mpml_ctx ctx, const double* r, double* z);
-/* Loss L = (z(r) - e)^T H (z(r) - e) / (e^T H e) of one pair and its weight
- * gradient (written to the gradient accumulator, which is zeroed first). */
+/* Loss L = 1 - z^T H e / sqrt(z^T H z * e^T H e) (one minus the H-cosine of
+ * z(r) and the error e; only the direction of z counts, as in CG) of one pair
+ * and its weight gradient (written to the gradient accumulator, which is
+ * zeroed first). */
 int mpml_nn_loss_grad(mpml_ctx ctx, const double* r, const double* e, double* loss);
 /* Trains on the current Newton system (after mpml_resample): reconstructs the
  * stretches, solves the first Newton system with Jacobi-PCG, takes
- * `samples` pairs (r_k, x* - x_k) along the way and runs Adam on the H-norm
- * loss.  Weights must be set (e.g. a seeded initialisation). */
+ * `samples` pairs (r_k, x* - x_k) along the way and runs Adam on the loss
+ * of mpml_nn_loss_grad.  Weights must be set (e.g. a seeded initialisation). */
 int mpml_nn_train(mpml_ctx ctx, const mpml_train_opts* opts, mpml_train_stats* stats);
 
 /* Allocation-free particle sort ----------------------------------------

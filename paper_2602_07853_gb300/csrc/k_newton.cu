@@ -2242,13 +2242,23 @@ __global__ void k_sub(const float* __restrict__ a, const float* __restrict__ b, 
   if (i < n) y[i] = dinv[i] > 0.f ? a[i] - b[i] : 0.f;
 }
 
-// loss gradient w.r.t. the network output: gy = 2 s sqrt(D^-1) H d / den
-__global__ void k_nn_gy(const float* __restrict__ hd, const float* __restrict__ dinv, const double* s_ptr,
-                        double den, float* gy, int64_t n) {
+// loss gradient w.r.t. the network output, L = 1 - a / sqrt(b c) with
+// a = z^T r, b = z^T H z, c = e^T H e:
+//   dL/dz = -r / sqrt(b c) + a H z / (sqrt(c) b^(3/2)),  gy = s sqrt(D^-1) dL/dz
+__global__ void k_nn_gy(const float* __restrict__ hz, const float* __restrict__ r, const float* __restrict__ dinv,
+                        const DevScalars* sc, double cden, float* gy, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float di = dinv[i];
-  gy[i] = di > 0.f ? (float)(2.0 * *s_ptr / den) * sqrtf(di) * hd[i] : 0.f;
+  if (!(di > 0.f)) {
+    gy[i] = 0.f;
+    return;
+  }
+  const double a = sc->nn_a, b = sc->nn_b, s = sc->nn_s;
+  const double sb = sqrt(b > 0.0 ? b : 1e-300), sc_ = sqrt(cden);
+  const float cr = (float)(-s / (sb * sc_));
+  const float ch = (float)(s * a / (sc_ * sb * sb * sb));
+  gy[i] = sqrtf(di) * (cr * r[i] + ch * hz[i]);
 }
 
 // FP32 HVP y = H p on the current linearisation (q faces initialised to m p)
@@ -2260,32 +2270,32 @@ static void hvp_f32(mpml_ctx_s* c, const float* p, float* y) {
   c->launches++;
 }
 
-// one training pair (r in c->nr, e given): loss, and the weight gradient
-// accumulated (scaled) on the device
-static int nn_pair(mpml_ctx_s* c, const float* e, double den, float scale, double* loss_out, bool backward) {
+// one training pair (r in c->nr; den = e^T H e): loss 1 - cos_H(z(r), e), and
+// the weight gradient accumulated (scaled) on the device
+static int nn_pair(mpml_ctx_s* c, double den, float scale, double* loss_out, bool backward) {
   DevScalars* d = dscal(c);
   const int64_t ns = c->nb * BV, n3 = 3 * ns;
   const unsigned nb = (unsigned)c->nb;
   k_rz_jacobi<<<nb, BV, 0, c->s>>>((const float*)c->nr.p, (const float*)c->ndinv.p, d, part_b(c), 0);
   nn_apply(c, &d->nn_s, nullptr, nullptr);
   float* z = (float*)c->nz.p;
-  float* hd = (float*)c->nnhd.p;
-  k_sub<<<div_up(n3, 256), 256, 0, c->s>>>(z, e, (const float*)c->ndinv.p, z, n3);
-  hvp_f32(c, z, hd);
-  double* acc = &d->slope;
-  cudaMemsetAsync(acc, 0, sizeof(double), c->s);
-  k_dot_ff<<<nb, BV, 0, c->s>>>(z, hd, (const float*)c->ndinv.p, acc);
+  float* hz = (float*)c->nnhd.p;
+  hvp_f32(c, z, hz);
+  cudaMemsetAsync(&d->nn_a, 0, 2 * sizeof(double), c->s);
+  k_dot_ff<<<nb, BV, 0, c->s>>>(z, (const float*)c->nr.p, (const float*)c->ndinv.p, &d->nn_a);
+  k_dot_ff<<<nb, BV, 0, c->s>>>(z, hz, (const float*)c->ndinv.p, &d->nn_b);
   c->launches += 4;
   if (backward) {
-    // reuse z's buffer for gy (d = z - e is no longer needed)
-    k_nn_gy<<<div_up(n3, 256), 256, 0, c->s>>>(hd, (const float*)c->ndinv.p, &d->nn_s, den, z, n3);
+    // gy overwrites z (no longer needed)
+    k_nn_gy<<<div_up(n3, 256), 256, 0, c->s>>>(hz, (const float*)c->nr.p, (const float*)c->ndinv.p, d, den, z, n3);
     nn_backward(c, z, scale);
     c->launches++;
   }
   if (loss_out) {
     int rc = read_scalars(c);
     if (rc) return rc;
-    *loss_out = c->hscal->slope / den;
+    const double a = c->hscal->nn_a, b = c->hscal->nn_b;
+    *loss_out = b > 0.0 ? 1.0 - a / sqrt(b * den) : 1.0;
   }
   return cuda_status(cudaGetLastError());
 }
@@ -2369,7 +2379,7 @@ int nn_train(mpml_ctx_s* c, int epochs, int batch, float lr, double* loss_first,
       const int j = order[jj];
       cudaMemcpyAsync(c->nr.p, R + (int64_t)j * n3, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
       double l = 0;
-      if ((rc = nn_pair(c, E + (int64_t)j * n3, den[j], 1.0f / (float)batch, &l, true))) return rc;
+      if ((rc = nn_pair(c, den[j], 1.0f / (float)batch, &l, true))) return rc;
       lsum += l;
       if (++inb == batch || jj == ns_ - 1) {
         nn_adam(c, lr, ++c->nn_adam_step);
@@ -2416,7 +2426,7 @@ int nn_loss_grad_host(mpml_ctx_s* c, const void* r_nodes, const void* e_nodes, d
   // zero the gradient accumulator, then one pair with scale 1
   std::vector<float> zeros((size_t)nn_weight_count(), 0.f);
   (void)zeros;
-  return nn_pair(c, e, den, 1.0f, loss, true);
+  return nn_pair(c, den, 1.0f, loss, true);
 }
 
 template <typename T>

@@ -2,8 +2,9 @@
 // grid (3 -> 16 -> 16 -> 3 channels, ReLU on the hidden layers, no biases),
 // used inside flexible CG as z = D^-1 r + s D^-1/2 NN(D^-1/2 r / s), s the RMS
 // of D^-1/2 r over free DOFs, and trained on residual / error pairs of the
-// method's own Newton systems with the H-norm loss
-//   L = (z(r) - e)^T H (z(r) - e) / (e^T H e).
+// method's own Newton systems with the loss one minus the H-cosine of the
+// preconditioned residual and the error e = H^-1 r,
+//   L = 1 - z^T r / sqrt(z^T H z * e^T H e).
 //
 // Convolutions are BF16 implicit GEMMs on tensor cores (mma.sync m16n8k16,
 // FP32 accumulation): one CTA per 8^3 brick, the 10^3 halo block of the

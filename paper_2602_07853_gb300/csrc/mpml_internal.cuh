@@ -73,6 +73,7 @@ struct DevScalars {
   double rr_last;  // r^T r at the last CG update
   double pq;       // p^T H p of the current direction
   double nn_s;     // RMS of D^-1/2 r (network input scale)
+  double nn_a, nn_b;  // training: z^T r and z^T H z of the current pair
   double nfree;    // number of free DOF components
   double rzj;      // r^T D^-1 r (Jacobi) of the current residual
   double rr_ring[32];  // r^T r history (stall test of flexible CG)
