@@ -1805,7 +1805,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
   while (!done && alive) {
     const unsigned long long t_h0 = (A.pf && blockIdx.x == 0 && threadIdx.x == 0) ? gtimer() : 0ull;
     // ---------------- phase H ----------------
-    double pmp = 0, pkp = 0;
+    float pmp = 0.f, pkp = 0.f;  // per-thread FP32 partials, summed in FP64 below
     for (int jc = blockIdx.x; jc < A.ncb; jc += G) {
       const int id = A.cblist[jc];
       if (threadIdx.x < NBR) s_nbr[threadIdx.x] = A.nbr[id * NBR + threadIdx.x];
@@ -1816,26 +1816,54 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
         mbar_arrive_expect_tx(bar, HVP_C_BYTES);
         tma_load_1d(Cs, A.C + (int64_t)id * 27 * BV, HVP_C_BYTES, bar);
       }
-      for (int i = threadIdx.x; i < 729; i += blockDim.x) {
-        const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
-        const int t = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
-        const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
-        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-        if (t >= 0) {
-          const int64_t o = (int64_t)t * 3 * BV + l;
-          v0 = pnew_at(A, o, beta, pold);
-          v1 = pnew_at(A, o + BV, beta, pold);
-          v2 = pnew_at(A, o + 2 * BV, beta, pold);
-          if (t == id) {  // owner: store p_new and count its mass energy
-            pnext[o] = v0;
-            pnext[o + BV] = v1;
-            pnext[o + 2 * BV] = v2;
-            pmp += (double)(A.m[(int64_t)id * BV + l] * (v0 * v0 + v1 * v1 + v2 * v2));
+      {
+        // every thread owns at most 3 of the 729 halo slots: issue all loads first
+        int tt[3], ll[3];
+        float dv[3][3], rv[3][3], pv[3][3], mv[3];
+  #pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int i = threadIdx.x + k * 256;
+          tt[k] = -1;
+          ll[k] = 0;
+          mv[k] = 0.f;
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) dv[k][a] = rv[k][a] = pv[k][a] = 0.f;
+          if (i < 729) {
+            const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+            const int t = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+            const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+            tt[k] = t;
+            ll[k] = l;
+            if (t >= 0) {
+              const int64_t o = (int64_t)t * 3 * BV + l;
+  #pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                dv[k][a] = __ldcg(A.dinv + o + a * BV);
+                rv[k][a] = __ldcg(A.r + o + a * BV);
+                pv[k][a] = __ldcg(pold + o + a * BV);
+              }
+              if (t == id) mv[k] = __ldcg(A.m + (int64_t)id * BV + l);
+            }
           }
         }
-        sv[0][i] = v0;
-        sv[1][i] = v1;
-        sv[2][i] = v2;
+  #pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int i = threadIdx.x + k * 256;
+          if (i >= 729) continue;
+          float v[3];
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) v[a] = dv[k][a] > 0.f ? dv[k][a] * rv[k][a] + beta * pv[k][a] : 0.f;
+          if (tt[k] == id) {
+            const int64_t o = (int64_t)id * 3 * BV + ll[k];
+            pnext[o] = v[0];
+            pnext[o + BV] = v[1];
+            pnext[o + 2 * BV] = v[2];
+            pmp += mv[k] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          }
+          sv[0][i] = v[0];
+          sv[1][i] = v[1];
+          sv[2][i] = v[2];
+        }
       }
       __syncthreads();
       const bool ok = mbar_wait_bounded(bar, tma_phase);
@@ -1854,7 +1882,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
           float dkd = 0.f;
 #pragma unroll
           for (int rr = 0; rr < 9; ++rr) dkd += D[rr] * KD[h][rr];
-          pkp += (double)dkd;
+          pkp += dkd;
         }
       }
       __syncthreads();
@@ -1910,7 +1938,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
         pnext[o + BV] = v1;
         pnext[o + 2 * BV] = v2;
         const float mi = A.m[(int64_t)id * BV + l];
-        pmp += (double)(mi * (v0 * v0 + v1 * v1 + v2 * v2));
+        pmp += mi * (v0 * v0 + v1 * v1 + v2 * v2);
         if (v0 != 0.f) atomicAdd(A.q + o, mi * v0);
         if (v1 != 0.f) atomicAdd(A.q + o + BV, mi * v1);
         if (v2 != 0.f) atomicAdd(A.q + o + 2 * BV, mi * v2);
@@ -1924,7 +1952,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       z[0] = 0.0;
       z[1] = 0.0;
     }
-    block_atomic2(pmp, pkp, accH);
+    block_atomic2((double)pmp, (double)pkp, accH);
     if (!grid_barrier(A.gbar, &s_flag)) {
       alive = false;
       break;
@@ -1945,31 +1973,37 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
     }
     const float alpha = (float)(rz / pq);
     // ---------------- phase A ----------------
-    double rzl = 0, rrl = 0;
+    float rzl = 0.f, rrl = 0.f;
     for (int jb = blockIdx.x; jb < A.nb; jb += G) {
+      float2 d2[3], p2[3], q2[3], x2[3], r2[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
-        const float2 d2 = *reinterpret_cast<const float2*>(A.dinv + o);
-        const float2 p2 = *reinterpret_cast<const float2*>(pnext + o);
-        const float2 q2 = *reinterpret_cast<const float2*>(A.q + o);
-        float2 x2 = *reinterpret_cast<const float2*>(A.x + o);
-        float2 r2 = *reinterpret_cast<const float2*>(A.r + o);
-        if (d2.x > 0.f) {
-          x2.x += alpha * p2.x;
-          r2.x -= alpha * q2.x;
+        d2[a] = __ldcg(reinterpret_cast<const float2*>(A.dinv + o));
+        p2[a] = __ldcg(reinterpret_cast<const float2*>(pnext + o));
+        q2[a] = __ldcg(reinterpret_cast<const float2*>(A.q + o));
+        x2[a] = __ldcg(reinterpret_cast<const float2*>(A.x + o));
+        r2[a] = __ldcg(reinterpret_cast<const float2*>(A.r + o));
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
+        if (d2[a].x > 0.f) {
+          x2[a].x += alpha * p2[a].x;
+          r2[a].x -= alpha * q2[a].x;
         }
-        if (d2.y > 0.f) {
-          x2.y += alpha * p2.y;
-          r2.y -= alpha * q2.y;
+        if (d2[a].y > 0.f) {
+          x2[a].y += alpha * p2[a].y;
+          r2[a].y -= alpha * q2[a].y;
         }
-        *reinterpret_cast<float2*>(A.x + o) = x2;
-        *reinterpret_cast<float2*>(A.r + o) = r2;
+        *reinterpret_cast<float2*>(A.x + o) = x2[a];
+        *reinterpret_cast<float2*>(A.r + o) = r2[a];
         *reinterpret_cast<float2*>(A.q + o) = make_float2(0.f, 0.f);
-        const float srz = (d2.x > 0.f ? r2.x * d2.x * r2.x : 0.f) + (d2.y > 0.f ? r2.y * d2.y * r2.y : 0.f);
-        const float srr = (d2.x > 0.f ? r2.x * r2.x : 0.f) + (d2.y > 0.f ? r2.y * r2.y : 0.f);
-        rzl += (double)srz;
-        rrl += (double)srr;
+        const float srz = (d2[a].x > 0.f ? r2[a].x * d2[a].x * r2[a].x : 0.f) +
+                          (d2[a].y > 0.f ? r2[a].y * d2[a].y * r2[a].y : 0.f);
+        const float srr = (d2[a].x > 0.f ? r2[a].x * r2[a].x : 0.f) + (d2[a].y > 0.f ? r2[a].y * r2[a].y : 0.f);
+        rzl += srz;
+        rrl += srr;
       }
     }
     double* accA = A.acc + 2 * ((2 * it + 1) & 3);
@@ -1978,7 +2012,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       z[0] = 0.0;
       z[1] = 0.0;
     }
-    block_atomic2(rzl, rrl, accA);
+    block_atomic2((double)rzl, (double)rrl, accA);
     if (!grid_barrier(A.gbar, &s_flag)) {
       alive = false;
       break;
@@ -2009,12 +2043,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
 
 static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
   static int max_blocks = -1;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_pcg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_C_SMEM);
-    attr = true;
-  }
   if (max_blocks < 0) {
+    cudaFuncSetAttribute(k_pcg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_C_SMEM);
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
