@@ -58,7 +58,9 @@ class Scene(C.Structure):
                 ("gravity", C.c_double * 3), ("n_mats", C.c_int), ("model", C.c_int * MAX_MATS),
                 ("mu", C.c_double * MAX_MATS), ("lam", C.c_double * MAX_MATS),
                 ("wall_layers", C.c_int), ("has_plate", C.c_int), ("plate_lo", C.c_double * 3),
-                ("plate_hi", C.c_double * 3), ("plate_vel", C.c_double * 3), ("time", C.c_double)]
+                ("plate_hi", C.c_double * 3), ("plate_vel", C.c_double * 3), ("time", C.c_double),
+                ("plastic", C.c_int * MAX_MATS), ("yield_stress", C.c_double * MAX_MATS),
+                ("friction_angle", C.c_double * MAX_MATS)]
 
 
 class Solver(C.Structure):
@@ -113,6 +115,7 @@ def lib():
             "orc_stretch_from_tau": (C.c_int, [C.c_int, C.c_double, C.c_double, _D, _D]),
             "orc_svd3": (None, [_D, _D, _D, _D]),
             "orc_sym_eigen": (None, [C.c_int, _D, _D, _D]),
+            "orc_return_map": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -191,6 +194,17 @@ def sym_eigen(A):
     return ev, Q
 
 
+ELASTIC, VON_MISES, DRUCKER_PRAGER = 0, 1, 2
+
+
+def return_map(plastic, mu, lam, yield_stress, friction_angle, F):
+    """Plastic return map of one deformation gradient; returns (kind, F_new)."""
+    Fn = np.ascontiguousarray(np.asarray(F, dtype=np.float64).reshape(9).copy())
+    kind = lib().orc_return_map(int(plastic), float(mu), float(lam), float(yield_stress),
+                                float(friction_angle), _dp(Fn))
+    return kind, Fn.reshape(3, 3)
+
+
 def lame(E, nu):
     """mu = E / (2 (1 + nu)), lam = E nu / ((1 + nu)(1 - 2 nu)) (standard; not stated in the paper)."""
     return E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
@@ -201,7 +215,8 @@ def lame(E, nu):
 # ----------------------------------------------------------------------------
 def make_scene(n, dx, dt, gravity=(0.0, -9.8, 0.0), materials=((FIXED_COROTATED, 1e5, 0.3),),
                wall_layers=1, plate=None, inv_dx=None, time=0.0):
-    """materials: sequence of (model, E, nu).  plate: (lo3, hi3, vel3) or None."""
+    """materials: sequence of (model, E, nu) or (model, E, nu, plastic, yield_stress,
+    friction_angle_radians).  plate: (lo3, hi3, vel3) or None."""
     sc = Scene()
     n = (n, n, n) if np.isscalar(n) else tuple(n)
     for a in range(3):
@@ -211,9 +226,12 @@ def make_scene(n, dx, dt, gravity=(0.0, -9.8, 0.0), materials=((FIXED_COROTATED,
     sc.inv_dx = float(inv_dx if inv_dx is not None else 1.0 / dx)
     sc.dt = float(dt)
     sc.n_mats = len(materials)
-    for k, (model, E, nu) in enumerate(materials):
+    for k, mt in enumerate(materials):
+        model, E, nu = mt[:3]
         mu, lam = lame(E, nu)
         sc.model[k], sc.mu[k], sc.lam[k] = int(model), mu, lam
+        if len(mt) > 3:
+            sc.plastic[k], sc.yield_stress[k], sc.friction_angle[k] = int(mt[3]), float(mt[4]), float(mt[5])
     sc.wall_layers = int(wall_layers)
     if plate is not None:
         sc.has_plate = 1

@@ -1064,6 +1064,62 @@ void orc_set_node_velocity(orc_state* st, const double* v_new) {
 /* ========================================================================
  * Algorithm 4: Load
  * ====================================================================== */
+/* ------------------------------------------------------------------------
+ * Plasticity (config-5 materials).  The paper lists von Mises (li2022) and
+ * Drucker-Prager sand (klar2016) among the materials MPM Lite runs and, in
+ * its plasticity discussion, applies the return map to the particle's
+ * elastic F after the update of Load (the semi-implicit treatment).  Both
+ * maps act on the Hencky strain eps_i = log s_i of F = U diag(s) V^T with the
+ * StVK-Hencky Kirchhoff stress tau = 2 mu eps + lam tr(eps) I:
+ *   von Mises: |dev tau| <= sqrt(2/3) sigma_y; outside, the deviatoric strain
+ *     is scaled back to the surface (radial return), tr(eps) kept.
+ *   Drucker-Prager (cohesionless, friction angle phi):
+ *     |dev tau| + alpha tr(tau) <= 0, alpha = sqrt(2/3) 2 sin(phi) / (3 - sin(phi));
+ *     tr(eps) > 0 (tension): projected to the apex, eps = 0; otherwise the
+ *     excess dgamma = |dev eps| + (3 lam + 2 mu) / (2 mu) alpha tr(eps), when
+ *     positive, is removed from |dev eps| along dev eps, tr(eps) kept.
+ * ---------------------------------------------------------------------- */
+int orc_return_map(int plastic, double mu, double lam, double yield_stress, double friction_angle,
+                   double F[9]) {
+  if (plastic == ORC_ELASTIC) return 0;
+  double U[9], sg[3], V[9];
+  orc_svd3(F, U, sg, V);
+  if (!(sg[0] > 0 && sg[1] > 0 && sg[2] > 0)) return -1;
+  double e[3] = {log(sg[0]), log(sg[1]), log(sg[2])};
+  const double tr = e[0] + e[1] + e[2];
+  double d[3] = {e[0] - tr / 3, e[1] - tr / 3, e[2] - tr / 3};
+  const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  int kind = 0;
+  if (plastic == ORC_VON_MISES) {
+    const double lim = sqrt(2.0 / 3.0) * yield_stress / (2 * mu); /* |dev eps| on the surface */
+    if (dn <= lim) return 0;
+    for (int i = 0; i < 3; ++i) e[i] = tr / 3 + d[i] * (lim / dn);
+    kind = 1;
+  } else if (plastic == ORC_DRUCKER_PRAGER) {
+    const double sp = sin(friction_angle);
+    const double alpha = sqrt(2.0 / 3.0) * 2 * sp / (3 - sp);
+    if (tr > 0) {
+      e[0] = e[1] = e[2] = 0;
+      kind = 2;
+    } else {
+      const double dg = dn + (3 * lam + 2 * mu) / (2 * mu) * tr * alpha;
+      if (dg <= 0) return 0;
+      for (int i = 0; i < 3; ++i) e[i] -= dg * d[i] / dn;
+      kind = 3;
+    }
+  } else {
+    return -1;
+  }
+  /* F = U diag(exp(eps)) V^T */
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0;
+      for (int k = 0; k < 3; ++k) acc += U[3 * r + k] * exp(e[k]) * V[3 * c + k];
+      F[3 * r + c] = acc;
+    }
+  return kind;
+}
+
 int orc_load(orc_state* st, double* x, double* v, double* F, double* G, double* mp,
              double* Vp, int* mat) {
   const orc_scene* s = &st->sc;
@@ -1094,6 +1150,11 @@ int orc_load(orc_state* st, double* x, double* v, double* F, double* G, double* 
     for (int r = 0; r < 9; ++r) A[r] = s->dt * Gp[r];
     A[0] += 1; A[4] += 1; A[8] += 1;
     m3_mul(A, st->F + 9 * p, Fn);
+    {
+      const int k = st->mat[p];
+      if (s->plastic[k] != ORC_ELASTIC)
+        orc_return_map(s->plastic[k], s->mu[k], s->lam[k], s->yield_stress[k], s->friction_angle[k], Fn);
+    }
     for (int a = 0; a < 3; ++a) {
       x[3 * p + a] = st->x[3 * p + a] + s->dt * vp[a];
       v[3 * p + a] = vp[a];

@@ -31,6 +31,7 @@ extern "C" {
 #define ORC_MAX_MATS 4
 
 enum { ORC_FIXED_COROTATED = 0, ORC_NEO_HOOKEAN = 1, ORC_HENCKY = 2 };
+enum { ORC_ELASTIC = 0, ORC_VON_MISES = 1, ORC_DRUCKER_PRAGER = 2 };
 
 enum {
   ORC_OK = 0,
@@ -54,6 +55,12 @@ typedef struct {
   int has_plate;       /* moving Dirichlet box */
   double plate_lo[3], plate_hi[3], plate_vel[3];
   double time;         /* time at the start of the step (moves the plate) */
+  /* plasticity per material (0 none): return map on the particle's elastic
+   * F after its update in Load; yield stress (von Mises), friction angle in
+   * radians (Drucker-Prager) */
+  int plastic[ORC_MAX_MATS];
+  double yield_stress[ORC_MAX_MATS];
+  double friction_angle[ORC_MAX_MATS];
 } orc_scene;
 
 typedef struct {
@@ -150,6 +157,12 @@ int orc_kirchhoff(int model, double mu, double lam, const double F[9],
 int orc_stretch_from_tau(int model, double mu, double lam,
                          const double tau[9], double S[9]);
 void orc_svd3(const double F[9], double U[9], double s[3], double V[9]);
+/* Plastic return map of one elastic deformation gradient (in place), in the
+ * Hencky strain eps = log(s) of F = U diag(s) V^T; U, V kept.  Returns
+ * 0 (admissible, unchanged), 1 (von Mises radial return), 2 (Drucker-Prager
+ * apex: s = 1), 3 (Drucker-Prager cone), -1 (det F <= 0: unchanged). */
+int orc_return_map(int plastic, double mu, double lam, double yield_stress, double friction_angle,
+                   double F[9]);
 void orc_sym_eigen(int n, const double* A, double* evals, double* evecs);
 
 #ifdef __cplusplus
