@@ -78,7 +78,21 @@ enum { MPML_PRECOND_JACOBI = 0, MPML_PRECOND_LEARNED = 1 };
 typedef struct {
   int model;
   double mu, lambda;
+  /* Plasticity (0 = elastic): MPML_VON_MISES (yield_stress sigma_y) or
+   * MPML_DRUCKER_PRAGER (cohesionless, friction_angle in radians).  The return
+   * map acts on each particle's elastic F after its update in mpml_g2p, in
+   * the Hencky strain eps = log(s) of F = U diag(s) V^T (U, V kept):
+   *   von Mises: |dev tau| <= sqrt(2/3) sigma_y with tau = 2 mu eps +
+   *     lambda tr(eps) I; outside, dev eps is scaled back to the surface.
+   *   Drucker-Prager: |dev tau| + alpha tr(tau) <= 0,
+   *     alpha = sqrt(2/3) 2 sin(phi) / (3 - sin(phi)); tr(eps) > 0 maps to
+   *     eps = 0, otherwise the excess of |dev eps| is removed.
+   * The paper lists both materials and treats plasticity on the particle F
+   * after Load's update (the semi-implicit form). */
+  int plastic;
+  double yield_stress, friction_angle;
 } mpml_material;
+enum { MPML_ELASTIC = 0, MPML_VON_MISES = 1, MPML_DRUCKER_PRAGER = 2 };
 
 /* Scene: grid, time step, gravity (folded into the inertia target
  * vhat = v^n + dt g), precision, Dirichlet boundary.  Nodes with an index

@@ -25,7 +25,55 @@ struct XferInfo {
   int nm;
   int nf;  // accumulator fields
   MatParams<double> mat[MPML_MAX_MATS];
+  // plasticity per material: kind, yield stress, Drucker-Prager alpha
+  int plastic[MPML_MAX_MATS];
+  double ys[MPML_MAX_MATS], alpha[MPML_MAX_MATS];
 };
+
+// Plastic return map of one particle's elastic F (in place), in the Hencky
+// strain eps = log(s) of F = U diag(s) V^T with U, V kept; tau = 2 mu eps +
+// lam tr(eps) I.  Von Mises: |dev eps| beyond sqrt(2/3) ys / (2 mu) is scaled
+// back to it.  Drucker-Prager (cohesionless): tr(eps) > 0 -> eps = 0;
+// otherwise dgamma = |dev eps| + (3 lam + 2 mu) / (2 mu) alpha tr(eps) > 0 is
+// removed from |dev eps| along dev eps.  F with a non-positive singular value
+// is left unchanged.
+template <typename T>
+__device__ void return_map(int kind, double mu_, double lam_, double ys, double alpha_, T F[9]) {
+  T H[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) H[i] = F[i] - ((i % 4 == 0) ? T(1) : T(0));
+  T U[9], s[3], e[3], V[9], Jm1;
+  svd_from_h<T>(H, U, s, e, V, Jm1);
+  if (!(s[0] > T(0) && s[1] > T(0) && s[2] > T(0))) return;
+  T eps[3] = {log1p(e[0]), log1p(e[1]), log1p(e[2])};
+  const T mu = (T)mu_, lam = (T)lam_;
+  const T tr = eps[0] + eps[1] + eps[2];
+  const T d[3] = {eps[0] - tr / T(3), eps[1] - tr / T(3), eps[2] - tr / T(3)};
+  const T dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (kind == MPML_VON_MISES) {
+    const T lim = (T)(sqrt(2.0 / 3.0) * ys / (2.0 * mu_));
+    if (dn <= lim) return;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) eps[i] = tr / T(3) + d[i] * (lim / dn);
+  } else if (kind == MPML_DRUCKER_PRAGER) {
+    if (tr > T(0)) {
+      eps[0] = eps[1] = eps[2] = T(0);
+    } else {
+      const T dg = dn + (T(3) * lam + T(2) * mu) / (T(2) * mu) * tr * (T)alpha_;
+      if (dg <= T(0)) return;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) eps[i] -= dg * d[i] / dn;
+    }
+  } else {
+    return;
+  }
+  const T ex[3] = {exp(eps[0]), exp(eps[1]), exp(eps[2])};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[3 * r + c] = U[3 * r] * ex[0] * V[3 * c] + U[3 * r + 1] * ex[1] * V[3 * c + 1] +
+                                               U[3 * r + 2] * ex[2] * V[3 * c + 2];
+}
 
 __device__ __forceinline__ void base_of(const double xa[3], double inv_dx, int b[3], double f[3]) {
 #pragma unroll
@@ -315,7 +363,7 @@ __global__ void __launch_bounds__(256) k_g2p(int64_t np, const T* __restrict__ x
     for (int q = 0; q < 9; ++q) Gp[q] += w * src[(3 + q) * BV];
   }
   const T dt = (T)xi.dt;
-  T Fp[9];
+  T Fp[9], Fn[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) Fp[i] = Fs[9 * p + i];
 #pragma unroll
@@ -325,8 +373,13 @@ __global__ void __launch_bounds__(256) k_g2p(int64_t np, const T* __restrict__ x
       T acc = Fp[3 * r + cc];
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc += dt * Gp[3 * r + k] * Fp[3 * k + cc];
-      Fo[9 * p + 3 * r + cc] = acc;
+      Fn[3 * r + cc] = acc;
     }
+  const int km = mats[p];
+  if (km >= 0 && km < xi.nm && xi.plastic[km] != MPML_ELASTIC)
+    return_map<T>(xi.plastic[km], xi.mat[km].mu, xi.mat[km].lam, xi.ys[km], xi.alpha[km], Fn);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Fo[9 * p + i] = Fn[i];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     xo[3 * p + a] = xs[3 * p + a] + dt * vp[a];
@@ -355,6 +408,10 @@ static XferInfo xfer_info(mpml_ctx_s* c) {
     xi.mat[k].model = m.model;
     xi.mat[k].mu = m.mu;
     xi.mat[k].lam = m.lambda;
+    xi.plastic[k] = k < c->nm ? m.plastic : MPML_ELASTIC;
+    xi.ys[k] = m.yield_stress;
+    const double sp = sin(m.friction_angle);
+    xi.alpha[k] = sqrt(2.0 / 3.0) * 2.0 * sp / (3.0 - sp);
   }
   return xi;
 }

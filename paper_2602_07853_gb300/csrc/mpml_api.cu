@@ -21,6 +21,10 @@ bool bad_desc(const mpml_scene_desc* d, const mpml_material* mats, int n_mats) {
   for (int k = 0; k < n_mats; ++k) {
     if (mats[k].model < 0 || mats[k].model > 2) return true;
     if (!(mats[k].mu > 0)) return true;
+    if (mats[k].plastic < MPML_ELASTIC || mats[k].plastic > MPML_DRUCKER_PRAGER) return true;
+    if (mats[k].plastic == MPML_VON_MISES && !(mats[k].yield_stress >= 0)) return true;
+    if (mats[k].plastic == MPML_DRUCKER_PRAGER && !(mats[k].friction_angle >= 0 && mats[k].friction_angle < 1.5707963))
+      return true;
   }
   // P2Q shared-memory accumulators: 729 centres x (13 + 7 n_mats) fields
   const size_t es = d->precision == MPML_FP64 ? 8 : 4;

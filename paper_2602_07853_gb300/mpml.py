@@ -21,6 +21,7 @@ ERR_ARG, ERR_OUT_OF_DOMAIN, ERR_NONFINITE, ERR_STRETCH, ERR_TIMEOUT, ERR_CUDA, E
 ERR_TOO_LARGE = -8
 NOALLOC_MAX_SLOTS = 1 << 21
 FIXED_COROTATED, NEO_HOOKEAN, HENCKY = 0, 1, 2
+ELASTIC, VON_MISES, DRUCKER_PRAGER = 0, 1, 2
 FP32, FP64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
@@ -31,7 +32,8 @@ F_NODE_MASS, F_NODE_VEL, F_NODE_VHAT, F_NODE_FIXED, F_NODE_VNEW = 10, 11, 12, 13
 
 
 class mpml_material(C.Structure):
-    _fields_ = [("model", C.c_int), ("mu", C.c_double), ("lambda_", C.c_double)]
+    _fields_ = [("model", C.c_int), ("mu", C.c_double), ("lambda_", C.c_double), ("plastic", C.c_int),
+                ("yield_stress", C.c_double), ("friction_angle", C.c_double)]
 
 
 class mpml_scene_desc(C.Structure):
@@ -292,9 +294,10 @@ def scene_desc(n, dx, dt, gravity=(0.0, -9.8, 0.0), precision=FP32, wall_layers=
     return d
 
 
-def material(model, mu, lam):
+def material(model, mu, lam, plastic=ELASTIC, yield_stress=0.0, friction_angle=0.0):
     m = mpml_material()
     m.model, m.mu, m.lambda_ = int(model), float(mu), float(lam)
+    m.plastic, m.yield_stress, m.friction_angle = int(plastic), float(yield_stress), float(friction_angle)
     return m
 
 

@@ -22,6 +22,7 @@ from typing import List, Optional, Tuple
 import numpy as np
 
 FIXED_COROTATED, NEO_HOOKEAN, HENCKY = 0, 1, 2
+ELASTIC, VON_MISES, DRUCKER_PRAGER = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -30,6 +31,9 @@ class Material:
     E: float
     nu: float
     rho: float = 1000.0
+    plastic: int = ELASTIC
+    yield_stress: float = 0.0
+    friction_angle: float = 0.0  # radians
 
 
 @dataclasses.dataclass
@@ -167,6 +171,33 @@ def pressed_block(n: int = 128, seed: int = 3, ppc: int = 8) -> Scene:
     hi = ((x0 + wx) * dx, top + 2 * dx, (x0 + wx) * dx)
     sc.plate = (lo, hi, (0.0, -0.1, 0.0))
     return _finish(sc, x, np.zeros_like(x), np.zeros(len(x), np.int64), ppc)
+
+
+def slab_on_sand(n: int = 256, seed: int = 5, ppc: int = 8, dt: float = 2e-3) -> Scene:
+    """A von Mises slab dropped onto a Drucker-Prager sand box (Hencky elasticity).
+    Slab 0.6 x 0.1 x 0.6 at x, z in [0.35, 0.95], y in [0.5, 0.6] (E = 5e5, nu = 0.3,
+    yield stress 2e3, rho = 1000); sand box 0.55 x 0.35 x 0.55 at x, z in [0.05, 0.6],
+    y in [1/256, 0.35 + 1/256] (E = 1e6, nu = 0.3, friction angle 30 degrees, rho = 2000).
+    Box edges are snapped to the voxel grid of size 1/n."""
+    dx = 1.0 / n
+    sc = Scene(f"slab_on_sand_{n}", (n, n, n), dx, float(n), dt, (0.0, -9.8, 0.0),
+               [Material(HENCKY, 5e5, 0.3, 1000.0, VON_MISES, 2e3, 0.0),
+                Material(HENCKY, 1e6, 0.3, 2000.0, DRUCKER_PRAGER, 0.0, float(np.radians(30.0)))])
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def box(lo, hi):
+        a = [int(round(v * n)) for v in lo]
+        b = [int(round(v * n)) for v in hi]
+        return _grid_voxels(a, b)
+
+    y0 = 1.0 / 256
+    slab = box((0.35, 0.5, 0.35), (0.95, 0.6, 0.95))
+    sand = box((0.05, max(y0, 1.0 / n), 0.05), (0.6, 0.35 + y0, 0.6))
+    xs = seed_voxels(slab, dx, ppc, rng)
+    xb = seed_voxels(sand, dx, ppc, rng)
+    x = np.concatenate([xs, xb])
+    mat = np.concatenate([np.zeros(len(xs), np.int64), np.ones(len(xb), np.int64)])
+    return _finish(sc, x, np.zeros_like(x), mat, ppc)
 
 
 def colliding_cubes(n: int = 64, seed: int = 6, ppc: int = 8, speed: float = 1.0) -> Scene:

@@ -23,7 +23,8 @@ class GpuSim:
         self.prec = precision
         self.npdt = NP_DTYPE[precision]
         desc = m.scene_desc(sc.n, sc.dx, sc.dt, sc.gravity, precision, sc.wall_layers, sc.plate, sc.inv_dx)
-        self.mats = [m.material(mt.model, *m.lame_parameters(mt.E, mt.nu)) for mt in sc.materials]
+        self.mats = [m.material(mt.model, *m.lame_parameters(mt.E, mt.nu), mt.plastic, mt.yield_stress,
+                                mt.friction_angle) for mt in sc.materials]
         self.stream = torch.cuda.current_stream()
         self.ctx = m.mpml_create(desc, self.mats, self.stream.cuda_stream)
         self.t = None

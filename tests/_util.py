@@ -7,7 +7,8 @@ from paper_2602_07853_gb300 import scenes
 
 def oracle_scene(sc: scenes.Scene, time=0.0):
     return oracle.make_scene(sc.n, sc.dx, sc.dt, sc.gravity,
-                             [(m.model, m.E, m.nu) for m in sc.materials],
+                             [(m.model, m.E, m.nu, m.plastic, m.yield_stress, m.friction_angle)
+                              for m in sc.materials],
                              wall_layers=sc.wall_layers, plate=sc.plate, inv_dx=sc.inv_dx, time=time)
 
 
