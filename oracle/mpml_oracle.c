@@ -1005,9 +1005,11 @@ int orc_pcg(const orc_state* st, const double* b, double* x, double rtol, int ma
   return it;
 }
 
-/* Newton on Phi(v) (Algorithm 3 line 12), x0 = vhat with Dirichlet values.
- * Stop when ||g|| <= max(newton_rtol ||g(v0)||, newton_atol); Jacobi-PCG to
- * cg_rtol; Armijo backtracking by halving. */
+/* Newton on Phi(v) (Algorithm 3), x0 = vhat with Dirichlet values.
+ * Stop when ||g|| <= max(newton_rtol ||g(v0)||, newton_atol, 1e-12 ||M vhat||)
+ * (the last term is the rounding level of the gradient: a body at rest or in
+ * free fall starts at g(v0) = 0 up to rounding, which the relative test cannot
+ * reduce further); Jacobi-PCG to cg_rtol; Armijo backtracking by halving. */
 int orc_newton(orc_state* st, const orc_solver* opt, orc_stats* stats) {
   long n = 3 * st->nn;
   double* v = st->vnew;
@@ -1022,11 +1024,16 @@ int orc_newton(orc_state* st, const orc_solver* opt, orc_stats* stats) {
   double phi;
   orc_eval(st, v, &phi, g);
   double g0 = sqrt(dot(n, g, g)), gn = g0;
+  double mv2 = 0;
+  for (long i = 0; i < st->nn; ++i)
+    if (!st->fixed[i])
+      for (int r = 0; r < 3; ++r) mv2 += (st->m_i[i] * st->vhat[3 * i + r]) * (st->m_i[i] * st->vhat[3 * i + r]);
+  const double gfloor = 1e-12 * sqrt(mv2);
   stats->g0_norm = g0;
   stats->phi0 = phi;
   int status = ORC_OK, it = 0;
   while (1) {
-    if (gn <= opt->newton_rtol * g0 || gn <= opt->newton_atol) break;
+    if (gn <= opt->newton_rtol * g0 || gn <= opt->newton_atol || gn <= gfloor) break;
     if (it >= opt->newton_max) { status = ORC_WARN_NOT_CONVERGED; break; }
     if (orc_linearize(st, v, 1)) { status = ORC_ERR_NONFINITE; break; }
     for (long i = 0; i < n; ++i) rhs[i] = -g[i];
