@@ -129,7 +129,9 @@ typedef struct {
   double cg_rtol;      /* stop CG when ||r|| <= cg_rtol ||r0|| (default 1e-6) */
   int cg_max;          /* CG iteration cap per Newton iteration */
   double newton_rtol;  /* stop Newton when ||g|| <= newton_rtol ||g(v0)|| */
-  double newton_atol;  /* ... or when ||g|| <= newton_atol */
+  double newton_atol;  /* ... or when ||g|| <= newton_atol (and always when ||g|| <= 1e-12 ||M vhat||,
+                          the rounding level of the gradient: a body at rest or in free fall
+                          starts from g(v0) = 0 up to rounding) */
   int newton_max;      /* Newton iteration cap */
   double ls_c1;        /* Armijo constant */
   int ls_max;          /* maximal number of step halvings */
@@ -176,6 +178,17 @@ int mpml_resample(mpml_ctx ctx, const mpml_particles* p);
 /* Algorithm 3, implicit.  Synchronises (convergence tests); fills stats if
  * non-NULL.  opts may be NULL (defaults). */
 int mpml_newton_step(mpml_ctx ctx, const mpml_solver_opts* opts, mpml_solve_stats* stats);
+/* Algorithm 3 for a batch of independent scenes (one context each, already
+ * resampled; FP32 single-material contexts sharing one CUDA stream; at most
+ * MPML_BATCH_MAX).  Each scene follows exactly the Newton / Jacobi-PCG / line-
+ * search logic of mpml_newton_step with its own tolerances and iteration
+ * counts, but the scenes advance in lockstep and every round of their CG
+ * solves is one persistent cooperative launch over all active scenes' bricks
+ * (per-scene scalars and FP64 sums).  stats: array of n (may be NULL).
+ * Scratch of the batch lives in ctxs[0].  Synchronises; returns the first
+ * error, else MPML_WARN_NOT_CONVERGED if any scene did not converge. */
+#define MPML_BATCH_MAX 128
+int mpml_newton_step_batch(mpml_ctx* ctxs, int n, const mpml_solver_opts* opts, mpml_solve_stats* stats);
 /* Algorithm 4.  Writes x, v, F, G, mass, volume, mat of p (the same arrays
  * or others of the same size) in the sorted order of the last resample.
  * Asynchronous for device memory; for MPML_MEM_HOST it synchronises after

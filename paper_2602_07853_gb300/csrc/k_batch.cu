@@ -1,0 +1,624 @@
+// Batched implicit solve: the Newton iterations of many independent scenes
+// (one library context each, FP32 single-material, one shared stream) run in
+// lockstep, and every round of their Jacobi-PCG solves is ONE persistent
+// cooperative launch over the union of the scenes' bricks.
+//
+// Each scene keeps its own scalars (alpha, beta, r.z, tolerance, iteration
+// count, convergence flag): a CTA looks the scene up per work item (cell brick,
+// node-only brick, node brick), the per-scene sums of every phase are added
+// atomically into per-scene FP64 accumulators, and after each bounded grid
+// barrier every CTA updates the scalars of all scenes identically.  Scenes that
+// converged skip their bricks; the launch ends when every scene has.  The
+// Newton logic per scene (convergence test, Armijo line search, update) is the
+// one of mpml_newton_step, evaluated for all active scenes with one host
+// synchronisation per stage instead of one per scene.
+#include <algorithm>
+#include <vector>
+
+#include "mpml_internal.cuh"
+
+namespace mpml {
+
+// pieces of the single-scene solver (k_newton.cu)
+int batch_alloc_solver(mpml_ctx_s* c);
+int batch_prep(mpml_ctx_s* c, double cg_rtol, int cg_max);
+void batch_slope_launch(mpml_ctx_s* c);
+void batch_energy_launch(mpml_ctx_s* c, double alpha);
+void batch_axpy_launch(mpml_ctx_s* c, double alpha);
+
+struct BScene {
+  const int* cblist;
+  const int* nolist;
+  const int* nbr;
+  const uint8_t* cflag;
+  const float* C;
+  const float* m;
+  const float* dinv;
+  float* x;
+  float* r;
+  float* pa;
+  float* pb;
+  float* q;
+  DevScalars* sc;
+  int ncb, nnob, nb, pad;
+};
+
+constexpr int BATCH_MAX = MPML_BATCH_MAX;
+constexpr unsigned BC_BYTES = 27u * BV * 4u;  // 27-number tangents of one brick
+constexpr size_t BC_SMEM = BC_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
+
+__device__ __forceinline__ double bwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block sums of (a, b) added atomically to acc[0..1] (thread 0)
+__device__ __forceinline__ void bblock_atomic2(float a_, float b_, double* acc) {
+  __shared__ double red[2][32];
+  double a = bwarp_sum((double)a_), b = bwarp_sum((double)b_);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += red[0][w];
+      sb += red[1][w];
+    }
+    if (sa != 0.0) atomicAdd(acc, sa);
+    if (sb != 0.0) atomicAdd(acc + 1, sb);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool bgrid_barrier(unsigned* gbar, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gbar + 1;
+    const unsigned g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
+      gbar[0] = 0;
+      __threadfence();
+      atomicAdd(gbar + 1, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*vgen == g) {
+        if (++spins > (1u << 25)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+__device__ __forceinline__ unsigned bsmem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool bmbar_wait(uint64_t* bar, unsigned phase) {
+  const unsigned a = bsmem_u32(bar);
+  for (unsigned it = 0; it < (1u << 24); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// D' = sum_o p_o (x) sgn_o over the 8 corners of local cell l
+__device__ __forceinline__ void bgather_D(int l, const float (*sv)[729], float D[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) D[q] = 0.f;
+  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int i = ((lz + ((o >> 2) & 1)) * 9 + (ly + ((o >> 1) & 1))) * 9 + (lx + (o & 1));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float pa = sv[a][i];
+      D[3 * a + 0] += (o & 1) ? pa : -pa;
+      D[3 * a + 1] += (o & 2) ? pa : -pa;
+      D[3 * a + 2] += (o & 4) ? pa : -pa;
+    }
+  }
+}
+
+struct BatchArgs {
+  const BScene* scenes;
+  const int2* cw;  // (scene, cell brick index) work items
+  const int2* nw;  // (scene, node-only brick index)
+  const int2* aw;  // (scene, brick) for the vector update
+  int ncw, nnw, naw, nsc;
+  double* acc;     // [4][nsc][2] rotating per-scene accumulators
+  unsigned* gbar;
+  int cg_max;
+  int* status;
+};
+
+__global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
+  extern __shared__ __align__(128) unsigned char psm[];
+  float* Cs = reinterpret_cast<float*>(psm);
+  float (*sv)[729] = reinterpret_cast<float (*)[729]>(psm + BC_BYTES);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(psm + BC_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  __shared__ int s_nbr[NBR];
+  __shared__ int s_flag, s_alldone;
+  __shared__ double s_rz[BATCH_MAX], s_tol2[BATCH_MAX], s_rr[BATCH_MAX];
+  __shared__ float s_alpha[BATCH_MAX], s_beta[BATCH_MAX];
+  __shared__ int s_done[BATCH_MAX], s_it[BATCH_MAX];
+  __shared__ unsigned char s_flip[BATCH_MAX];  // p ping-pong parity per scene
+  const int S = A.nsc, G = gridDim.x;
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    const DevScalars* d = A.scenes[s].sc;
+    s_rz[s] = d->rz;
+    s_tol2[s] = d->tol2;
+    s_rr[s] = d->rr_last;
+    s_done[s] = d->done;
+    s_it[s] = 0;
+    s_alpha[s] = 0.f;
+    s_beta[s] = 0.f;
+    s_flip[s] = 0;
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bsmem_u32(bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned tma_phase = 0;
+  bool alive = true;
+  int round = 0;
+  while (alive) {
+    if (threadIdx.x == 0) {
+      int all = 1;
+      for (int s = 0; s < S; ++s) all &= s_done[s];
+      s_alldone = all;
+    }
+    __syncthreads();
+    if (s_alldone) break;
+    double* accH = A.acc + (size_t)2 * S * ((2 * round) & 3);
+    double* accA = A.acc + (size_t)2 * S * ((2 * round + 1) & 3);
+    if (blockIdx.x == 0) {  // slot of phase 2 round + 2, last read two barriers ago
+      double* z = A.acc + (size_t)2 * S * ((2 * round + 2) & 3);
+      for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) z[i] = 0.0;
+    }
+    // ---------------- phase H: p update (staged) and HVP ----------------
+    for (int w = blockIdx.x; w < A.ncw; w += G) {
+      const int2 item = A.cw[w];
+      const int s = item.x;
+      if (s_done[s]) continue;
+      const BScene& B = A.scenes[s];
+      const float beta = s_beta[s];
+      const float* pold = s_flip[s] ? B.pb : B.pa;
+      float* pnext = s_flip[s] ? B.pa : B.pb;
+      const int id = B.cblist[item.y];
+      if (threadIdx.x < NBR) s_nbr[threadIdx.x] = B.nbr[id * NBR + threadIdx.x];
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bsmem_u32(bar)), "r"(BC_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                bsmem_u32(Cs)),
+            "l"(B.C + (int64_t)id * 27 * BV), "r"(BC_BYTES), "r"(bsmem_u32(bar))
+            : "memory");
+      }
+      float pmp = 0.f, pkp = 0.f;
+      for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+        const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+        const int t = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+        const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+        float v[3] = {0.f, 0.f, 0.f};
+        if (t >= 0) {
+          const int64_t o = (int64_t)t * 3 * BV + l;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float di = __ldcg(B.dinv + o + a * BV);
+            v[a] = di > 0.f ? di * __ldcg(B.r + o + a * BV) + beta * __ldcg(pold + o + a * BV) : 0.f;
+          }
+          if (t == id) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) pnext[o + a * BV] = v[a];
+            pmp += __ldcg(B.m + (int64_t)id * BV + l) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          }
+        }
+        sv[0][i] = v[0];
+        sv[1][i] = v[1];
+        sv[2][i] = v[2];
+      }
+      __syncthreads();
+      const bool ok = bmbar_wait(bar, tma_phase);
+      tma_phase ^= 1u;
+      if (!ok && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+      float KD[2][9];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int l = threadIdx.x + h * 256;
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr) KD[h][rr] = 0.f;
+        if (ok && B.cflag[(int64_t)id * BV + l]) {
+          float D[9], c[27];
+          bgather_D(l, sv, D);
+#pragma unroll
+          for (int q = 0; q < 27; ++q) c[q] = Cs[q * BV + l];
+          apply_c27(c, D, KD[h]);
+#pragma unroll
+          for (int rr = 0; rr < 9; ++rr) pkp += D[rr] * KD[h][rr];
+        }
+      }
+      __syncthreads();
+      float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(Cs);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int rr = 0; rr < 9; ++rr) skd[rr][threadIdx.x + h * 256] = KD[h][rr];
+      __syncthreads();
+      for (int i = threadIdx.x; i < 729; i += blockDim.x) {
+        const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+        float y[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          const int cx = nx - (o & 1), cy = ny - ((o >> 1) & 1), cz = nz - ((o >> 2) & 1);
+          if (cx < 0 || cy < 0 || cz < 0 || cx > 7 || cy > 7 || cz > 7) continue;
+          const int cc = (cz * 8 + cy) * 8 + cx;
+          const float s0 = (o & 1) ? 1.f : -1.f, s1 = (o & 2) ? 1.f : -1.f, s2 = (o & 4) ? 1.f : -1.f;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) y[a] += skd[3 * a][cc] * s0 + skd[3 * a + 1][cc] * s1 + skd[3 * a + 2][cc] * s2;
+        }
+        const bool own = nx < 8 && ny < 8 && nz < 8;
+        const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
+        if (own) {
+          const int l = nz * 64 + ny * 8 + nx;
+          const float mi = B.m[(int64_t)id * BV + l];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            float* dst = B.q + (int64_t)id * 3 * BV + a * BV + l;
+            const float val = y[a] + mi * sv[a][i];
+            if (excl) *dst = val;
+            else if (val != 0.f) atomicAdd(dst, val);
+          }
+        } else {
+          const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+          if (t < 0) continue;
+          const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (y[a] != 0.f) atomicAdd(B.q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
+        }
+      }
+      bblock_atomic2(pmp, pkp, accH + 2 * s);  // ends with a barrier: Cs / sv / s_nbr free
+    }
+    // node-only bricks: p_new and the mass term
+    for (int w = blockIdx.x; w < A.nnw; w += G) {
+      const int2 item = A.nw[w];
+      const int s = item.x;
+      if (s_done[s]) continue;
+      const BScene& B = A.scenes[s];
+      const float beta = s_beta[s];
+      const float* pold = s_flip[s] ? B.pb : B.pa;
+      float* pnext = s_flip[s] ? B.pa : B.pb;
+      const int id = B.nolist[item.y];
+      float pmp = 0.f;
+      for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+        const int64_t o = (int64_t)id * 3 * BV + l;
+        const float mi = B.m[(int64_t)id * BV + l];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float di = B.dinv[o + a * BV];
+          const float v = di > 0.f ? di * B.r[o + a * BV] + beta * pold[o + a * BV] : 0.f;
+          pnext[o + a * BV] = v;
+          pmp += mi * v * v;
+          if (v != 0.f) atomicAdd(B.q + o + a * BV, mi * v);
+        }
+      }
+      bblock_atomic2(pmp, 0.f, accH + 2 * s);
+    }
+    if (!bgrid_barrier(A.gbar, &s_flag)) {
+      alive = false;
+      break;
+    }
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      if (s_done[s]) continue;
+      const double pq = __ldcg(accH + 2 * s) + __ldcg(accH + 2 * s + 1);
+      if (!(pq > 0.0)) {
+        s_done[s] = 1;  // breakdown: keep the current iterate
+        s_alpha[s] = 0.f;
+      } else {
+        s_alpha[s] = (float)(s_rz[s] / pq);
+      }
+    }
+    __syncthreads();
+    // ---------------- phase A: x, r update and the new dots ----------------
+    // slot of phase 2 round + 3 was last read before the barrier just passed
+    if (blockIdx.x == 0) {
+      double* z = A.acc + (size_t)2 * S * ((2 * round + 3) & 3);
+      for (int i = threadIdx.x; i < 2 * S; i += blockDim.x) z[i] = 0.0;
+    }
+    for (int w = blockIdx.x; w < A.naw; w += G) {
+      const int2 item = A.aw[w];
+      const int s = item.x;
+      if (s_done[s]) continue;
+      const BScene& B = A.scenes[s];
+      const float alpha = s_alpha[s];
+      const float* pn = s_flip[s] ? B.pa : B.pb;
+      float rzl = 0.f, rrl = 0.f;
+      for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int64_t o = ((int64_t)item.y * 3 + a) * BV + l;
+          const float d = __ldcg(B.dinv + o);
+          float x = __ldcg(B.x + o), r = __ldcg(B.r + o);
+          if (d > 0.f) {
+            x += alpha * __ldcg(pn + o);
+            r -= alpha * __ldcg(B.q + o);
+            rzl += r * d * r;
+            rrl += r * r;
+          }
+          B.x[o] = x;
+          B.r[o] = r;
+          B.q[o] = 0.f;
+        }
+      }
+      bblock_atomic2(rzl, rrl, accA + 2 * s);
+    }
+    if (!bgrid_barrier(A.gbar, &s_flag)) {
+      alive = false;
+      break;
+    }
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      if (s_done[s]) continue;
+      const double rzn = __ldcg(accA + 2 * s), rrn = __ldcg(accA + 2 * s + 1);
+      const int it = ++s_it[s];
+      s_rr[s] = rrn;
+      if (rrn <= s_tol2[s] || it >= A.cg_max || !(rrn == rrn)) s_done[s] = 1;
+      s_beta[s] = (float)(rzn / s_rz[s]);
+      s_rz[s] = rzn;
+      s_flip[s] ^= 1;
+    }
+    __syncthreads();
+    ++round;
+  }
+  if (!alive && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+  if (blockIdx.x == 0)
+    for (int s = threadIdx.x; s < S; s += blockDim.x) {
+      DevScalars* d = A.scenes[s].sc;
+      d->iters = s_it[s];
+      d->rr_last = s_rr[s];
+      d->rz = s_rz[s];
+      d->done = 1;
+    }
+}
+
+namespace {
+
+int read_all(const std::vector<mpml_ctx_s*>& cs) {
+  if (cs.empty()) return MPML_OK;
+  cudaStream_t s = cs[0]->s;
+  for (mpml_ctx_s* c : cs) {
+    cudaMemcpyAsync(c->hscal, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(c->hstatus, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+  }
+  return cuda_status(cudaStreamSynchronize(s));
+}
+
+int pcg_batch(mpml_ctx_s* owner, const std::vector<mpml_ctx_s*>& cs, int cg_max) {
+  static int max_blocks = -1;
+  if (max_blocks < 0) {
+    cudaFuncSetAttribute(k_pcg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BC_SMEM);
+    int per_sm = 0, nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batch, 256, BC_SMEM) != cudaSuccess) per_sm = 0;
+    max_blocks = per_sm * nsm;
+  }
+  if (max_blocks <= 0) return MPML_ERR_CUDA;
+  const int S = (int)cs.size();
+  std::vector<BScene> sc(S);
+  std::vector<int2> cw, nw, aw;
+  for (int i = 0; i < S; ++i) {
+    mpml_ctx_s* c = cs[i];
+    BScene& b = sc[i];
+    b.cblist = (const int*)c->cblist.p;
+    b.nolist = (const int*)c->nolist.p;
+    b.nbr = (const int*)c->nbr.p;
+    b.cflag = (const uint8_t*)c->cflag.p;
+    b.C = (const float*)c->cK.p;
+    b.m = (const float*)c->nmass.p;
+    b.dinv = (const float*)c->ndinv.p;
+    b.x = (float*)c->nx.p;
+    b.r = (float*)c->nr.p;
+    b.pa = (float*)c->np.p;
+    b.pb = (float*)c->np2.p;
+    b.q = (float*)c->nq.p;
+    b.sc = (DevScalars*)c->scal.p;
+    b.ncb = (int)c->ncb;
+    b.nnob = (int)c->nnob;
+    b.nb = (int)c->nb;
+    b.pad = 0;
+    for (int j = 0; j < (int)c->ncb; ++j) cw.push_back(make_int2(i, j));
+    for (int j = 0; j < (int)c->nnob; ++j) nw.push_back(make_int2(i, j));
+    for (int j = 0; j < (int)c->nb; ++j) aw.push_back(make_int2(i, j));
+  }
+  // interleave the scenes' cell bricks so that uneven scenes spread over all CTAs
+  std::stable_sort(cw.begin(), cw.end(), [&](const int2& a, const int2& b) { return a.y < b.y; });
+  const size_t bytes_sc = sizeof(BScene) * S, bytes_w = sizeof(int2) * (cw.size() + nw.size() + aw.size());
+  const size_t acc_bytes = sizeof(double) * 8 * S;
+  const size_t off_w = (bytes_sc + 255) & ~size_t(255);
+  const size_t off_acc = (off_w + bytes_w + 255) & ~size_t(255);
+  const size_t off_bar = off_acc + acc_bytes;
+  int rc;
+  if ((rc = ensure(owner->bbatch, off_bar + 16))) return rc;
+  char* base = (char*)owner->bbatch.p;
+  std::vector<char> host(off_acc);
+  memcpy(host.data(), sc.data(), bytes_sc);
+  int2* hw = reinterpret_cast<int2*>(host.data() + off_w);
+  std::copy(cw.begin(), cw.end(), hw);
+  std::copy(nw.begin(), nw.end(), hw + cw.size());
+  std::copy(aw.begin(), aw.end(), hw + cw.size() + nw.size());
+  cudaStream_t s = owner->s;
+  cudaMemcpyAsync(base, host.data(), off_acc, cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(base + off_acc, 0, acc_bytes + 16, s);
+  for (mpml_ctx_s* c : cs) {
+    // q starts at zero (phase A zeroes it after each use)
+    cudaMemsetAsync(c->nq.p, 0, sizeof(float) * 3 * c->nb * BV, s);
+  }
+  BatchArgs a;
+  a.scenes = reinterpret_cast<const BScene*>(base);
+  a.cw = reinterpret_cast<const int2*>(base + off_w);
+  a.nw = a.cw + cw.size();
+  a.aw = a.nw + nw.size();
+  a.ncw = (int)cw.size();
+  a.nnw = (int)nw.size();
+  a.naw = (int)aw.size();
+  a.nsc = S;
+  a.acc = reinterpret_cast<double*>(base + off_acc);
+  a.gbar = reinterpret_cast<unsigned*>(base + off_bar);
+  a.cg_max = cg_max;
+  a.status = (int*)owner->status.p;
+  void* args[] = {&a};
+  rc = cuda_status(cudaLaunchCooperativeKernel((const void*)k_pcg_batch, dim3(max_blocks), dim3(256), args, BC_SMEM, s));
+  owner->launches++;
+  return rc;
+}
+
+}  // namespace
+
+int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve_stats* st) {
+  int rc;
+  std::vector<mpml_ctx_s*> all(ctxs, ctxs + n);
+  std::vector<int> it(n, 0), status(n, MPML_OK), active(n, 0);
+  std::vector<double> g0(n, 0.0), gn(n, 0.0), phi(n, 0.0), gfloor(n, 0.0);
+  mpml_ctx_s* owner = ctxs[0];
+  std::vector<mpml_ctx_s*> work;
+  for (int i = 0; i < n; ++i) {
+    memset(&st[i], 0, sizeof(mpml_solve_stats));
+    mpml_ctx_s* c = ctxs[i];
+    st[i].n_particles = c->np_count;
+    st[i].n_bricks = c->nb;
+    if ((rc = batch_alloc_solver(c))) return rc;
+    if (c->nb == 0) continue;
+    if ((rc = batch_prep(c, o->cg_rtol, o->cg_max))) return rc;
+    work.push_back(c);
+    active[i] = 1;
+  }
+  if ((rc = read_all(work))) return rc;
+  for (int i = 0; i < n; ++i) {
+    if (!active[i]) continue;
+    mpml_ctx_s* c = ctxs[i];
+    if (*c->hstatus & ST_NONFINITE) return MPML_ERR_NONFINITE;
+    g0[i] = gn[i] = sqrt(c->hscal->gg);
+    gfloor[i] = 1e-12 * sqrt(c->hscal->mv2);
+    phi[i] = c->hscal->phi_in + c->hscal->phi_el;
+    st[i].g0_norm = g0[i];
+    st[i].phi0 = phi[i];
+  }
+  while (true) {
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i) {
+      if (!active[i]) continue;
+      if (gn[i] <= o->newton_rtol * g0[i] || gn[i] <= o->newton_atol || gn[i] <= gfloor[i]) {
+        active[i] = 0;
+        continue;
+      }
+      if (it[i] >= o->newton_max) {
+        status[i] = MPML_WARN_NOT_CONVERGED;
+        active[i] = 0;
+        continue;
+      }
+      idx.push_back(i);
+    }
+    if (idx.empty()) break;
+    std::vector<mpml_ctx_s*> cs;
+    for (int i : idx) cs.push_back(ctxs[i]);
+    // one cooperative launch for every active scene's Jacobi-PCG solve
+    if ((rc = pcg_batch(owner, cs, o->cg_max))) return rc;
+    if ((rc = read_all(cs))) return rc;
+    for (int i : idx) {
+      mpml_ctx_s* c = ctxs[i];
+      const int k = it[i];
+      const double rr0 = c->hscal->rr0;
+      if (k < 64) {
+        st[i].cg_iters[k] = c->hscal->iters;
+        st[i].cg_rel_resid[k] = rr0 > 0 ? sqrt(c->hscal->rr_last / rr0) : 0.0;
+      }
+      st[i].cg_iters_total += c->hscal->iters;
+      batch_slope_launch(c);
+    }
+    if ((rc = read_all(cs))) return rc;
+    std::vector<double> slope(n), alpha(n, 1.0);
+    std::vector<int> accepted(n, 0);
+    for (int i : idx) slope[i] = ctxs[i]->hscal->slope;
+    for (int ls = 0; ls <= o->ls_max; ++ls) {
+      std::vector<mpml_ctx_s*> pend;
+      std::vector<int> pidx;
+      for (int i : idx)
+        if (!accepted[i]) {
+          batch_energy_launch(ctxs[i], alpha[i]);
+          pend.push_back(ctxs[i]);
+          pidx.push_back(i);
+        }
+      if (pend.empty()) break;
+      if ((rc = read_all(pend))) return rc;
+      for (int i : pidx) {
+        const mpml_ctx_s* c = ctxs[i];
+        const double pt = c->hscal->phi_in + c->hscal->phi_el;
+        if (c->hscal->infeasible == 0 && pt <= phi[i] + o->ls_c1 * alpha[i] * slope[i])
+          accepted[i] = 1;
+        else
+          alpha[i] *= 0.5;
+      }
+    }
+    std::vector<mpml_ctx_s*> upd;
+    for (int i : idx) {
+      const int k = it[i]++;
+      if (k < 64) st[i].alpha[k] = accepted[i] ? alpha[i] : 0.0;
+      if (!accepted[i]) {
+        status[i] = MPML_WARN_NOT_CONVERGED;
+        active[i] = 0;
+        continue;
+      }
+      batch_axpy_launch(ctxs[i], alpha[i]);
+      if ((rc = batch_prep(ctxs[i], o->cg_rtol, o->cg_max))) return rc;
+      upd.push_back(ctxs[i]);
+    }
+    if ((rc = read_all(upd))) return rc;
+    for (int i : idx) {
+      if (!active[i]) continue;
+      const mpml_ctx_s* c = ctxs[i];
+      gn[i] = sqrt(c->hscal->gg);
+      phi[i] = c->hscal->phi_in + c->hscal->phi_el;
+    }
+  }
+  int worst = MPML_OK;
+  for (int i = 0; i < n; ++i) {
+    st[i].newton_iters = it[i];
+    st[i].g_norm = gn[i];
+    st[i].phi = phi[i];
+    st[i].status = status[i];
+    if (status[i] != MPML_OK) worst = status[i];
+  }
+  // device-side errors (timeouts, non-finite values) latched in any context
+  for (int i = 0; i < n; ++i) {
+    const int sw = *ctxs[i]->hstatus | *owner->hstatus;
+    if (sw & ST_TIMEOUT) return MPML_ERR_TIMEOUT;
+    if (sw & ST_NONFINITE) return MPML_ERR_NONFINITE;
+  }
+  return worst;
+}
+
+}  // namespace mpml

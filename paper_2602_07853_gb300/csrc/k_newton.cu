@@ -374,19 +374,6 @@ __device__ __forceinline__ void rot_to_quat(const double R[9], double q[4]) {
   for (int i = 0; i < 4; ++i) q[i] /= n;
 }
 
-// rotation matrix (row-major) of a unit quaternion (w, x, y, z)
-template <typename T>
-__device__ __forceinline__ void quat_to_rot(T w, T x, T y, T z, T R[9]) {
-  R[0] = T(1) - T(2) * (y * y + z * z);
-  R[1] = T(2) * (x * y - z * w);
-  R[2] = T(2) * (x * z + y * w);
-  R[3] = T(2) * (x * y + z * w);
-  R[4] = T(1) - T(2) * (x * x + z * z);
-  R[5] = T(2) * (y * z - x * w);
-  R[6] = T(2) * (x * z - y * w);
-  R[7] = T(2) * (y * z + x * w);
-  R[8] = T(1) - T(2) * (x * x + y * y);
-}
 
 // F - I = dt G + s + dt G s with S = I + s (symmetric, packed xx yy zz xy xz yz)
 __device__ __forceinline__ void trial_h(const double Gd[9], const double s6[6], double sm[9], double H[9]) {
@@ -533,7 +520,8 @@ __global__ void __launch_bounds__(512) k_node_init(const uint8_t* __restrict__ n
   const int id = blockIdx.x, l = threadIdx.x;
   const int64_t slot = (int64_t)id * BV + l;
   const bool dof = nflag[slot] & NF_DOF;
-  double ein = 0;
+  const bool free_ = dof && !(nflag[slot] & NF_FIXED);
+  double ein = 0, mv2 = 0;
   const double mi = dof ? (double)m[slot] : 0.0;
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -542,10 +530,11 @@ __global__ void __launch_bounds__(512) k_node_init(const uint8_t* __restrict__ n
     g[o] = mi * d;
     diag[o] = (T)mi;
     ein += 0.5 * mi * d * d;
+    if (free_) mv2 += (mi * vhat[o]) * (mi * vhat[o]);
   }
-  double vals[1] = {ein};
-  double* const dst[1] = {&sc->phi_in};
-  block_add<1>(vals, dst);
+  double vals[2] = {ein, mv2};
+  double* const dst[2] = {&sc->phi_in, &sc->mv2};
+  block_add<2>(vals, dst);
 }
 
 // pointer to a node slot addressed from a cell brick (local node 0..8 per axis)
@@ -890,56 +879,12 @@ __global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cbli
 constexpr unsigned HVP_C_BYTES = 27u * BV * 4u;
 constexpr size_t HVP_C_SMEM = HVP_C_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
 
+
 __device__ __forceinline__ void apply_compressed(const float* __restrict__ Cs, int l, const float D[9], float KD[9]) {
   float c[27];
 #pragma unroll
   for (int q = 0; q < 27; ++q) c[q] = Cs[q * BV + l];
-  float U[9], V[9], Qd[9];
-  quat_to_rot<float>(c[0], c[1], c[2], c[3], U);
-  quat_to_rot<float>(c[4], c[5], c[6], c[7], V);
-  quat_to_rot<float>(c[8], c[9], c[10], c[11], Qd);
-  const float sm[9] = {c[12], c[15], c[16], c[15], c[13], c[17], c[16], c[17], c[14]};
-  float W[9];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) W[3 * a + b] = V[3 * a + b] + sm[3 * a] * V[b] + sm[3 * a + 1] * V[3 + b] + sm[3 * a + 2] * V[6 + b];
-  // M = U^T D W
-  float T1[9], M[9];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) T1[3 * i + b] = U[i] * D[b] + U[3 + i] * D[3 + b] + U[6 + i] * D[6 + b];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) M[3 * i + j] = T1[3 * i] * W[j] + T1[3 * i + 1] * W[3 + j] + T1[3 * i + 2] * W[6 + j];
-  float Mt[9];
-  // diagonal block
-  float y[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) y[k] = c[18 + k] * (Qd[k] * M[0] + Qd[3 + k] * M[4] + Qd[6 + k] * M[8]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) Mt[4 * i] = Qd[3 * i] * y[0] + Qd[3 * i + 1] * y[1] + Qd[3 * i + 2] * y[2];
-  // pairs (0,1), (0,2), (1,2): flip (M_ij + M_ji)/sqrt2, twist (M_ij - M_ji)/sqrt2
-  const int PI[3] = {0, 0, 1}, PJ[3] = {1, 2, 2};
-#pragma unroll
-  for (int p = 0; p < 3; ++p) {
-    const int i = PI[p], j = PJ[p];
-    const float f = 0.5f * c[21 + p] * (M[3 * i + j] + M[3 * j + i]);
-    const float t = 0.5f * c[24 + p] * (M[3 * i + j] - M[3 * j + i]);
-    Mt[3 * i + j] = f + t;
-    Mt[3 * j + i] = f - t;
-  }
-  // K D' = U Mt W^T
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) T1[3 * a + j] = U[3 * a] * Mt[j] + U[3 * a + 1] * Mt[3 + j] + U[3 * a + 2] * Mt[6 + j];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) KD[3 * a + b] = T1[3 * a] * W[3 * b] + T1[3 * a + 1] * W[3 * b + 1] + T1[3 * a + 2] * W[3 * b + 2];
+  apply_c27(c, D, KD);
 }
 
 __global__ void __launch_bounds__(256, 3) k_hvp_c27(const int* __restrict__ cblist, const int* __restrict__ nbr,
@@ -2543,12 +2488,13 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
   if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max)) || (rc = read_scalars(c))) return rc;
   if (*c->hstatus & ST_NONFINITE) return MPML_ERR_NONFINITE;
   double g0 = sqrt(c->hscal->gg), gn = g0;
+  const double gfloor = 1e-12 * sqrt(c->hscal->mv2);  // rounding level of the gradient
   double phi = c->hscal->phi_in + c->hscal->phi_el;
   st->g0_norm = g0;
   st->phi0 = phi;
   int status = MPML_OK, it = 0;
   while (true) {
-    if (gn <= o->newton_rtol * g0 || gn <= o->newton_atol) break;
+    if (gn <= o->newton_rtol * g0 || gn <= o->newton_atol || gn <= gfloor) break;
     if (it >= o->newton_max) {
       status = MPML_WARN_NOT_CONVERGED;
       break;
@@ -2680,6 +2626,45 @@ static int hvp_bench_t(mpml_ctx_s* c, int iters, double* mean_ms) {
 
 int hvp_bench(mpml_ctx_s* c, int iters, double* mean_ms) {
   return c->fp64 ? hvp_bench_t<double>(c, iters, mean_ms) : hvp_bench_t<float>(c, iters, mean_ms);
+}
+
+// ---- pieces of the solver used by the batched driver (k_batch.cu) ----------
+int batch_alloc_solver(mpml_ctx_s* c) {
+  int rc = alloc_solver<float>(c);
+  if (rc) return rc;
+  return ensure(c->np2, sizeof(float) * 3 * (c->nb ? c->nb : 1) * BV);
+}
+
+int batch_prep(mpml_ctx_s* c, double cg_rtol, int cg_max) { return prep_t<float>(c, 1, 1, cg_rtol, cg_max); }
+
+void batch_slope_launch(mpml_ctx_s* c) {
+  DevScalars* d = dscal(c);
+  cudaMemsetAsync(&d->slope, 0, sizeof(double), c->s);
+  k_dot<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const double*)c->ng.p, (const float*)c->nx.p, &d->slope);
+  c->launches++;
+}
+
+void batch_energy_launch(mpml_ctx_s* c, double alpha) {
+  SolveInfo si = solve_info(c);
+  DevScalars* d = dscal(c);
+  cudaMemsetAsync(&d->phi_in, 0, sizeof(double), c->s);
+  cudaMemsetAsync(&d->phi_el, 0, sizeof(double), c->s);
+  cudaMemsetAsync(&d->infeasible, 0, sizeof(int), c->s);
+  k_energy_nodes<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const float*)c->nmass.p,
+                                                         (const double*)c->nvnew.p, (const float*)c->nx.p,
+                                                         (const double*)c->nvhat.p, alpha, d);
+  if (c->ncb > 0)
+    k_energy_cells<float><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
+                                                             (const uint8_t*)c->cflag.p, (const float*)c->cacc.p,
+                                                             (const double*)c->cs.p, (const double*)c->nvnew.p,
+                                                             (const float*)c->nx.p, alpha, si, d);
+  c->launches += 2;
+}
+
+void batch_axpy_launch(mpml_ctx_s* c, double alpha) {
+  k_axpy<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const float*)c->ndinv.p, (const float*)c->nx.p, alpha,
+                                                 (double*)c->nvnew.p);
+  c->launches++;
 }
 
 }  // namespace mpml

@@ -283,7 +283,7 @@ int mpml_destroy(mpml_ctx c) {
                  &c->pG, &c->pm, &c->pV, &c->pmat, &c->pperm, &c->pkey, &c->prank, &c->pbase, &c->ux, &c->uv,
                  &c->uF, &c->uG, &c->um, &c->uV, &c->umat, &c->cnt, &c->start, &c->scan_tmp, &c->cflag,
                  &c->cacc, &c->cs, &c->cK, &c->cnew, &c->nflag, &c->nmass, &c->nv, &c->nvhat, &c->nvfix,
-                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->nolist,
+                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->bbatch, &c->nolist,
                  &c->nnw, &c->nnact, &c->nny, &c->nnpart, &c->nz, &c->nns_r, &c->nns_e, &c->nnhd};
   for (Buf* b : bufs) free_buf(*b);
   if (c->hscal) cudaFreeHost(c->hscal);
@@ -395,6 +395,38 @@ int mpml_newton_step(mpml_ctx c, const mpml_solver_opts* o, mpml_solve_stats* st
   int rc2 = sync_status(c);
   if (rc2) return rc2;
   c->stage = 3;
+  return rc;
+}
+
+int mpml_newton_step_batch(mpml_ctx* ctxs, int n, const mpml_solver_opts* o, mpml_solve_stats* stats) {
+  if (!ctxs || n < 1 || n > MPML_BATCH_MAX) return MPML_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    mpml_ctx c = ctxs[i];
+    if (!c || c->stage < 1 || c->fp64 || !c->compressed || c->s != ctxs[0]->s || c->device != ctxs[0]->device)
+      return MPML_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return MPML_ERR_ARG;
+  }
+  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 2};
+  if (!o) o = &def;
+  std::vector<mpml_solve_stats> local;
+  if (!stats) {
+    local.resize(n);
+    stats = local.data();
+  }
+  int rc;
+  for (int i = 0; i < n; ++i)
+    if ((rc = stretch_all(ctxs[i]))) return rc;
+  for (int i = 0; i < n; ++i)
+    if ((rc = sync_status(ctxs[i]))) return rc;
+  rc = newton_batch(ctxs, n, o, stats);
+  if (rc < 0) return rc;
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->have_lin = 1;
+    int rc2 = sync_status(ctxs[i]);
+    if (rc2) return rc2;
+    ctxs[i]->stage = 3;
+  }
   return rc;
 }
 

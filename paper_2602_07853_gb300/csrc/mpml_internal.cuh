@@ -74,6 +74,7 @@ struct DevScalars {
   double pq;       // p^T H p of the current direction
   double nn_s;     // RMS of D^-1/2 r (network input scale)
   double nn_a, nn_b;  // training: z^T r and z^T H z of the current pair
+  double mv2;      // sum over free DOFs of (m vhat)^2 (Newton's rounding floor)
   double nfree;    // number of free DOF components
   double rzj;      // r^T D^-1 r (Jacobi) of the current residual
   double rr_ring[32];  // r^T r history (stall test of flexible CG)
@@ -136,6 +137,7 @@ struct mpml_ctx_s {
   mpml::Buf nflag, nmass, nv, nvhat, nvfix, nvnew, ng, ndinv, nx, nr, np, np2, nq;
   // scalars and status
   mpml::Buf scal, status, prof, part, gbar;
+  mpml::Buf bbatch;  // batched solver: scene table, work lists, accumulators (first context of a batch)
   // learned preconditioner: weights/grads/Adam + bf16 copies, activations,
   // network output, wgrad partials, z, training samples
   mpml::Buf nnw, nnact, nny, nnpart, nz, nns_r, nns_e, nnhd;
@@ -179,6 +181,7 @@ int resample_device(mpml_ctx_s* c, const void* x, const void* v, const void* F, 
 int p2q_q2n(mpml_ctx_s* c);
 int stretch_all(mpml_ctx_s* c);
 int newton_solve(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st);
+int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve_stats* st);
 int g2p_device(mpml_ctx_s* c, void* x, void* v, void* F, void* G, void* m, void* V, int32_t* mat);
 
 // operator-level helpers used by the introspection API
@@ -272,6 +275,73 @@ __device__ void jacobi3(const T Ain[9], T ev[3], T Q[9]) {
   ev[0] = A[0];
   ev[1] = A[4];
   ev[2] = A[8];
+}
+
+// rotation matrix (row-major) of a unit quaternion (w, x, y, z)
+template <typename T>
+__device__ __forceinline__ void quat_to_rot(T w, T x, T y, T z, T R[9]) {
+  R[0] = T(1) - T(2) * (y * y + z * z);
+  R[1] = T(2) * (x * y - z * w);
+  R[2] = T(2) * (x * z + y * w);
+  R[3] = T(2) * (x * y + z * w);
+  R[4] = T(1) - T(2) * (x * x + z * z);
+  R[5] = T(2) * (y * z - x * w);
+  R[6] = T(2) * (x * z - y * w);
+  R[7] = T(2) * (y * z + x * w);
+  R[8] = T(1) - T(2) * (x * x + y * y);
+}
+
+// FP32 HVP of one cell on the compressed tangent (27 floats):
+// K D' = U Mt W^T with M = U^T D' W, W = S V, and Mt the clamped eigen-modes of
+// the isotropic tangent applied to M (3x3 block in the eigenbasis Qd on the
+// diagonal of M, flip / twist modes on its off-diagonal pairs).
+__device__ __forceinline__ void apply_c27(const float c[27], const float D[9], float KD[9]) {
+  float U[9], V[9], Qd[9];
+  quat_to_rot<float>(c[0], c[1], c[2], c[3], U);
+  quat_to_rot<float>(c[4], c[5], c[6], c[7], V);
+  quat_to_rot<float>(c[8], c[9], c[10], c[11], Qd);
+  const float sm[9] = {c[12], c[15], c[16], c[15], c[13], c[17], c[16], c[17], c[14]};
+  float W[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) W[3 * a + b] = V[3 * a + b] + sm[3 * a] * V[b] + sm[3 * a + 1] * V[3 + b] + sm[3 * a + 2] * V[6 + b];
+  // M = U^T D W
+  float T1[9], M[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) T1[3 * i + b] = U[i] * D[b] + U[3 + i] * D[3 + b] + U[6 + i] * D[6 + b];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) M[3 * i + j] = T1[3 * i] * W[j] + T1[3 * i + 1] * W[3 + j] + T1[3 * i + 2] * W[6 + j];
+  float Mt[9];
+  // diagonal block
+  float y[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) y[k] = c[18 + k] * (Qd[k] * M[0] + Qd[3 + k] * M[4] + Qd[6 + k] * M[8]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Mt[4 * i] = Qd[3 * i] * y[0] + Qd[3 * i + 1] * y[1] + Qd[3 * i + 2] * y[2];
+  // pairs (0,1), (0,2), (1,2): flip (M_ij + M_ji)/sqrt2, twist (M_ij - M_ji)/sqrt2
+  const int PI[3] = {0, 0, 1}, PJ[3] = {1, 2, 2};
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int i = PI[p], j = PJ[p];
+    const float f = 0.5f * c[21 + p] * (M[3 * i + j] + M[3 * j + i]);
+    const float t = 0.5f * c[24 + p] * (M[3 * i + j] - M[3 * j + i]);
+    Mt[3 * i + j] = f + t;
+    Mt[3 * j + i] = f - t;
+  }
+  // K D' = U Mt W^T
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) T1[3 * a + j] = U[3 * a] * Mt[j] + U[3 * a + 1] * Mt[3 + j] + U[3 * a + 2] * Mt[6 + j];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) KD[3 * a + b] = T1[3 * a] * W[3 * b] + T1[3 * a + 1] * W[3 * b + 1] + T1[3 * a + 2] * W[3 * b + 2];
 }
 
 // Signed SVD of F = I + H from the eigen-decomposition of F^T F - I =

@@ -86,6 +86,8 @@ EXPORTS = {
     "mpml_resample": (C.c_int, [C.c_void_p, C.POINTER(mpml_particles)]),
     "mpml_newton_step": (C.c_int, [C.c_void_p, C.POINTER(mpml_solver_opts), C.POINTER(mpml_solve_stats)]),
     "mpml_g2p": (C.c_int, [C.c_void_p, C.POINTER(mpml_particles)]),
+    "mpml_newton_step_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(mpml_solver_opts),
+                                         C.POINTER(mpml_solve_stats)]),
     "mpml_counts": (C.c_int, [C.c_void_p, _I64]),
     "mpml_get_keys": (C.c_int, [C.c_void_p, C.c_int, _I64]),
     "mpml_get_field": (C.c_int, [C.c_void_p, C.c_int, _D]),
@@ -176,6 +178,16 @@ def mpml_newton_step(ctx, opts: mpml_solver_opts | None = None, stats: mpml_solv
     rc = load().mpml_newton_step(ctx, C.byref(opts) if opts is not None else None, C.byref(stats))
     _check(rc, "mpml_newton_step")
     return rc, stats
+
+
+def mpml_newton_step_batch(ctxs, opts: mpml_solver_opts | None = None):
+    """Lockstep Newton solves of several contexts; returns (status, [mpml_solve_stats])."""
+    n = len(ctxs)
+    arr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    stats = (mpml_solve_stats * n)()
+    rc = load().mpml_newton_step_batch(arr, n, C.byref(opts) if opts is not None else None, stats)
+    _check(rc, "mpml_newton_step_batch")
+    return rc, list(stats)
 
 
 def mpml_g2p(ctx, p: mpml_particles):

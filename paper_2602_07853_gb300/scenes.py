@@ -200,6 +200,39 @@ def slab_on_sand(n: int = 256, seed: int = 5, ppc: int = 8, dt: float = 2e-3) ->
     return _finish(sc, x, np.zeros_like(x), mat, ppc)
 
 
+def batch_scene(index: int, n: int = 64, ppc: int = 8, dt: float = 1e-3,
+                extent: Optional[int] = None) -> Scene:
+    """Scene ``index`` of the many-scene batch: its own n^3 unit domain, one fixed-corotated
+    shape dropped onto the floor at 1 m/s.  Seeded with 4 + index: extent e ~ U{8..48} voxels
+    (or ``extent``), shape box (e^3) / sphere (diameter e) / torus (R = 0.3 e, r = 0.15 e),
+    E log-uniform in [1e4, 1e7] Pa, nu uniform in [0.2, 0.45]; the shape is centred in x, z
+    with its lowest voxel in row 2, so that it reaches the sticky floor within about 8 steps."""
+    rng = np.random.Generator(np.random.PCG64(4 + index))
+    e = int(rng.integers(8, 49)) if extent is None else int(extent)
+    shape = int(rng.integers(0, 3))
+    E = float(10 ** rng.uniform(4.0, 7.0))
+    nu = float(rng.uniform(0.2, 0.45))
+    dx = 1.0 / n
+    sc = Scene(f"batch_{index}_{['box', 'sphere', 'torus'][shape]}{e}", (n, n, n), dx, float(n), dt,
+               (0.0, -9.8, 0.0), [Material(FIXED_COROTATED, E, nu)])
+    lo = np.array([(n - e) // 2, 2, (n - e) // 2])
+    g = _grid_voxels(lo, lo + e)
+    c = (g + 0.5 - lo - e / 2.0)  # voxel centres relative to the shape centre, in voxels
+    if shape == 1:
+        keep = np.sum(c * c, axis=1) <= (e / 2.0) ** 2
+    elif shape == 2:
+        R, r = 0.3 * e, 0.15 * e
+        rho = np.sqrt(c[:, 0] ** 2 + c[:, 2] ** 2)
+        keep = (rho - R) ** 2 + c[:, 1] ** 2 <= r * r
+    else:
+        keep = np.ones(len(g), bool)
+    vox = g[keep]
+    x = seed_voxels(vox, dx, ppc, rng)
+    v = np.zeros_like(x)
+    v[:, 1] = -1.0
+    return _finish(sc, x, v, np.zeros(len(x), np.int64), ppc)
+
+
 def colliding_cubes(n: int = 64, seed: int = 6, ppc: int = 8, speed: float = 1.0) -> Scene:
     """Two 0.1 m elastic cubes (E=5e3, nu=0.3, rho=1e3) moving at +-speed along x, no gravity
     (the linear-momentum experiment of Sec. 6.6; its speed is not given, 1 m/s here)."""

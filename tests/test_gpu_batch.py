@@ -1,0 +1,116 @@
+"""Batched implicit solve (mpml_newton_step_batch): several independent scenes in
+lockstep, every CG round one persistent launch, against the same scenes solved
+one by one with mpml_newton_step and against the FP64 oracle.
+
+Tolerances: both solvers stop at relative residual 1e-6, so the node velocities
+agree to ~1e-6 relative (checked at 1e-4 as in test_gpu_parity); CG counts of a
+scene agree within 2 iterations (FP32 sums in a different order); positions
+after 3 steps within 1e-4 dx of the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2602_07853_gb300.mpml as m
+from paper_2602_07853_gb300 import scenes
+from tests._util import make_oracle
+from tests._gpu import GpuSim, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+# default solver options: a shape in free fall starts from g(v0) = 0 up to rounding, which
+# the library's rounding floor (1e-12 ||M vhat||) accepts as converged
+OPTS = dict()
+
+
+def small_batch(count=5):
+    # scenes of uneven size on 32^3 domains (extents 6..14 voxels, all three shapes)
+    return [scenes.batch_scene(i, n=32, extent=6 + 2 * i) for i in range(count)]
+
+
+def test_batch_matches_single_scene_solves():
+    scs = small_batch()
+    sims = [GpuSim(sc, m.FP32) for sc in scs]
+    for g in sims:
+        g.set_particles()
+    # step the scenes until they touch the floor, one by one and batched side by side
+    ref = [GpuSim(sc, m.FP32) for sc in scs]
+    for g in ref:
+        g.set_particles()
+    for step in range(10):
+        for g in sims + ref:
+            m.mpml_set_time(g.ctx, step * g.sc.dt)
+            g.resample()
+        rc, stats = m.mpml_newton_step_batch([g.ctx for g in sims], m.solver_opts(**OPTS))
+        assert rc >= 0
+        for i, (g, sb) in enumerate(zip(ref, stats)):
+            rc1, s1 = g.newton(m.solver_opts(**OPTS))
+            info = (step, i, s1.status, sb.status, s1.newton_iters, sb.newton_iters, s1.g0_norm, sb.g0_norm,
+                    s1.g_norm, sb.g_norm, list(s1.alpha[:s1.newton_iters]), list(sb.alpha[:sb.newton_iters]),
+                    list(s1.cg_iters[:s1.newton_iters]), list(sb.cg_iters[:sb.newton_iters]))
+            assert s1.status == 0 and sb.status == 0, info
+            # the same first Newton system: Jacobi-PCG counts agree; later iterates differ by
+            # FP32 rounding, which can move the 1e-6 Newton stop by one iteration
+            assert abs(s1.newton_iters - sb.newton_iters) <= 1
+            if s1.newton_iters and sb.newton_iters:
+                assert abs(s1.cg_iters[0] - sb.cg_iters[0]) <= 2, (s1.cg_iters[0], sb.cg_iters[0])
+            assert sb.g_norm <= max(1e-6 * sb.g0_norm, 1e-11)
+        for g, gr in zip(sims, ref):
+            v_b, v_1 = g.field(m.F_NODE_VNEW), gr.field(m.F_NODE_VNEW)
+            assert rel_err(v_b, v_1) <= 1e-4
+            g.g2p()
+            gr.g2p()
+    # the shapes reached the sticky floor: some scene needed Newton iterations with contact
+    assert any(s.newton_iters >= 1 for s in stats)
+    for g in sims + ref:
+        g.close()
+
+
+def test_batch_scene_against_oracle():
+    sc = scenes.batch_scene(2, n=32, extent=10)
+    other = scenes.batch_scene(1, n=32, extent=8)
+    g, h = GpuSim(sc, m.FP32), GpuSim(other, m.FP32)
+    g.set_particles()
+    h.set_particles()
+    o = make_oracle(sc)
+    p_o = g.inputs()
+    for step in range(3):
+        t = step * sc.dt
+        o.set_time(t)
+        rc, p_o, _ = o.step(p_o)
+        assert rc >= 0
+        for s in (g, h):
+            m.mpml_set_time(s.ctx, t)
+            s.resample()
+        rc, _ = m.mpml_newton_step_batch([g.ctx, h.ctx], m.solver_opts(**OPTS))
+        assert rc >= 0
+        g.g2p()
+        h.g2p()
+    err = np.abs(g.particles()["x"] - p_o["x"]).max()
+    assert err <= 1e-4 * sc.dx, err
+    g.close()
+    h.close()
+
+
+def test_batch_rejects_mixed_contexts():
+    sc = scenes.batch_scene(0, n=32, extent=6)
+    a, b = GpuSim(sc, m.FP32), GpuSim(sc, m.FP64)
+    a.set_particles()
+    b.set_particles()
+    a.resample()
+    b.resample()
+    with pytest.raises(m.MPMLError) as e:
+        m.mpml_newton_step_batch([a.ctx, b.ctx])
+    assert e.value.code == m.ERR_ARG
+    with pytest.raises(m.MPMLError):
+        m.mpml_newton_step_batch([a.ctx, a.ctx])
+    a.close()
+    b.close()
