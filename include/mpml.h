@@ -178,16 +178,24 @@ int mpml_resample(mpml_ctx ctx, const mpml_particles* p);
 /* Algorithm 3, implicit.  Synchronises (convergence tests); fills stats if
  * non-NULL.  opts may be NULL (defaults). */
 int mpml_newton_step(mpml_ctx ctx, const mpml_solver_opts* opts, mpml_solve_stats* stats);
-/* Algorithm 3 for a batch of independent scenes (one context each, already
- * resampled; FP32 single-material contexts sharing one CUDA stream; at most
- * MPML_BATCH_MAX).  Each scene follows exactly the Newton / Jacobi-PCG / line-
- * search logic of mpml_newton_step with its own tolerances and iteration
- * counts, but the scenes advance in lockstep and every round of their CG
- * solves is one persistent cooperative launch over all active scenes' bricks
- * (per-scene scalars and FP64 sums).  stats: array of n (may be NULL).
- * Scratch of the batch lives in ctxs[0].  Synchronises; returns the first
- * error, else MPML_WARN_NOT_CONVERGED if any scene did not converge. */
+/* Batches of independent scenes (one context each, on one device; each context
+ * on its own stream or a shared one; at most MPML_BATCH_MAX, all distinct).
+ * Not in the paper: the workload statement asks for many scenes of uneven
+ * size solved in one persistent launch.
+ * mpml_resample_batch: Algorithm 2 for every scene with one host wait for the
+ *   whole batch (device particle arrays only; parts is an array of n).
+ * mpml_newton_step_batch: Algorithm 3 for every scene (FP32 single-material
+ *   contexts, already resampled).  Each scene follows exactly the Newton /
+ *   Jacobi-PCG / line-search logic of mpml_newton_step with its own
+ *   tolerances and iteration counts, but the scenes advance in lockstep and
+ *   every round of their CG solves is one persistent cooperative launch over
+ *   all active scenes' bricks (per-scene scalars and FP64 sums), issued on
+ *   ctxs[0]'s stream after every scene's stream and followed by all of them
+ *   (events).  stats: array of n (may be NULL).  The batch's scratch lives in
+ *   ctxs[0].  Synchronises; returns the first error, else
+ *   MPML_WARN_NOT_CONVERGED if any scene did not converge. */
 #define MPML_BATCH_MAX 128
+int mpml_resample_batch(mpml_ctx* ctxs, const mpml_particles* parts, int n);
 int mpml_newton_step_batch(mpml_ctx* ctxs, int n, const mpml_solver_opts* opts, mpml_solve_stats* stats);
 /* Algorithm 4.  Writes x, v, F, G, mass, volume, mat of p (the same arrays
  * or others of the same size) in the sorted order of the last resample.

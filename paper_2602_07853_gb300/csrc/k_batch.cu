@@ -1,7 +1,10 @@
 // Batched implicit solve: the Newton iterations of many independent scenes
-// (one library context each, FP32 single-material, one shared stream) run in
-// lockstep, and every round of their Jacobi-PCG solves is ONE persistent
-// cooperative launch over the union of the scenes' bricks.
+// (one library context each, FP32 single-material, on one device; each on its
+// own stream or a shared one) run in lockstep, and every round of their
+// Jacobi-PCG solves is ONE persistent cooperative launch over the union of the
+// scenes' bricks.  The per-scene kernels (prep, energy, update) stay on each
+// context's stream, so scenes on different streams overlap; events order
+// them against the shared launch, which runs on the first context's stream.
 //
 // Each scene keeps its own scalars (alpha, beta, r.z, tolerance, iteration
 // count, convergence flag): a CTA looks the scene up per work item (cell brick,
@@ -406,14 +409,29 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
 
 namespace {
 
+// the scalars and status of every context, each copied on its own stream,
+// then one wait per distinct stream
 int read_all(const std::vector<mpml_ctx_s*>& cs) {
-  if (cs.empty()) return MPML_OK;
-  cudaStream_t s = cs[0]->s;
+  std::vector<cudaStream_t> streams;
   for (mpml_ctx_s* c : cs) {
-    cudaMemcpyAsync(c->hscal, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(c->hstatus, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(c->hscal, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(c->hstatus, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    if (std::find(streams.begin(), streams.end(), c->s) == streams.end()) streams.push_back(c->s);
   }
-  return cuda_status(cudaStreamSynchronize(s));
+  for (cudaStream_t s : streams) {
+    const int rc = cuda_status(cudaStreamSynchronize(s));
+    if (rc) return rc;
+  }
+  return MPML_OK;
+}
+
+int ensure_event(mpml_ctx_s* c) {
+  if (c->bev) return MPML_OK;
+  if (cudaEventCreateWithFlags(&c->bev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return MPML_ERR_CUDA;
+  }
+  return MPML_OK;
 }
 
 int pcg_batch(mpml_ctx_s* owner, const std::vector<mpml_ctx_s*>& cs, int cg_max) {
@@ -471,6 +489,14 @@ int pcg_batch(mpml_ctx_s* owner, const std::vector<mpml_ctx_s*>& cs, int cg_max)
   std::copy(nw.begin(), nw.end(), hw + cw.size());
   std::copy(aw.begin(), aw.end(), hw + cw.size() + nw.size());
   cudaStream_t s = owner->s;
+  // the shared launch runs on the first context's stream after every scene's prep
+  if ((rc = ensure_event(owner))) return rc;
+  for (mpml_ctx_s* c : cs) {
+    if (c->s == s) continue;
+    if ((rc = ensure_event(c))) return rc;
+    cudaEventRecord(c->bev, c->s);
+    cudaStreamWaitEvent(s, c->bev, 0);
+  }
   cudaMemcpyAsync(base, host.data(), off_acc, cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(base + off_acc, 0, acc_bytes + 16, s);
   for (mpml_ctx_s* c : cs) {
@@ -493,7 +519,12 @@ int pcg_batch(mpml_ctx_s* owner, const std::vector<mpml_ctx_s*>& cs, int cg_max)
   void* args[] = {&a};
   rc = cuda_status(cudaLaunchCooperativeKernel((const void*)k_pcg_batch, dim3(max_blocks), dim3(256), args, BC_SMEM, s));
   owner->launches++;
-  return rc;
+  if (rc) return rc;
+  // every scene's stream continues after the shared launch
+  cudaEventRecord(owner->bev, s);
+  for (mpml_ctx_s* c : cs)
+    if (c->s != s) cudaStreamWaitEvent(c->s, owner->bev, 0);
+  return cuda_status(cudaGetLastError());
 }
 
 }  // namespace

@@ -397,9 +397,10 @@ static GridInfo grid_info(mpml_ctx_s* c) {
   return g;
 }
 
+// First half of the resample: brick flags and their compaction, with the
+// counts copied to the host (asynchronously; the caller synchronises).
 template <typename T>
-static int resample_t(mpml_ctx_s* c, const void* x_, const void* v_, const void* F_, const void* G_,
-                      const void* m_, const void* V_, const int32_t* mat, int32_t* perm_out) {
+static int resample_begin_t(mpml_ctx_s* c, const void* x_) {
   const T* x = (const T*)x_;
   const int64_t np = c->np_count;
   GridInfo g = grid_info(c);
@@ -424,7 +425,20 @@ static int resample_t(mpml_ctx_s* c, const void* x_, const void* v_, const void*
   // counts (and the status word) to the host: one synchronisation per resample
   cudaMemcpyAsync(c->hscal, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(c->hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, s);
-  if ((rc = cuda_status(cudaStreamSynchronize(s)))) return rc;
+  return cuda_status(cudaGetLastError());
+}
+
+// Second half, after the counts arrived: neighbours, keys, counting sort,
+// gather, DOF nodes and the Dirichlet set.
+template <typename T>
+static int resample_end_t(mpml_ctx_s* c, const void* x_, const void* v_, const void* F_, const void* G_,
+                          const void* m_, const void* V_, const int32_t* mat, int32_t* perm_out) {
+  const T* x = (const T*)x_;
+  const int64_t np = c->np_count;
+  GridInfo g = grid_info(c);
+  int rc;
+  int* status = (int*)c->status.p;
+  cudaStream_t s = c->s;
   if (*c->hstatus & ST_NONFINITE) return MPML_ERR_NONFINITE;
   if (*c->hstatus & ST_OUT_OF_DOMAIN) return MPML_ERR_OUT_OF_DOMAIN;
   c->nb = c->hscal->counter[5];
@@ -493,10 +507,22 @@ static int resample_t(mpml_ctx_s* c, const void* x_, const void* v_, const void*
   return cuda_status(cudaGetLastError());
 }
 
+int resample_device_begin(mpml_ctx_s* c, const void* x) {
+  return c->fp64 ? resample_begin_t<double>(c, x) : resample_begin_t<float>(c, x);
+}
+
+int resample_device_end(mpml_ctx_s* c, const void* x, const void* v, const void* F, const void* G, const void* m,
+                        const void* V, const int32_t* mat, int32_t* perm_out) {
+  if (c->fp64) return resample_end_t<double>(c, x, v, F, G, m, V, mat, perm_out);
+  return resample_end_t<float>(c, x, v, F, G, m, V, mat, perm_out);
+}
+
 int resample_device(mpml_ctx_s* c, const void* x, const void* v, const void* F, const void* G, const void* m,
                     const void* V, const int32_t* mat, int32_t* perm_out) {
-  if (c->fp64) return resample_t<double>(c, x, v, F, G, m, V, mat, perm_out);
-  return resample_t<float>(c, x, v, F, G, m, V, mat, perm_out);
+  int rc = resample_device_begin(c, x);
+  if (rc) return rc;
+  if ((rc = cuda_status(cudaStreamSynchronize(c->s)))) return rc;
+  return resample_device_end(c, x, v, F, G, m, V, mat, perm_out);
 }
 
 }  // namespace mpml

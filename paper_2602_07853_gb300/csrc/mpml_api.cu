@@ -292,6 +292,7 @@ int mpml_destroy(mpml_ctx c) {
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (cudaEvent_t e : c->pcg_ev)
     if (e) cudaEventDestroy(e);
+  if (c->bev) cudaEventDestroy(c->bev);
   delete c;
   return MPML_OK;
 }
@@ -398,12 +399,39 @@ int mpml_newton_step(mpml_ctx c, const mpml_solver_opts* o, mpml_solve_stats* st
   return rc;
 }
 
+int mpml_resample_batch(mpml_ctx* ctxs, const mpml_particles* parts, int n) {
+  if (!ctxs || !parts || n < 1 || n > MPML_BATCH_MAX) return MPML_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || bad_particles(&parts[i]) || parts[i].mem != MPML_MEM_DEVICE) return MPML_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return MPML_ERR_ARG;
+  }
+  int rc;
+  // first halves on every stream, one wait per context, then the second halves
+  for (int i = 0; i < n; ++i) {
+    mpml_ctx c = ctxs[i];
+    cudaMemsetAsync(c->status.p, 0, sizeof(int), c->s);
+    c->np_count = parts[i].n;
+    if ((rc = resample_device_begin(c, parts[i].x))) return rc;
+  }
+  for (int i = 0; i < n; ++i)
+    if ((rc = cuda_status(cudaStreamSynchronize(ctxs[i]->s)))) return rc;
+  for (int i = 0; i < n; ++i) {
+    mpml_ctx c = ctxs[i];
+    const mpml_particles& p = parts[i];
+    if ((rc = resample_device_end(c, p.x, p.v, p.F, p.G, p.mass, p.volume, p.mat, p.perm))) return rc;
+    if ((rc = p2q_q2n(c))) return rc;
+    c->stage = 1;
+    c->have_lin = 0;
+  }
+  return MPML_OK;
+}
+
 int mpml_newton_step_batch(mpml_ctx* ctxs, int n, const mpml_solver_opts* o, mpml_solve_stats* stats) {
   if (!ctxs || n < 1 || n > MPML_BATCH_MAX) return MPML_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     mpml_ctx c = ctxs[i];
-    if (!c || c->stage < 1 || c->fp64 || !c->compressed || c->s != ctxs[0]->s || c->device != ctxs[0]->device)
-      return MPML_ERR_ARG;
+    if (!c || c->stage < 1 || c->fp64 || !c->compressed || c->device != ctxs[0]->device) return MPML_ERR_ARG;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return MPML_ERR_ARG;
   }

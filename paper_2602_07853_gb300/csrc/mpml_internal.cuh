@@ -138,6 +138,7 @@ struct mpml_ctx_s {
   // scalars and status
   mpml::Buf scal, status, prof, part, gbar;
   mpml::Buf bbatch;  // batched solver: scene table, work lists, accumulators (first context of a batch)
+  cudaEvent_t bev = nullptr;  // batched solver: orders this context's stream against the shared launch
   // learned preconditioner: weights/grads/Adam + bf16 copies, activations,
   // network output, wgrad partials, z, training samples
   mpml::Buf nnw, nnact, nny, nnpart, nz, nns_r, nns_e, nnhd;
@@ -178,6 +179,9 @@ int cuda_status(cudaError_t e);
 
 int resample_device(mpml_ctx_s* c, const void* x, const void* v, const void* F, const void* G,
                     const void* m, const void* V, const int32_t* mat, int32_t* perm_out);
+int resample_device_begin(mpml_ctx_s* c, const void* x);
+int resample_device_end(mpml_ctx_s* c, const void* x, const void* v, const void* F, const void* G,
+                        const void* m, const void* V, const int32_t* mat, int32_t* perm_out);
 int p2q_q2n(mpml_ctx_s* c);
 int stretch_all(mpml_ctx_s* c);
 int newton_solve(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st);

@@ -88,6 +88,7 @@ EXPORTS = {
     "mpml_g2p": (C.c_int, [C.c_void_p, C.POINTER(mpml_particles)]),
     "mpml_newton_step_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(mpml_solver_opts),
                                          C.POINTER(mpml_solve_stats)]),
+    "mpml_resample_batch": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(mpml_particles), C.c_int]),
     "mpml_counts": (C.c_int, [C.c_void_p, _I64]),
     "mpml_get_keys": (C.c_int, [C.c_void_p, C.c_int, _I64]),
     "mpml_get_field": (C.c_int, [C.c_void_p, C.c_int, _D]),
@@ -178,6 +179,14 @@ def mpml_newton_step(ctx, opts: mpml_solver_opts | None = None, stats: mpml_solv
     rc = load().mpml_newton_step(ctx, C.byref(opts) if opts is not None else None, C.byref(stats))
     _check(rc, "mpml_newton_step")
     return rc, stats
+
+
+def mpml_resample_batch(ctxs, parts):
+    """Algorithm 2 for several contexts (device particles) with one host wait."""
+    n = len(ctxs)
+    arr = (C.c_void_p * n)(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    ps = (mpml_particles * n)(*parts)
+    return _check(load().mpml_resample_batch(arr, ps, n), "mpml_resample_batch")
 
 
 def mpml_newton_step_batch(ctxs, opts: mpml_solver_opts | None = None):
