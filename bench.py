@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--check-every", type=int, default=16)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner comparison")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the extra measurements of the other workloads (batch, plasticity, large block)")
     return ap.parse_args()
 
 
@@ -205,6 +207,114 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def other_configs(m, scenes, args, peaks):
+    """Secondary measurements (not the headline value): the 64-scene batch (config 4), the
+    von Mises / Drucker-Prager slab on sand at 256^3 (config 5) and the HVP of the 3-8M pressed
+    block, each with CUDA events, inputs resident, warm-up first."""
+    import torch
+
+    out = {}
+    steps = max(2, min(args.steps, 4))
+
+    def make(sc, stream):
+        mats = [m.material(mt.model, *m.lame_parameters(mt.E, mt.nu), mt.plastic, mt.yield_stress,
+                           mt.friction_angle) for mt in sc.materials]
+        desc = m.scene_desc(sc.n, sc.dx, sc.dt, sc.gravity, m.FP32, sc.wall_layers, sc.plate, sc.inv_dx)
+        ctx = m.mpml_create(desc, mats, stream.cuda_stream)
+        p = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.particles(np.float32).items()}
+        parts = m.particles_from_tensors(p["x"], p["v"], p["F"], p["G"], p["mp"], p["Vp"], p["mat"])
+        return ctx, p, parts
+
+    # config 4: 64 scenes of uneven size, one context and stream each, batched solve
+    n_sc = 64
+    scs = [scenes.batch_scene(i) for i in range(n_sc)]
+    streams = [torch.cuda.Stream() for _ in scs]
+    made = [make(sc, st) for sc, st in zip(scs, streams)]
+    ctxs = [c for c, _, _ in made]
+    parts = [pp for _, _, pp in made]
+    init = [{k: v.clone() for k, v in p.items()} for _, p, _ in made]
+    torch.cuda.synchronize()
+
+    def run_batch(k0, k):
+        ms, newton, cg = [], 0, 0
+        for s in range(k0, k0 + k):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            for c in ctxs:
+                m.mpml_set_time(c, s * scs[0].dt)
+            m.mpml_resample_batch(ctxs, parts)
+            rc, st = m.mpml_newton_step_batch(ctxs)
+            for c, pp in zip(ctxs, parts):
+                m.mpml_g2p(c, pp)
+            torch.cuda.synchronize()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+            newton += sum(x.newton_iters for x in st)
+            cg += sum(x.cg_iters_total for x in st)
+        return ms, newton, cg
+
+    run_batch(0, 3)  # warm-up
+    for (_, p, _), q in zip(made, init):
+        for key in p:
+            p[key].copy_(q[key])
+    torch.cuda.synchronize()
+    ms, newton, cg = run_batch(0, 8)
+    out["batch64"] = {"workload": "64 fixed-corotated scenes (box / sphere / torus, extents 8-48 voxels, E log-uniform "
+                                  "1e4-1e7, nu 0.2-0.45) each on its own 64^3 grid, dropped at 1 m/s, dt = 1e-3, "
+                                  "steps 0-7 from rest above the floor",
+                      "particles": int(sum(int(p["x"].shape[0]) for _, p, _ in made)),
+                      "steps_per_s": 1e3 * len(ms) / float(np.sum(ms)), "ms_per_step": float(np.mean(ms)),
+                      "newton_iters_per_step": newton / len(ms), "cg_iters_per_step": cg / len(ms),
+                      "solver": "mpml_resample_batch + mpml_newton_step_batch (one persistent PCG launch per "
+                                "Newton round over all scenes), one stream per scene"}
+    for c in ctxs:
+        m.mpml_destroy(c)
+    del made, init
+    torch.cuda.empty_cache()
+
+    # config 5 at full size and the 3-8M pressed block: step time and HVP bandwidth
+    for key, sc, nstep in (("slab_on_sand_256", scenes.slab_on_sand(256), 2),
+                           ("pressed_block_236", scenes.pressed_block(236), 2)):
+        stream = torch.cuda.current_stream()
+        ctx, p, pp = make(sc, stream)
+        times, newton, cg = [], 0, 0
+        for s in range(nstep + 1):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m.mpml_set_time(ctx, s * sc.dt)
+            m.mpml_resample(ctx, pp)
+            rc, st = m.mpml_newton_step(ctx, m.solver_opts())
+            m.mpml_g2p(ctx, pp)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if s > 0:  # the first step is the warm-up
+                times.append(a.elapsed_time(b))
+                newton += st.newton_iters
+                cg += st.cg_iters_total
+        counts = m.mpml_counts(ctx)
+        vhat = m.mpml_get_field(ctx, m.F_NODE_VHAT)
+        m.mpml_stretch(ctx)
+        m.mpml_linearize(ctx, vhat)
+        hvp_ms = m.mpml_hvp_bench(ctx, 20)
+        k_bytes = (108.0 if len(sc.materials) == 1 else 180.0)
+        alg = k_bytes * counts["cells"] + 28.0 * counts["nodes"]
+        gbs = alg / (hvp_ms / 1e3) / 1e9
+        out[key] = {"particles": int(counts["particles"]), "active_cells": int(counts["cells"]),
+                    "dof_nodes": int(counts["nodes"]), "steps_per_s": 1e3 * len(times) / float(np.sum(times)),
+                    "ms_per_step": float(np.mean(times)), "newton_iters_per_step": newton / len(times),
+                    "cg_iters_per_step": cg / len(times),
+                    "hvp": {"kernel": "k_hvp_c27" if len(sc.materials) == 1 else "k_hvp_tma (45-number tangent)",
+                            "mean_ms": hvp_ms, "bytes": alg, "gbs": gbs, "frac": gbs / peaks["hbm_gbs"],
+                            "bytes_rule": f"{int(k_bytes)} B per active cell + 28 B per DOF node, working set "
+                                          f"{alg / 1e6:.0f} MB vs 129 MB L2"}}
+        m.mpml_destroy(ctx)
+        del p
+        torch.cuda.empty_cache()
+    return out
+
+
 def learned_comparison(m, ctx, parts, reset, one_step, args, stream, flush):
     """Trains the learned preconditioner on the workload's first Newton system (untimed), then
     times the same steps with flexible CG (CUDA events, L2 flushed as for the main number)."""
@@ -378,6 +488,9 @@ def run_ours(args, rank, world, local_rank):
     learned = None
     if not args.no_learned:
         learned = learned_comparison(m, ctx, parts, reset, one_step, args, stream, flush)
+    others = None
+    if not args.no_other_configs and rank == 0:
+        others = other_configs(m, scenes, args, peaks)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -403,6 +516,7 @@ def run_ours(args, rank, world, local_rank):
                 "newton_iters_per_s": float(np.sum(newton_its)) / (total_ms / 1e3),
                 "cg_iters_last_step": last_cg,
                 "hvp_gbs": hvp["gbs"] if hvp else None, "hvp": hvp, "learned_precond": learned,
+                "other_configs": others,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
