@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--check-every", type=int, default=16)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner comparison")
+    ap.add_argument("--hvp-probe", choices=["pressed_block_236", "slab_on_sand_256", "two_spheres_168"],
+                    help="only build this workload, take one step, and time the standalone HVP (for profilers)")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="skip the extra measurements of the other workloads (batch, plasticity, large block)")
     return ap.parse_args()
@@ -525,8 +527,41 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def hvp_probe(args):
+    """One workload, one implicit step, then a few standalone HVP launches on its tangent."""
+    import torch
+
+    import paper_2602_07853_gb300.mpml as m
+    from paper_2602_07853_gb300 import scenes
+
+    sc = {"pressed_block_236": lambda: scenes.pressed_block(236), "slab_on_sand_256": lambda: scenes.slab_on_sand(256),
+          "two_spheres_168": lambda: scenes.two_spheres(168, gap=1.0 / 168)}[args.hvp_probe]()
+    m.load()
+    stream = torch.cuda.current_stream()
+    mats = [m.material(mt.model, *m.lame_parameters(mt.E, mt.nu), mt.plastic, mt.yield_stress, mt.friction_angle)
+            for mt in sc.materials]
+    desc = m.scene_desc(sc.n, sc.dx, sc.dt, sc.gravity, m.FP32, sc.wall_layers, sc.plate, sc.inv_dx)
+    ctx = m.mpml_create(desc, mats, stream.cuda_stream)
+    p = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.particles(np.float32).items()}
+    pp = m.particles_from_tensors(p["x"], p["v"], p["F"], p["G"], p["mp"], p["Vp"], p["mat"])
+    m.mpml_resample(ctx, pp)
+    rc, st = m.mpml_newton_step(ctx, m.solver_opts())
+    counts = m.mpml_counts(ctx)
+    m.mpml_stretch(ctx)
+    m.mpml_linearize(ctx, m.mpml_get_field(ctx, m.F_NODE_VHAT))
+    ms = m.mpml_hvp_bench(ctx, max(args.steps, 1))
+    k_bytes = 108.0 if len(sc.materials) == 1 else 180.0
+    alg = k_bytes * counts["cells"] + 28.0 * counts["nodes"]
+    print(json.dumps({"probe": args.hvp_probe, "cells": counts["cells"], "nodes": counts["nodes"], "hvp_ms": ms,
+                      "hvp_gbs": alg / (ms / 1e3) / 1e9, "newton_rc": rc}), flush=True)
+    m.mpml_destroy(ctx)
+    return 0
+
+
 def main():
     args = parse()
+    if args.hvp_probe:
+        return hvp_probe(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
