@@ -353,7 +353,24 @@ def learned_comparison(m, ctx, parts, reset, one_step, args, stream, flush):
         cg.append(st.cg_iters_total)
         fb.append(st.fcg_fallbacks)
         nw.append(st.newton_iters)
+    # direction quality on a Newton system the network was not trained on (one step later):
+    # mean 1 - cos_H(z(r), e) of the trained network and of Jacobi (zero network)
+    trained = m.mpml_nn_get_weights(ctx)
+    reset()
+    m.mpml_set_time(ctx, 0.0)
+    m.mpml_resample(ctx, parts)
+    m.mpml_newton_step(ctx, m.solver_opts())
+    m.mpml_g2p(ctx, parts)
+    m.mpml_set_time(ctx, 2e-3)
+    m.mpml_resample(ctx, parts)
+    ev = m.mpml_nn_train(ctx, m.train_opts(samples=16, epochs=1, batch=4, lr=0.0))
+    m.mpml_nn_set_weights(ctx, [np.zeros(s) for s in m.NN_SHAPES])
+    ev0 = m.mpml_nn_train(ctx, m.train_opts(samples=16, epochs=1, batch=4, lr=0.0))
+    m.mpml_nn_set_weights(ctx, trained)
     return {"steps_per_s": 1e3 * len(ms) / float(np.sum(ms)), "ms_per_step": float(np.mean(ms)),
+            "unseen_system_loss": {"learned": ev.loss_first, "jacobi": ev0.loss_first,
+                                   "definition": "mean 1 - cos_H(z(r), e) over 16 (r, e) pairs of the next "
+                                                 "step's first Newton system"},
             "cg_iters_per_step": float(np.mean(cg)), "newton_iters_per_step": float(np.mean(nw)),
             "fcg_fallbacks_per_step": float(np.mean(fb)), "train_s": train_s, "train_samples": tr.samples,
             "loss_first": tr.loss_first, "loss_last": tr.loss_last,

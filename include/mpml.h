@@ -299,7 +299,9 @@ int mpml_nn_loss_grad(mpml_ctx ctx, const double* r, const double* e, double* lo
 /* Trains on the current Newton system (after mpml_resample): reconstructs the
  * stretches, solves the first Newton system with Jacobi-PCG, takes
  * `samples` pairs (r_k, x* - x_k) along the way and runs Adam on the loss
- * of mpml_nn_loss_grad.  Weights must be set (e.g. a seeded initialisation). */
+ * of mpml_nn_loss_grad.  Weights must be set (e.g. a seeded initialisation).
+ * Pairs whose error is at rounding level are skipped.  lr = 0 evaluates the
+ * current weights instead (mean loss in loss_first, weights unchanged). */
 int mpml_nn_train(mpml_ctx ctx, const mpml_train_opts* opts, mpml_train_stats* stats);
 
 /* Allocation-free particle sort ----------------------------------------

@@ -2327,8 +2327,11 @@ int nn_train(mpml_ctx_s* c, int epochs, int batch, float lr, double* loss_first,
   const int64_t n3 = 3 * c->nb * BV;
   float* R = (float*)c->nns_r.p;
   float* E = (float*)c->nns_e.p;
-  // e^T H e of every pair
+  // e^T H e of every pair; pairs whose error is at rounding level (a late
+  // sample of a stiff system, where x* - x_k keeps only FP32 noise) are not
+  // used: their direction carries no information
   std::vector<double> den(ns_);
+  std::vector<int> use;
   for (int j = 0; j < ns_; ++j) {
     float* e = E + (int64_t)j * n3;
     hvp_f32(c, e, (float*)c->nnhd.p);
@@ -2336,34 +2339,40 @@ int nn_train(mpml_ctx_s* c, int epochs, int batch, float lr, double* loss_first,
     cudaMemsetAsync(&d->slope, 0, sizeof(double), c->s);
     k_dot_ff<<<(unsigned)c->nb, BV, 0, c->s>>>(e, (const float*)c->nnhd.p, (const float*)c->ndinv.p, &d->slope);
     if ((rc = read_scalars(c))) return rc;
-    den[j] = c->hscal->slope > 0 ? c->hscal->slope : 1.0;
+    den[j] = c->hscal->slope;
+    if (den[j] > 1e-10 * den[0] && std::isfinite(den[j])) use.push_back(j);
   }
+  if (use.empty()) return MPML_ERR_NONFINITE;
   if (batch < 1) batch = 1;
   uint64_t rng = 0x9e3779b97f4a7c15ull;
-  std::vector<int> order(ns_);
+  const int nu = (int)use.size();
+  std::vector<int> order(nu);
   for (int ep = 0; ep < epochs; ++ep) {
-    for (int j = 0; j < ns_; ++j) order[j] = j;
-    for (int j = ns_ - 1; j > 0; --j) {  // Fisher-Yates with a fixed LCG
+    for (int j = 0; j < nu; ++j) order[j] = use[j];
+    for (int j = nu - 1; j > 0; --j) {  // Fisher-Yates with a fixed LCG
       rng = rng * 6364136223846793005ull + 1442695040888963407ull;
       const int k = (int)((rng >> 33) % (uint64_t)(j + 1));
       std::swap(order[j], order[k]);
     }
     double lsum = 0;
     int inb = 0;
-    for (int jj = 0; jj < ns_; ++jj) {
+    for (int jj = 0; jj < nu; ++jj) {
       const int j = order[jj];
       cudaMemcpyAsync(c->nr.p, R + (int64_t)j * n3, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->s);
       double l = 0;
-      if ((rc = nn_pair(c, den[j], 1.0f / (float)batch, &l, true))) return rc;
+      // lr = 0: evaluation only (no gradient, no update)
+      if ((rc = nn_pair(c, den[j], 1.0f / (float)batch, &l, lr != 0.f))) return rc;
       lsum += l;
-      if (++inb == batch || jj == ns_ - 1) {
-        nn_adam(c, lr, ++c->nn_adam_step);
-        if ((rc = nn_refresh_weights(c))) return rc;
+      if (++inb == batch || jj == nu - 1) {
+        if (lr != 0.f) {
+          nn_adam(c, lr, ++c->nn_adam_step);
+          if ((rc = nn_refresh_weights(c))) return rc;
+        }
         inb = 0;
       }
     }
-    if (ep == 0 && loss_first) *loss_first = lsum / ns_;
-    if (loss_last) *loss_last = lsum / ns_;
+    if (ep == 0 && loss_first) *loss_first = lsum / nu;
+    if (loss_last) *loss_last = lsum / nu;
   }
   return cuda_status(cudaStreamSynchronize(c->s));
 }
