@@ -342,34 +342,35 @@ struct CellOut {
 };
 
 // unit quaternion (w, x, y, z) of a rotation matrix (row-major), Shepperd's method
-__device__ __forceinline__ void rot_to_quat(const double R[9], double q[4]) {
-  const double tr = R[0] + R[4] + R[8];
+template <typename T>
+__device__ __forceinline__ void rot_to_quat(const T R[9], T q[4]) {
+  const T tr = R[0] + R[4] + R[8];
   if (tr > 0) {
-    const double s = 2.0 * sqrt(tr + 1.0);
-    q[0] = 0.25 * s;
+    const T s = T(2) * sqrt(tr + T(1));
+    q[0] = T(0.25) * s;
     q[1] = (R[7] - R[5]) / s;
     q[2] = (R[2] - R[6]) / s;
     q[3] = (R[3] - R[1]) / s;
   } else if (R[0] > R[4] && R[0] > R[8]) {
-    const double s = 2.0 * sqrt(1.0 + R[0] - R[4] - R[8]);
+    const T s = T(2) * sqrt(T(1) + R[0] - R[4] - R[8]);
     q[0] = (R[7] - R[5]) / s;
-    q[1] = 0.25 * s;
+    q[1] = T(0.25) * s;
     q[2] = (R[1] + R[3]) / s;
     q[3] = (R[2] + R[6]) / s;
   } else if (R[4] > R[8]) {
-    const double s = 2.0 * sqrt(1.0 + R[4] - R[0] - R[8]);
+    const T s = T(2) * sqrt(T(1) + R[4] - R[0] - R[8]);
     q[0] = (R[2] - R[6]) / s;
     q[1] = (R[1] + R[3]) / s;
-    q[2] = 0.25 * s;
+    q[2] = T(0.25) * s;
     q[3] = (R[5] + R[7]) / s;
   } else {
-    const double s = 2.0 * sqrt(1.0 + R[8] - R[0] - R[4]);
+    const T s = T(2) * sqrt(T(1) + R[8] - R[0] - R[4]);
     q[0] = (R[3] - R[1]) / s;
     q[1] = (R[2] + R[6]) / s;
     q[2] = (R[5] + R[7]) / s;
-    q[3] = 0.25 * s;
+    q[3] = T(0.25) * s;
   }
-  const double n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const T n = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
 #pragma unroll
   for (int i = 0; i < 4; ++i) q[i] /= n;
 }
@@ -391,57 +392,153 @@ __device__ __forceinline__ void trial_h(const double Gd[9], const double s6[6], 
     }
 }
 
-template <typename T>
-__device__ void cell_material(const MatParams<double>& M, double V, const double Gd[9] /* dt*G */,
-                              const double s6[6], double kq, double kk, bool want_k, CellOut<T>& out) {
-  double sm[9], H[9];
-  trial_h(Gd, s6, sm, H);
-  double U[9], s[3], e[3], Vv[9], Jm1;
-  svd_from_h<double>(H, U, s, e, Vv, Jm1);
-  Spec<double> sp;
-  if (!spectral<double>(M, s, e, Jm1, sp)) {
-    out.ok = false;
+// Eigenvalues of a symmetric 3x3 matrix (row-major), closed form by the
+// trigonometric solution of the characteristic cubic (FP64).
+__device__ __forceinline__ void sym3_eigenvalues(const double A[9], double w[3]) {
+  const double p1 = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+  const double q = (A[0] + A[4] + A[8]) / 3.0;
+  const double d0 = A[0] - q, d1 = A[4] - q, d2 = A[8] - q;
+  const double p2 = d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * p1;
+  if (!(p2 > 0.0)) {
+    w[0] = w[1] = w[2] = q;
     return;
   }
-  out.psi += V * sp.psi;
-  // W = S V = V + s V
-  double W[9];
+  const double p = sqrt(p2 / 6.0), ip = 1.0 / p;
+  const double b0 = d0 * ip, b1 = d1 * ip, b2 = d2 * ip, b01 = A[1] * ip, b02 = A[2] * ip, b12 = A[5] * ip;
+  double r = 0.5 * (b0 * (b1 * b2 - b12 * b12) - b01 * (b01 * b2 - b12 * b02) + b02 * (b01 * b12 - b1 * b02));
+  r = r < -1.0 ? -1.0 : (r > 1.0 ? 1.0 : r);
+  const double phi = acos(r) / 3.0;
+  w[0] = q + 2.0 * p * cos(phi);
+  w[2] = q + 2.0 * p * cos(phi + 2.0943951023931954923);
+  w[1] = 3.0 * q - w[0] - w[2];
+}
+
+// J - 1 of F = I + H from the invariants of H, without cancellation
+__device__ __forceinline__ double jm1_of_h(const double H[9]) {
+  const double trH = H[0] + H[4] + H[8];
+  double trH2 = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) trH2 += H[3 * a + b] * H[3 * b + a];
+  const double detH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                      H[2] * (H[3] * H[7] - H[4] * H[6]);
+  return trH + 0.5 * (trH * trH - trH2) + detH;
+}
+
+// Split Neo-Hookean P S^T of F = (I + dt G)(I + s) = I + H in FP64 without an
+// SVD: tau = mu J^{-2/3} dev(b) + kappa/2 (J^2 - 1) I with b - I = H + H^T +
+// H H^T, and P S^T = tau (I + dt G)^{-T}.  Returns false for J <= 0.
+__device__ bool nh_closed_form(const MatParams<double>& M, const double Gd[9], const double H[9], double PSt[9]) {
+  const double Jm1 = jm1_of_h(H);
+  if (!(Jm1 > -1.0)) return false;
+  double B[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      double acc = Vv[3 * a + b];
+      double acc = H[3 * a + b] + H[3 * b + a];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) acc += sm[3 * a + k] * Vv[3 * k + b];
-      W[3 * a + b] = acc;
+      for (int k = 0; k < 3; ++k) acc += H[3 * a + k] * H[3 * b + k];
+      B[3 * a + b] = acc;
     }
-  // Q += kq V U diag(d1) W^T   (P S^T = U diag(d1) V^T S = U diag(d1) W^T)
+  const double I1m3 = B[0] + B[4] + B[8];
+  const double kap = 2.0 / 3.0 * M.mu + M.lam;
+  const double cm1 = expm1(-2.0 / 3.0 * log1p(Jm1));  // J^{-2/3} - 1
+  const double c = 1.0 + cm1;
+  const double iso = 0.5 * kap * Jm1 * (2.0 + Jm1), mc = M.mu * c;
+  double tau[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) tau[q] = mc * B[q];
+  tau[0] += iso - mc * I1m3 / 3.0;
+  tau[4] += iso - mc * I1m3 / 3.0;
+  tau[8] += iso - mc * I1m3 / 3.0;
+  // A = I + dt G; A^{-T} = cof(A) / det(A)
+  const double a0 = 1.0 + Gd[0], a1 = Gd[1], a2 = Gd[2], a3 = Gd[3], a4 = 1.0 + Gd[4], a5 = Gd[5], a6 = Gd[6],
+               a7 = Gd[7], a8 = 1.0 + Gd[8];
+  double cof[9] = {a4 * a8 - a5 * a7, a5 * a6 - a3 * a8, a3 * a7 - a4 * a6,
+                   a2 * a7 - a1 * a8, a0 * a8 - a2 * a6, a1 * a6 - a0 * a7,
+                   a1 * a5 - a2 * a4, a2 * a3 - a0 * a5, a0 * a4 - a1 * a3};
+  const double det = a0 * cof[0] + a1 * cof[1] + a2 * cof[2];
+  const double idet = 1.0 / det;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      double acc = 0;
+    for (int b = 0; b < 3; ++b)
+      PSt[3 * a + b] = (tau[3 * a] * cof[b] + tau[3 * a + 1] * cof[3 + b] + tau[3 * a + 2] * cof[6 + b]) * idet;
+  return true;
+}
+
+// Energy density of F = I + H (FP64) from the eigenvalues of F^T F - I only;
+// returns false when it is undefined.  Fixed-corotated with J <= 0 (an inverted
+// cell, where the signed SVD is needed) reports `need_svd`.
+__device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double& psi, bool& need_svd) {
+  need_svd = false;
+  const double Jm1 = jm1_of_h(H);
+  if (M.model == MPML_NEO_HOOKEAN) {
+    if (!(Jm1 > -1.0)) return false;
+    const double I1m3 = 2.0 * (H[0] + H[4] + H[8]) + [&] {
+      double q = 0;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) acc += U[3 * a + k] * sp.d1[k] * W[3 * b + k];
-      out.Q[3 * a + b] += kq * V * acc;
-    }
-  if (!want_k) return;
-  T Ut[9], Wt[9], d2[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    Ut[i] = (T)U[i];
-    Wt[i] = (T)W[i];
-    d2[i] = (T)sp.d2[i];
+      for (int i = 0; i < 9; ++i) q += H[i] * H[i];
+      return q;
+    }();
+    const double kap = 2.0 / 3.0 * M.mu + M.lam;
+    const double cm1 = expm1(-2.0 / 3.0 * log1p(Jm1));
+    psi = 0.5 * M.mu * ((1.0 + cm1) * I1m3 + 3.0 * cm1) + 0.25 * kap * (2.0 * x_minus_log1p(Jm1) + Jm1 * Jm1);
+    return true;
   }
-  const T kv = (T)(kk * V);
+  if (M.model == MPML_FIXED_COROTATED && !(Jm1 > -1.0)) {
+    need_svd = true;
+    return true;
+  }
+  double E[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double acc = H[3 * a + b] + H[3 * b + a];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += H[3 * k + a] * H[3 * k + b];
+      E[3 * a + b] = acc;
+    }
+  double w[3], e[3];
+  sym3_eigenvalues(E, w);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const double li = w[i] > -1.0 ? w[i] : -1.0;
+    e[i] = li / (1.0 + sqrt(1.0 + li));  // singular value - 1
+  }
+  if (M.model == MPML_FIXED_COROTATED) {
+    psi = M.mu * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) + 0.5 * M.lam * Jm1 * Jm1;
+    return true;
+  }
+  // Hencky
+  if (!(Jm1 > -1.0) || !(e[0] > -1.0 && e[1] > -1.0 && e[2] > -1.0)) return false;
+  const double l0 = log1p(e[0]), l1 = log1p(e[1]), l2 = log1p(e[2]), tr = l0 + l1 + l2;
+  psi = M.mu * (l0 * l0 + l1 * l1 + l2 * l2) + 0.5 * M.lam * tr * tr;
+  return true;
+}
+
+// The projected tangent of one cell in the storage precision T from the signed
+// SVD (U, V, W = S V) and the isotropic eigen-data of psi: the 45-number
+// packed form and the 27-number compressed form (quaternions of U, V and of
+// the eigenbasis of the 3x3 block, S - I, clamped scaled eigenvalues).
+template <typename T>
+__device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[9], const T pp[3], const T pm[3], T kv,
+                              const double s6[6], CellOut<T>& out) {
   // diagonal block: eigen-decomposition of d2, clamp
   T ev[3], Qd[9];
   jacobi3<T>(d2, ev, Qd);
   {
     // compressed record (valid for single-material cells)
-    double Qq[9], q[4];
+    double Qq[9], q[4], Ud[9], Vd[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Qq[i] = (double)Qd[i];
+    for (int i = 0; i < 9; ++i) {
+      Qq[i] = (double)Qd[i];
+      Ud[i] = (double)Ut[i];
+      Vd[i] = (double)Vt[i];
+    }
     const double det = Qq[0] * (Qq[4] * Qq[8] - Qq[5] * Qq[7]) - Qq[1] * (Qq[3] * Qq[8] - Qq[5] * Qq[6]) +
                        Qq[2] * (Qq[3] * Qq[7] - Qq[4] * Qq[6]);
     if (det < 0) {
@@ -449,13 +546,13 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
       Qq[5] = -Qq[5];
       Qq[8] = -Qq[8];
     }
-    rot_to_quat(U, q);
+    rot_to_quat<double>(Ud, q);
 #pragma unroll
     for (int i = 0; i < 4; ++i) out.C[i] = (T)q[i];
-    rot_to_quat(Vv, q);
+    rot_to_quat<double>(Vd, q);
 #pragma unroll
     for (int i = 0; i < 4; ++i) out.C[4 + i] = (T)q[i];
-    rot_to_quat(Qq, q);
+    rot_to_quat<double>(Qq, q);
 #pragma unroll
     for (int i = 0; i < 4; ++i) out.C[8 + i] = (T)q[i];
 #pragma unroll
@@ -464,8 +561,8 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
     for (int m = 0; m < 3; ++m) out.C[18 + m] = ev[m] > T(0) ? kv * ev[m] : T(0);
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-      out.C[21 + p] = sp.pp[p] > 0 ? kv * (T)sp.pp[p] : T(0);
-      out.C[24 + p] = sp.pm[p] > 0 ? kv * (T)sp.pm[p] : T(0);
+      out.C[21 + p] = pp[p] > T(0) ? kv * pp[p] : T(0);
+      out.C[24 + p] = pm[p] > T(0) ? kv * pm[p] : T(0);
     }
   }
 #pragma unroll
@@ -494,7 +591,7 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
     const int i = pair_i(p), j = pair_j(p);
 #pragma unroll
     for (int sg = 0; sg < 2; ++sg) {
-      const T lamv = (T)(sg == 0 ? sp.pp[p] : sp.pm[p]);
+      const T lamv = sg == 0 ? pp[p] : pm[p];
       if (!(lamv > T(0))) continue;
       const T sgn = sg == 0 ? T(1) : T(-1);
       T d[9];
@@ -510,6 +607,107 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
         for (int cc = r; cc < 9; ++cc) out.K[k45(r, cc)] += lam * d[r] * d[cc];
     }
   }
+}
+
+
+template <typename T>
+__device__ void cell_material(const MatParams<double>& M, double V, const double Gd[9] /* dt*G */,
+                              const double s6[6], double kq, double kk, bool want_k, CellOut<T>& out) {
+  double sm[9], H[9];
+  trial_h(Gd, s6, sm, H);
+  if constexpr (sizeof(T) == 4) {
+    if (M.model == MPML_NEO_HOOKEAN) {
+      // stress and energy in closed form (FP64); the tangent from an FP32 SVD
+      double psi, PSt[9];
+      bool need_svd;
+      if (!nh_closed_form(M, Gd, H, PSt) || !psi_from_h(M, H, psi, need_svd)) {
+        out.ok = false;
+        return;
+      }
+      out.psi += V * psi;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) out.Q[q] += kq * V * PSt[q];
+      if (!want_k) return;
+      float Hf[9], Uf[9], sf[3], ef[3], Vf[9], Jm1f, Wf[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Hf[q] = (float)H[q];
+      svd_from_h<float>(Hf, Uf, sf, ef, Vf, Jm1f);
+      MatParams<float> Mf;
+      Mf.model = M.model;
+      Mf.mu = (float)M.mu;
+      Mf.lam = (float)M.lam;
+      Spec<float> spf;
+      if (!spectral<float>(Mf, sf, ef, Jm1f, spf)) {
+        out.ok = false;
+        return;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          float acc = Vf[3 * a + b];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) acc += (float)sm[3 * a + k] * Vf[3 * k + b];
+          Wf[3 * a + b] = acc;
+        }
+      build_tangent<T>(Uf, Vf, Wf, spf.d2, spf.pp, spf.pm, (float)(kk * V), s6, out);
+      return;
+    }
+  }
+  double U[9], s[3], e[3], Vv[9], Jm1;
+  svd_from_h<double>(H, U, s, e, Vv, Jm1);
+  Spec<double> sp;
+  if (!spectral<double>(M, s, e, Jm1, sp)) {
+    out.ok = false;
+    return;
+  }
+  {
+    // the energy by the same formula as the line search (k_energy_cells)
+    double psi;
+    bool need_svd;
+    if (!psi_from_h(M, H, psi, need_svd)) {
+      out.ok = false;
+      return;
+    }
+    out.psi += V * (need_svd ? sp.psi : psi);
+  }
+  // W = S V = V + s V
+  double W[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double acc = Vv[3 * a + b];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += sm[3 * a + k] * Vv[3 * k + b];
+      W[3 * a + b] = acc;
+    }
+  // Q += kq V U diag(d1) W^T   (P S^T = U diag(d1) V^T S = U diag(d1) W^T)
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double acc = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += U[3 * a + k] * sp.d1[k] * W[3 * b + k];
+      out.Q[3 * a + b] += kq * V * acc;
+    }
+  if (!want_k) return;
+  T Ut[9], Wt[9], Vt[9], d2[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    Ut[i] = (T)U[i];
+    Wt[i] = (T)W[i];
+    Vt[i] = (T)Vv[i];
+    d2[i] = (T)sp.d2[i];
+  }
+  T pp[3], pm[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    pp[p] = (T)sp.pp[p];
+    pm[p] = (T)sp.pm[p];
+  }
+  build_tangent<T>(Ut, Vt, Wt, d2, pp, pm, (T)(kk * V), s6, out);
 }
 
 // node init: g = m (v - vhat) (FP64), diag = m, inertia energy (all bricks, 512 thr)
@@ -1365,14 +1563,23 @@ __global__ void __launch_bounds__(256) k_energy_cells(const int* __restrict__ cb
 #pragma unroll
       for (int q = 0; q < 6; ++q) s6[q] = cs[(((int64_t)id * si.nm + k) * 6 + q) * BV + l];
       trial_h(Gd, s6, sm, H);
-      double U[9], s[3], e[3], Vv[9], Jm1;
-      svd_from_h<double>(H, U, s, e, Vv, Jm1);
-      Spec<double> sp;
-      if (!spectral<double>(si.mat[k], s, e, Jm1, sp)) {
+      double psi;
+      bool need_svd;
+      if (!psi_from_h(si.mat[k], H, psi, need_svd)) {
         bad = 1;
         continue;
       }
-      esum += V * sp.psi;
+      if (need_svd) {
+        double U[9], s[3], e[3], Vv[9], Jm1;
+        svd_from_h<double>(H, U, s, e, Vv, Jm1);
+        Spec<double> sp;
+        if (!spectral<double>(si.mat[k], s, e, Jm1, sp)) {
+          bad = 1;
+          continue;
+        }
+        psi = sp.psi;
+      }
+      esum += V * psi;
     }
   }
   if (bad) atomicAdd(&sc->infeasible, 1);
