@@ -198,12 +198,38 @@ __device__ bool invert_principal(int model, double mu, double lam, const double 
     if (d < 0) return false;
     double lo = 0.5, hi = 0.5 + sqrt(d);
     if (fc_h(mu, lam, t, lo) < 0 || fc_h(mu, lam, t, hi) > 0) return false;
-    for (int it = 0; it < 200; ++it) {
-      double mid = 0.5 * (lo + hi);
-      if (mid <= lo || mid >= hi) break;
-      if (fc_h(mu, lam, t, mid) > 0) lo = mid; else hi = mid;
+    // safeguarded Newton on h(J) = prod s_i(J) - J (decreasing on the bracket):
+    // a Newton step that leaves the bracket is replaced by bisection
+    double J = exp((t[0] + t[1] + t[2]) / (2 * mu + 3 * lam));
+    if (!(J > lo && J < hi)) J = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; ++it) {
+      const double cJ = lam * J * (J - 1), dc = lam * (2 * J - 1);
+      double sv[3], prod = 1, dprod = 0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double disc = 0.25 + (t[i] - cJ) / (2 * mu);
+        sv[i] = 0.5 + sqrt(disc > 0 ? disc : 0);
+      }
+      prod = sv[0] * sv[1] * sv[2];
+      const double h = prod - J;
+      if (h > 0) lo = J; else hi = J;
+      if (h == 0) break;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double r = sv[i] - 0.5;  // sqrt(disc)
+        const double ds = r > 0 ? -dc / (4 * mu * r) : 0;
+        dprod += ds * (prod / sv[i]);
+      }
+      const double dh = dprod - 1;
+      double Jn = (dh < 0) ? J - h / dh : 0.5 * (lo + hi);
+      if (!(Jn > lo && Jn < hi)) Jn = 0.5 * (lo + hi);
+      if (fabs(Jn - J) <= 4e-16 * J || hi - lo <= 2e-16 * hi) {
+        J = Jn;
+        break;
+      }
+      J = Jn;
     }
-    return fc_sigma(mu, lam, t, 0.5 * (lo + hi), s);
+    return fc_sigma(mu, lam, t, J, s);
   }
   return false;
 }
@@ -469,6 +495,56 @@ __device__ bool nh_closed_form(const MatParams<double>& M, const double Gd[9], c
   return true;
 }
 
+// Fixed-corotated P S^T of F = (I + dt G)(I + s) = I + H in FP64 without an
+// SVD: the rotation R of the polar decomposition by Newton's iteration
+// X <- (X + X^-T) / 2 from X = F (quadratic convergence; F is near a
+// rotation), then P S^T = 2 mu (F - R) S + lam (J - 1) J (I + dt G)^{-T}.
+// Returns false for J <= 0 (inverted cells keep the signed-SVD path).
+__device__ bool fc_closed_form(const MatParams<double>& M, const double Gd[9], const double H[9], const double sm[9],
+                               double PSt[9]) {
+  const double Jm1 = jm1_of_h(H);
+  if (!(Jm1 > -1.0)) return false;
+  double X[9] = {1.0 + H[0], H[1], H[2], H[3], 1.0 + H[4], H[5], H[6], H[7], 1.0 + H[8]};
+  for (int it = 0; it < 12; ++it) {
+    const double c0 = X[4] * X[8] - X[5] * X[7], c1 = X[5] * X[6] - X[3] * X[8], c2 = X[3] * X[7] - X[4] * X[6];
+    const double c3 = X[2] * X[7] - X[1] * X[8], c4 = X[0] * X[8] - X[2] * X[6], c5 = X[1] * X[6] - X[0] * X[7];
+    const double c6 = X[1] * X[5] - X[2] * X[4], c7 = X[2] * X[3] - X[0] * X[5], c8 = X[0] * X[4] - X[1] * X[3];
+    const double idet = 1.0 / (X[0] * c0 + X[1] * c1 + X[2] * c2);
+    const double cof[9] = {c0, c1, c2, c3, c4, c5, c6, c7, c8};  // X^{-T} = cof / det
+    double diff = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double xn = 0.5 * (X[q] + cof[q] * idet);
+      diff = fmax(diff, fabs(xn - X[q]));
+      X[q] = xn;
+    }
+    if (diff <= 4e-16) break;
+  }
+  // F - R with F = I + H
+  double FR[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) FR[q] = ((q % 4 == 0) ? 1.0 : 0.0) + H[q] - X[q];
+  const double J = 1.0 + Jm1;
+  const double kJ = M.lam * Jm1 * J;
+  const double a0 = 1.0 + Gd[0], a1 = Gd[1], a2 = Gd[2], a3 = Gd[3], a4 = 1.0 + Gd[4], a5 = Gd[5], a6 = Gd[6],
+               a7 = Gd[7], a8 = 1.0 + Gd[8];
+  const double cof[9] = {a4 * a8 - a5 * a7, a5 * a6 - a3 * a8, a3 * a7 - a4 * a6,
+                         a2 * a7 - a1 * a8, a0 * a8 - a2 * a6, a1 * a6 - a0 * a7,
+                         a1 * a5 - a2 * a4, a2 * a3 - a0 * a5, a0 * a4 - a1 * a3};
+  const double idet = 1.0 / (a0 * cof[0] + a1 * cof[1] + a2 * cof[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      // (F - R) S with S = I + sm (symmetric)
+      double fs = FR[3 * a + b];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) fs += FR[3 * a + k] * sm[3 * k + b];
+      PSt[3 * a + b] = 2.0 * M.mu * fs + kJ * cof[3 * a + b] * idet;
+    }
+  return true;
+}
+
 // Energy density of F = I + H (FP64) from the eigenvalues of F^T F - I only;
 // returns false when it is undefined.  Fixed-corotated with J <= 0 (an inverted
 // cell, where the signed SVD is needed) reports `need_svd`.
@@ -616,11 +692,18 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
   double sm[9], H[9];
   trial_h(Gd, s6, sm, H);
   if constexpr (sizeof(T) == 4) {
-    if (M.model == MPML_NEO_HOOKEAN) {
-      // stress and energy in closed form (FP64); the tangent from an FP32 SVD
-      double psi, PSt[9];
+    double PSt[9];
+    const bool closed = (M.model == MPML_NEO_HOOKEAN && nh_closed_form(M, Gd, H, PSt)) ||
+                        (M.model == MPML_FIXED_COROTATED && fc_closed_form(M, Gd, H, sm, PSt));
+    if (M.model == MPML_NEO_HOOKEAN && !closed) {
+      out.ok = false;
+      return;
+    }
+    if (closed) {
+      // stress and energy without an FP64 SVD; the tangent from an FP32 SVD
+      double psi;
       bool need_svd;
-      if (!nh_closed_form(M, Gd, H, PSt) || !psi_from_h(M, H, psi, need_svd)) {
+      if (!psi_from_h(M, H, psi, need_svd) || need_svd) {
         out.ok = false;
         return;
       }
