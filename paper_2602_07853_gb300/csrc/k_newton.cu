@@ -1956,15 +1956,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag) {
   return *s_flag != 0;
 }
 
-// block sums of 2 values added atomically to acc[0..1] (thread 0)
-__device__ __forceinline__ void block_atomic2(double a, double b, double* acc) {
+// Warp sum of FP32 values in float-float arithmetic (error-free two-sum at
+// every level, the rounding errors carried in a second float), returned as
+// a double on lane 0: FP64-grade accuracy without a chain of FP64 additions.
+__device__ __forceinline__ double warp_sum_ff(float v) {
+  float hi = v, lo = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_down_sync(0xffffffffu, hi, o), bl = __shfl_down_sync(0xffffffffu, lo, o);
+    const float s = hi + bh;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (bh - bp);
+    lo = lo + bl + e;
+    hi = s;
+  }
+  return (double)hi + (double)lo;
+}
+
+// block sums of 2 FP32 per-thread partials (float-float within warps, FP64
+// across warps) added atomically to acc[0..1] (thread 0)
+__device__ __forceinline__ void block_atomic2(float a, float b, double* acc) {
   __shared__ double red2[2][32];
-  a = warp_sum(a);
-  b = warp_sum(b);
+  const double wa = warp_sum_ff(a), wb = warp_sum_ff(b);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    red2[0][wid] = a;
-    red2[1][wid] = b;
+    red2[0][wid] = wa;
+    red2[1][wid] = wb;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -2187,7 +2204,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       z[0] = 0.0;
       z[1] = 0.0;
     }
-    block_atomic2((double)pmp, (double)pkp, accH);
+    block_atomic2(pmp, pkp, accH);
     if (!grid_barrier(A.gbar, &s_flag)) {
       alive = false;
       break;
@@ -2247,7 +2264,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       z[0] = 0.0;
       z[1] = 0.0;
     }
-    block_atomic2((double)rzl, (double)rrl, accA);
+    block_atomic2(rzl, rrl, accA);
     if (!grid_barrier(A.gbar, &s_flag)) {
       alive = false;
       break;
