@@ -94,6 +94,7 @@ def lib():
             "orc_unload": (C.c_int, [_VP, C.c_long, _D, _D, _D, _D, _D, _D, _I]),
             "orc_stretch": (C.c_int, [_VP]),
             "orc_newton": (C.c_int, [_VP, C.POINTER(Solver), C.POINTER(Stats)]),
+            "orc_explicit": (C.c_int, [_VP]),
             "orc_load": (C.c_int, [_VP, _D, _D, _D, _D, _D, _D, _I]),
             "orc_count": (C.c_long, [_VP, C.c_int]),
             "orc_get_perm": (None, [_VP, _L]),
@@ -285,6 +286,18 @@ class Oracle:
         solver = solver or default_solver()
         rc = lib().orc_newton(self._h, C.byref(solver), C.byref(st))
         return rc, st
+
+    def explicit(self):
+        """Algorithm 3, explicit branch: node velocities from the explicit internal force."""
+        return lib().orc_explicit(self._h)
+
+    def explicit_step(self, particles):
+        """Algorithm 1 with the explicit integrator: (status, new particles (sorted))."""
+        rc = self.unload(**particles)
+        if rc:
+            return rc, None
+        self.explicit()
+        return self.load()
 
     def load(self):
         n = self.count("particles")

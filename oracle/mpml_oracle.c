@@ -962,6 +962,21 @@ void orc_explicit_force(const orc_state* st, double* f) {
     }
 }
 
+/* Algorithm 3, explicit branch: f_i = -sum_c sum_k V_ck tau_ck grad w_ic
+ * (the explicit internal force of Sec. 4), v_i^{n+1} = vhat_i + dt f_i / m_i
+ * on free DOFs (gravity is in vhat as in the implicit branch), prescribed
+ * values on Dirichlet nodes. */
+int orc_explicit(orc_state* st) {
+  double* f = (double*)malloc(sizeof(double) * 3 * (st->nn ? st->nn : 1));
+  orc_explicit_force(st, f);
+  for (long i = 0; i < st->nn; ++i)
+    for (int r = 0; r < 3; ++r)
+      st->vnew[3 * i + r] = st->fixed[i] ? st->vfix[3 * i + r]
+                                         : st->vhat[3 * i + r] + st->sc.dt * f[3 * i + r] / st->m_i[i];
+  free(f);
+  return ORC_OK;
+}
+
 static double dot(long n, const double* a, const double* b) {
   double s = 0;
   for (long i = 0; i < n; ++i) s += a[i] * b[i];

@@ -99,6 +99,9 @@ int orc_unload(orc_state* st, long np, const double* x, const double* v,
 /* Algorithm 3 (implicit): stretch reconstruction then the Newton solve. */
 int orc_stretch(orc_state* st);
 int orc_newton(orc_state* st, const orc_solver* opt, orc_stats* stats);
+/* Algorithm 3, explicit branch (after orc_unload): v^{n+1} = vhat + dt f / m
+ * with the explicit internal force, Dirichlet values on fixed nodes. */
+int orc_explicit(orc_state* st);
 /* Algorithm 4.  Writes the updated particles in the sorted order. */
 int orc_load(orc_state* st, double* x, double* v, double* F, double* G,
              double* mp, double* Vp, int* mat);
