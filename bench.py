@@ -276,6 +276,30 @@ def other_configs(m, scenes, args, peaks):
     del made, init
     torch.cuda.empty_cache()
 
+    # the explicit integrator on the two-sphere workload (dt below the elastic CFL limit)
+    sc = scenes.two_spheres(168, gap=1.0 / 168, dt=5e-5)
+    stream = torch.cuda.current_stream()
+    ctx, p, pp = make(sc, stream)
+    ms = []
+    for s in range(3 + 10):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m.mpml_set_time(ctx, s * sc.dt)
+        m.mpml_resample(ctx, pp)
+        m.mpml_explicit_step(ctx)
+        m.mpml_g2p(ctx, pp)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if s >= 3:
+            ms.append(a.elapsed_time(b))
+    out["explicit_two_spheres_168"] = {"dt": sc.dt, "particles": int(sc.num_particles),
+                                       "steps_per_s": 1e3 * len(ms) / float(np.sum(ms)),
+                                       "ms_per_step": float(np.mean(ms)),
+                                       "solver": "mpml_resample + mpml_explicit_step + mpml_g2p"}
+    m.mpml_destroy(ctx)
+    del p
+    torch.cuda.empty_cache()
+
     # config 5 at full size and the 3-8M pressed block: step time and HVP bandwidth
     for key, sc, nstep in (("slab_on_sand_256", scenes.slab_on_sand(256), 2),
                            ("pressed_block_236", scenes.pressed_block(236), 2)):

@@ -178,6 +178,13 @@ int mpml_resample(mpml_ctx ctx, const mpml_particles* p);
 /* Algorithm 3, implicit.  Synchronises (convergence tests); fills stats if
  * non-NULL.  opts may be NULL (defaults). */
 int mpml_newton_step(mpml_ctx ctx, const mpml_solver_opts* opts, mpml_solve_stats* stats);
+/* Algorithm 3, explicit branch (after mpml_resample; instead of
+ * mpml_newton_step): node velocities v^{n+1} = vhat + dt f / m with the
+ * explicit internal force f_i = -sum_c sum_k V_ck tau_ck grad w_ic (Sec. 4),
+ * Dirichlet values on fixed nodes; no stretch reconstruction or solve.  The
+ * step is stable only below the elastic CFL limit (dt < dx / sqrt(E / rho)
+ * roughly).  Asynchronous; follow with mpml_g2p. */
+int mpml_explicit_step(mpml_ctx ctx);
 /* Batches of independent scenes (one context each, on one device; each context
  * on its own stream or a shared one; at most MPML_BATCH_MAX, all distinct).
  * Not in the paper: the workload statement asks for many scenes of uneven
@@ -296,6 +303,9 @@ int mpml_nn_apply(mpml_ctx ctx, const double* r, double* z);
  * and its weight gradient (written to the gradient accumulator, which is
  * zeroed first). */
 int mpml_nn_loss_grad(mpml_ctx ctx, const double* r, const double* e, double* loss);
+/* One Adam step (learning rate lr > 0) with the weight gradient left by
+ * mpml_nn_loss_grad, which it then zeroes: training on caller-chosen pairs. */
+int mpml_nn_adam_step(mpml_ctx ctx, float lr);
 /* Trains on the current Newton system (after mpml_resample): reconstructs the
  * stretches, solves the first Newton system with Jacobi-PCG, takes
  * `samples` pairs (r_k, x* - x_k) along the way and runs Adam on the loss

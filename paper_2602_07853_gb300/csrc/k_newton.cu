@@ -2862,6 +2862,80 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
   return status;
 }
 
+// ---- explicit integrator (Algorithm 3, explicit branch) ---------------------
+// f_i = -sum_c sum_k V_ck tau_ck grad w_ic with grad w_ic = +-1/(4 dx) per
+// component; the P2Q accumulators already hold the extensive V_ck tau_ck.
+template <typename T>
+__global__ void __launch_bounds__(256) k_explicit_cells(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                                        const uint8_t* __restrict__ cflag, const T* __restrict__ acc,
+                                                        SolveInfo si, double* f) {
+  const int id = cblist[blockIdx.x];
+  const double gw = 0.25 / si.dx;
+  for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+    if (!cflag[(int64_t)id * BV + l]) continue;
+    double t6[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < si.nm; ++k)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) t6[q] += (double)acc[((int64_t)id * si.nf + acc_tau(k) + q) * BV + l];
+    const double Tm[9] = {t6[0], t6[3], t6[4], t6[3], t6[1], t6[5], t6[4], t6[5], t6[2]};
+    const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const double g0 = (o & 1) ? gw : -gw, g1 = (o & 2) ? gw : -gw, g2 = (o & 4) ? gw : -gw;
+      const int nx = lx + (o & 1), ny = ly + ((o >> 1) & 1), nz = lz + ((o >> 2) & 1);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double* fp = node_ptr(f, id, nbr, nx, ny, nz, a);
+        if (fp) atomicAdd(fp, -(Tm[3 * a] * g0 + Tm[3 * a + 1] * g1 + Tm[3 * a + 2] * g2));
+      }
+    }
+  }
+}
+
+// v^{n+1} = vhat + dt f / m on free DOFs, prescribed values on Dirichlet nodes
+template <typename T>
+__global__ void __launch_bounds__(512) k_explicit_nodes(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
+                                                        const double* __restrict__ vhat,
+                                                        const double* __restrict__ vfix, const double* __restrict__ f,
+                                                        double dt, double* vnew) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  const int64_t slot = (int64_t)id * BV + l;
+  const uint8_t fl = nflag[slot];
+  const double mi = (double)m[slot];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+    double v = 0.0;
+    if (fl & NF_FIXED)
+      v = vfix[o];
+    else if ((fl & NF_DOF) && mi > 0.0)
+      v = vhat[o] + dt * f[o] / mi;
+    vnew[o] = v;
+  }
+}
+
+template <typename T>
+static int explicit_t(mpml_ctx_s* c) {
+  int rc = alloc_solver<T>(c);
+  if (rc) return rc;
+  if (c->nb == 0) return MPML_OK;
+  SolveInfo si = solve_info(c);
+  double* f = (double*)c->ng.p;
+  cudaMemsetAsync(f, 0, sizeof(double) * 3 * c->nb * BV, c->s);
+  if (c->ncb > 0) {
+    k_explicit_cells<T><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
+                                                           (const uint8_t*)c->cflag.p, (const T*)c->cacc.p, si, f);
+    c->launches++;
+  }
+  k_explicit_nodes<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
+                                                       (const double*)c->nvhat.p, (const double*)c->nvfix.p, f,
+                                                       c->d.dt, (double*)c->nvnew.p);
+  c->launches++;
+  return cuda_status(cudaGetLastError());
+}
+
+int explicit_solve(mpml_ctx_s* c) { return c->fp64 ? explicit_t<double>(c) : explicit_t<float>(c); }
+
 int newton_solve(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st) {
   return c->fp64 ? newton_t<double>(c, o, st) : newton_t<float>(c, o, st);
 }

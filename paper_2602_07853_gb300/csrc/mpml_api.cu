@@ -458,6 +458,15 @@ int mpml_newton_step_batch(mpml_ctx* ctxs, int n, const mpml_solver_opts* o, mpm
   return rc;
 }
 
+int mpml_explicit_step(mpml_ctx c) {
+  if (!c || c->stage < 1) return MPML_ERR_ARG;
+  int rc = explicit_solve(c);
+  if (rc) return rc;
+  c->stage = 3;
+  c->have_lin = 0;
+  return MPML_OK;
+}
+
 int mpml_g2p(mpml_ctx c, const mpml_particles* p) {
   if (!c || bad_particles(p) || c->stage < 1 || p->n != c->np_count) return MPML_ERR_ARG;
   const int64_t n = p->n;
@@ -655,6 +664,15 @@ int mpml_nn_apply(mpml_ctx c, const double* r, double* z) {
   free_buf(rin);
   free_buf(zout);
   return rc;
+}
+
+int mpml_nn_adam_step(mpml_ctx c, float lr) {
+  if (!c || !c->nn_ready || !(lr > 0.f)) return MPML_ERR_ARG;
+  int rc = nn_ensure(c);
+  if (rc) return rc;
+  nn_adam(c, lr, ++c->nn_adam_step);
+  if ((rc = nn_refresh_weights(c))) return rc;
+  return cuda_status(cudaStreamSynchronize(c->s));
 }
 
 int mpml_nn_loss_grad(mpml_ctx c, const double* r, const double* e, double* loss) {

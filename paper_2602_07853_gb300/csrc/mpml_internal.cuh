@@ -185,6 +185,7 @@ int resample_device_end(mpml_ctx_s* c, const void* x, const void* v, const void*
 int p2q_q2n(mpml_ctx_s* c);
 int stretch_all(mpml_ctx_s* c);
 int newton_solve(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st);
+int explicit_solve(mpml_ctx_s* c);
 int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve_stats* st);
 int g2p_device(mpml_ctx_s* c, void* x, void* v, void* F, void* G, void* m, void* V, int32_t* mat);
 

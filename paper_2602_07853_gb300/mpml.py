@@ -86,6 +86,7 @@ EXPORTS = {
     "mpml_resample": (C.c_int, [C.c_void_p, C.POINTER(mpml_particles)]),
     "mpml_newton_step": (C.c_int, [C.c_void_p, C.POINTER(mpml_solver_opts), C.POINTER(mpml_solve_stats)]),
     "mpml_g2p": (C.c_int, [C.c_void_p, C.POINTER(mpml_particles)]),
+    "mpml_explicit_step": (C.c_int, [C.c_void_p]),
     "mpml_newton_step_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(mpml_solver_opts),
                                          C.POINTER(mpml_solve_stats)]),
     "mpml_resample_batch": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(mpml_particles), C.c_int]),
@@ -108,6 +109,7 @@ EXPORTS = {
     "mpml_nn_get_grad": (C.c_int, [C.c_void_p, C.POINTER(C.c_float)]),
     "mpml_nn_apply": (C.c_int, [C.c_void_p, _D, _D]),
     "mpml_nn_loss_grad": (C.c_int, [C.c_void_p, _D, _D, _D]),
+    "mpml_nn_adam_step": (C.c_int, [C.c_void_p, C.c_float]),
     "mpml_nn_train": (C.c_int, [C.c_void_p, C.POINTER(mpml_train_opts), C.POINTER(mpml_train_stats)]),
     "mpml_sort_particles_noalloc": (C.c_int, [C.POINTER(C.c_int), C.c_double, C.c_int, C.c_void_p, C.c_int64,
                                               C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -197,6 +199,10 @@ def mpml_newton_step_batch(ctxs, opts: mpml_solver_opts | None = None):
     rc = load().mpml_newton_step_batch(arr, n, C.byref(opts) if opts is not None else None, stats)
     _check(rc, "mpml_newton_step_batch")
     return rc, list(stats)
+
+
+def mpml_explicit_step(ctx):
+    return _check(load().mpml_explicit_step(ctx), "mpml_explicit_step")
 
 
 def mpml_g2p(ctx, p: mpml_particles):
@@ -408,6 +414,10 @@ def mpml_nn_loss_grad(ctx, r, e):
     _check(load().mpml_nn_loss_grad(ctx, r.ctypes.data_as(_D), e.ctypes.data_as(_D), C.byref(loss)),
            "mpml_nn_loss_grad")
     return loss.value, mpml_nn_get_grad(ctx)
+
+
+def mpml_nn_adam_step(ctx, lr):
+    return _check(load().mpml_nn_adam_step(ctx, float(lr)), "mpml_nn_adam_step")
 
 
 def train_opts(samples=32, rtol=1e-8, cg_max=20000, epochs=20, batch=4, lr=1e-3):

@@ -181,3 +181,26 @@ def test_trained_network_gains_over_jacobi_on_an_unseen_system():
     assert ev_learned.loss_first < ev_jacobi.loss_first
     del trained
     g.close()
+
+
+def test_adam_step_on_caller_pairs():
+    """mpml_nn_adam_step applies the gradient of mpml_nn_loss_grad and zeroes it; a few steps
+    on one pair lower that pair's loss."""
+    sc = small_scene()
+    g, o, vhat = linearized_pair(sc)
+    m.mpml_nn_set_weights(g.ctx, m.nn_init_weights(5, gain=0.5))
+    rng = np.random.default_rng(9)
+    d = o.diag()
+    r = rng.standard_normal(vhat.shape) * (d > 0)
+    e = rng.standard_normal(vhat.shape) * (d > 0)
+    l0, grad0 = m.mpml_nn_loss_grad(g.ctx, r, e)
+    w0 = m.mpml_nn_get_weights(g.ctx)
+    m.mpml_nn_adam_step(g.ctx, 1e-3)
+    assert all(np.abs(x).max() == 0 for x in m.mpml_nn_get_grad(g.ctx))
+    assert any(not np.array_equal(a, b) for a, b in zip(w0, m.mpml_nn_get_weights(g.ctx)))
+    for _ in range(20):
+        m.mpml_nn_loss_grad(g.ctx, r, e)
+        m.mpml_nn_adam_step(g.ctx, 1e-3)
+    l1, _ = m.mpml_nn_loss_grad(g.ctx, r, e)
+    assert l1 < l0
+    g.close()
