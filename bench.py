@@ -300,6 +300,40 @@ def other_configs(m, scenes, args, peaks):
     del p
     torch.cuda.empty_cache()
 
+    # particles-per-cell independence (the paper's claim for integration without particles):
+    # Newton time should stay flat over PPC 8 / 16 / 24 while P2Q and G2P grow with PPC
+    ppc_rows = []
+    for ppc in (8, 16, 24):
+        sc = scenes.two_spheres(128, gap=1.0 / 128, ppc=ppc)
+        stream = torch.cuda.current_stream()
+        ctx, p, pp = make(sc, stream)
+        init = {k: v.clone() for k, v in p.items()}
+        acc = {"unload": [], "integrate": [], "load": []}
+        for s in range(1 + 3):
+            for k in p:
+                p[k].copy_(init[k])
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
+            m.mpml_resample(ctx, pp)
+            ev[1].record(stream)
+            rc, st = m.mpml_newton_step(ctx, m.solver_opts())
+            ev[2].record(stream)
+            m.mpml_g2p(ctx, pp)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            if s >= 1:
+                acc["unload"].append(ev[0].elapsed_time(ev[1]))
+                acc["integrate"].append(ev[1].elapsed_time(ev[2]))
+                acc["load"].append(ev[2].elapsed_time(ev[3]))
+        ppc_rows.append({"ppc": ppc, "particles": int(sc.num_particles),
+                         "unload_ms": float(np.mean(acc["unload"])), "integrate_ms": float(np.mean(acc["integrate"])),
+                         "load_ms": float(np.mean(acc["load"])), "newton_iters": int(st.newton_iters),
+                         "cg_iters": int(st.cg_iters_total)})
+        m.mpml_destroy(ctx)
+        del p, init
+        torch.cuda.empty_cache()
+    out["ppc_independence_two_spheres_128"] = ppc_rows
+
     # config 5 at full size and the 3-8M pressed block: step time and HVP bandwidth
     for key, sc, nstep in (("slab_on_sand_256", scenes.slab_on_sand(256), 2),
                            ("pressed_block_236", scenes.pressed_block(236), 2)):
