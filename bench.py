@@ -207,6 +207,26 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# Multi-rank aggregation (replicas: one process per GPU, no data-path collective)
+# ---------------------------------------------------------------------------
+def max_over_ranks(value, dist, device):
+    """The largest per-rank duration over all ranks (every rank receives it); `dist` is
+    torch.distributed or None for a single process."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, seconds):
+    """Whole-job steps/s: every rank runs `steps` steps of its own replica."""
+    return world * steps / seconds
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def other_configs(m, scenes, args, peaks):
@@ -501,16 +521,12 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     launches = m.mpml_kernel_launches(ctx) - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(np.sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), dist, "cuda")
     hvp_n, hvp_ms, hvp_bytes = m.mpml_hvp_timing(ctx)
     pcg_n, pcg_iters, pcg_ms = m.mpml_pcg_timing(ctx)
     m.mpml_set_profiling(ctx, 0)
     counts = m.mpml_counts(ctx)
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_throughput(world, args.steps, total_ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     e2e = None
@@ -536,9 +552,10 @@ def run_ours(args, rank, world, local_rank):
             m.mpml_newton_step(ctx, opts)
             m.mpml_g2p(ctx, hparts)  # synchronises after the device-to-host copies
             t_e2e += time.perf_counter() - t0
+        t_e2e = max_over_ranks(t_e2e, dist, "cuda")
         n = sc.num_particles
         per = 4 * (3 + 3 + 9 + 9 + 1 + 1) + 4
-        e2e = {"value": world * args.steps / t_e2e, "unit": "steps/s", "h2d_bytes_per_step": n * per,
+        e2e = {"value": job_throughput(world, args.steps, t_e2e), "unit": "steps/s", "h2d_bytes_per_step": n * per,
                "d2h_bytes_per_step": n * per}
 
     peaks, peak_kind = measured_peaks()

@@ -274,3 +274,49 @@ def test_full_size_two_spheres():
     # the oracle's own FP64 gradient at the GPU solution meets the Newton tolerance
     assert np.linalg.norm(g1) <= 2e-6 * np.linalg.norm(g_o)
     g.close()
+
+
+def mixture_scene(nmat, seed=11, n=16, count=4000):
+    """Random particles of nmat materials (all three models), so most cells mix them (Sec. 4.4)."""
+    rng = np.random.default_rng(seed)
+    mats = [scenes.Material(scenes.FIXED_COROTATED, 1e5, 0.3), scenes.Material(scenes.NEO_HOOKEAN, 3e4, 0.4, rho=2000.0),
+            scenes.Material(scenes.HENCKY, 5e4, 0.25, rho=1500.0), scenes.Material(scenes.FIXED_COROTATED, 2e5, 0.35)]
+    sc = scenes.Scene("mixture", (n, n, n), 1.0 / n, float(n), 1e-3, (0.0, -9.8, 0.0), mats[:nmat])
+    x = rng.uniform(2.6 / n, 1 - 2.6 / n, (count, 3))
+    sc.x = x
+    sc.v = 0.1 * rng.standard_normal((count, 3))
+    sc.G = 0.1 * rng.standard_normal((count, 3, 3))
+    sc.F = np.eye(3) + 0.02 * rng.standard_normal((count, 3, 3))
+    sc.Vp = np.full(count, sc.dx ** 3 / 8)
+    sc.mat = rng.integers(0, nmat, count).astype(np.int32)
+    sc.mp = np.array([mt.rho for mt in sc.materials])[sc.mat] * sc.Vp
+    return sc
+
+
+@pytest.mark.parametrize("precision,nmat", [(m.FP32, 4), (m.FP64, 3)])
+def test_material_mixtures_up_to_the_slot_limit(precision, nmat):
+    """Four materials in FP32 and three in FP64 (the P2Q shared-memory budget): unload fields,
+    stretches, energy, gradient and HVP against the oracle."""
+    sc = mixture_scene(nmat)
+    g, o, _ = both(sc, precision)
+    tol = TOL[precision]
+    for f, name in [(m.F_CELL_VOL, "V_ck"), (m.F_CELL_TAU, "tau_ck"), (m.F_NODE_MASS, "m_i"), (m.F_NODE_VEL, "v_i")]:
+        assert rel_err(g.field(f), o.field(name)) <= tol, name
+    assert o.stretch() == 0
+    m.mpml_stretch(g.ctx)
+    V = o.field("V_ck")
+    mask = V > 0
+    assert (mask.sum(axis=1) >= 3).any()  # cells that hold three or more materials
+    S_g, S_o = g.field(m.F_CELL_STRETCH), o.field("S_ck")
+    assert rel_err(S_g[mask] - np.eye(3), S_o[mask] - np.eye(3)) <= tol
+    nn = o.count("nodes")
+    rng = np.random.default_rng(12)
+    v = (o.field("vhat") + 0.05 * rng.standard_normal((nn, 3))).astype(g.npdt).astype(np.float64)
+    phi_o, g_o = o.eval(v)
+    phi_g, g_g = m.mpml_eval(g.ctx, v)
+    assert abs(phi_g - phi_o) <= tol * abs(phi_o)
+    assert rel_err(g_g, g_o) <= tol
+    o.linearize(v, project=True)
+    p = rng.standard_normal((nn, 3)).astype(g.npdt).astype(np.float64)
+    assert rel_err(m.mpml_hvp(g.ctx, p), o.hvp(p)) <= tol
+    g.close()
