@@ -101,3 +101,25 @@ def test_slab_on_sand_plasticity(precision):
     Fs = ref["F"][sand].reshape(-1, 3, 3)
     ortho = np.abs(np.einsum("nij,nkj->nik", Fs, Fs) - np.eye(3)).max(axis=(1, 2)) < 1e-12
     assert ortho.any()
+
+
+@pytest.mark.parametrize("precision,tol", [(m.FP64, 1e-12), (m.FP32, 1e-6)])
+def test_linear_momentum_of_colliding_cubes(precision, tol):
+    """Sec. 6.6: two cubes colliding head-on without gravity or walls in reach keep their
+    total linear momentum (the paper reports ~1e-14); 20 implicit steps through the impact."""
+    sc = scenes.colliding_cubes(64, speed=1.0)
+    g = GpuSim(sc, precision)
+    g.set_particles()
+    p0 = g.particles()
+    mom0 = (p0["mp"][:, None] * p0["v"]).sum(axis=0)
+    scale = (p0["mp"] * np.abs(p0["v"][:, 0])).sum()
+    newton = 0
+    for s in range(20):
+        rc, st = g.step(s * sc.dt)
+        assert rc == 0
+        newton += st.newton_iters
+    p = g.particles()
+    mom = (p["mp"][:, None] * p["v"]).sum(axis=0)
+    assert newton > 0                                   # the impact needed Newton solves
+    assert np.abs(mom - mom0).max() <= tol * scale, (mom, mom0)
+    g.close()
