@@ -1033,74 +1033,65 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
   return false;
 }
 
-// FP32 HVP with the brick's K block (45 x 512 floats = 92160 B) brought into
-// shared memory by one TMA bulk copy issued before the p halo is staged; the
-// K region is reused for the per-cell K D' results, so two CTAs fit per SM.
-constexpr unsigned HVP_K_BYTES = 45u * BV * 4u;
-constexpr size_t HVP_TMA_SMEM = HVP_K_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
-
-__global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cblist, const int* __restrict__ nbr,
-                                                    const uint8_t* __restrict__ cflag, const float* __restrict__ K,
-                                                    const float* __restrict__ p, const float* __restrict__ m,
-                                                    float* q, DevScalars* sc, int finalize, DevProf* pf,
-                                                    int* status, double* part) {
+// Standalone FP32 HVP of one cell brick per CTA on the 27-number compressed
+// (C27) or the 45-number packed tangent, read straight from global memory
+// (read-only during the kernel, coalesced per tangent entry; measured faster
+// than a TMA copy into shared memory: 27 KB of shared memory per CTA lets
+// three CTAs share an SM with more loads in flight).
+constexpr size_t HVP_G_SMEM = sizeof(float) * 3 * 729 + 4 + sizeof(float) * 9 * BV;
+template <bool C27>
+__global__ void __launch_bounds__(256, 3) k_hvp_glob(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                                     const uint8_t* __restrict__ cflag, const float* __restrict__ K,
+                                                     const float* __restrict__ p, const float* __restrict__ m,
+                                                     float* q, DevScalars* sc, int finalize, DevProf* pf,
+                                                     int* status, double* part) {
   __shared__ int s_done;
   if (threadIdx.x == 0) s_done = finalize ? sc->done : 0;
   __syncthreads();
   if (s_done) return;
   prof_begin(pf);
-  extern __shared__ __align__(128) unsigned char hsm[];
-  float* Ks = reinterpret_cast<float*>(hsm);  // [45][512], later [9][512] K D'
-  float (*sv)[729] = reinterpret_cast<float (*)[729]>(hsm + HVP_K_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(hsm + HVP_K_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  extern __shared__ __align__(128) unsigned char gsm[];
+  float (*sv)[729] = reinterpret_cast<float (*)[729]>(gsm);
+  float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(gsm + sizeof(float) * 3 * 729 + 4);
   __shared__ int s_nbr[NBR];
   const int id = cblist[blockIdx.x];
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
   if (threadIdx.x < NBR) s_nbr[threadIdx.x] = nbr[id * NBR + threadIdx.x];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(bar, HVP_K_BYTES);
-    tma_load_1d(Ks, K + (int64_t)id * 45 * BV, HVP_K_BYTES, bar);
-  }
   stage_nodes_sn<float, float>(id, s_nbr, p, sv);
   __syncthreads();
-  const bool ok = mbar_wait_bounded(bar, 0);
-  if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-  double pkp = 0;
-  float KD[2][9];
+  float pkp = 0.f;
+  const float* Kb = K + (int64_t)id * (C27 ? 27 : 45) * BV;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int l = threadIdx.x + h * 256;
+    float KD[9];
 #pragma unroll
-    for (int r = 0; r < 9; ++r) KD[h][r] = 0.f;
-    if (ok && cflag[(int64_t)id * BV + l]) {
+    for (int r = 0; r < 9; ++r) KD[r] = 0.f;
+    if (cflag[(int64_t)id * BV + l]) {
       float D[9];
       gather_D<float>(l, sv, D);
+      if (C27) {
+        float c[27];
+#pragma unroll
+        for (int qq = 0; qq < 27; ++qq) c[qq] = __ldg(Kb + qq * BV + l);
+        apply_c27(c, D, KD);
+      } else
 #pragma unroll
       for (int r = 0; r < 9; ++r) {
-        KD[h][r] += Ks[k45(r, r) * BV + l] * D[r];
+        KD[r] += __ldg(Kb + k45(r, r) * BV + l) * D[r];
 #pragma unroll
         for (int cc = r + 1; cc < 9; ++cc) {
-          const float kv = Ks[k45(r, cc) * BV + l];
-          KD[h][r] += kv * D[cc];
-          KD[h][cc] += kv * D[r];
+          const float kv = __ldg(Kb + k45(r, cc) * BV + l);
+          KD[r] += kv * D[cc];
+          KD[cc] += kv * D[r];
         }
       }
-      float dkd = 0.f;
 #pragma unroll
-      for (int r = 0; r < 9; ++r) dkd += D[r] * KD[h][r];
-      pkp += (double)dkd;
+      for (int r = 0; r < 9; ++r) pkp += D[r] * KD[r];
     }
+#pragma unroll
+    for (int r = 0; r < 9; ++r) skd[r][l] = KD[r];
   }
-  __syncthreads();  // every thread is done reading K: reuse the region for K D'
-  float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(Ks);
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int r = 0; r < 9; ++r) skd[r][threadIdx.x + h * 256] = KD[h][r];
   __syncthreads();
   for (int i = threadIdx.x; i < 729; i += blockDim.x) {
     const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
@@ -1133,7 +1124,7 @@ __global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cbli
         if (y[a] != 0.f) atomicAdd(q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
     }
   }
-  double vals[1] = {pkp};
+  double vals[1] = {(double)pkp};
   block_store<1>(vals, part);
   if (finalize && arrive_last(&sc->counter[CNT_HVP])) {
     double tot[1];
@@ -1153,13 +1144,11 @@ __global__ void __launch_bounds__(256, 2) k_hvp_tma(const int* __restrict__ cbli
   prof_end(pf);
 }
 
-// FP32 HVP on the compressed tangent (27 floats per cell, single material):
-// K D' = U Mt W^T with M = U^T D' W, W = S V, and Mt the clamped eigen-modes of
-// the isotropic tangent applied to M (3x3 block in the eigenbasis Qd on the
-// diagonal of M, flip / twist modes on its off-diagonal pairs).
+// Shared memory of the persistent solver's HVP phase: the brick's 27-number
+// tangents (27 x 512 floats, one TMA bulk copy), the 9^3 p halo and the
+// mbarrier.
 constexpr unsigned HVP_C_BYTES = 27u * BV * 4u;
 constexpr size_t HVP_C_SMEM = HVP_C_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
-
 
 __device__ __forceinline__ void apply_compressed(const float* __restrict__ Cs, int l, const float D[9], float KD[9]) {
   float c[27];
@@ -1168,110 +1157,6 @@ __device__ __forceinline__ void apply_compressed(const float* __restrict__ Cs, i
   apply_c27(c, D, KD);
 }
 
-__global__ void __launch_bounds__(256, 3) k_hvp_c27(const int* __restrict__ cblist, const int* __restrict__ nbr,
-                                                    const uint8_t* __restrict__ cflag, const float* __restrict__ K,
-                                                    const float* __restrict__ p, const float* __restrict__ m,
-                                                    float* q, DevScalars* sc, int finalize, DevProf* pf,
-                                                    int* status, double* part) {
-  __shared__ int s_done;
-  if (threadIdx.x == 0) s_done = finalize ? sc->done : 0;
-  __syncthreads();
-  if (s_done) return;
-  prof_begin(pf);
-  extern __shared__ __align__(128) unsigned char csm[];
-  float* Cs = reinterpret_cast<float*>(csm);  // [27][512], later [9][512] K D'
-  float (*sv)[729] = reinterpret_cast<float (*)[729]>(csm + HVP_C_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(csm + HVP_C_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
-  __shared__ int s_nbr[NBR];
-  const int id = cblist[blockIdx.x];
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  if (threadIdx.x < NBR) s_nbr[threadIdx.x] = nbr[id * NBR + threadIdx.x];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(bar, HVP_C_BYTES);
-    tma_load_1d(Cs, K + (int64_t)id * 27 * BV, HVP_C_BYTES, bar);
-  }
-  stage_nodes_sn<float, float>(id, s_nbr, p, sv);
-  __syncthreads();
-  const bool ok = mbar_wait_bounded(bar, 0);
-  if (!ok && threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
-  double pkp = 0;
-  float KD[2][9];
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int l = threadIdx.x + h * 256;
-#pragma unroll
-    for (int r = 0; r < 9; ++r) KD[h][r] = 0.f;
-    if (ok && cflag[(int64_t)id * BV + l]) {
-      float D[9];
-      gather_D<float>(l, sv, D);
-      apply_compressed(Cs, l, D, KD[h]);
-      float dkd = 0.f;
-#pragma unroll
-      for (int r = 0; r < 9; ++r) dkd += D[r] * KD[h][r];
-      pkp += (double)dkd;
-    }
-  }
-  __syncthreads();  // all reads of the tangent done: reuse the region for K D'
-  float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(Cs);
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int r = 0; r < 9; ++r) skd[r][threadIdx.x + h * 256] = KD[h][r];
-  __syncthreads();
-  for (int i = threadIdx.x; i < 729; i += blockDim.x) {
-    const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
-    float y[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int o = 0; o < 8; ++o) {
-      const int cx = nx - (o & 1), cy = ny - ((o >> 1) & 1), cz = nz - ((o >> 2) & 1);
-      if (cx < 0 || cy < 0 || cz < 0 || cx > 7 || cy > 7 || cz > 7) continue;
-      const int cc = (cz * 8 + cy) * 8 + cx;
-      const float s0 = (o & 1) ? 1.f : -1.f, s1 = (o & 2) ? 1.f : -1.f, s2 = (o & 4) ? 1.f : -1.f;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) y[a] += skd[3 * a][cc] * s0 + skd[3 * a + 1][cc] * s1 + skd[3 * a + 2][cc] * s2;
-    }
-    const bool own = nx < 8 && ny < 8 && nz < 8;
-    const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
-    if (own) {
-      const int l = nz * 64 + ny * 8 + nx;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        float* dst = q + (int64_t)id * 3 * BV + a * BV + l;
-        if (excl) *dst = y[a] + m[(int64_t)id * BV + l] * sv[a][i];
-        else if (y[a] != 0.f) atomicAdd(dst, y[a]);
-      }
-    } else {
-      const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
-      if (t < 0) continue;
-      const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (y[a] != 0.f) atomicAdd(q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
-    }
-  }
-  double vals[1] = {pkp};
-  block_store<1>(vals, part);
-  if (finalize && arrive_last(&sc->counter[CNT_HVP])) {
-    double tot[1];
-    block_sum_parts<1>(part, gridDim.x, tot);
-    if (threadIdx.x == 0) {
-      const double pq = sc->pMp + tot[0];
-      if (!(pq > 0.0)) {
-        sc->done = 1;
-        sc->alpha = 0;
-      } else {
-        sc->alpha = sc->rz / pq;
-      }
-      sc->pq = pq;
-      sc->counter[CNT_HVP] = 0;
-    }
-  }
-  prof_end(pf);
-}
 
 // HVP over cell bricks: q = M p + sum_c B^T K B p (faces atomically).
 template <typename T>
@@ -1772,26 +1657,17 @@ constexpr size_t hvp_smem_bytes() {
 template <typename T>
 static void launch_hvp(mpml_ctx_s* c, const T* p, T* q, int finalize) {
   DevProf* pf = c->profiling ? (DevProf*)c->prof.p : nullptr;
-  if (sizeof(T) == 4 && c->compressed) {
-    static bool attr_c = false;
-    if (!attr_c) {
-      cudaFuncSetAttribute(k_hvp_c27, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_C_SMEM);
-      attr_c = true;
-    }
-    k_hvp_c27<<<(unsigned)c->ncb, 256, HVP_C_SMEM, c->s>>>(
-        (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
-        (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
-        part_hvp(c));
-  } else if (sizeof(T) == 4) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_hvp_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_TMA_SMEM);
-      attr = true;
-    }
-    k_hvp_tma<<<(unsigned)c->ncb, 256, HVP_TMA_SMEM, c->s>>>(
-        (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
-        (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
-        part_hvp(c));
+  if (sizeof(T) == 4) {
+    if (c->compressed)
+      k_hvp_glob<true><<<(unsigned)c->ncb, 256, HVP_G_SMEM, c->s>>>(
+          (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
+          (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
+          part_hvp(c));
+    else
+      k_hvp_glob<false><<<(unsigned)c->ncb, 256, HVP_G_SMEM, c->s>>>(
+          (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
+          (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
+          part_hvp(c));
   } else {
     static bool attr = false;
     if (!attr) {
