@@ -385,7 +385,7 @@ def other_configs(m, scenes, args, peaks):
                     "dof_nodes": int(counts["nodes"]), "steps_per_s": 1e3 * len(times) / float(np.sum(times)),
                     "ms_per_step": float(np.mean(times)), "newton_iters_per_step": newton / len(times),
                     "cg_iters_per_step": cg / len(times),
-                    "hvp": {"kernel": "k_hvp_c27" if len(sc.materials) == 1 else "k_hvp_tma (45-number tangent)",
+                    "hvp": {"kernel": "k_hvp_glob (27-number tangent)" if len(sc.materials) == 1 else "k_hvp_glob (45-number tangent)",
                             "mean_ms": hvp_ms, "bytes": alg, "gbs": gbs, "frac": gbs / peaks["hbm_gbs"],
                             "bytes_rule": f"{int(k_bytes)} B per active cell + 28 B per DOF node, working set "
                                           f"{alg / 1e6:.0f} MB vs 129 MB L2"}}
