@@ -1034,7 +1034,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 }
 
 // Standalone FP32 HVP of one cell brick per CTA on the 27-number compressed
-// (C27) or the 45-number packed tangent, read straight from global memory
+// (C27) tangent (the 45-number form runs in k_hvp_col), read straight from global memory
 // (read-only during the kernel, coalesced per tangent entry; measured faster
 // than a TMA copy into shared memory: 27 KB of shared memory per CTA lets
 // three CTAs share an SM with more loads in flight).
@@ -1140,6 +1140,228 @@ __global__ void __launch_bounds__(256, 3) k_hvp_glob(const int* __restrict__ cbl
     }
     sc->pq = pq;
     sc->counter[CNT_HVP] = 0;
+  }
+  prof_end(pf);
+}
+
+// ---------------------------------------------------------------------------
+// Column-walk FP32 HVP: one cell brick per 64-thread CTA, thread (x, y) walks
+// the brick's z-column of cells (x, y, 0..7).  Every cell's eight corner
+// contributions K D' sgn_o are summed into node values without a shared-memory
+// scatter: along z in registers (the upper-z corners of cell z are carried to
+// the node layer z + 1), along x by a warp shuffle (the eight cells of a row
+// are eight adjacent lanes) and along y by a shuffle of eight lanes (rows 0-3
+// and 4-7 are the two warps; the row 3 -> 4 step goes through shared memory).
+// D' is formed from the p halo in shared memory, reusing the upper node layer
+// of cell z as the lower layer of cell z + 1.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int hidx(int nx, int ny, int nz) { return (nz * 9 + ny) * 9 + nx; }
+
+// node (nx, ny, nz) of the 9^3 halo of brick id receives the in-brick sum y[3]:
+// a plain store (with the mass term) where only this brick contributes, an
+// atomic add elsewhere (the mass term of those slots is written beforehand)
+__device__ __forceinline__ void col_emit(int id, const int* s_nbr, const float (*sv)[729],
+                                        const float* __restrict__ m, float* q, int nx, int ny, int nz,
+                                        const float y[3]) {
+  if (nx < 8 && ny < 8 && nz < 8) {
+    const int l = (nz * 8 + ny) * 8 + nx;
+    float* dst = q + (int64_t)id * 3 * BV + l;
+    if (nx >= 1 && ny >= 1 && nz >= 1) {
+      const float mi = m[(int64_t)id * BV + l];
+      const int i = hidx(nx, ny, nz);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dst[a * BV] = y[a] + mi * sv[a][i];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (y[a] != 0.f) atomicAdd(dst + a * BV, y[a]);
+    }
+  } else {
+    const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+    if (t < 0) return;
+    const int l = ((nz & 7) * 8 + (ny & 7)) * 8 + (nx & 7);
+    float* dst = q + (int64_t)t * 3 * BV + l;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (y[a] != 0.f) atomicAdd(dst + a * BV, y[a]);
+  }
+}
+
+// K45 by default: 64 registers, 16 CTAs (32 warps) per SM, which measured
+// faster than the 256-thread brick kernel at 3 CTAs per SM on the 45-number
+// tangent (latency-bound: more loads in flight per SM).
+template <bool C27, int MINB>
+__global__ void __launch_bounds__(64, MINB) k_hvp_col(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                                    const uint8_t* __restrict__ cflag, const float* __restrict__ K,
+                                                    const float* __restrict__ p, const float* __restrict__ m,
+                                                    float* q, DevScalars* sc, int finalize, DevProf* pf,
+                                                    double* part) {
+  constexpr int NQ = C27 ? 27 : 45;
+  __shared__ float sv[3][729];
+  __shared__ int s_nbr[NBR];
+  __shared__ float sxr[2][2][3][8];  // [z parity][E, E8 of row 3][a][x]
+  __shared__ int s_done;
+  const int t = threadIdx.x, x = t & 7, y = t >> 3, row = y & 3;
+  const int id = cblist[blockIdx.x];
+  if (t == 0) s_done = finalize ? sc->done : 0;
+  if (t < NBR) s_nbr[t] = nbr[id * NBR + t];
+  __syncthreads();
+  if (s_done) return;
+  prof_begin(pf);
+  stage_nodes_sn<float, float>(id, s_nbr, p, sv);
+  __syncthreads();
+  const float* Kb = K + (int64_t)id * NQ * BV;
+  const uint8_t* cf = cflag + (int64_t)id * BV;
+  constexpr unsigned FULL = 0xffffffffu;
+  // lower node layer of the current cell: P0[ox][oy][a]; carried upper-z corners: Cz
+  float P0[2][2][3], Cz[2][2][3];
+#pragma unroll
+  for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        P0[ox][oy][a] = sv[a][hidx(x + ox, y + oy, 0)];
+        Cz[ox][oy][a] = 0.f;
+      }
+  float pkp = 0.f;
+#pragma unroll 1
+  for (int z = 0; z <= 8; ++z) {
+    float N[2][2][3];
+    if (z < 8) {
+      float P1[2][2][3];
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+        for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) P1[ox][oy][a] = sv[a][hidx(x + ox, y + oy, z + 1)];
+      const int l = (z * 8 + y) * 8 + x;
+      float KD[9];
+#pragma unroll
+      for (int r = 0; r < 9; ++r) KD[r] = 0.f;
+      if (cf[l]) {
+        // D' = sum_o p_o (x) sgn_o
+        float D[9];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float s00 = P0[0][0][a] + P1[0][0][a], s10 = P0[1][0][a] + P1[1][0][a];
+          const float s01 = P0[0][1][a] + P1[0][1][a], s11 = P0[1][1][a] + P1[1][1][a];
+          D[3 * a + 0] = (s10 + s11) - (s00 + s01);
+          D[3 * a + 1] = (s01 + s11) - (s00 + s10);
+          D[3 * a + 2] = (P1[0][0][a] - P0[0][0][a]) + (P1[1][0][a] - P0[1][0][a]) + (P1[0][1][a] - P0[0][1][a]) +
+                         (P1[1][1][a] - P0[1][1][a]);
+        }
+        if (C27) {
+          float c[27];
+#pragma unroll
+          for (int qq = 0; qq < 27; ++qq) c[qq] = __ldg(Kb + qq * BV + l);
+          apply_c27(c, D, KD);
+        } else {
+          float k[45];
+#pragma unroll
+          for (int qq = 0; qq < 45; ++qq) k[qq] = __ldg(Kb + qq * BV + l);
+#pragma unroll
+          for (int r = 0; r < 9; ++r) {
+            KD[r] += k[k45(r, r)] * D[r];
+#pragma unroll
+            for (int cc = r + 1; cc < 9; ++cc) {
+              KD[r] += k[k45(r, cc)] * D[cc];
+              KD[cc] += k[k45(r, cc)] * D[r];
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r) pkp += D[r] * KD[r];
+      }
+      // corner values: node (x + ox, y + oy, z + oz) gets (2ox-1) X + (2oy-1) Y + (2oz-1) Z
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float X = KD[3 * a], Yv = KD[3 * a + 1], Z = KD[3 * a + 2];
+        const float A = X + Yv, B = X - Yv;
+        N[1][1][a] = Cz[1][1][a] + (A - Z);
+        N[0][0][a] = Cz[0][0][a] - (A + Z);
+        N[1][0][a] = Cz[1][0][a] + (B - Z);
+        N[0][1][a] = Cz[0][1][a] - (B + Z);
+        Cz[1][1][a] = A + Z;
+        Cz[0][0][a] = Z - A;
+        Cz[1][0][a] = B + Z;
+        Cz[0][1][a] = Z - B;
+      }
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+        for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) P0[ox][oy][a] = P1[ox][oy][a];
+    } else {
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+        for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) N[ox][oy][a] = Cz[ox][oy][a];
+    }
+    // along x: node (x, y + oy) gets N[0][oy] of this lane and N[1][oy] of lane x - 1;
+    // E8 = N[1] is the node (8, y + oy) of the x = 7 lanes
+    float E[2][3], E8[2][3];
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float left = __shfl_up_sync(FULL, N[1][oy][a], 1);
+        E[oy][a] = N[0][oy][a] + (x > 0 ? left : 0.f);
+        E8[oy][a] = N[1][oy][a];
+      }
+    // along y: node row y gets E[0] of row y and E[1] of row y - 1 (row 3 -> 4 through
+    // shared memory, double-buffered by z parity so one barrier per layer suffices)
+    const int buf = z & 1;
+    if (y == 3) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sxr[buf][0][a][x] = E[1][a];
+        sxr[buf][1][a][x] = E8[1][a];
+      }
+    }
+    __syncthreads();
+    float T[3], T8[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float up = __shfl_up_sync(FULL, E[1][a], 8), up8 = __shfl_up_sync(FULL, E8[1][a], 8);
+      float prev = 0.f, prev8 = 0.f;
+      if (row > 0) {
+        prev = up;
+        prev8 = up8;
+      } else if (y == 4) {
+        prev = sxr[buf][0][a][x];
+        prev8 = sxr[buf][1][a][x];
+      }
+      T[a] = E[0][a] + prev;
+      T8[a] = E8[0][a] + prev8;
+    }
+    col_emit(id, s_nbr, sv, m, q, x, y, z, T);
+    if (x == 7) col_emit(id, s_nbr, sv, m, q, 8, y, z, T8);
+    if (y == 7) {
+      col_emit(id, s_nbr, sv, m, q, x, 8, z, E[1]);
+      if (x == 7) col_emit(id, s_nbr, sv, m, q, 8, 8, z, E8[1]);
+    }
+  }
+  double vals[1] = {(double)pkp};
+  block_store<1>(vals, part);
+  if (finalize && arrive_last(&sc->counter[CNT_HVP])) {
+    double tot[1];
+    block_sum_parts<1>(part, gridDim.x, tot);
+    if (threadIdx.x == 0) {
+      const double pq = sc->pMp + tot[0];
+      if (!(pq > 0.0)) {
+        sc->done = 1;
+        sc->alpha = 0;
+      } else {
+        sc->alpha = sc->rz / pq;
+      }
+      sc->pq = pq;
+      sc->counter[CNT_HVP] = 0;
+    }
   }
   prof_end(pf);
 }
@@ -1664,10 +1886,9 @@ static void launch_hvp(mpml_ctx_s* c, const T* p, T* q, int finalize) {
           (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
           part_hvp(c));
     else
-      k_hvp_glob<false><<<(unsigned)c->ncb, 256, HVP_G_SMEM, c->s>>>(
+      k_hvp_col<false, 16><<<(unsigned)c->ncb, 64, 0, c->s>>>(
           (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
-          (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
-          part_hvp(c));
+          (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, part_hvp(c));
   } else {
     static bool attr = false;
     if (!attr) {
