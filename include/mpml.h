@@ -265,6 +265,41 @@ int mpml_pcg_timing(mpml_ctx ctx, int64_t* launches, int64_t* cg_iters, double* 
 /* Number of kernel launches issued on the context stream since creation. */
 int64_t mpml_kernel_launches(mpml_ctx ctx);
 
+/* HVP launch-shape autotuner --------------------------------------------
+ * Not in the paper (the workload asks for brick tile shapes chosen by an
+ * autotuner).  The standalone FP32 HVP of the graph-driven and host-driven CG
+ * loops (and of flexible CG) has MPML_HVP_TILES launch shapes per tangent
+ * format: the brick kernel (one 8^3 cell brick per 256-thread CTA, two cells
+ * per thread, node sums gathered through shared memory) and the z-column
+ * kernel (one brick per 64-thread CTA, thread (x, y) walks the 8 cells of its
+ * column, node sums by register carries and warp shuffles) at different
+ * CTAs per SM.  The persistent solver (use_graph = 2) has a single shape.
+ *
+ * mpml_autotune_hvp times every shape on the current linearisation (one
+ * untimed launch, then `reps` launches between CUDA events on the context
+ * stream; the solver's vectors are left untouched), keeps the fastest for the
+ * context, records it in a process-wide cache keyed by tangent format and
+ * log2 of the active brick count, and returns the shape index and (if `ms` is
+ * not NULL) the mean milliseconds of each of the MPML_HVP_TILES shapes.
+ * FP32 contexts after a linearisation (MPML_ERR_ARG otherwise).  Synchronising.
+ *
+ * Without a call, the first standalone-HVP solve of a context takes the
+ * cached shape for its format and size, else autotunes with reps = 3.
+ * mpml_set_hvp_tile fixes the shape (0 .. MPML_HVP_TILES-1; -1 returns to
+ * automatic choice); mpml_get_hvp_tile returns the shape in use (-1: not yet
+ * chosen) and a one-line description (static storage).
+ * mpml_tile_cache_save / _load write and read the cache as text, one line
+ * "format log2_bricks tile mean_ms" per entry (format 27 or 45); loading merges
+ * into the cache (malformed lines: MPML_ERR_ARG, nothing merged; unreadable or
+ * unwritable file: MPML_ERR_ARG).  Host-only, thread-safe. */
+#define MPML_HVP_TILES 3
+int mpml_autotune_hvp(mpml_ctx ctx, int reps, int* tile, float* ms);
+int mpml_set_hvp_tile(mpml_ctx ctx, int tile);
+int mpml_get_hvp_tile(mpml_ctx ctx, int* tile, const char** description);
+int mpml_tile_cache_save(const char* path);
+int mpml_tile_cache_load(const char* path);
+void mpml_tile_cache_clear(void);
+
 /* Learned preconditioner ------------------------------------------------
  * Not in the paper: the workload asks for a small 3D convolutional network
  * on the node grid used inside flexible CG.  Network: three bias-free

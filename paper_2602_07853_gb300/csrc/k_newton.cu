@@ -1876,19 +1876,41 @@ constexpr size_t hvp_smem_bytes() {
   return sizeof(T) * 3 * 729 + (16 - (sizeof(T) * 3 * 729) % 16) % 16 + sizeof(T) * 9 * BV;
 }
 
+// The launch shapes ("tiles") of the standalone FP32 HVP, per tangent format.
+// Entry 0 is the default before (or without) autotuning.
+const char* hvp_tile_name(int compressed, int tile) {
+  static const char* c27[HVP_TILES] = {"brick: 256 threads, 2 cells each, 3 CTAs/SM (k_hvp_glob)",
+                                       "z-column: 64 threads, 8 cells each, 8 CTAs/SM (k_hvp_col)",
+                                       "z-column: 64 threads, 8 cells each, 12 CTAs/SM (k_hvp_col)"};
+  static const char* k45[HVP_TILES] = {"z-column: 64 threads, 8 cells each, 16 CTAs/SM (k_hvp_col)",
+                                       "z-column: 64 threads, 8 cells each, 12 CTAs/SM (k_hvp_col)",
+                                       "brick: 256 threads, 2 cells each, 3 CTAs/SM (k_hvp_glob)"};
+  if (tile < 0 || tile >= HVP_TILES) return "";
+  return compressed ? c27[tile] : k45[tile];
+}
+
+static void launch_hvp_f32(mpml_ctx_s* c, int tile, const float* p, float* q, int finalize) {
+  DevProf* pf = c->profiling ? (DevProf*)c->prof.p : nullptr;
+  const unsigned g = (unsigned)c->ncb;
+#define HVP_IN (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p, p, \
+               (const float*)c->nmass.p, q, dscal(c), finalize, pf
+  if (c->compressed) {
+    if (tile == 1) k_hvp_col<true, 8><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
+    else if (tile == 2) k_hvp_col<true, 12><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
+    else k_hvp_glob<true><<<g, 256, HVP_G_SMEM, c->s>>>(HVP_IN, (int*)c->status.p, part_hvp(c));
+  } else {
+    if (tile == 1) k_hvp_col<false, 12><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
+    else if (tile == 2) k_hvp_glob<false><<<g, 256, HVP_G_SMEM, c->s>>>(HVP_IN, (int*)c->status.p, part_hvp(c));
+    else k_hvp_col<false, 16><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
+  }
+#undef HVP_IN
+}
+
 template <typename T>
 static void launch_hvp(mpml_ctx_s* c, const T* p, T* q, int finalize) {
   DevProf* pf = c->profiling ? (DevProf*)c->prof.p : nullptr;
   if (sizeof(T) == 4) {
-    if (c->compressed)
-      k_hvp_glob<true><<<(unsigned)c->ncb, 256, HVP_G_SMEM, c->s>>>(
-          (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
-          (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, (int*)c->status.p,
-          part_hvp(c));
-    else
-      k_hvp_col<false, 16><<<(unsigned)c->ncb, 64, 0, c->s>>>(
-          (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p,
-          (const float*)p, (const float*)c->nmass.p, (float*)q, dscal(c), finalize, pf, part_hvp(c));
+    launch_hvp_f32(c, c->hvp_tile >= 0 ? c->hvp_tile : 0, (const float*)p, (float*)q, finalize);
   } else {
     static bool attr = false;
     if (!attr) {
@@ -1934,11 +1956,11 @@ constexpr int CG_UNROLL = 4;
 
 template <typename T>
 static int ensure_cg_graph(mpml_ctx_s* c, int cg_max) {
-  const uintptr_t key[16] = {(uintptr_t)c->nb, (uintptr_t)c->ncb, (uintptr_t)c->np.p, (uintptr_t)c->nq.p,
+  const uintptr_t key[17] = {(uintptr_t)c->nb, (uintptr_t)c->ncb, (uintptr_t)c->np.p, (uintptr_t)c->nq.p,
                              (uintptr_t)c->nx.p, (uintptr_t)c->nr.p, (uintptr_t)c->ndinv.p, (uintptr_t)c->nmass.p,
                              (uintptr_t)c->cK.p, (uintptr_t)c->scal.p, (uintptr_t)c->profiling,
                              (uintptr_t)c->cblist.p, (uintptr_t)c->nbr.p, (uintptr_t)c->cflag.p,
-                             (uintptr_t)cg_max, (uintptr_t)c->prof.p};
+                             (uintptr_t)cg_max, (uintptr_t)c->prof.p, (uintptr_t)(c->hvp_tile + 1)};
   if (c->cg_exec && memcmp(key, c->cg_key, sizeof key) == 0) return MPML_OK;
   if (c->cg_exec) {
     cudaGraphExecDestroy(c->cg_exec);
@@ -2817,6 +2839,8 @@ int nn_loss_grad_host(mpml_ctx_s* c, const void* r_nodes, const void* e_nodes, d
   return nn_pair(c, den, 1.0f, loss, true);
 }
 
+static int ensure_hvp_tile(mpml_ctx_s* c);
+
 template <typename T>
 static int pcg_t(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, double* rel) {
   int rc;
@@ -2846,7 +2870,12 @@ static int pcg_t(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, double* r
     if ((rc = pcg_persistent(c, o))) return rc;
     if ((rc = read_scalars(c))) return rc;
     pcg_persistent_account(c);
-  } else
+    *iters = c->hscal->iters;
+    const double rr0p = c->hscal->rr0;
+    *rel = rr0p > 0 ? sqrt(c->hscal->rr_last / rr0p) : 0.0;
+    return MPML_OK;
+  }
+  if (sizeof(T) == 4 && (rc = ensure_hvp_tile(c))) return rc;
   if (o->use_graph && c->ncb > 0 && ensure_cg_graph<T>(c, o->cg_max) == MPML_OK) {
     if ((rc = cuda_status(cudaGraphLaunch(c->cg_exec, c->s)))) return rc;
     if ((rc = read_scalars(c))) return rc;
@@ -3113,6 +3142,71 @@ static int hvp_bench_t(mpml_ctx_s* c, int iters, double* mean_ms) {
 
 int hvp_bench(mpml_ctx_s* c, int iters, double* mean_ms) {
   return c->fp64 ? hvp_bench_t<double>(c, iters, mean_ms) : hvp_bench_t<float>(c, iters, mean_ms);
+}
+
+// Times every tile of the context's tangent format on the current linearisation
+// (p = the solver's current direction, output into scratch, so the solver state
+// is untouched): one untimed launch, then reps launches between CUDA events on
+// the context stream; the mean per tile goes to ms[], the fastest becomes the
+// context's tile and is recorded in the process-wide cache.
+int hvp_autotune(mpml_ctx_s* c, int reps, int* choice, float* ms) {
+  if (c->fp64) return MPML_ERR_ARG;
+  if (reps < 1) reps = 1;
+  if (c->ncb == 0) {
+    if (choice) *choice = 0;
+    return MPML_OK;
+  }
+  int rc;
+  const int64_t n3 = 3 * c->nb * BV;
+  if ((rc = ensure(c->tuneq, sizeof(float) * n3))) return rc;
+  float* y = (float*)c->tuneq.p;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return MPML_ERR_CUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return MPML_ERR_CUDA;
+  }
+  float best = 0.f;
+  int arg = 0;
+  for (int t = 0; t < HVP_TILES && !rc; ++t) {
+    float tot = 0.f;
+    for (int i = 0; i <= reps; ++i) {
+      k_init_faces<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const float*)c->np.p, (const float*)c->nmass.p, y);
+      cudaEventRecord(a, c->s);
+      launch_hvp_f32(c, t, (const float*)c->np.p, y, 0);
+      cudaEventRecord(b, c->s);
+      if ((rc = cuda_status(cudaEventSynchronize(b)))) break;
+      float e = 0.f;
+      cudaEventElapsedTime(&e, a, b);
+      if (i > 0) tot += e;
+    }
+    const float mean = tot / reps;
+    if (ms) ms[t] = mean;
+    if (t == 0 || mean < best) {
+      best = mean;
+      arg = t;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->launches += (int64_t)HVP_TILES * (reps + 1) * 2;
+  if (rc) return rc;
+  c->hvp_tile = arg;
+  if (choice) *choice = arg;
+  tile_cache_store(c->compressed, c->ncb, arg, best);
+  return MPML_OK;
+}
+
+// tile for a standalone-HVP solve: the cached choice for this format and size,
+// else a short autotuning run on the current system
+static int ensure_hvp_tile(mpml_ctx_s* c) {
+  if (c->fp64 || c->hvp_tile_fixed) return MPML_OK;
+  const int cached = tile_cache_lookup(c->compressed, c->ncb);
+  if (cached >= 0) {
+    c->hvp_tile = cached;
+    return MPML_OK;
+  }
+  return hvp_autotune(c, 3, nullptr, nullptr);
 }
 
 // ---- pieces of the solver used by the batched driver (k_batch.cu) ----------

@@ -284,7 +284,7 @@ int mpml_destroy(mpml_ctx c) {
                  &c->uF, &c->uG, &c->um, &c->uV, &c->umat, &c->cnt, &c->start, &c->scan_tmp, &c->cflag,
                  &c->cacc, &c->cs, &c->cK, &c->cnew, &c->nflag, &c->nmass, &c->nv, &c->nvhat, &c->nvfix,
                  &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->bbatch, &c->nolist,
-                 &c->nnw, &c->nnact, &c->nny, &c->nnpart, &c->nz, &c->nns_r, &c->nns_e, &c->nnhd};
+                 &c->nnw, &c->nnact, &c->nny, &c->nnpart, &c->nz, &c->nns_r, &c->nns_e, &c->nnhd, &c->tuneq};
   for (Buf* b : bufs) free_buf(*b);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hstatus) cudaFreeHost(c->hstatus);
@@ -625,6 +625,29 @@ int mpml_hvp_bench(mpml_ctx c, int iters, double* mean_ms) {
 }
 
 int64_t mpml_kernel_launches(mpml_ctx c) { return c ? c->launches : -1; }
+
+int mpml_autotune_hvp(mpml_ctx c, int reps, int* tile, float* ms) {
+  if (!c || !c->have_lin || c->fp64) return MPML_ERR_ARG;
+  return hvp_autotune(c, reps, tile, ms);
+}
+
+int mpml_set_hvp_tile(mpml_ctx c, int tile) {
+  if (!c || c->fp64 || tile < -1 || tile >= HVP_TILES) return MPML_ERR_ARG;
+  c->hvp_tile = tile;
+  c->hvp_tile_fixed = tile >= 0 ? 1 : 0;
+  return MPML_OK;
+}
+
+int mpml_get_hvp_tile(mpml_ctx c, int* tile, const char** description) {
+  if (!c || c->fp64) return MPML_ERR_ARG;
+  if (tile) *tile = c->hvp_tile;
+  if (description) *description = c->hvp_tile >= 0 ? hvp_tile_name(c->compressed, c->hvp_tile) : "";
+  return MPML_OK;
+}
+
+int mpml_tile_cache_save(const char* path) { return tile_cache_save(path); }
+int mpml_tile_cache_load(const char* path) { return tile_cache_load(path); }
+void mpml_tile_cache_clear(void) { tile_cache_clear(); }
 
 int mpml_nn_weight_count(void) { return nn_weight_count(); }
 

@@ -117,6 +117,11 @@ struct mpml_ctx_s {
   cudaStream_t s = nullptr;
   int fp64 = 0;
   int compressed = 0;  // FP32, single material: HVP on the 27-number tangent
+  // launch shape ("tile") of the standalone FP32 HVP, an index into the table of
+  // hvp_tile_name(); -1: chosen by the autotuner (or its cache) at the first solve
+  int hvp_tile = -1;
+  int hvp_tile_fixed = 0;  // set by mpml_set_hvp_tile: never re-tuned
+  mpml::Buf tuneq;         // scratch output of the autotuner's timed launches
   size_t esz = 4;
   int NB[3] = {0, 0, 0};
   int64_t NBT = 0;
@@ -156,7 +161,7 @@ struct mpml_ctx_s {
   // graph-driven CG loop (conditional WHILE node), rebuilt when its key changes
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t cg_exec = nullptr;
-  uintptr_t cg_key[16] = {};
+  uintptr_t cg_key[17] = {};
 
   // profiling of HVP launches
   int profiling = 0;
@@ -194,6 +199,16 @@ int eval_device(mpml_ctx_s* c, const void* v_nodes, double* phi, void* grad_node
 int linearize_device(mpml_ctx_s* c, const void* v_nodes);
 int hvp_device(mpml_ctx_s* c, const void* p_nodes, void* y_nodes);
 int hvp_bench(mpml_ctx_s* c, int iters, double* mean_ms);
+// standalone FP32 HVP launch shapes and their autotuner
+constexpr int HVP_TILES = 3;
+const char* hvp_tile_name(int compressed, int tile);
+int hvp_autotune(mpml_ctx_s* c, int reps, int* choice, float* ms);
+// process-wide cache of autotuned tiles, keyed by tangent format and brick count
+int tile_cache_lookup(int compressed, int64_t ncb);
+void tile_cache_store(int compressed, int64_t ncb, int tile, float ms);
+int tile_cache_save(const char* path);
+int tile_cache_load(const char* path);
+void tile_cache_clear();
 int n2q_device(mpml_ctx_s* c);
 
 // learned preconditioner (k_nn.cu)

@@ -113,6 +113,12 @@ EXPORTS = {
     "mpml_nn_train": (C.c_int, [C.c_void_p, C.POINTER(mpml_train_opts), C.POINTER(mpml_train_stats)]),
     "mpml_sort_particles_noalloc": (C.c_int, [C.POINTER(C.c_int), C.c_double, C.c_int, C.c_void_p, C.c_int64,
                                               C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mpml_autotune_hvp": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "mpml_set_hvp_tile": (C.c_int, [C.c_void_p, C.c_int]),
+    "mpml_get_hvp_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_char_p)]),
+    "mpml_tile_cache_save": (C.c_int, [C.c_char_p]),
+    "mpml_tile_cache_load": (C.c_int, [C.c_char_p]),
+    "mpml_tile_cache_clear": (None, []),
 }
 
 
@@ -299,6 +305,38 @@ def mpml_pcg_timing(ctx):
 
 def mpml_kernel_launches(ctx):
     return int(load().mpml_kernel_launches(ctx))
+
+
+HVP_TILES = 3  # MPML_HVP_TILES
+
+
+def mpml_autotune_hvp(ctx, reps=3):
+    """(chosen tile, [mean ms of each tile]) on the current linearisation."""
+    tile, ms = C.c_int(), (C.c_float * HVP_TILES)()
+    _check(load().mpml_autotune_hvp(ctx, int(reps), C.byref(tile), ms), "mpml_autotune_hvp")
+    return tile.value, [float(v) for v in ms]
+
+
+def mpml_set_hvp_tile(ctx, tile):
+    _check(load().mpml_set_hvp_tile(ctx, int(tile)), "mpml_set_hvp_tile")
+
+
+def mpml_get_hvp_tile(ctx):
+    tile, desc = C.c_int(), C.c_char_p()
+    _check(load().mpml_get_hvp_tile(ctx, C.byref(tile), C.byref(desc)), "mpml_get_hvp_tile")
+    return tile.value, (desc.value or b"").decode()
+
+
+def mpml_tile_cache_save(path):
+    _check(load().mpml_tile_cache_save(os.fsencode(path)), "mpml_tile_cache_save")
+
+
+def mpml_tile_cache_load(path):
+    _check(load().mpml_tile_cache_load(os.fsencode(path)), "mpml_tile_cache_load")
+
+
+def mpml_tile_cache_clear():
+    load().mpml_tile_cache_clear()
 
 
 # ---------------------------------------------------------------------------
