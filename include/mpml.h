@@ -140,7 +140,7 @@ typedef struct {
   int use_graph;       /* how the CG loop runs: 0 host-driven launches; 1 one CUDA graph launch
                           with a device-side conditional WHILE loop; 2 (default when opts is
                           NULL) one persistent cooperative kernel with bounded grid barriers
-                          (FP32 single-material contexts; others use 1) */
+                          (FP32 contexts; FP64 contexts use 1) */
 } mpml_solver_opts;
 
 typedef struct {

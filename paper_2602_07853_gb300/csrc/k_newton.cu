@@ -1371,6 +1371,14 @@ __global__ void __launch_bounds__(64, MINB) k_hvp_col(const int* __restrict__ cb
 // mbarrier.
 constexpr unsigned HVP_C_BYTES = 27u * BV * 4u;
 constexpr size_t HVP_C_SMEM = HVP_C_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
+// the column-walk phase H adds the z-exchange of the four 64-thread groups
+// (12 floats per thread) and their row 3 -> 4 partials (3 layers x 2 x 3 x 8)
+constexpr size_t HVP_X_FLOATS = 4 * 12 * 64, HVP_R_FLOATS = 4 * 3 * 2 * 3 * 8;
+constexpr size_t HVP_C_SMEM_COL = HVP_C_SMEM + sizeof(float) * (HVP_X_FLOATS + HVP_R_FLOATS);
+// 45-number tangent in the persistent solver: the brick's 45 x 512 floats by one
+// bulk copy; the exchange buffers overlay the tangent block once it is used
+constexpr unsigned HVP_K_BYTES45 = 45u * BV * 4u;
+constexpr size_t HVP_K_SMEM45 = HVP_K_BYTES45 + sizeof(float) * 3 * 729 + 16 + 16;
 
 __device__ __forceinline__ void apply_compressed(const float* __restrict__ Cs, int l, const float D[9], float KD[9]) {
   float c[27];
@@ -2012,14 +2020,15 @@ static int ensure_cg_graph(mpml_ctx_s* c, int cg_max) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent Jacobi-PCG (FP32, compressed tangent): the whole CG solve in one
-// cooperative launch.  Each iteration has two phases separated by grid
-// barriers:
+// Persistent Jacobi-PCG (FP32; 27-number compressed or 45-number packed
+// tangent): the whole CG solve in one cooperative launch.  Each iteration has
+// two phases separated by grid barriers:
 //   H: for every cell brick of this CTA, stage p_new = D^-1 r + beta p_old on
 //      the 9^3 node block (the update of p fused into the halo staging; the
-//      owner writes p_new to the other p buffer), apply K (TMA-staged tangent)
-//      and scatter q; bricks holding only DOF nodes get p_new and the mass
-//      term.  Partials: p^T M p, p^T K p.
+//      owner writes p_new to the other p buffer), apply K (the brick's tangent
+//      block by one TMA bulk copy) in the column walk of phase_h_col and add
+//      q; bricks holding only DOF nodes get p_new and the mass term.
+//      Partials: p^T M p, p^T K p.
 //   A: x += alpha p_new, r -= alpha q, q = 0, partials r^T D^-1 r, r^T r.
 // Every CTA sums the per-CTA partials in the same order, so all take the same
 // decisions (alpha, beta, convergence) without another barrier.  Barrier
@@ -2148,11 +2157,224 @@ __device__ __forceinline__ float pnew_at(const PcgArgs& A, int64_t o, float beta
   return di > 0.f ? di * A.r[o] + beta * pold[o] : 0.f;
 }
 
+// node (nx, ny, nz) of the 9^3 halo of brick id receives y[3] inside the
+// persistent solver, where q starts at zero: own nodes take the mass term too
+// (plain store where only this brick contributes, atomic add elsewhere).
+__device__ __forceinline__ void col_emit_m(int id, const int* s_nbr, const float (*sv)[729],
+                                          const float* __restrict__ m, float* q, int nx, int ny, int nz,
+                                          const float y[3]) {
+  if (nx < 8 && ny < 8 && nz < 8) {
+    const int l = (nz * 8 + ny) * 8 + nx;
+    float* dst = q + (int64_t)id * 3 * BV + l;
+    const float mi = __ldcg(m + (int64_t)id * BV + l);
+    const int i = hidx(nx, ny, nz);
+    if (nx >= 1 && ny >= 1 && nz >= 1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dst[a * BV] = y[a] + mi * sv[a][i];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float val = y[a] + mi * sv[a][i];
+        if (val != 0.f) atomicAdd(dst + a * BV, val);
+      }
+    }
+  } else {
+    const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+    if (t < 0) return;
+    const int l = ((nz & 7) * 8 + (ny & 7)) * 8 + (nx & 7);
+    float* dst = q + (int64_t)t * 3 * BV + l;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (y[a] != 0.f) atomicAdd(dst + a * BV, y[a]);
+  }
+}
+
+// corner contributions of one cell: lower-z corners into N (added), upper-z
+// corners returned in U; node (x + ox, y + oy, z + oz) gets
+// (2ox-1) X + (2oy-1) Y + (2oz-1) Z of the cell's K D' rows (X, Y, Z)
+__device__ __forceinline__ void col_corners(const float KD[9], float N[2][2][3], float U[2][2][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float X = KD[3 * a], Yv = KD[3 * a + 1], Z = KD[3 * a + 2];
+    const float Ap = X + Yv, B = X - Yv;
+    N[1][1][a] += Ap - Z;
+    N[0][0][a] -= Ap + Z;
+    N[1][0][a] += B - Z;
+    N[0][1][a] -= B + Z;
+    U[1][1][a] = Ap + Z;
+    U[0][0][a] = Z - Ap;
+    U[1][0][a] = B + Z;
+    U[0][1][a] = Z - B;
+  }
+}
+
+// D' = sum_o p_o (x) sgn_o from the lower (P0) and upper (P1) node layers of a cell
+__device__ __forceinline__ void col_D(const float P0[2][2][3], const float P1[2][2][3], float D[9]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float s00 = P0[0][0][a] + P1[0][0][a], s10 = P0[1][0][a] + P1[1][0][a];
+    const float s01 = P0[0][1][a] + P1[0][1][a], s11 = P0[1][1][a] + P1[1][1][a];
+    D[3 * a + 0] = (s10 + s11) - (s00 + s01);
+    D[3 * a + 1] = (s01 + s11) - (s00 + s10);
+    D[3 * a + 2] = (P1[0][0][a] - P0[0][0][a]) + (P1[1][0][a] - P0[1][0][a]) + (P1[0][1][a] - P0[0][1][a]) +
+                   (P1[1][1][a] - P0[1][1][a]);
+  }
+}
+
+// Phase H of one brick in the column walk: the CTA's four 64-thread groups take
+// two z-layers of cells each (group g: cells z = 2g, 2g + 1 of column (x, y));
+// node layers are summed along z in registers, across groups through shared
+// memory (layer 2g gets group g-1's upper corners), along x by warp shuffles and
+// along y by shuffles of eight lanes (rows 3 -> 4 through shared memory).
+// Returns the thread's sum of D' . K D'.
+template <bool K45>
+__device__ __forceinline__ float phase_h_col(int id, const int* s_nbr, const float (*sv)[729], const float* Cs,
+                                             const uint8_t* __restrict__ cflag, const float* __restrict__ m, float* q,
+                                             float* X, float* R, bool ok) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int t = threadIdx.x, g = t >> 6, x = t & 7, y = (t >> 3) & 7, row = y & 3, c64 = t & 63;
+  float pkp = 0.f;
+  float Pa[2][2][3], Pb[2][2][3];
+  float Na[2][2][3], Nb[2][2][3], Nc[2][2][3];
+#pragma unroll
+  for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        Pa[ox][oy][a] = sv[a][hidx(x + ox, y + oy, 2 * g)];
+        Pb[ox][oy][a] = sv[a][hidx(x + ox, y + oy, 2 * g + 1)];
+        Na[ox][oy][a] = 0.f;
+      }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int l = (2 * g + h) * 64 + c64;
+    float KD[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) KD[r] = 0.f;
+    if (ok && cflag[(int64_t)id * BV + l]) {
+      float D[9];
+      col_D(Pa, Pb, D);
+      if (K45) {
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+          KD[r] += Cs[k45(r, r) * BV + l] * D[r];
+#pragma unroll
+          for (int cc = r + 1; cc < 9; ++cc) {
+            const float kv = Cs[k45(r, cc) * BV + l];
+            KD[r] += kv * D[cc];
+            KD[cc] += kv * D[r];
+          }
+        }
+      } else {
+        float c[27];
+#pragma unroll
+        for (int qq = 0; qq < 27; ++qq) c[qq] = Cs[qq * BV + l];
+        apply_c27(c, D, KD);
+      }
+#pragma unroll
+      for (int r = 0; r < 9; ++r) pkp += D[r] * KD[r];
+    }
+    if (h == 0) {
+      col_corners(KD, Na, Nb);  // Nb <- upper corners of cell 2g (lower of cell 2g+1 added next)
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+        for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            Pa[ox][oy][a] = Pb[ox][oy][a];
+            Pb[ox][oy][a] = sv[a][hidx(x + ox, y + oy, 2 * g + 2)];
+          }
+    } else {
+      col_corners(KD, Nb, Nc);
+    }
+  }
+  // across groups: node layer 2g + 2 = this group's Nc + group g+1's Na
+  if (K45) __syncthreads();  // X overlays the tangent block: every cell has been applied
+  if (g < 3) {
+    float* Xg = X + g * 12 * 64;
+#pragma unroll
+    for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Xg[((ox * 2 + oy) * 3 + a) * 64 + c64] = Nc[ox][oy][a];
+  }
+  __syncthreads();
+  if (g > 0) {
+    const float* Xg = X + (g - 1) * 12 * 64;
+#pragma unroll
+    for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Na[ox][oy][a] += Xg[((ox * 2 + oy) * 3 + a) * 64 + c64];
+  }
+  // along x (shuffles), then the row-3 partials of every layer into shared memory
+  const int nl = g == 3 ? 3 : 2;
+  float E[3][2][3], E8[3][2][3];
+#pragma unroll
+  for (int L = 0; L < 3; ++L) {
+    if (L == 2 && nl < 3) break;
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float n0 = L == 0 ? Na[0][oy][a] : (L == 1 ? Nb[0][oy][a] : Nc[0][oy][a]);
+        const float n1 = L == 0 ? Na[1][oy][a] : (L == 1 ? Nb[1][oy][a] : Nc[1][oy][a]);
+        const float left = __shfl_up_sync(FULL, n1, 1);
+        E[L][oy][a] = n0 + (x > 0 ? left : 0.f);
+        E8[L][oy][a] = n1;
+      }
+    if (y == 3) {
+      float* Rg = R + (g * 3 + L) * 48;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        Rg[a * 8 + x] = E[L][1][a];
+        Rg[24 + a * 8 + x] = E8[L][1][a];
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int L = 0; L < 3; ++L) {
+    if (L == 2 && nl < 3) break;
+    const int nz = L == 2 ? 8 : 2 * g + L;
+    const float* Rg = R + (g * 3 + L) * 48;
+    float T[3], T8[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float up = __shfl_up_sync(FULL, E[L][1][a], 8), up8 = __shfl_up_sync(FULL, E8[L][1][a], 8);
+      float prev = 0.f, prev8 = 0.f;
+      if (row > 0) {
+        prev = up;
+        prev8 = up8;
+      } else if (y == 4) {
+        prev = Rg[a * 8 + x];
+        prev8 = Rg[24 + a * 8 + x];
+      }
+      T[a] = E[L][0][a] + prev;
+      T8[a] = E8[L][0][a] + prev8;
+    }
+    col_emit_m(id, s_nbr, sv, m, q, x, y, nz, T);
+    if (x == 7) col_emit_m(id, s_nbr, sv, m, q, 8, y, nz, T8);
+    if (y == 7) {
+      col_emit_m(id, s_nbr, sv, m, q, x, 8, nz, E[L][1]);
+      if (x == 7) col_emit_m(id, s_nbr, sv, m, q, 8, 8, nz, E8[L][1]);
+    }
+  }
+  return pkp;
+}
+
+template <bool K45>
 __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
+  constexpr unsigned KB = K45 ? HVP_K_BYTES45 : HVP_C_BYTES;
+  constexpr int NQ = K45 ? 45 : 27;
   extern __shared__ __align__(128) unsigned char psm[];
   float* Cs = reinterpret_cast<float*>(psm);
-  float (*sv)[729] = reinterpret_cast<float (*)[729]>(psm + HVP_C_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(psm + HVP_C_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  float (*sv)[729] = reinterpret_cast<float (*)[729]>(psm + KB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(psm + KB + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
   __shared__ int s_nbr[NBR];
   __shared__ int s_flag;
   __shared__ double s_sum[2];
@@ -2184,8 +2406,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       if (threadIdx.x == 0) {
         // order the previous brick's generic accesses to Cs before the async copy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(bar, HVP_C_BYTES);
-        tma_load_1d(Cs, A.C + (int64_t)id * 27 * BV, HVP_C_BYTES, bar);
+        mbar_arrive_expect_tx(bar, KB);
+        tma_load_1d(Cs, A.C + (int64_t)id * NQ * BV, KB, bar);
       }
       {
         // every thread owns at most 3 of the 729 halo slots: issue all loads first
@@ -2240,63 +2462,11 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       const bool ok = mbar_wait_bounded(bar, tma_phase);
       tma_phase ^= 1u;
       if (!ok && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
-      float KD[2][9];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int l = threadIdx.x + h * 256;
-#pragma unroll
-        for (int rr = 0; rr < 9; ++rr) KD[h][rr] = 0.f;
-        if (ok && A.cflag[(int64_t)id * BV + l]) {
-          float D[9];
-          gather_D<float>(l, sv, D);
-          apply_compressed(Cs, l, D, KD[h]);
-          float dkd = 0.f;
-#pragma unroll
-          for (int rr = 0; rr < 9; ++rr) dkd += D[rr] * KD[h][rr];
-          pkp += dkd;
-        }
+      {
+        float* Xs = K45 ? Cs : reinterpret_cast<float*>(psm + HVP_C_SMEM);
+        pkp += phase_h_col<K45>(id, s_nbr, sv, Cs, A.cflag, A.m, A.q, Xs, Xs + HVP_X_FLOATS, ok);
+        __syncthreads();  // Cs / sv / s_nbr / exchange buffers are reused by the next brick
       }
-      __syncthreads();
-      float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(Cs);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int rr = 0; rr < 9; ++rr) skd[rr][threadIdx.x + h * 256] = KD[h][rr];
-      __syncthreads();
-      for (int i = threadIdx.x; i < 729; i += blockDim.x) {
-        const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
-        float y[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-          const int cx = nx - (o & 1), cy = ny - ((o >> 1) & 1), cz = nz - ((o >> 2) & 1);
-          if (cx < 0 || cy < 0 || cz < 0 || cx > 7 || cy > 7 || cz > 7) continue;
-          const int cc = (cz * 8 + cy) * 8 + cx;
-          const float s0 = (o & 1) ? 1.f : -1.f, s1 = (o & 2) ? 1.f : -1.f, s2 = (o & 4) ? 1.f : -1.f;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) y[a] += skd[3 * a][cc] * s0 + skd[3 * a + 1][cc] * s1 + skd[3 * a + 2][cc] * s2;
-        }
-        const bool own = nx < 8 && ny < 8 && nz < 8;
-        const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
-        if (own) {
-          const int l = nz * 64 + ny * 8 + nx;
-          const float mi = A.m[(int64_t)id * BV + l];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            float* dst = A.q + (int64_t)id * 3 * BV + a * BV + l;
-            const float val = y[a] + mi * sv[a][i];
-            if (excl) *dst = val;
-            else if (val != 0.f) atomicAdd(dst, val);
-          }
-        } else {
-          const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
-          if (t < 0) continue;
-          const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-            if (y[a] != 0.f) atomicAdd(A.q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
-        }
-      }
-      __syncthreads();  // Cs / sv / s_nbr are reused by the next brick
     }
     // bricks with DOF nodes but no cells: p_new and the mass term
     for (int jn = blockIdx.x; jn < A.nnob; jn += G) {
@@ -2413,18 +2583,21 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
 }
 
 static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
-  static int max_blocks = -1;
-  if (max_blocks < 0) {
-    cudaFuncSetAttribute(k_pcg_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HVP_C_SMEM);
+  // one occupancy query per tangent format (27-number compressed, 45-number packed)
+  static int max_blocks[2] = {-1, -1};
+  const int k45 = c->compressed ? 0 : 1;
+  const void* kfn = k45 ? (const void*)k_pcg_persistent<true> : (const void*)k_pcg_persistent<false>;
+  const size_t smem = k45 ? HVP_K_SMEM45 : HVP_C_SMEM_COL;
+  if (max_blocks[k45] < 0) {
+    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0, nsm = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, 256, HVP_C_SMEM) != cudaSuccess)
-      per_sm = 0;
-    max_blocks = per_sm * nsm;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem) != cudaSuccess) per_sm = 0;
+    max_blocks[k45] = per_sm * nsm;
   }
-  if (max_blocks <= 0) return MPML_ERR_CUDA;
-  int G = max_blocks;
+  if (max_blocks[k45] <= 0) return MPML_ERR_CUDA;
+  const int G = max_blocks[k45];
   int rc;
   // barrier words (2 unsigned) followed by the 4 x 2 rotating accumulators
   if ((rc = ensure(c->gbar, 16 + 8 * sizeof(double))) || (rc = ensure(c->np2, sizeof(float) * 3 * c->nb * BV)))
@@ -2457,8 +2630,7 @@ static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
   void* args[] = {&a};
   const bool timed = c->profiling && c->pcg_ev[0] && c->pcg_ev[1];
   if (timed) cudaEventRecord(c->pcg_ev[0], c->s);
-  rc = cuda_status(cudaLaunchCooperativeKernel((const void*)k_pcg_persistent, dim3(G), dim3(256), args, HVP_C_SMEM,
-                                               c->s));
+  rc = cuda_status(cudaLaunchCooperativeKernel(kfn, dim3(G), dim3(256), args, smem, c->s));
   if (timed) cudaEventRecord(c->pcg_ev[1], c->s);
   c->launches++;
   return rc;
@@ -2866,7 +3038,7 @@ static int pcg_t(mpml_ctx_s* c, const mpml_solver_opts* o, int* iters, double* r
     *iters = fit + jit;
     return MPML_OK;
   }
-  if (sizeof(T) == 4 && c->compressed && o->use_graph == 2) {
+  if (sizeof(T) == 4 && o->use_graph == 2) {
     if ((rc = pcg_persistent(c, o))) return rc;
     if ((rc = read_scalars(c))) return rc;
     pcg_persistent_account(c);
