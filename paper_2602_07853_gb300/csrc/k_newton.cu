@@ -2087,7 +2087,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag) {
 // Warp sum of FP32 values in float-float arithmetic (error-free two-sum at
 // every level, the rounding errors carried in a second float), returned as
 // a double on lane 0: FP64-grade accuracy without a chain of FP64 additions.
-__device__ __forceinline__ double warp_sum_ff(float v) {
+__device__ __forceinline__ void warp_sum_ff(float v, float& hi_out, float& lo_out) {
   float hi = v, lo = 0.f;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -2098,18 +2098,21 @@ __device__ __forceinline__ double warp_sum_ff(float v) {
     lo = lo + bl + e;
     hi = s;
   }
-  return (double)hi + (double)lo;
+  hi_out = hi;
+  lo_out = lo;
 }
 
 // block sums of 2 FP32 per-thread partials (float-float within warps, FP64
 // across warps) added atomically to acc[0..1] (thread 0)
 __device__ __forceinline__ void block_atomic2(float a, float b, double* acc) {
   __shared__ double red2[2][32];
-  const double wa = warp_sum_ff(a), wb = warp_sum_ff(b);
+  float ah, al, bh, bl;
+  warp_sum_ff(a, ah, al);
+  warp_sum_ff(b, bh, bl);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    red2[0][wid] = wa;
-    red2[1][wid] = wb;
+  if (lane == 0) {  // FP64 only on lane 0 (FP64 instructions are slow on this part)
+    red2[0][wid] = (double)ah + (double)al;
+    red2[1][wid] = (double)bh + (double)bl;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -2377,7 +2380,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(psm + KB + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
   __shared__ int s_nbr[NBR];
   __shared__ int s_flag;
-  __shared__ double s_sum[2];
+  __shared__ float s_coef;  // alpha or beta, formed in FP64 by thread 0
+  __shared__ int s_stop;    // breakdown / convergence decided by thread 0
   DevScalars* sc = A.sc;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -2385,11 +2389,15 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
   }
   __syncthreads();
   unsigned tma_phase = 0;
-  double rz = sc->rz;
-  const double tol2 = sc->tol2;
+  // FP64 scalar state of the recurrences: thread 0 only, in shared memory
+  __shared__ double s_rz, s_rr_last, s_tol2;
+  if (threadIdx.x == 0) {
+    s_rz = sc->rz;
+    s_tol2 = sc->tol2;
+    s_rr_last = sc->rr_last;
+  }
   int done = sc->done;
   int it = 0;
-  double rr_last = sc->rr_last;
   float beta = 0.f;
   float* pold = A.pa;
   float* pnext = A.pb;
@@ -2498,21 +2506,22 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       alive = false;
       break;
     }
+    // the scalar recurrences in FP64 on thread 0 only (FP64 is slow on this part)
     if (threadIdx.x == 0) {
-      s_sum[0] = __ldcg(accH);
-      s_sum[1] = __ldcg(accH + 1);
+      const double pq = __ldcg(accH) + __ldcg(accH + 1);
+      s_stop = !(pq > 0.0);  // breakdown
+      s_coef = s_stop ? 0.f : (float)(s_rz / pq);
+      if (A.pf && blockIdx.x == 0) {
+        A.pf->ns += gtimer() - t_h0;
+        A.pf->count += 1;
+      }
     }
     __syncthreads();
-    const double pq = s_sum[0] + s_sum[1];
-    if (A.pf && blockIdx.x == 0 && threadIdx.x == 0) {
-      A.pf->ns += gtimer() - t_h0;
-      A.pf->count += 1;
-    }
-    if (!(pq > 0.0)) {
-      done = 1;  // breakdown
+    if (s_stop) {
+      done = 1;
       break;
     }
-    const float alpha = (float)(rz / pq);
+    const float alpha = s_coef;
     // ---------------- phase A ----------------
     float rzl = 0.f, rrl = 0.f;
     for (int jb = blockIdx.x; jb < A.nb; jb += G) {
@@ -2558,17 +2567,17 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       alive = false;
       break;
     }
+    ++it;
     if (threadIdx.x == 0) {
-      s_sum[0] = __ldcg(accA);
-      s_sum[1] = __ldcg(accA + 1);
+      const double rzn = __ldcg(accA), rrn = __ldcg(accA + 1);
+      s_rr_last = rrn;
+      s_stop = (rrn <= s_tol2 || it >= A.cg_max || !(rrn == rrn)) ? 1 : 0;
+      s_coef = (float)(rzn / s_rz);
+      s_rz = rzn;
     }
     __syncthreads();
-    const double rzn = s_sum[0], rrn = s_sum[1];
-    ++it;
-    rr_last = rrn;
-    if (rrn <= tol2 || it >= A.cg_max || !(rrn == rrn)) done = 1;
-    beta = (float)(rzn / rz);
-    rz = rzn;
+    done = s_stop;
+    beta = s_coef;
     float* tmp = pold;
     pold = pnext;
     pnext = tmp;
@@ -2576,8 +2585,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
   if (!alive && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     sc->iters = it;
-    sc->rr_last = rr_last;
-    sc->rz = rz;
+    sc->rr_last = s_rr_last;
+    sc->rz = s_rz;
     sc->done = 1;
   }
 }
