@@ -50,20 +50,34 @@ constexpr int BATCH_MAX = MPML_BATCH_MAX;
 constexpr unsigned BC_BYTES = 27u * BV * 4u;  // 27-number tangents of one brick
 constexpr size_t BC_SMEM = BC_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
 
-__device__ __forceinline__ double bwarp_sum(double v) {
+// warp sum of FP32 values in float-float arithmetic (error-free two-sum at every
+// level, the rounding errors carried in lo); FP64 only where lane 0 converts the pair
+__device__ __forceinline__ void bwarp_sum_ff(float v, float& hi_out, float& lo_out) {
+  float hi = v, lo = 0.f;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float bh = __shfl_down_sync(0xffffffffu, hi, o), bl = __shfl_down_sync(0xffffffffu, lo, o);
+    const float s = hi + bh;
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + (bh - bp);
+    lo = lo + bl + e;
+    hi = s;
+  }
+  hi_out = hi;
+  lo_out = lo;
 }
 
-// block sums of (a, b) added atomically to acc[0..1] (thread 0)
+// block sums of (a, b) added atomically to acc[0..1] (thread 0); FP64 only on
+// lane 0 and thread 0 (FP64 instructions are slow on this part)
 __device__ __forceinline__ void bblock_atomic2(float a_, float b_, double* acc) {
   __shared__ double red[2][32];
-  double a = bwarp_sum((double)a_), b = bwarp_sum((double)b_);
+  float ah, al, bh, bl;
+  bwarp_sum_ff(a_, ah, al);
+  bwarp_sum_ff(b_, bh, bl);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    red[0][wid] = a;
-    red[1][wid] = b;
+    red[0][wid] = (double)ah + (double)al;
+    red[1][wid] = (double)bh + (double)bl;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
