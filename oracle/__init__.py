@@ -34,7 +34,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FIXED_COROTATED, NEO_HOOKEAN, HENCKY = 0, 1, 2
+FIXED_COROTATED, NEO_HOOKEAN, HENCKY, WATER = 0, 1, 2, 3
 OK, WARN_NOT_CONVERGED, ERR_ARG, ERR_OUT_OF_DOMAIN, ERR_NONFINITE, ERR_STRETCH = 0, 1, -1, -2, -3, -4
 MAX_MATS = 4
 

@@ -206,6 +206,25 @@ static int spectral(int model, double mu, double lam, const double s[3], spec_t*
     }
     return 0;
   }
+  if (model == ORC_WATER) {
+    /* Sec. "Water": psi = kappa/2 (J - 1)^2, kappa = lam + 2/3 mu (bulk modulus);
+     * undefined for J <= 0 (no inverted fluid) */
+    if (!(J > 0)) return 1;
+    double kap = lam + 2.0 / 3.0 * mu;
+    o->psi = 0.5 * kap * (J - 1) * (J - 1);
+    for (int i = 0; i < 3; ++i) {
+      int j = (i + 1) % 3, k = (i + 2) % 3;
+      o->d1[i] = kap * (J - 1) * s[j] * s[k];
+      o->d2[3 * i + i] = kap * (s[j] * s[k]) * (s[j] * s[k]);
+    }
+    for (int p = 0; p < 3; ++p) {
+      int i = PAIR_I[p], j = PAIR_J[p], k = PAIR_K[p];
+      o->d2[3 * i + j] = o->d2[3 * j + i] = kap * s[k] * (2 * J - 1);
+      o->pp[p] = -kap * (J - 1) * s[k];
+      o->pm[p] = kap * (J - 1) * s[k];
+    }
+    return 0;
+  }
   if (model == ORC_HENCKY) {
     /* StVK with Hencky strain, Sec. 4.3.1:
      *   psi = mu sum (log s_i)^2 + lam/2 (sum log s_i)^2 */
@@ -409,6 +428,16 @@ int orc_stretch_from_tau(int model, double mu, double lam, const double tau[9], 
       }
       if (fc_sigma(mu, lam, t, 0.5 * (lo + hi), s)) return ORC_ERR_STRETCH;
     }
+  } else if (model == ORC_WATER) {
+    /* Sec. "Water": the pressure pi = tr(tau)/3 = kappa J (J - 1) inverted on the
+     * root J >= 1/2, J = (1 + sqrt(1 + 4 pi / kappa)) / 2; S = J^(1/3) I */
+    double kap = lam + 2.0 / 3.0 * mu;
+    if (!(kap > 0)) return ORC_ERR_STRETCH;
+    double pi = (t[0] + t[1] + t[2]) / 3;
+    double d = 1 + 4 * pi / kap;
+    if (!(d >= 0)) return ORC_ERR_STRETCH;
+    double J = 0.5 * (1 + sqrt(d));
+    s[0] = s[1] = s[2] = cbrt(J);
   } else {
     return ORC_ERR_ARG;
   }
@@ -1145,6 +1174,7 @@ int orc_return_map(int plastic, double mu, double lam, double yield_stress, doub
 int orc_load(orc_state* st, double* x, double* v, double* F, double* G, double* mp,
              double* Vp, int* mat) {
   const orc_scene* s = &st->sc;
+  int bad_j = 0;
   for (long c = 0; c < st->nc; ++c) {
     double* vc = st->v_c_new + 3 * c;
     vc[0] = vc[1] = vc[2] = 0;
@@ -1176,6 +1206,14 @@ int orc_load(orc_state* st, double* x, double* v, double* F, double* G, double* 
       const int k = st->mat[p];
       if (s->plastic[k] != ORC_ELASTIC)
         orc_return_map(s->plastic[k], s->mu[k], s->lam[k], s->yield_stress[k], s->friction_angle[k], Fn);
+      if (s->model[k] == ORC_WATER) {
+        /* Sec. "Water": J_p^{n+1} = (1 + dt tr(G_p^{n+1})) J_p^n, F kept isotropic;
+         * a non-positive J is an error (F set to NaN) */
+        double Jn = (1 + s->dt * (Gp[0] + Gp[4] + Gp[8])) * m3_det(st->F + 9 * p);
+        double c = Jn > 0 ? cbrt(Jn) : NAN;
+        for (int r = 0; r < 9; ++r) Fn[r] = (r % 4 == 0) ? c : 0.0;
+        if (!(Jn > 0)) bad_j = 1;
+      }
     }
     for (int a = 0; a < 3; ++a) {
       x[3 * p + a] = st->x[3 * p + a] + s->dt * vp[a];
@@ -1187,7 +1225,7 @@ int orc_load(orc_state* st, double* x, double* v, double* F, double* G, double* 
     if (Vp) Vp[p] = st->Vp[p];
     if (mat) mat[p] = st->mat[p];
   }
-  return ORC_OK;
+  return bad_j ? ORC_ERR_NONFINITE : ORC_OK;
 }
 
 /* ========================================================================

@@ -30,7 +30,11 @@ extern "C" {
 
 #define ORC_MAX_MATS 4
 
-enum { ORC_FIXED_COROTATED = 0, ORC_NEO_HOOKEAN = 1, ORC_HENCKY = 2 };
+/* ORC_WATER: the inviscid fluid of Sec. "Water": psi(J) = kappa/2 (J - 1)^2 of
+ * J = det F only, kappa = lam + 2/3 mu; pressure pi = kappa J (J - 1);
+ * base Jacobian by the closed-form root J >= 1/2, S = J^(1/3) I; particles
+ * carry F = J^(1/3) I and update J by the grid divergence. */
+enum { ORC_FIXED_COROTATED = 0, ORC_NEO_HOOKEAN = 1, ORC_HENCKY = 2, ORC_WATER = 3 };
 enum { ORC_ELASTIC = 0, ORC_VON_MISES = 1, ORC_DRUCKER_PRAGER = 2 };
 
 enum {

@@ -21,7 +21,7 @@ from typing import List, Optional, Tuple
 
 import numpy as np
 
-FIXED_COROTATED, NEO_HOOKEAN, HENCKY = 0, 1, 2
+FIXED_COROTATED, NEO_HOOKEAN, HENCKY, WATER = 0, 1, 2, 3
 ELASTIC, VON_MISES, DRUCKER_PRAGER = 0, 1, 2
 
 

@@ -10,7 +10,7 @@ import scipy.linalg
 
 import oracle
 
-MODELS = [oracle.FIXED_COROTATED, oracle.NEO_HOOKEAN, oracle.HENCKY]
+MODELS = [oracle.FIXED_COROTATED, oracle.NEO_HOOKEAN, oracle.HENCKY, oracle.WATER]
 MU, LAM = oracle.lame(1e5, 0.3)
 
 
@@ -168,7 +168,8 @@ def test_kirchhoff_fixed_corotated_polar_form():
                            atol=1e-9 * np.abs(P).max())
 
 
-@pytest.mark.parametrize("model", MODELS)
+# water keeps J only (its reconstruction is J^(1/3) I, pinned in test_oracle_water)
+@pytest.mark.parametrize("model", [m for m in MODELS if m != oracle.WATER])
 @pytest.mark.parametrize("scale", [1e-4, 1e-2, 0.15])
 def test_stretch_round_trip(model, scale):
     """tau = P(F) F^T then reconstruct: S = sqrtm(F F^T) (the left stretch; scipy), and
