@@ -65,7 +65,7 @@ typedef enum {
   MPML_ERR_TOO_LARGE = -8      /* size above a fixed capacity (mpml_sort_particles_noalloc) */
 } mpml_status;
 
-enum { MPML_FIXED_COROTATED = 0, MPML_NEO_HOOKEAN = 1, MPML_HENCKY = 2 };
+enum { MPML_FIXED_COROTATED = 0, MPML_NEO_HOOKEAN = 1, MPML_HENCKY = 2, MPML_WATER = 3 };
 enum { MPML_FP32 = 0, MPML_FP64 = 1 };
 enum { MPML_MEM_DEVICE = 0, MPML_MEM_HOST = 1 };
 enum { MPML_PRECOND_JACOBI = 0, MPML_PRECOND_LEARNED = 1 };
@@ -74,7 +74,12 @@ enum { MPML_PRECOND_JACOBI = 0, MPML_PRECOND_LEARNED = 1 };
  * MPML_HENCKY: StVK with Hencky strain (Sec. 4.3.1); MPML_NEO_HOOKEAN: split
  * Neo-Hookean, kappa = 2/3 mu + lambda (Sec. 4.3.2); MPML_FIXED_COROTATED:
  * psi = mu sum(s_i - 1)^2 + lambda/2 (J - 1)^2 (its stretch inverse is the
- * library's, the paper gives the general recipe of Sec. 4.3). */
+ * library's, the paper gives the general recipe of Sec. 4.3); MPML_WATER: the
+ * inviscid fluid of Sec. "Water", psi = kappa/2 (J - 1)^2 with the bulk modulus
+ * kappa = lambda + 2/3 mu > 0 (mu >= 0 may be 0), undefined for J <= 0: the base
+ * Jacobian is the root J >= 1/2 of kappa J (J - 1) = tr(tau)/3, S = J^(1/3) I;
+ * G2P sets such a particle's F to J^(1/3) I with J <- (1 + dt tr G_p) J (a
+ * non-positive J makes F NaN, reported by the next resample); elastic only. */
 typedef struct {
   int model;
   double mu, lambda;

@@ -146,6 +146,16 @@ __device__ double cbrt_signed(double z) { return z >= 0 ? cbrt(z) : -cbrt(-z); }
 
 // principal stretches from principal Kirchhoff stresses; false if none admissible
 __device__ bool invert_principal(int model, double mu, double lam, const double t[3], double s[3]) {
+  if (model == MPML_WATER) {
+    // Sec. "Water": pi = tr(tau)/3 = kappa J (J - 1), root J >= 1/2; S = J^(1/3) I
+    const double kap = lam + 2.0 / 3.0 * mu;
+    if (!(kap > 0)) return false;
+    const double d = 1.0 + 4.0 * ((t[0] + t[1] + t[2]) / 3.0) / kap;
+    if (!(d >= 0)) return false;
+    const double c = cbrt(0.5 * (1.0 + sqrt(d)));
+    s[0] = s[1] = s[2] = c;
+    return true;
+  }
   if (model == MPML_HENCKY) {
     // Sec. 4.3.1 closed form
     if (!(mu > 0 && lam > -2 * mu / 3)) return false;
@@ -566,6 +576,11 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
   }
   if (M.model == MPML_FIXED_COROTATED && !(Jm1 > -1.0)) {
     need_svd = true;
+    return true;
+  }
+  if (M.model == MPML_WATER) {
+    if (!(Jm1 > -1.0)) return false;
+    psi = 0.5 * (M.lam + 2.0 / 3.0 * M.mu) * Jm1 * Jm1;
     return true;
   }
   double E[9];

@@ -91,6 +91,22 @@ __device__ void kirchhoff(const MatParams<T>& M, const T F[9], T tau[6]) {
   T H[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) H[i] = F[i] - ((i % 4 == 0) ? T(1) : T(0));
+  if (M.model == MPML_WATER) {
+    // Sec. "Water": tau = pi I, pi = kappa J (J - 1), J - 1 from the invariants of H
+    T trH = H[0] + H[4] + H[8];
+    T trH2 = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) trH2 += H[3 * a + b] * H[3 * b + a];
+    T detH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+             H[2] * (H[3] * H[7] - H[4] * H[6]);
+    T Jm1 = trH + T(0.5) * (trH * trH - trH2) + detH;
+    T pi = (M.lam + T(2) / T(3) * M.mu) * Jm1 * (T(1) + Jm1);
+    tau[0] = tau[1] = tau[2] = pi;
+    tau[3] = tau[4] = tau[5] = T(0);
+    return;
+  }
   if (M.model == MPML_NEO_HOOKEAN) {
     // split form of Sec. 4.3.2: mu J^{-2/3} dev(b) + kappa/2 (J^2 - 1) I,
     // with b - I = H + H^T + H H^T and J - 1 from the invariants of H.
@@ -378,6 +394,15 @@ __global__ void __launch_bounds__(256) k_g2p(int64_t np, const T* __restrict__ x
   const int km = mats[p];
   if (km >= 0 && km < xi.nm && xi.plastic[km] != MPML_ELASTIC)
     return_map<T>(xi.plastic[km], xi.mat[km].mu, xi.mat[km].lam, xi.ys[km], xi.alpha[km], Fn);
+  if (km >= 0 && km < xi.nm && xi.mat[km].model == MPML_WATER) {
+    // Sec. "Water": J <- (1 + dt tr G_p) J, F kept isotropic; J <= 0 gives NaN
+    const T J0 = Fp[0] * (Fp[4] * Fp[8] - Fp[5] * Fp[7]) - Fp[1] * (Fp[3] * Fp[8] - Fp[5] * Fp[6]) +
+                 Fp[2] * (Fp[3] * Fp[7] - Fp[4] * Fp[6]);
+    const T Jn = (T(1) + dt * (Gp[0] + Gp[4] + Gp[8])) * J0;
+    const T c = Jn > T(0) ? cbrt(Jn) : T(NAN);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Fn[i] = (i % 4 == 0) ? c : T(0);
+  }
 #pragma unroll
   for (int i = 0; i < 9; ++i) Fo[9 * p + i] = Fn[i];
 #pragma unroll

@@ -19,8 +19,13 @@ bool bad_desc(const mpml_scene_desc* d, const mpml_material* mats, int n_mats) {
   if (d->precision != MPML_FP32 && d->precision != MPML_FP64) return true;
   if (d->wall_layers < 0) return true;
   for (int k = 0; k < n_mats; ++k) {
-    if (mats[k].model < 0 || mats[k].model > 2) return true;
-    if (!(mats[k].mu > 0)) return true;
+    if (mats[k].model < 0 || mats[k].model > MPML_WATER) return true;
+    if (mats[k].model == MPML_WATER) {
+      if (!(mats[k].mu >= 0) || !(mats[k].lambda + 2.0 / 3.0 * mats[k].mu > 0)) return true;
+      if (mats[k].plastic != MPML_ELASTIC) return true;
+    } else if (!(mats[k].mu > 0)) {
+      return true;
+    }
     if (mats[k].plastic < MPML_ELASTIC || mats[k].plastic > MPML_DRUCKER_PRAGER) return true;
     if (mats[k].plastic == MPML_VON_MISES && !(mats[k].yield_stress >= 0)) return true;
     if (mats[k].plastic == MPML_DRUCKER_PRAGER && !(mats[k].friction_angle >= 0 && mats[k].friction_angle < 1.5707963))

@@ -560,6 +560,26 @@ __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm
     }
     return true;
   }
+  if (M.model == MPML_WATER) {
+    // Sec. "Water": psi = kappa/2 (J - 1)^2, kappa = lam + 2/3 mu; no inverted fluid
+    if (!(J > T(0))) return false;
+    const T kap = lam + T(2) / T(3) * mu;
+    o.psi = T(0.5) * kap * Jm1 * Jm1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int j = (i + 1) % 3, k = (i + 2) % 3;
+      o.d1[i] = kap * Jm1 * s[j] * s[k];
+      o.d2[4 * i] = kap * (s[j] * s[k]) * (s[j] * s[k]);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int i = pair_i(p), j = pair_j(p), k = pair_k(p);
+      o.d2[3 * i + j] = o.d2[3 * j + i] = kap * s[k] * (T(2) * J - T(1));
+      o.pp[p] = -kap * Jm1 * s[k];
+      o.pm[p] = kap * Jm1 * s[k];
+    }
+    return true;
+  }
   if (M.model == MPML_HENCKY) {
     if (!(s[0] > T(0) && s[1] > T(0) && s[2] > T(0))) return false;
     const T l[3] = {log1p_t(e[0]), log1p_t(e[1]), log1p_t(e[2])};

@@ -20,7 +20,7 @@ OK, WARN_NOT_CONVERGED = 0, 1
 ERR_ARG, ERR_OUT_OF_DOMAIN, ERR_NONFINITE, ERR_STRETCH, ERR_TIMEOUT, ERR_CUDA, ERR_NOMEM = -1, -2, -3, -4, -5, -6, -7
 ERR_TOO_LARGE = -8
 NOALLOC_MAX_SLOTS = 1 << 21
-FIXED_COROTATED, NEO_HOOKEAN, HENCKY = 0, 1, 2
+FIXED_COROTATED, NEO_HOOKEAN, HENCKY, WATER = 0, 1, 2, 3
 ELASTIC, VON_MISES, DRUCKER_PRAGER = 0, 1, 2
 FP32, FP64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1

@@ -233,6 +233,32 @@ def batch_scene(index: int, n: int = 64, ppc: int = 8, dt: float = 1e-3,
     return _finish(sc, x, v, np.zeros(len(x), np.int64), ppc)
 
 
+def dam_break(n: int = 64, seed: int = 8, ppc: int = 8, dt: float = 1e-3, with_cube: bool = True) -> Scene:
+    """Water column collapsing in the unit box (Sec. "Water"): voxels x in [0.05, 0.4),
+    y in [1/n, 0.55), z in [0.05, 0.95) of water (E = 1e5, nu = 0.45: bulk modulus
+    3.3e5 Pa, rho = 1000), gravity, sticky walls; with ``with_cube`` a fixed-corotated
+    cube (E = 1e5, nu = 0.3, rho = 500) of 0.15 m rests on the floor in the flow's path,
+    so mixed water / solid cells arise when the front reaches it."""
+    mats = [Material(WATER, 1e5, 0.45)]
+    if with_cube:
+        mats.append(Material(FIXED_COROTATED, 1e5, 0.3, rho=500.0))
+    sc = Scene("dam_break", (n, n, n), 1.0 / n, float(n), dt, (0.0, -9.8, 0.0), mats)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lo = np.array([0.05, 1.0 / n, 0.05])
+    hi = np.array([0.4, 0.55, 0.95])
+    vw = _grid_voxels(tuple(np.ceil(lo * n - 1e-9).astype(int)), tuple(np.floor(hi * n + 1e-9).astype(int)))
+    xw = seed_voxels(vw, sc.dx, ppc, rng)
+    xs, ms = [xw], [np.zeros(len(xw), np.int64)]
+    if with_cube:
+        c0 = np.array([0.6, 1.0 / n, 0.425])
+        vc = _grid_voxels(tuple(np.round(c0 * n).astype(int)), tuple(np.round((c0 + 0.15) * n).astype(int)))
+        xc = seed_voxels(vc, sc.dx, ppc, rng)
+        xs.append(xc)
+        ms.append(np.ones(len(xc), np.int64))
+    x = np.concatenate(xs)
+    return _finish(sc, x, np.zeros_like(x), np.concatenate(ms), ppc)
+
+
 def colliding_cubes(n: int = 64, seed: int = 6, ppc: int = 8, speed: float = 1.0) -> Scene:
     """Two 0.1 m elastic cubes (E=5e3, nu=0.3, rho=1e3) moving at +-speed along x, no gravity
     (the linear-momentum experiment of Sec. 6.6; its speed is not given, 1 m/s here)."""
