@@ -1009,6 +1009,8 @@ __device__ __forceinline__ void prof_end(DevProf* pf) {
 }
 
 // ---------------------------------------------------------------------------
+// [persistent-solver source: begin] (bench.py hashes this region to tie an ncu
+// capture to the kernel version it measured)
 // TMA bulk copy + mbarrier helpers (sm_90+ PTX, used on sm_103a)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -2672,6 +2674,7 @@ static void pcg_persistent_account(mpml_ctx_s* c) {
   c->pcg_launches += 1;
   c->pcg_iters += c->hscal->iters;
 }
+// [persistent-solver source: end]
 
 // ---------------------------------------------------------------------------
 // Flexible CG with the learned preconditioner (FP32 contexts).  Notay's FCG

@@ -297,6 +297,7 @@ __device__ void jacobi3(const T Ain[9], T ev[3], T Q[9]) {
   ev[2] = A[8];
 }
 
+// [persistent-solver source: begin]
 // rotation matrix (row-major) of a unit quaternion (w, x, y, z)
 template <typename T>
 __device__ __forceinline__ void quat_to_rot(T w, T x, T y, T z, T R[9]) {
@@ -363,6 +364,7 @@ __device__ __forceinline__ void apply_c27(const float c[27], const float D[9], f
 #pragma unroll
     for (int b = 0; b < 3; ++b) KD[3 * a + b] = T1[3 * a] * W[3 * b] + T1[3 * a + 1] * W[3 * b + 1] + T1[3 * a + 2] * W[3 * b + 2];
 }
+// [persistent-solver source: end]
 
 // Signed SVD of F = I + H from the eigen-decomposition of F^T F - I =
 // H + H^T + H^T H, returning s = singular values (s0 >= s1 >= |s2|, s2 < 0
