@@ -416,6 +416,7 @@ def other_configs(m, scenes, args, peaks):
         vhat = m.mpml_get_field(ctx, m.F_NODE_VHAT)
         m.mpml_stretch(ctx)
         m.mpml_linearize(ctx, vhat)
+        tile, tile_ms = m.mpml_autotune_hvp(ctx, 5)  # the standalone HVP's fastest launch shape
         hvp_ms = m.mpml_hvp_bench(ctx, 20)
         k_bytes = (108.0 if len(sc.materials) == 1 else 180.0)
         alg = k_bytes * counts["cells"] + 28.0 * counts["nodes"]
@@ -424,7 +425,7 @@ def other_configs(m, scenes, args, peaks):
                     "dof_nodes": int(counts["nodes"]), "steps_per_s": 1e3 * len(times) / float(np.sum(times)),
                     "ms_per_step": float(np.mean(times)), "newton_iters_per_step": newton / len(times),
                     "cg_iters_per_step": cg / len(times),
-                    "hvp": {"kernel": "k_hvp_glob (27-number tangent)" if len(sc.materials) == 1 else "k_hvp_glob (45-number tangent)",
+                    "hvp": {"kernel": m.mpml_get_hvp_tile(ctx)[1], "tile_ms": tile_ms,
                             "mean_ms": hvp_ms, "bytes": alg, "gbs": gbs, "frac": gbs / peaks["hbm_gbs"],
                             "bytes_rule": f"{int(k_bytes)} B per active cell + 28 B per DOF node, working set "
                                           f"{alg / 1e6:.0f} MB vs 129 MB L2"}}
@@ -680,11 +681,13 @@ def hvp_probe(args):
     counts = m.mpml_counts(ctx)
     m.mpml_stretch(ctx)
     m.mpml_linearize(ctx, m.mpml_get_field(ctx, m.F_NODE_VHAT))
+    tile, tile_ms = m.mpml_autotune_hvp(ctx, 3)
     ms = m.mpml_hvp_bench(ctx, max(args.steps, 1))
     k_bytes = 108.0 if len(sc.materials) == 1 else 180.0
     alg = k_bytes * counts["cells"] + 28.0 * counts["nodes"]
     print(json.dumps({"probe": args.hvp_probe, "cells": counts["cells"], "nodes": counts["nodes"], "hvp_ms": ms,
-                      "hvp_gbs": alg / (ms / 1e3) / 1e9, "newton_rc": rc}), flush=True)
+                      "hvp_gbs": alg / (ms / 1e3) / 1e9, "tile": m.mpml_get_hvp_tile(ctx)[1], "tile_ms": tile_ms,
+                      "newton_rc": rc}), flush=True)
     m.mpml_destroy(ctx)
     return 0
 
