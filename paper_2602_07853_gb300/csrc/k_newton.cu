@@ -480,7 +480,7 @@ __device__ bool nh_closed_form(const MatParams<double>& M, const double Gd[9], c
     }
   const double I1m3 = B[0] + B[4] + B[8];
   const double kap = 2.0 / 3.0 * M.mu + M.lam;
-  const double cm1 = expm1(-2.0 / 3.0 * log1p(Jm1));  // J^{-2/3} - 1
+  const double cm1 = jpow_m23_m1(Jm1);  // J^{-2/3} - 1
   const double c = 1.0 + cm1;
   const double iso = 0.5 * kap * Jm1 * (2.0 + Jm1), mc = M.mu * c;
   double tau[9];
@@ -570,7 +570,7 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
       return q;
     }();
     const double kap = 2.0 / 3.0 * M.mu + M.lam;
-    const double cm1 = expm1(-2.0 / 3.0 * log1p(Jm1));
+    const double cm1 = jpow_m23_m1(Jm1);
     psi = 0.5 * M.mu * ((1.0 + cm1) * I1m3 + 3.0 * cm1) + 0.25 * kap * (2.0 * x_minus_log1p(Jm1) + Jm1 * Jm1);
     return true;
   }

@@ -511,6 +511,29 @@ __device__ __forceinline__ T x_minus_log1p(T x) {
   return x - log1p_t(x);
 }
 
+// (1 + x)^(-2/3) - 1: for |x| < 0.05 the binomial series sum_{k=1..12} C(-2/3, k) x^k
+// (remainder below 4e-18), in Horner form with the exact rational coefficients;
+// otherwise expm1(-2/3 log1p(x)).  Saves two FP64 transcendentals per cell.
+template <typename T>
+__device__ __forceinline__ T jpow_m23_m1(T x) {
+  if (fabs(x) < T(0.05)) {
+    T acc = T(41273960.0 / 129140163.0);
+    acc = acc * x - T(4717024.0 / 14348907.0);
+    acc = acc * x + T(1621477.0 / 4782969.0);
+    acc = acc * x - T(559130.0 / 1594323.0);
+    acc = acc * x + T(21505.0 / 59049.0);
+    acc = acc * x - T(7480.0 / 19683.0);
+    acc = acc * x + T(2618.0 / 6561.0);
+    acc = acc * x - T(308.0 / 729.0);
+    acc = acc * x + T(110.0 / 243.0);
+    acc = acc * x - T(40.0 / 81.0);
+    acc = acc * x + T(5.0 / 9.0);
+    acc = acc * x - T(2.0 / 3.0);
+    return acc * x;
+  }
+  return expm1_t(T(-2) / T(3) * log1p_t(x));
+}
+
 __device__ __forceinline__ int pair_i(int p) { return p == 2 ? 1 : 0; }
 __device__ __forceinline__ int pair_j(int p) { return p == 0 ? 1 : 2; }
 __device__ __forceinline__ int pair_k(int p) { return 2 - p; }
@@ -540,8 +563,7 @@ __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm
   if (M.model == MPML_NEO_HOOKEAN) {
     if (!(J > T(0))) return false;
     const T kap = T(2) / T(3) * mu + lam;
-    const T lJ = log1p_t(Jm1);
-    const T cm1 = expm1_t(T(-2) / T(3) * lJ);  // J^{-2/3} - 1
+    const T cm1 = jpow_m23_m1(Jm1);  // J^{-2/3} - 1
     const T c = T(1) + cm1;
     const T I1m3 = e[0] * (T(2) + e[0]) + e[1] * (T(2) + e[1]) + e[2] * (T(2) + e[2]);
     const T I1 = T(3) + I1m3;
