@@ -1057,6 +1057,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 }
 
 // [persistent-solver source: end]
+// streamed read-only load: no L1 allocation, L2 fetches in 256-byte sectors
+// (the tangent block is read once per launch, in 128-byte rows per warp)
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
 // Standalone FP32 HVP of one cell brick per CTA on the 27-number compressed
 // (C27) tangent (the 45-number form runs in k_hvp_col), read straight from global memory
 // (read-only during the kernel, coalesced per tangent entry; measured faster
@@ -1097,15 +1105,15 @@ __global__ void __launch_bounds__(256, 3) k_hvp_glob(const int* __restrict__ cbl
       if (C27) {
         float c[27];
 #pragma unroll
-        for (int qq = 0; qq < 27; ++qq) c[qq] = __ldg(Kb + qq * BV + l);
+        for (int qq = 0; qq < 27; ++qq) c[qq] = ld_stream(Kb + qq * BV + l);
         apply_c27(c, D, KD);
       } else
 #pragma unroll
       for (int r = 0; r < 9; ++r) {
-        KD[r] += __ldg(Kb + k45(r, r) * BV + l) * D[r];
+        KD[r] += ld_stream(Kb + k45(r, r) * BV + l) * D[r];
 #pragma unroll
         for (int cc = r + 1; cc < 9; ++cc) {
-          const float kv = __ldg(Kb + k45(r, cc) * BV + l);
+          const float kv = ld_stream(Kb + k45(r, cc) * BV + l);
           KD[r] += kv * D[cc];
           KD[cc] += kv * D[r];
         }
@@ -1281,12 +1289,12 @@ __global__ void __launch_bounds__(64, MINB) k_hvp_col(const int* __restrict__ cb
         if (C27) {
           float c[27];
 #pragma unroll
-          for (int qq = 0; qq < 27; ++qq) c[qq] = __ldg(Kb + qq * BV + l);
+          for (int qq = 0; qq < 27; ++qq) c[qq] = ld_stream(Kb + qq * BV + l);
           apply_c27(c, D, KD);
         } else {
           float k[45];
 #pragma unroll
-          for (int qq = 0; qq < 45; ++qq) k[qq] = __ldg(Kb + qq * BV + l);
+          for (int qq = 0; qq < 45; ++qq) k[qq] = ld_stream(Kb + qq * BV + l);
 #pragma unroll
           for (int r = 0; r < 9; ++r) {
             KD[r] += k[k45(r, r)] * D[r];
@@ -1915,9 +1923,9 @@ constexpr size_t hvp_smem_bytes() {
 // The launch shapes ("tiles") of the standalone FP32 HVP, per tangent format.
 // Entry 0 is the default before (or without) autotuning.
 const char* hvp_tile_name(int compressed, int tile) {
-  static const char* c27[HVP_TILES] = {"brick: 256 threads, 2 cells each, 3 CTAs/SM (k_hvp_glob)",
-                                       "z-column: 64 threads, 8 cells each, 8 CTAs/SM (k_hvp_col)",
-                                       "z-column: 64 threads, 8 cells each, 12 CTAs/SM (k_hvp_col)"};
+  static const char* c27[HVP_TILES] = {"z-column: 64 threads, 8 cells each, 12 CTAs/SM (k_hvp_col)",
+                                       "brick: 256 threads, 2 cells each, 3 CTAs/SM (k_hvp_glob)",
+                                       "z-column: 64 threads, 8 cells each, 8 CTAs/SM (k_hvp_col)"};
   static const char* k45[HVP_TILES] = {"z-column: 64 threads, 8 cells each, 16 CTAs/SM (k_hvp_col)",
                                        "z-column: 64 threads, 8 cells each, 12 CTAs/SM (k_hvp_col)",
                                        "brick: 256 threads, 2 cells each, 3 CTAs/SM (k_hvp_glob)"};
@@ -1931,9 +1939,9 @@ static void launch_hvp_f32(mpml_ctx_s* c, int tile, const float* p, float* q, in
 #define HVP_IN (const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p, (const float*)c->cK.p, p, \
                (const float*)c->nmass.p, q, dscal(c), finalize, pf
   if (c->compressed) {
-    if (tile == 1) k_hvp_col<true, 8><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
-    else if (tile == 2) k_hvp_col<true, 12><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
-    else k_hvp_glob<true><<<g, 256, HVP_G_SMEM, c->s>>>(HVP_IN, (int*)c->status.p, part_hvp(c));
+    if (tile == 1) k_hvp_glob<true><<<g, 256, HVP_G_SMEM, c->s>>>(HVP_IN, (int*)c->status.p, part_hvp(c));
+    else if (tile == 2) k_hvp_col<true, 8><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
+    else k_hvp_col<true, 12><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
   } else {
     if (tile == 1) k_hvp_col<false, 12><<<g, 64, 0, c->s>>>(HVP_IN, part_hvp(c));
     else if (tile == 2) k_hvp_glob<false><<<g, 256, HVP_G_SMEM, c->s>>>(HVP_IN, (int*)c->status.p, part_hvp(c));
