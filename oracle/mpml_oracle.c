@@ -251,9 +251,61 @@ static int spectral(int model, double mu, double lam, const double s[3], spec_t*
   return 1;
 }
 
+/* Split Neo-Hookean energy of Sec. 4.3.2, mu/2 (J^(-2/3) I1 - 3) + kappa/4 (J^2 - 1
+ * - 2 log J), evaluated from H = F - I so that small strains keep their relative
+ * accuracy: the energy is second order in H but both brackets are differences of
+ * first-order terms.  With c = J^(-2/3) - 1 (binomial series in x = J - 1 for
+ * |x| < 0.05, coefficients C(-2/3, k) by their product recurrence),
+ *   J^(-2/3) I1 - 3 = [3 c + 2 x] + [(I1 - 3) - 2 x] + c (I1 - 3),
+ * where 3 c + 2 x drops the series' linear term, (I1 - 3) - 2 x = |H|^2 + tr(H^2)
+ * - (tr H)^2 - 2 det H, and J^2 - 1 - 2 log J = x^2 + 2 (x - log(1 + x)) with
+ * x - log(1 + x) from its Taylor series for |x| < 0.05. */
+static double nh_energy(double mu, double lam, const double F[9]) {
+  double H[9];
+  for (int i = 0; i < 9; ++i) H[i] = F[i] - ((i % 4 == 0) ? 1.0 : 0.0);
+  double trH = H[0] + H[4] + H[8], hF2 = 0, trH2 = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      hF2 += H[3 * a + b] * H[3 * a + b];
+      trH2 += H[3 * a + b] * H[3 * b + a];
+    }
+  double detH = m3_det(H);
+  double x = trH + 0.5 * (trH * trH - trH2) + detH; /* J - 1 */
+  if (!(x > -1)) return INFINITY;
+  double I1m3 = 2 * trH + hF2, b2 = hF2 + trH2 - trH * trH - 2 * detH;
+  double kap = 2.0 / 3.0 * mu + lam;
+  double c, a2, xml;
+  if (fabs(x) < 0.05) {
+    double coef = 1, pw = 1;
+    c = 0;
+    a2 = 0;
+    for (int k = 1; k <= 16; ++k) {
+      coef *= (-2.0 / 3.0 - (k - 1)) / k;
+      pw *= x;
+      c += coef * pw;
+      if (k >= 2) a2 += 3 * coef * pw;
+    }
+    xml = 0;
+    pw = x;
+    for (int k = 2; k <= 18; ++k) {
+      pw *= x;
+      xml += ((k % 2) ? -pw : pw) / k;
+    }
+  } else {
+    c = pow(1 + x, -2.0 / 3.0) - 1;
+    a2 = 3 * c + 2 * x;
+    xml = x - log1p(x);
+  }
+  return 0.5 * mu * (a2 + b2 + c * I1m3) + 0.25 * kap * (x * x + 2 * xml);
+}
+
 int orc_psi(int model, double mu, double lam, const double F[9], double* psi) {
   double U[9], s[3], V[9];
   spec_t sp;
+  if (model == ORC_NEO_HOOKEAN) {
+    *psi = nh_energy(mu, lam, F);
+    return isfinite(*psi) ? 0 : 1;
+  }
   orc_svd3(F, U, s, V);
   if (spectral(model, mu, lam, s, &sp)) { *psi = INFINITY; return 1; }
   *psi = sp.psi;
@@ -845,15 +897,17 @@ static void trial_F(const orc_scene* s, const double Gc[9], const double S[9], d
   m3_mul(A, S, Fc);
 }
 
-int orc_eval(orc_state* st, const double* v, double* phi, double* grad) {
+/* the incremental potential's two parts: inertia (returned in *e_in) and the
+ * elastic sum (*e_el); the gradient when grad != NULL */
+static int eval_parts(orc_state* st, const double* v, double* e_in, double* e_el, double* grad) {
   const orc_scene* s = &st->sc;
   const int K = s->n_mats;
-  double E = 0;
+  double Ein = 0, E = 0;
   if (grad) memset(grad, 0, sizeof(double) * 3 * st->nn);
   for (long i = 0; i < st->nn; ++i)
     for (int r = 0; r < 3; ++r) {
       double d = v[3 * i + r] - st->vhat[3 * i + r];
-      E += 0.5 * st->m_i[i] * d * d;
+      Ein += 0.5 * st->m_i[i] * d * d;
       if (grad) grad[3 * i + r] += st->m_i[i] * d;
     }
   int bad = 0;
@@ -886,7 +940,15 @@ int orc_eval(orc_state* st, const double* v, double* phi, double* grad) {
   if (grad)
     for (long i = 0; i < st->nn; ++i)
       if (st->fixed[i]) grad[3 * i] = grad[3 * i + 1] = grad[3 * i + 2] = 0;
-  *phi = bad ? INFINITY : E;
+  *e_in = Ein;
+  *e_el = bad ? INFINITY : E;
+  return bad;
+}
+
+int orc_eval(orc_state* st, const double* v, double* phi, double* grad) {
+  double ein, eel;
+  int bad = eval_parts(st, v, &ein, &eel, grad);
+  *phi = bad ? INFINITY : ein + eel;
   return bad;
 }
 
@@ -1085,12 +1147,25 @@ int orc_newton(orc_state* st, const orc_solver* opt, orc_stats* stats) {
     int cgit = orc_pcg(st, rhs, dv, opt->cg_rtol, opt->cg_max, &rr);
     if (it < 64) stats->cg_iters[it] = cgit;
     stats->cg_iters_total += cgit;
-    double slope = dot(n, g, dv), alpha = 1, phit = INFINITY;
+    /* Armijo test of App. B on the energy change Phi(v + a dv) - Phi(v): the
+     * inertia part is a A + a^2 B / 2 in closed form (A = sum m (v - vhat).dv,
+     * B = sum m |dv|^2), the elastic part a difference of elastic sums, so that
+     * no two nearly equal inertia sums are subtracted */
+    double slope = dot(n, g, dv), alpha = 1, A = 0, B = 0;
+    for (long i = 0; i < st->nn; ++i)
+      for (int r = 0; r < 3; ++r) {
+        const long q = 3 * i + r;
+        A += st->m_i[i] * (v[q] - st->vhat[q]) * dv[q];
+        B += st->m_i[i] * dv[q] * dv[q];
+      }
+    double ein0, eel0, eint, eelt = INFINITY;
+    eval_parts(st, v, &ein0, &eel0, NULL);
     int accepted = 0;
     for (int ls = 0; ls <= opt->ls_max; ++ls) {
       for (long i = 0; i < n; ++i) vt[i] = v[i] + alpha * dv[i];
-      orc_eval(st, vt, &phit, NULL);
-      if (phit <= phi + opt->ls_c1 * alpha * slope) { accepted = 1; break; }
+      int bad = eval_parts(st, vt, &eint, &eelt, NULL);
+      double dphi = alpha * A + 0.5 * alpha * alpha * B + (eelt - eel0);
+      if (!bad && dphi <= opt->ls_c1 * alpha * slope) { accepted = 1; break; }
       alpha *= 0.5;
     }
     if (it < 64) stats->alpha[it] = accepted ? alpha : 0;

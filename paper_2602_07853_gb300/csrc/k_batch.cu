@@ -547,7 +547,7 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
   int rc;
   std::vector<mpml_ctx_s*> all(ctxs, ctxs + n);
   std::vector<int> it(n, 0), status(n, MPML_OK), active(n, 0);
-  std::vector<double> g0(n, 0.0), gn(n, 0.0), phi(n, 0.0), gfloor(n, 0.0);
+  std::vector<double> g0(n, 0.0), gn(n, 0.0), phi(n, 0.0), phi_el(n, 0.0), gfloor(n, 0.0);
   mpml_ctx_s* owner = ctxs[0];
   std::vector<mpml_ctx_s*> work;
   for (int i = 0; i < n; ++i) {
@@ -569,6 +569,7 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
     g0[i] = gn[i] = sqrt(c->hscal->gg);
     gfloor[i] = 1e-12 * sqrt(c->hscal->mv2);
     phi[i] = c->hscal->phi_in + c->hscal->phi_el;
+    phi_el[i] = c->hscal->phi_el;
     st[i].g0_norm = g0[i];
     st[i].phi0 = phi[i];
   }
@@ -605,9 +606,13 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
       batch_slope_launch(c);
     }
     if ((rc = read_all(cs))) return rc;
-    std::vector<double> slope(n), alpha(n, 1.0);
+    std::vector<double> slope(n), lsA(n), lsB(n), alpha(n, 1.0), phit_el(n, 0.0);
     std::vector<int> accepted(n, 0);
-    for (int i : idx) slope[i] = ctxs[i]->hscal->slope;
+    for (int i : idx) {
+      slope[i] = ctxs[i]->hscal->slope;
+      lsA[i] = ctxs[i]->hscal->ls_a;
+      lsB[i] = ctxs[i]->hscal->ls_b;
+    }
     for (int ls = 0; ls <= o->ls_max; ++ls) {
       std::vector<mpml_ctx_s*> pend;
       std::vector<int> pidx;
@@ -621,8 +626,11 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
       if ((rc = read_all(pend))) return rc;
       for (int i : pidx) {
         const mpml_ctx_s* c = ctxs[i];
-        const double pt = c->hscal->phi_in + c->hscal->phi_el;
-        if (c->hscal->infeasible == 0 && pt <= phi[i] + o->ls_c1 * alpha[i] * slope[i])
+        // Armijo on the energy change (inertia part in closed form, elastic part as a
+        // difference of elastic sums), as in the single-scene solver
+        phit_el[i] = c->hscal->phi_el;
+        const double dphi = alpha[i] * lsA[i] + 0.5 * alpha[i] * alpha[i] * lsB[i] + (phit_el[i] - phi_el[i]);
+        if (c->hscal->infeasible == 0 && dphi <= o->ls_c1 * alpha[i] * slope[i])
           accepted[i] = 1;
         else
           alpha[i] *= 0.5;
@@ -647,6 +655,7 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
       const mpml_ctx_s* c = ctxs[i];
       gn[i] = sqrt(c->hscal->gg);
       phi[i] = c->hscal->phi_in + c->hscal->phi_el;
+      phi_el[i] = c->hscal->phi_el;
     }
   }
   int worst = MPML_OK;

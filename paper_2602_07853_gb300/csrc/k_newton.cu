@@ -563,15 +563,21 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
   const double Jm1 = jm1_of_h(H);
   if (M.model == MPML_NEO_HOOKEAN) {
     if (!(Jm1 > -1.0)) return false;
-    const double I1m3 = 2.0 * (H[0] + H[4] + H[8]) + [&] {
-      double q = 0;
+    const double trH = H[0] + H[4] + H[8];
+    double hF2 = 0, trH2 = 0;
 #pragma unroll
-      for (int i = 0; i < 9; ++i) q += H[i] * H[i];
-      return q;
-    }();
-    const double kap = 2.0 / 3.0 * M.mu + M.lam;
-    const double cm1 = jpow_m23_m1(Jm1);
-    psi = 0.5 * M.mu * ((1.0 + cm1) * I1m3 + 3.0 * cm1) + 0.25 * kap * (2.0 * x_minus_log1p(Jm1) + Jm1 * Jm1);
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        hF2 += H[3 * a + b] * H[3 * a + b];
+        trH2 += H[3 * a + b] * H[3 * b + a];
+      }
+    const double detH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                        H[2] * (H[3] * H[7] - H[4] * H[6]);
+    const double I1m3 = 2.0 * trH + hF2;
+    // I1 - 3 - 2 (J - 1) with J - 1 = tr H + ((tr H)^2 - tr H^2)/2 + det H: second order only
+    const double b2 = hF2 + trH2 - trH * trH - 2.0 * detH;
+    psi = nh_psi(M.mu, 2.0 / 3.0 * M.mu + M.lam, Jm1, I1m3, b2);
     return true;
   }
   if (M.model == MPML_FIXED_COROTATED && !(Jm1 > -1.0)) {
@@ -1242,7 +1248,21 @@ __global__ void __launch_bounds__(64, MINB) k_hvp_col(const int* __restrict__ cb
   __syncthreads();
   if (s_done) return;
   prof_begin(pf);
-  stage_nodes_sn<float, float>(id, s_nbr, p, sv);
+  for (int i = t; i < 729; i += 64) {  // the 9^3 p halo, streamed (read once per brick)
+    const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+    const int tb = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+    const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+    if (tb >= 0) {
+      const float* src = p + (int64_t)tb * 3 * BV + l;
+      v0 = ld_stream(src);
+      v1 = ld_stream(src + BV);
+      v2 = ld_stream(src + 2 * BV);
+    }
+    sv[0][i] = v0;
+    sv[1][i] = v1;
+    sv[2][i] = v2;
+  }
   __syncthreads();
   const float* Kb = K + (int64_t)id * NQ * BV;
   const uint8_t* cf = cflag + (int64_t)id * BV;
@@ -1745,6 +1765,36 @@ __global__ void __launch_bounds__(512) k_dot(const double* __restrict__ a, const
   double vals[1] = {s};
   double* const dst[1] = {out};
   block_add<1>(vals, dst);
+}
+
+// Line-search set-up for the direction x: slope g^T x and the coefficients of the
+// exact inertia change along it, sum_i m_i/2 |v_i + a x_i - vhat_i|^2 - (the same at
+// a = 0) = a A + a^2 B / 2 with A = sum m (v - vhat).x, B = sum m |x|^2.  Evaluating
+// the change this way avoids subtracting two nearly equal inertia sums whose
+// terms carry the rounding of v + a x (relative to |v|, not to |v - vhat|).
+template <typename T>
+__global__ void __launch_bounds__(512) k_ls_setup(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
+                                                  const double* __restrict__ g, const double* __restrict__ v,
+                                                  const double* __restrict__ vhat, const T* __restrict__ x,
+                                                  DevScalars* sc) {
+  const int id = blockIdx.x, l = threadIdx.x;
+  const int64_t slot = (int64_t)id * BV + l;
+  double sl = 0, A = 0, B = 0;
+  const bool dof = (nflag[slot] & NF_DOF) != 0;
+  const double mi = (double)m[slot];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+    const double xv = (double)x[o];
+    sl += g[o] * xv;
+    if (dof) {
+      A += mi * (v[o] - vhat[o]) * xv;
+      B += mi * xv * xv;
+    }
+  }
+  double vals[3] = {sl, A, B};
+  double* const dst[3] = {&sc->slope, &sc->ls_a, &sc->ls_b};
+  block_add<3>(vals, dst);
 }
 
 // line-search energy at v + alpha x: inertia over all bricks
@@ -3151,6 +3201,7 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
   double g0 = sqrt(c->hscal->gg), gn = g0;
   const double gfloor = 1e-12 * sqrt(c->hscal->mv2);  // rounding level of the gradient
   double phi = c->hscal->phi_in + c->hscal->phi_el;
+  double phi_el = c->hscal->phi_el;  // elastic energy at the current iterate
   st->g0_norm = g0;
   st->phi0 = phi;
   int status = MPML_OK, it = 0;
@@ -3170,19 +3221,25 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
       st->cg_rel_resid[it] = rel;
     }
     st->cg_iters_total += cgit;
-    // slope g^T dx
+    // slope g^T dx and the exact inertia change along dx
     DevScalars* d = dscal(c);
-    cudaMemsetAsync(&d->slope, 0, sizeof(double), c->s);
-    k_dot<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const double*)c->ng.p, (const T*)c->nx.p, &d->slope);
+    cudaMemsetAsync(&d->slope, 0, 3 * sizeof(double), c->s);
+    k_ls_setup<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
+                                                   (const double*)c->ng.p, (const double*)c->nvnew.p,
+                                                   (const double*)c->nvhat.p, (const T*)c->nx.p, d);
     c->launches++;
     if ((rc = read_scalars(c))) return rc;
-    const double slope = c->hscal->slope;
-    double alpha = 1.0, phit = 0;
+    const double slope = c->hscal->slope, lsA = c->hscal->ls_a, lsB = c->hscal->ls_b;
+    double alpha = 1.0, phit = 0, phit_el = 0;
     bool accepted = false;
     for (int ls = 0; ls <= o->ls_max; ++ls) {
       int inf = 0;
       if ((rc = energy_t<T>(c, alpha, &phit, &inf))) return rc;
-      if (inf == 0 && phit <= phi + o->ls_c1 * alpha * slope) {
+      phit_el = c->hscal->phi_el;
+      // Armijo on the energy change: inertia part in closed form, elastic part as a
+      // difference of the (accurately evaluated) elastic sums
+      const double dphi = alpha * lsA + 0.5 * alpha * alpha * lsB + (phit_el - phi_el);
+      if (inf == 0 && dphi <= o->ls_c1 * alpha * slope) {
         accepted = true;
         break;
       }
@@ -3201,6 +3258,7 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max, 0)) || (rc = read_scalars(c))) return rc;
     gn = sqrt(c->hscal->gg);
     phi = phit;
+    phi_el = phit_el;
   }
   st->newton_iters = it;
   st->g_norm = gn;
@@ -3441,8 +3499,10 @@ int batch_prep(mpml_ctx_s* c, double cg_rtol, int cg_max) { return prep_t<float>
 
 void batch_slope_launch(mpml_ctx_s* c) {
   DevScalars* d = dscal(c);
-  cudaMemsetAsync(&d->slope, 0, sizeof(double), c->s);
-  k_dot<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const double*)c->ng.p, (const float*)c->nx.p, &d->slope);
+  cudaMemsetAsync(&d->slope, 0, 3 * sizeof(double), c->s);
+  k_ls_setup<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const float*)c->nmass.p,
+                                                     (const double*)c->ng.p, (const double*)c->nvnew.p,
+                                                     (const double*)c->nvhat.p, (const float*)c->nx.p, d);
   c->launches++;
 }
 

@@ -69,6 +69,8 @@ struct DevScalars {
   double phi_el;   // elastic energy sum
   double phi_in;   // inertia sum
   double slope;    // g^T dx
+  double ls_a;     // sum m (v - vhat) . dx over DOF nodes (line search, inertia)
+  double ls_b;     // sum m |dx|^2 over DOF nodes
   double tol2;     // (cg_rtol)^2 rr0
   double rr_last;  // r^T r at the last CG update
   double pq;       // p^T H p of the current direction
@@ -534,6 +536,40 @@ __device__ __forceinline__ T jpow_m23_m1(T x) {
   return expm1_t(T(-2) / T(3) * log1p_t(x));
 }
 
+// 3 ((1 + x)^(-2/3) - 1) + 2 x, which is second order in x: for |x| < 0.05 from the
+// binomial series without its linear term (so the first-order parts cancel exactly),
+// otherwise from jpow_m23_m1 directly.
+template <typename T>
+__device__ __forceinline__ T nh_a2(T x) {
+  if (fabs(x) < T(0.05)) {
+    T acc = T(41273960.0 / 129140163.0);
+    acc = acc * x - T(4717024.0 / 14348907.0);
+    acc = acc * x + T(1621477.0 / 4782969.0);
+    acc = acc * x - T(559130.0 / 1594323.0);
+    acc = acc * x + T(21505.0 / 59049.0);
+    acc = acc * x - T(7480.0 / 19683.0);
+    acc = acc * x + T(2618.0 / 6561.0);
+    acc = acc * x - T(308.0 / 729.0);
+    acc = acc * x + T(110.0 / 243.0);
+    acc = acc * x - T(40.0 / 81.0);
+    acc = acc * x + T(5.0 / 9.0);
+    return T(3) * acc * x * x;
+  }
+  return T(3) * jpow_m23_m1(x) + T(2) * x;
+}
+
+// Split Neo-Hookean energy (Sec. 4.3.2) mu/2 (J^(-2/3) I1 - 3) + kappa/4 (J^2 - 1 - 2 log J)
+// from second-order quantities only, so that small strains keep their relative
+// accuracy (the first-order parts of J^(-2/3) I1 - 3 cancel analytically):
+//   J^(-2/3) I1 - 3 = [3 cm1 + 2 (J-1)] + [I1 - 3 - 2 (J-1)] + cm1 (I1 - 3),
+//   cm1 = J^(-2/3) - 1, with b2 = I1 - 3 - 2 (J-1) supplied by the caller as a sum of
+//   second-order terms; J^2 - 1 - 2 log J = (J-1)^2 + 2 ((J-1) - log(1 + (J-1))).
+template <typename T>
+__device__ __forceinline__ T nh_psi(T mu, T kap, T Jm1, T I1m3, T b2) {
+  const T cm1 = jpow_m23_m1(Jm1);
+  return T(0.5) * mu * (nh_a2(Jm1) + b2 + cm1 * I1m3) + T(0.25) * kap * (T(2) * x_minus_log1p(Jm1) + Jm1 * Jm1);
+}
+
 __device__ __forceinline__ int pair_i(int p) { return p == 2 ? 1 : 0; }
 __device__ __forceinline__ int pair_j(int p) { return p == 0 ? 1 : 2; }
 __device__ __forceinline__ int pair_k(int p) { return 2 - p; }
@@ -568,8 +604,10 @@ __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm
     const T I1m3 = e[0] * (T(2) + e[0]) + e[1] * (T(2) + e[1]) + e[2] * (T(2) + e[2]);
     const T I1 = T(3) + I1m3;
     const T J2m1 = Jm1 * (T(2) + Jm1);
-    o.psi = T(0.5) * mu * (c * I1m3 + T(3) * cm1) +
-            T(0.25) * kap * (T(2) * x_minus_log1p(Jm1) + Jm1 * Jm1);
+    // I1 - 3 - 2 (J - 1) = sum e_i^2 - 2 (e0 e1 + e0 e2 + e1 e2) - 2 e0 e1 e2
+    const T b2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] - T(2) * (e[0] * e[1] + e[0] * e[2] + e[1] * e[2]) -
+                 T(2) * e[0] * e[1] * e[2];
+    o.psi = nh_psi(mu, kap, Jm1, I1m3, b2);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int j = (i + 1) % 3, k = (i + 2) % 3;

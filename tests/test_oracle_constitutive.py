@@ -246,3 +246,23 @@ def test_fixed_corotated_rejects_below_half_volume():
     t = 2 * MU * s * (s - 1) + LAM * J * (J - 1)
     with pytest.raises(ValueError):
         oracle.stretch_from_tau(oracle.FIXED_COROTATED, MU, LAM, np.diag(t))
+
+
+@pytest.mark.parametrize("scale", [1e-7, 1e-5, 1e-3, 3e-2, 0.2])
+def test_neo_hookean_energy_keeps_relative_accuracy_at_small_strain(scale):
+    """The split Neo-Hookean energy of Sec. 4.3.2 against a 50-digit evaluation of the
+    same formula (mpmath): second order in the strain, so a direct FP64 evaluation of
+    J^(-2/3) I1 - 3 loses about eps / strain^2 of relative accuracy; the oracle's form
+    keeps it (1e-12 relative here), which the line search needs near convergence."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(int(1e3 * scale) + 7)
+    for _ in range(20):
+        F = np.eye(3) + scale * rng.standard_normal((3, 3))
+        Fm = mp.matrix([[mp.mpf(float(F[i, j])) for j in range(3)] for i in range(3)])
+        J = mp.det(Fm)
+        I1 = sum(Fm[i, j] ** 2 for i in range(3) for j in range(3))
+        kap = mp.mpf(2) / 3 * MU + LAM
+        ref = MU / 2 * (J ** (mp.mpf(-2) / 3) * I1 - 3) + kap / 4 * (J ** 2 - 1 - 2 * mp.log(J))
+        got = oracle.psi(oracle.NEO_HOOKEAN, MU, LAM, F)
+        assert abs(got - float(ref)) <= 1e-12 * abs(float(ref)), (scale, got, float(ref))
