@@ -66,7 +66,7 @@ class Scene(C.Structure):
 class Solver(C.Structure):
     _fields_ = [("cg_rtol", C.c_double), ("cg_max", C.c_int), ("newton_rtol", C.c_double),
                 ("newton_atol", C.c_double), ("newton_max", C.c_int), ("ls_c1", C.c_double),
-                ("ls_max", C.c_int)]
+                ("ls_max", C.c_int), ("fixed_point", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -243,10 +243,10 @@ def make_scene(n, dx, dt, gravity=(0.0, -9.8, 0.0), materials=((FIXED_COROTATED,
 
 
 def default_solver(cg_rtol=1e-6, cg_max=10000, newton_rtol=1e-6, newton_atol=0.0, newton_max=50,
-                   ls_c1=1e-4, ls_max=30):
+                   ls_c1=1e-4, ls_max=30, fixed_point=0):
     s = Solver()
     s.cg_rtol, s.cg_max, s.newton_rtol, s.newton_atol = cg_rtol, cg_max, newton_rtol, newton_atol
-    s.newton_max, s.ls_c1, s.ls_max = newton_max, ls_c1, ls_max
+    s.newton_max, s.ls_c1, s.ls_max, s.fixed_point = newton_max, ls_c1, ls_max, int(fixed_point)
     return s
 
 

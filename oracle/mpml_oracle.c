@@ -1116,6 +1116,42 @@ int orc_pcg(const orc_state* st, const double* b, double* x, double rtol, int ma
  * (the last term is the rounding level of the gradient: a body at rest or in
  * free fall starts at g(v0) = 0 up to rounding, which the relative test cannot
  * reduce further); Jacobi-PCG to cg_rtol; Armijo backtracking by halving. */
+/* Sec. "Fixed-Point Plasticity" (plasticity updated inside each Newton
+ * iteration, the linear solves see elasticity only): at iterate v, each slot of
+ * a plastic material takes its trial F = (I + dt G_c(v)) B to the yield surface
+ * by the material's return map; where that changes F, the slot's base becomes
+ * B = (I + dt G_c(v))^{-1} F^E, so that F_c(v) = F^E.  Returns the number of
+ * slots changed. */
+static long plastic_project(orc_state* st, const double* v) {
+  const orc_scene* s = &st->sc;
+  const int K = s->n_mats;
+  long changed = 0;
+  for (long c = 0; c < st->nc; ++c) {
+    double Gc[9], A[9], Ai[9];
+    cell_vgrad(st, c, v, Gc);
+    for (int r = 0; r < 9; ++r) A[r] = s->dt * Gc[r];
+    A[0] += 1; A[4] += 1; A[8] += 1;
+    double det = m3_det(A);
+    if (!(det > 0)) continue;
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) / det; Ai[1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) / det; Ai[3] = (A[5] * A[6] - A[3] * A[8]) / det;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) / det; Ai[5] = (A[2] * A[3] - A[0] * A[5]) / det;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) / det; Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
+    for (int k = 0; k < K; ++k) {
+      if (st->V_ck[K * c + k] == 0 || s->plastic[k] == ORC_ELASTIC) continue;
+      double* B = st->S_ck + 9 * (K * c + k);
+      double F[9];
+      m3_mul(A, B, F);
+      if (orc_return_map(s->plastic[k], s->mu[k], s->lam[k], s->yield_stress[k], s->friction_angle[k], F) == 0)
+        continue;
+      m3_mul(Ai, F, B);
+      ++changed;
+    }
+  }
+  return changed;
+}
+
 int orc_newton(orc_state* st, const orc_solver* opt, orc_stats* stats) {
   long n = 3 * st->nn;
   double* v = st->vnew;
@@ -1127,6 +1163,7 @@ int orc_newton(orc_state* st, const orc_solver* opt, orc_stats* stats) {
   for (long i = 0; i < st->nn; ++i)
     for (int r = 0; r < 3; ++r)
       v[3 * i + r] = st->fixed[i] ? st->vfix[3 * i + r] : st->vhat[3 * i + r];
+  if (opt->fixed_point) plastic_project(st, v);
   double phi;
   orc_eval(st, v, &phi, g);
   double g0 = sqrt(dot(n, g, g)), gn = g0;
@@ -1172,6 +1209,7 @@ int orc_newton(orc_state* st, const orc_solver* opt, orc_stats* stats) {
     ++it;
     if (!accepted) { status = ORC_WARN_NOT_CONVERGED; break; }
     memcpy(v, vt, sizeof(double) * n);
+    if (opt->fixed_point) plastic_project(st, v);
     orc_eval(st, v, &phi, g);
     gn = sqrt(dot(n, g, g));
   }

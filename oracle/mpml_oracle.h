@@ -75,6 +75,8 @@ typedef struct {
   int newton_max;
   double ls_c1;        /* Armijo constant */
   int ls_max;          /* halvings */
+  int fixed_point;     /* Sec. "Fixed-Point Plasticity": project the plastic slots'
+                          trial F onto the yield surface at every Newton iterate */
 } orc_solver;
 
 typedef struct {
