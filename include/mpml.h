@@ -146,6 +146,14 @@ typedef struct {
                           with a device-side conditional WHILE loop; 2 (default when opts is
                           NULL) one persistent cooperative kernel with bounded grid barriers
                           (FP32 contexts; FP64 contexts use 1) */
+  int plastic_fixed_point; /* 0 (default): plasticity by the particles' return map after G2P
+                          (semi-implicit); 1: Sec. "Fixed-Point Plasticity": at v0 and after
+                          every accepted Newton step each plastic slot's trial F =
+                          (I + dt G_c(v)) B is return-mapped and its base replaced by
+                          B = (I + dt G_c(v))^-1 F^E (a general 3x3 base for the rest of the
+                          solve), so the converged grid state satisfies the yield condition;
+                          the linear solves see elasticity only.  Single-scene solver only
+                          (mpml_newton_step_batch rejects it with MPML_ERR_ARG). */
 } mpml_solver_opts;
 
 typedef struct {
@@ -159,6 +167,7 @@ typedef struct {
   double phi0, phi;          /* incremental potential at v0 and at exit */
   int64_t n_particles, n_cells, n_nodes, n_bricks;
   int fcg_fallbacks;         /* learned solves that continued with Jacobi-PCG */
+  int plastic_projections;   /* fixed-point plasticity: slot projections that changed a base */
 } mpml_solve_stats;
 
 /* Lifecycle ----------------------------------------------------------- */

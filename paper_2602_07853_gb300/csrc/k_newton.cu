@@ -248,6 +248,9 @@ struct SolveInfo {
   double dt, dx;
   int nm, nf;
   MatParams<double> mat[MPML_MAX_MATS];
+  int b9;  // the base is the general 9-number one (fixed-point plastic solve)
+  int plastic[MPML_MAX_MATS];
+  double ys[MPML_MAX_MATS], alpha[MPML_MAX_MATS];
 };
 
 template <typename T>
@@ -413,10 +416,28 @@ __device__ __forceinline__ void rot_to_quat(const T R[9], T q[4]) {
 
 
 // F - I = dt G + s + dt G s with S = I + s (symmetric, packed xx yy zz xy xz yz)
-__device__ __forceinline__ void trial_h(const double Gd[9], const double s6[6], double sm[9], double H[9]) {
-  sm[0] = s6[0]; sm[1] = s6[3]; sm[2] = s6[4];
-  sm[3] = s6[3]; sm[4] = s6[1]; sm[5] = s6[5];
-  sm[6] = s6[4]; sm[7] = s6[5]; sm[8] = s6[2];
+// the base B - I (row-major) of slot k of a cell: the symmetric stretch S - I (6
+// numbers) of the stretch step, or, during a fixed-point plastic solve, the
+// general base (9 numbers) its projections leave
+__device__ __forceinline__ void load_base(const double* __restrict__ cs, int b9, int64_t id, int nm, int k, int l,
+                                          double bm[9]) {
+  if (b9) {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) bm[q] = cs[(((int64_t)id * nm + k) * 9 + q) * BV + l];
+    return;
+  }
+  double s6[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) s6[q] = cs[(((int64_t)id * nm + k) * 6 + q) * BV + l];
+  bm[0] = s6[0]; bm[1] = s6[3]; bm[2] = s6[4];
+  bm[3] = s6[3]; bm[4] = s6[1]; bm[5] = s6[5];
+  bm[6] = s6[4]; bm[7] = s6[5]; bm[8] = s6[2];
+}
+
+// H = (I + Gd)(I + bm) - I with bm = B - I
+__device__ __forceinline__ void trial_h(const double Gd[9], const double bm[9], double sm[9], double H[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) sm[q] = bm[q];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -546,10 +567,10 @@ __device__ bool fc_closed_form(const MatParams<double>& M, const double Gd[9], c
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      // (F - R) S with S = I + sm (symmetric)
+      // (F - R) B^T with B = I + sm (= (F - R) S for the stretch step's symmetric S)
       double fs = FR[3 * a + b];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) fs += FR[3 * a + k] * sm[3 * k + b];
+      for (int k = 0; k < 3; ++k) fs += FR[3 * a + k] * sm[3 * b + k];  // (F - R) B^T
       PSt[3 * a + b] = 2.0 * M.mu * fs + kJ * cof[3 * a + b] * idet;
     }
   return true;
@@ -623,7 +644,7 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
 // the eigenbasis of the 3x3 block, S - I, clamped scaled eigenvalues).
 template <typename T>
 __device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[9], const T pp[3], const T pm[3], T kv,
-                              const double s6[6], CellOut<T>& out) {
+                              const double bm[9], CellOut<T>& out) {
   // diagonal block: eigen-decomposition of d2, clamp
   T ev[3], Qd[9];
   jacobi3<T>(d2, ev, Qd);
@@ -653,6 +674,9 @@ __device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[
 #pragma unroll
     for (int i = 0; i < 4; ++i) out.C[8 + i] = (T)q[i];
 #pragma unroll
+    // the symmetric base S - I (xx, yy, zz, xy, xz, yz): this record is built only for
+    // the stretch step's symmetric base
+    const double s6[6] = {bm[0], bm[4], bm[8], bm[1], bm[2], bm[5]};
     for (int i = 0; i < 6; ++i) out.C[12 + i] = (T)s6[i];
 #pragma unroll
     for (int m = 0; m < 3; ++m) out.C[18 + m] = ev[m] > T(0) ? kv * ev[m] : T(0);
@@ -709,10 +733,10 @@ __device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[
 
 template <typename T>
 __device__ void cell_material(const MatParams<double>& M, double V, const double Gd[9] /* dt*G */,
-                              const double s6[6], double kq, double kk, bool want_k, CellOut<T>& out,
+                              const double bm[9] /* B - I */, double kq, double kk, bool want_k, CellOut<T>& out,
                               bool want_psi = true) {
   double sm[9], H[9];
-  trial_h(Gd, s6, sm, H);
+  trial_h(Gd, bm, sm, H);
   if constexpr (sizeof(T) == 4) {
     double PSt[9];
     const bool closed = (M.model == MPML_NEO_HOOKEAN && nh_closed_form(M, Gd, H, PSt)) ||
@@ -759,7 +783,7 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
           for (int k = 0; k < 3; ++k) acc += (float)sm[3 * a + k] * Vf[3 * k + b];
           Wf[3 * a + b] = acc;
         }
-      build_tangent<T>(Uf, Vf, Wf, spf.d2, spf.pp, spf.pm, (float)(kk * V), s6, out);
+      build_tangent<T>(Uf, Vf, Wf, spf.d2, spf.pp, spf.pm, (float)(kk * V), bm, out);
       return;
     }
   }
@@ -816,7 +840,7 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
     pp[p] = (T)sp.pp[p];
     pm[p] = (T)sp.pm[p];
   }
-  build_tangent<T>(Ut, Vt, Wt, d2, pp, pm, (T)(kk * V), s6, out);
+  build_tangent<T>(Ut, Vt, Wt, d2, pp, pm, (T)(kk * V), bm, out);
 }
 
 // node init: g = m (v - vhat) (FP64), diag = m, inertia energy (all bricks, 512 thr)
@@ -888,10 +912,9 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
     for (int k = 0; k < si.nm; ++k) {
       const double V = (double)acc[((int64_t)id * si.nf + acc_V(k)) * BV + l];
       if (V == 0.0) continue;
-      double s6[6];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) s6[q] = cs[(((int64_t)id * si.nm + k) * 6 + q) * BV + l];
-      cell_material<T>(si.mat[k], V, Gd, s6, kq, kk, want_k != 0, co, want_psi != 0);
+      double bm[9];
+      load_base(cs, si.b9, id, si.nm, k, l, bm);
+      cell_material<T>(si.mat[k], V, Gd, bm, kq, kk, want_k != 0, co, want_psi != 0);
     }
     if (!co.ok) {
       bad = 1;
@@ -1843,10 +1866,9 @@ __global__ void __launch_bounds__(256) k_energy_cells(const int* __restrict__ cb
     for (int k = 0; k < si.nm; ++k) {
       const double V = (double)acc[((int64_t)id * si.nf + acc_V(k)) * BV + l];
       if (V == 0.0) continue;
-      double s6[6], sm[9], H[9];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) s6[q] = cs[(((int64_t)id * si.nm + k) * 6 + q) * BV + l];
-      trial_h(Gd, s6, sm, H);
+      double bm[9], sm[9], H[9];
+      load_base(cs, si.b9, id, si.nm, k, l, bm);
+      trial_h(Gd, bm, sm, H);
       double psi;
       bool need_svd;
       if (!psi_from_h(si.mat[k], H, psi, need_svd)) {
@@ -1893,11 +1915,16 @@ static SolveInfo solve_info(mpml_ctx_s* c) {
   si.dx = c->d.dx;
   si.nm = c->nm;
   si.nf = acc_fields(c->nm);
+  si.b9 = c->fp_active;
   for (int k = 0; k < MPML_MAX_MATS; ++k) {
     const mpml_material& m = c->mats[k < c->nm ? k : 0];
     si.mat[k].model = m.model;
     si.mat[k].mu = m.mu;
     si.mat[k].lam = m.lambda;
+    si.plastic[k] = k < c->nm ? m.plastic : MPML_ELASTIC;
+    si.ys[k] = m.yield_stress;
+    const double sp = sin(m.friction_angle);
+    si.alpha[k] = sqrt(2.0 / 3.0) * 2.0 * sp / (3.0 - sp);
   }
   return si;
 }
@@ -1954,7 +1981,7 @@ static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg
                                      (const double*)c->nvhat.p, (double*)c->ng.p, (T*)c->ndinv.p, dscal(c));
   if (ncb > 0)
     k_prep<T><<<ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p,
-                                    (const T*)c->cacc.p, (const double*)c->cs.p, (const double*)c->nvnew.p, si,
+                                    (const T*)c->cacc.p, (const double*)(c->fp_active ? c->cB.p : c->cs.p), (const double*)c->nvnew.p, si,
                                     want_k ? (c->compressed ? 2 : 1) : 0, (T*)c->cK.p, (double*)c->ng.p,
                                     (T*)c->ndinv.p, dscal(c),
                                     (int*)c->status.p, want_psi);
@@ -3178,13 +3205,107 @@ static int energy_t(mpml_ctx_s* c, double alpha, double* phi, int* infeasible) {
   if (c->ncb > 0)
     k_energy_cells<T><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
                                                          (const uint8_t*)c->cflag.p, (const T*)c->cacc.p,
-                                                         (const double*)c->cs.p, (const double*)c->nvnew.p,
+                                                         (const double*)(c->fp_active ? c->cB.p : c->cs.p), (const double*)c->nvnew.p,
                                                          (const T*)c->nx.p, alpha, si, d);
   c->launches += 2;
   int rc = read_scalars(c);
   if (rc) return rc;
   *infeasible = c->hscal->infeasible;
   *phi = c->hscal->phi_in + c->hscal->phi_el;
+  return MPML_OK;
+}
+
+// ---- fixed-point plasticity (Sec. "Fixed-Point Plasticity") -------------------
+// the general bases start as the stretch step's symmetric S - I
+__global__ void __launch_bounds__(256) k_base_init(const int* __restrict__ cblist, const double* __restrict__ cs,
+                                                   int nm, double* cb) {
+  const int64_t id = cblist[blockIdx.x];
+  for (int l = threadIdx.x; l < BV; l += blockDim.x)
+    for (int k = 0; k < nm; ++k) {
+      double bm[9];
+      load_base(cs, 0, id, nm, k, l, bm);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) cb[((id * nm + k) * 9 + q) * BV + l] = bm[q];
+    }
+}
+
+// At the iterate v: each slot of a plastic material takes its trial F = (I + dt G_c(v)) B
+// to the yield surface by the material's return map (FP64); where that changes F the
+// base becomes B = (I + dt G_c(v))^{-1} F^E, so that F_c(v) = F^E.  The linear solves
+// then see elasticity only.
+__global__ void __launch_bounds__(256) k_plastic_fp(const int* __restrict__ cblist, const int* __restrict__ nbr,
+                                                    const uint8_t* __restrict__ cflag, const void* __restrict__ accv,
+                                                    int fp64, const double* __restrict__ v, SolveInfo si,
+                                                    double* cb, int* changed) {
+  __shared__ double sv[3][729];
+  const int id = cblist[blockIdx.x];
+  stage_nodes<double, double, double>(id, nbr, v, nullptr, 0.0, sv);
+  __syncthreads();
+  const double sgd = si.dt * 0.25 / si.dx;
+  int nch = 0;
+  for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+    if (!cflag[(int64_t)id * BV + l]) continue;
+    double D[9];
+    gather_D<double>(l, sv, D);
+    double A[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] = sgd * D[q] + ((q % 4 == 0) ? 1.0 : 0.0);
+    const double cof[9] = {A[4] * A[8] - A[5] * A[7], A[2] * A[7] - A[1] * A[8], A[1] * A[5] - A[2] * A[4],
+                           A[5] * A[6] - A[3] * A[8], A[0] * A[8] - A[2] * A[6], A[2] * A[3] - A[0] * A[5],
+                           A[3] * A[7] - A[4] * A[6], A[1] * A[6] - A[0] * A[7], A[0] * A[4] - A[1] * A[3]};
+    const double det = A[0] * cof[0] + A[1] * cof[3] + A[2] * cof[6];
+    if (!(det > 0.0)) continue;
+    for (int k = 0; k < si.nm; ++k) {
+      if (si.plastic[k] == MPML_ELASTIC) continue;
+      const double V = fp64 ? ((const double*)accv)[((int64_t)id * si.nf + acc_V(k)) * BV + l]
+                             : (double)((const float*)accv)[((int64_t)id * si.nf + acc_V(k)) * BV + l];
+      if (V == 0.0) continue;
+      double bm[9], F[9];
+      load_base(cb, 1, id, si.nm, k, l, bm);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          double acc = A[3 * a + b];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) acc += A[3 * a + q] * bm[3 * q + b];
+          F[3 * a + b] = acc;
+        }
+      if (!return_map<double>(si.plastic[k], si.mat[k].mu, si.mat[k].lam, si.ys[k], si.alpha[k], F)) continue;
+      // B = A^{-1} F^E, stored as B - I
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const double bv = (cof[3 * a] * F[b] + cof[3 * a + 1] * F[3 + b] + cof[3 * a + 2] * F[6 + b]) / det;
+          cb[(((int64_t)id * si.nm + k) * 9 + 3 * a + b) * BV + l] = bv - ((a == b) ? 1.0 : 0.0);
+        }
+      ++nch;
+    }
+  }
+  if (nch) atomicAdd(changed, nch);
+}
+
+// the general bases are used only inside one fixed-point solve
+struct FixedPointScope {
+  mpml_ctx_s* c;
+  ~FixedPointScope() { c->fp_active = 0; }
+};
+
+// projection of every plastic slot at the current iterate; *changed += slots changed
+template <typename T>
+static int plastic_project(mpml_ctx_s* c, int* changed) {
+  if (c->ncb == 0) return MPML_OK;
+  DevScalars* d = dscal(c);
+  cudaMemsetAsync(&d->nproj, 0, sizeof(int), c->s);
+  k_plastic_fp<<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
+                                                  (const uint8_t*)c->cflag.p, c->cacc.p, sizeof(T) == 8,
+                                                  (const double*)c->nvnew.p, solve_info(c), (double*)c->cB.p,
+                                                  &d->nproj);
+  c->launches++;
+  int rc = read_scalars(c);
+  if (rc) return rc;
+  *changed += c->hscal->nproj;
   return MPML_OK;
 }
 
@@ -3196,7 +3317,26 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     st->status = MPML_OK;
     return MPML_OK;
   }
+  bool fp = false;
+  if (o->plastic_fixed_point)
+    for (int k = 0; k < c->nm; ++k) fp = fp || c->mats[k].plastic != MPML_ELASTIC;
+  FixedPointScope scope{c};
+  if (fp) {
+    if (c->compressed) return MPML_ERR_ARG;
+    if ((rc = ensure(c->cB, sizeof(double) * 9 * c->nm * c->nb * BV))) return rc;
+    if (c->ncb > 0) {
+      k_base_init<<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const double*)c->cs.p, c->nm,
+                                                      (double*)c->cB.p);
+      c->launches++;
+    }
+    c->fp_active = 1;
+  }
   if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max)) || (rc = read_scalars(c))) return rc;
+  if (fp) {
+    // project at v0 (prep has set it), then the gradient with the projected bases
+    if ((rc = plastic_project<T>(c, &st->plastic_projections))) return rc;
+    if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max)) || (rc = read_scalars(c))) return rc;
+  }
   if (*c->hstatus & ST_NONFINITE) return MPML_ERR_NONFINITE;
   double g0 = sqrt(c->hscal->gg), gn = g0;
   const double gfloor = 1e-12 * sqrt(c->hscal->mv2);  // rounding level of the gradient
@@ -3253,6 +3393,15 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     }
     k_axpy<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nx.p, alpha, (double*)c->nvnew.p);
     c->launches++;
+    if (fp) {
+      // plastic projection at the new iterate; the energy changes with the bases
+      if ((rc = plastic_project<T>(c, &st->plastic_projections))) return rc;
+      if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max)) || (rc = read_scalars(c))) return rc;
+      gn = sqrt(c->hscal->gg);
+      phi = c->hscal->phi_in + c->hscal->phi_el;
+      phi_el = c->hscal->phi_el;
+      continue;
+    }
     // the energy at the new iterate is the accepted line-search value (same formula
     // at v + alpha dx); prep skips it where its closed forms apply
     if ((rc = prep_t<T>(c, 1, 1, o->cg_rtol, o->cg_max, 0)) || (rc = read_scalars(c))) return rc;
@@ -3518,7 +3667,7 @@ void batch_energy_launch(mpml_ctx_s* c, double alpha) {
   if (c->ncb > 0)
     k_energy_cells<float><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
                                                              (const uint8_t*)c->cflag.p, (const float*)c->cacc.p,
-                                                             (const double*)c->cs.p, (const double*)c->nvnew.p,
+                                                             (const double*)(c->fp_active ? c->cB.p : c->cs.p), (const double*)c->nvnew.p,
                                                              (const float*)c->nx.p, alpha, si, d);
   c->launches += 2;
 }

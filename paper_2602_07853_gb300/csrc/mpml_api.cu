@@ -254,7 +254,8 @@ int mpml_create(const mpml_scene_desc* desc, const mpml_material* mats, int n_ma
   c->s = (cudaStream_t)stream;
   c->fp64 = desc->precision == MPML_FP64;
   c->esz = c->fp64 ? 8 : 4;
-  c->compressed = (!c->fp64 && n_mats == 1) ? 1 : 0;
+  // the 27-number tangent assumes the symmetric base of the stretch step: elastic single-material FP32
+  c->compressed = (!c->fp64 && n_mats == 1 && mats[0].plastic == MPML_ELASTIC) ? 1 : 0;
   for (int a = 0; a < 3; ++a) c->NB[a] = (desc->n[a] >> 3) + 1;
   c->NBT = (int64_t)c->NB[0] * c->NB[1] * c->NB[2];
   cudaGetDevice(&c->device);
@@ -289,7 +290,7 @@ int mpml_destroy(mpml_ctx c) {
                  &c->uF, &c->uG, &c->um, &c->uV, &c->umat, &c->cnt, &c->start, &c->scan_tmp, &c->cflag,
                  &c->cacc, &c->cs, &c->cK, &c->cnew, &c->nflag, &c->nmass, &c->nv, &c->nvhat, &c->nvfix,
                  &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->bbatch, &c->nolist,
-                 &c->nnw, &c->nnact, &c->nny, &c->nnpart, &c->nz, &c->nns_r, &c->nns_e, &c->nnhd, &c->tuneq};
+                 &c->nnw, &c->nnact, &c->nny, &c->nnpart, &c->nz, &c->nns_r, &c->nns_e, &c->nnhd, &c->tuneq, &c->cB};
   for (Buf* b : bufs) free_buf(*b);
   if (c->hscal) cudaFreeHost(c->hscal);
   if (c->hstatus) cudaFreeHost(c->hstatus);
@@ -385,7 +386,7 @@ int mpml_stretch(mpml_ctx c) {
 
 int mpml_newton_step(mpml_ctx c, const mpml_solver_opts* o, mpml_solve_stats* st) {
   if (!c || c->stage < 1) return MPML_ERR_ARG;
-  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 2};
+  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 2, 0};
   if (!o) o = &def;
   mpml_solve_stats local;
   if (!st) st = &local;
@@ -440,8 +441,9 @@ int mpml_newton_step_batch(mpml_ctx* ctxs, int n, const mpml_solver_opts* o, mpm
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == c) return MPML_ERR_ARG;
   }
-  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 2};
+  mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 2, 0};
   if (!o) o = &def;
+  if (o->plastic_fixed_point) return MPML_ERR_ARG;  // single-scene solver only
   std::vector<mpml_solve_stats> local;
   if (!stats) {
     local.resize(n);

@@ -86,6 +86,7 @@ struct DevScalars {
   int iters;
   int cg_max;
   int bodies;      // executed bodies of the graph-driven CG loop
+  int nproj;       // fixed-point plasticity: slots whose base a projection changed
   int counter[8];  // last-block tickets per kernel kind
   int pad;
 };
@@ -124,6 +125,10 @@ struct mpml_ctx_s {
   int hvp_tile = -1;
   int hvp_tile_fixed = 0;  // set by mpml_set_hvp_tile: never re-tuned
   mpml::Buf tuneq;         // scratch output of the autotuner's timed launches
+  // fixed-point plastic solve: general bases B - I of every slot (9 numbers), used
+  // by the energy / gradient / tangent kernels while fp_active is set
+  mpml::Buf cB;
+  int fp_active = 0;
   size_t esz = 4;
   int NB[3] = {0, 0, 0};
   int64_t NBT = 0;
@@ -675,5 +680,52 @@ __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm
   }
   return false;
 }
+
+// Plastic return map of one particle's elastic F (in place), in the Hencky
+// strain eps = log(s) of F = U diag(s) V^T with U, V kept; tau = 2 mu eps +
+// lam tr(eps) I.  Von Mises: |dev eps| beyond sqrt(2/3) ys / (2 mu) is scaled
+// back to it.  Drucker-Prager (cohesionless): tr(eps) > 0 -> eps = 0;
+// otherwise dgamma = |dev eps| + (3 lam + 2 mu) / (2 mu) alpha tr(eps) > 0 is
+// removed from |dev eps| along dev eps.  F with a non-positive singular value
+// is left unchanged.  Returns whether F was changed.
+template <typename T>
+__device__ bool return_map(int kind, double mu_, double lam_, double ys, double alpha_, T F[9]) {
+  T H[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) H[i] = F[i] - ((i % 4 == 0) ? T(1) : T(0));
+  T U[9], s[3], e[3], V[9], Jm1;
+  svd_from_h<T>(H, U, s, e, V, Jm1);
+  if (!(s[0] > T(0) && s[1] > T(0) && s[2] > T(0))) return false;
+  T eps[3] = {log1p(e[0]), log1p(e[1]), log1p(e[2])};
+  const T mu = (T)mu_, lam = (T)lam_;
+  const T tr = eps[0] + eps[1] + eps[2];
+  const T d[3] = {eps[0] - tr / T(3), eps[1] - tr / T(3), eps[2] - tr / T(3)};
+  const T dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  if (kind == MPML_VON_MISES) {
+    const T lim = (T)(sqrt(2.0 / 3.0) * ys / (2.0 * mu_));
+    if (dn <= lim) return false;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) eps[i] = tr / T(3) + d[i] * (lim / dn);
+  } else if (kind == MPML_DRUCKER_PRAGER) {
+    if (tr > T(0)) {
+      eps[0] = eps[1] = eps[2] = T(0);
+    } else {
+      const T dg = dn + (T(3) * lam + T(2) * mu) / (T(2) * mu) * tr * (T)alpha_;
+      if (dg <= T(0)) return false;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) eps[i] -= dg * d[i] / dn;
+    }
+  } else {
+    return false;
+  }
+  const T ex[3] = {exp(eps[0]), exp(eps[1]), exp(eps[2])};
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F[3 * r + c] = U[3 * r] * ex[0] * V[3 * c] + U[3 * r + 1] * ex[1] * V[3 * c + 1] +
+                                               U[3 * r + 2] * ex[2] * V[3 * c + 2];
+  return true;
+}
+
 
 }  // namespace mpml
