@@ -794,7 +794,7 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
     out.ok = false;
     return;
   }
-  {
+  if (want_psi) {
     // the energy by the same formula as the line search (k_energy_cells)
     double psi;
     bool need_svd;
