@@ -144,11 +144,16 @@ def ncu_traffic():
     return d["dram_bytes_per_launch"]
 
 
+# tangent bytes per active cell: 25 FP32 numbers (compressed, one material) or 45 (packed)
+CMP_TANGENT_BYTES = 100.0
+PACKED_TANGENT_BYTES = 180.0
+
+
 def pcg_bytes_per_iter(n_cells, n_nodes):
-    """Algorithmic bytes of one CG iteration (FP32): the HVP reads the 27-number compressed tangent
-    of every active cell (108 B) and per DOF node p, m and writes q (28 B); the CG update makes
+    """Algorithmic bytes of one CG iteration (FP32): the HVP reads the compressed tangent of every
+    active cell (25 numbers, 100 B) and per DOF node p, m and writes q (28 B); the CG update makes
     about ten 12-byte vector passes per DOF node (x, r, p, q, D^-1 reads and writes)."""
-    return 108.0 * n_cells + (28.0 + 120.0) * n_nodes
+    return CMP_TANGENT_BYTES * n_cells + (28.0 + 120.0) * n_nodes
 
 
 # ---------------------------------------------------------------------------
@@ -418,7 +423,7 @@ def other_configs(m, scenes, args, peaks):
         m.mpml_linearize(ctx, vhat)
         tile, tile_ms = m.mpml_autotune_hvp(ctx, 5)  # the standalone HVP's fastest launch shape
         hvp_ms = m.mpml_hvp_bench(ctx, 20)
-        k_bytes = (108.0 if len(sc.materials) == 1 else 180.0)
+        k_bytes = CMP_TANGENT_BYTES if len(sc.materials) == 1 else PACKED_TANGENT_BYTES
         alg = k_bytes * counts["cells"] + 28.0 * counts["nodes"]
         gbs = alg / (hvp_ms / 1e3) / 1e9
         out[key] = {"particles": int(counts["particles"]), "active_cells": int(counts["cells"]),
@@ -683,7 +688,7 @@ def hvp_probe(args):
     m.mpml_linearize(ctx, m.mpml_get_field(ctx, m.F_NODE_VHAT))
     tile, tile_ms = m.mpml_autotune_hvp(ctx, 3)
     ms = m.mpml_hvp_bench(ctx, max(args.steps, 1))
-    k_bytes = 108.0 if len(sc.materials) == 1 else 180.0
+    k_bytes = CMP_TANGENT_BYTES if len(sc.materials) == 1 else PACKED_TANGENT_BYTES
     alg = k_bytes * counts["cells"] + 28.0 * counts["nodes"]
     print(json.dumps({"probe": args.hvp_probe, "cells": counts["cells"], "nodes": counts["nodes"], "hvp_ms": ms,
                       "hvp_gbs": alg / (ms / 1e3) / 1e9, "tile": m.mpml_get_hvp_tile(ctx)[1], "tile_ms": tile_ms,

@@ -47,7 +47,7 @@ struct BScene {
 };
 
 constexpr int BATCH_MAX = MPML_BATCH_MAX;
-constexpr unsigned BC_BYTES = 27u * BV * 4u;  // 27-number tangents of one brick
+constexpr unsigned BC_BYTES = (unsigned)NQC * BV * 4u;  // compressed tangents of one brick
 constexpr size_t BC_SMEM = BC_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
 
 // warp sum of FP32 values in float-float arithmetic (error-free two-sum at every
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 bsmem_u32(Cs)),
-            "l"(B.C + (int64_t)id * 27 * BV), "r"(BC_BYTES), "r"(bsmem_u32(bar))
+            "l"(B.C + (int64_t)id * NQC * BV), "r"(BC_BYTES), "r"(bsmem_u32(bar))
             : "memory");
       }
       float pmp = 0.f, pkp = 0.f;
@@ -269,11 +269,11 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
 #pragma unroll
         for (int rr = 0; rr < 9; ++rr) KD[h][rr] = 0.f;
         if (ok && B.cflag[(int64_t)id * BV + l]) {
-          float D[9], c[27];
+          float D[9], c[NQC];
           bgather_D(l, sv, D);
 #pragma unroll
-          for (int q = 0; q < 27; ++q) c[q] = Cs[q * BV + l];
-          apply_c27(c, D, KD[h]);
+          for (int q = 0; q < NQC; ++q) c[q] = Cs[q * BV + l];
+          apply_cmp(c, D, KD[h]);
 #pragma unroll
           for (int rr = 0; rr < 9; ++rr) pkp += D[rr] * KD[h][rr];
         }

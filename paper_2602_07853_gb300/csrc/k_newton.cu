@@ -372,10 +372,9 @@ template <typename T>
 struct CellOut {
   double Q[9];  // dt V P S^T / (4 dx)   (gradient, node contribution = Q sgn)
   T K[45];      // dt^2 V L^T A+ L / (16 dx^2)
-  // the same tangent as 27 numbers (single material): quaternions of U, V and
-  // of the eigenbasis of the 3x3 block, S - I (6), and the clamped, scaled
-  // eigenvalues of the block (3), flip (3) and twist (3) modes
-  T C[27];
+  // the same tangent as NQC numbers (single material): quaternion of U, W = S V,
+  // the clamped 3x3 block, flip and twist moduli (layout at apply_cmp)
+  T C[NQC];
   double psi;
   bool ok;
 };
@@ -640,8 +639,7 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
 
 // The projected tangent of one cell in the storage precision T from the signed
 // SVD (U, V, W = S V) and the isotropic eigen-data of psi: the 45-number
-// packed form and the 27-number compressed form (quaternions of U, V and of
-// the eigenbasis of the 3x3 block, S - I, clamped scaled eigenvalues).
+// packed form and the NQC-number compressed form (layout at apply_cmp).
 template <typename T>
 __device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[9], const T pp[3], const T pm[3], T kv,
                               const double bm[9], CellOut<T>& out) {
@@ -649,41 +647,38 @@ __device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[
   T ev[3], Qd[9];
   jacobi3<T>(d2, ev, Qd);
   {
-    // compressed record (valid for single-material cells)
-    double Qq[9], q[4], Ud[9], Vd[9];
+    // compressed record (valid for single-material cells; bm is the stretch
+    // step's symmetric base S - I)
+    double Ud[9], q[4];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      Qq[i] = (double)Qd[i];
-      Ud[i] = (double)Ut[i];
-      Vd[i] = (double)Vt[i];
-    }
-    const double det = Qq[0] * (Qq[4] * Qq[8] - Qq[5] * Qq[7]) - Qq[1] * (Qq[3] * Qq[8] - Qq[5] * Qq[6]) +
-                       Qq[2] * (Qq[3] * Qq[7] - Qq[4] * Qq[6]);
-    if (det < 0) {
-      Qq[2] = -Qq[2];
-      Qq[5] = -Qq[5];
-      Qq[8] = -Qq[8];
-    }
+    for (int i = 0; i < 9; ++i) Ud[i] = (double)Ut[i];
     rot_to_quat<double>(Ud, q);
 #pragma unroll
     for (int i = 0; i < 4; ++i) out.C[i] = (T)q[i];
-    rot_to_quat<double>(Vd, q);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) out.C[4 + i] = (T)q[i];
-    rot_to_quat<double>(Qq, q);
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) out.C[8 + i] = (T)q[i];
+      for (int b = 0; b < 3; ++b) {
+        double w = (double)Vt[3 * a + b];
 #pragma unroll
-    // the symmetric base S - I (xx, yy, zz, xy, xz, yz): this record is built only for
-    // the stretch step's symmetric base
-    const double s6[6] = {bm[0], bm[4], bm[8], bm[1], bm[2], bm[5]};
-    for (int i = 0; i < 6; ++i) out.C[12 + i] = (T)s6[i];
+        for (int k = 0; k < 3; ++k) w += bm[3 * a + k] * (double)Vt[3 * k + b];
+        out.C[4 + 3 * a + b] = (T)w;
+      }
+    double lp[3];
 #pragma unroll
-    for (int m = 0; m < 3; ++m) out.C[18 + m] = ev[m] > T(0) ? kv * ev[m] : T(0);
+    for (int m = 0; m < 3; ++m) lp[m] = ev[m] > T(0) ? (double)kv * (double)ev[m] : 0.0;
+    const int AI[6] = {0, 1, 2, 0, 0, 1}, AJ[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) acc += (double)Qd[3 * AI[e] + m] * lp[m] * (double)Qd[3 * AJ[e] + m];
+      out.C[13 + e] = (T)acc;
+    }
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
-      out.C[21 + p] = pp[p] > T(0) ? kv * pp[p] : T(0);
-      out.C[24 + p] = pm[p] > T(0) ? kv * pm[p] : T(0);
+      out.C[19 + p] = pp[p] > T(0) ? T(0.5) * kv * pp[p] : T(0);
+      out.C[22 + p] = pm[p] > T(0) ? T(0.5) * kv * pm[p] : T(0);
     }
   }
 #pragma unroll
@@ -906,7 +901,7 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
 #pragma unroll
     for (int q = 0; q < 45; ++q) co.K[q] = T(0);
 #pragma unroll
-    for (int q = 0; q < 27; ++q) co.C[q] = T(0);
+    for (int q = 0; q < NQC; ++q) co.C[q] = T(0);
     co.psi = 0;
     co.ok = true;
     for (int k = 0; k < si.nm; ++k) {
@@ -922,9 +917,9 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
     }
     esum += co.psi;
     if (want_k == 2) {  // compressed tangent (single material, FP32)
-      T* Kd = K + (int64_t)id * 27 * BV + l;
+      T* Kd = K + (int64_t)id * NQC * BV + l;
 #pragma unroll
-      for (int q = 0; q < 27; ++q) Kd[q * BV] = co.C[q];
+      for (int q = 0; q < NQC; ++q) Kd[q * BV] = co.C[q];
     } else if (want_k) {
       T* Kd = K + (int64_t)id * 45 * BV + l;
 #pragma unroll
@@ -1094,13 +1089,12 @@ __device__ __forceinline__ float ld_stream(const float* p) {
   return v;
 }
 
-// Standalone FP32 HVP of one cell brick per CTA on the 27-number compressed
-// (C27) tangent (the 45-number form runs in k_hvp_col), read straight from global memory
-// (read-only during the kernel, coalesced per tangent entry; measured faster
+// Standalone FP32 HVP of one cell brick per CTA on the compressed tangent (the
+// 45-number form runs in k_hvp_col), read straight from global memory (read-only during the kernel, coalesced per tangent entry; measured faster
 // than a TMA copy into shared memory: 27 KB of shared memory per CTA lets
 // three CTAs share an SM with more loads in flight).
 constexpr size_t HVP_G_SMEM = sizeof(float) * 3 * 729 + 4 + sizeof(float) * 9 * BV;
-template <bool C27>
+template <bool CMP>
 __global__ void __launch_bounds__(256, 3) k_hvp_glob(const int* __restrict__ cblist, const int* __restrict__ nbr,
                                                      const uint8_t* __restrict__ cflag, const float* __restrict__ K,
                                                      const float* __restrict__ p, const float* __restrict__ m,
@@ -1121,7 +1115,7 @@ __global__ void __launch_bounds__(256, 3) k_hvp_glob(const int* __restrict__ cbl
   stage_nodes_sn<float, float>(id, s_nbr, p, sv);
   __syncthreads();
   float pkp = 0.f;
-  const float* Kb = K + (int64_t)id * (C27 ? 27 : 45) * BV;
+  const float* Kb = K + (int64_t)id * (CMP ? NQC : 45) * BV;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int l = threadIdx.x + h * 256;
@@ -1131,11 +1125,11 @@ __global__ void __launch_bounds__(256, 3) k_hvp_glob(const int* __restrict__ cbl
     if (cflag[(int64_t)id * BV + l]) {
       float D[9];
       gather_D<float>(l, sv, D);
-      if (C27) {
-        float c[27];
+      if (CMP) {
+        float c[NQC];
 #pragma unroll
-        for (int qq = 0; qq < 27; ++qq) c[qq] = ld_stream(Kb + qq * BV + l);
-        apply_c27(c, D, KD);
+        for (int qq = 0; qq < NQC; ++qq) c[qq] = ld_stream(Kb + qq * BV + l);
+        apply_cmp(c, D, KD);
       } else
 #pragma unroll
       for (int r = 0; r < 9; ++r) {
@@ -1253,13 +1247,13 @@ __device__ __forceinline__ void col_emit(int id, const int* s_nbr, const float (
 // K45 by default: 64 registers, 16 CTAs (32 warps) per SM, which measured
 // faster than the 256-thread brick kernel at 3 CTAs per SM on the 45-number
 // tangent (latency-bound: more loads in flight per SM).
-template <bool C27, int MINB>
+template <bool CMP, int MINB>
 __global__ void __launch_bounds__(64, MINB) k_hvp_col(const int* __restrict__ cblist, const int* __restrict__ nbr,
                                                     const uint8_t* __restrict__ cflag, const float* __restrict__ K,
                                                     const float* __restrict__ p, const float* __restrict__ m,
                                                     float* q, DevScalars* sc, int finalize, DevProf* pf,
                                                     double* part) {
-  constexpr int NQ = C27 ? 27 : 45;
+  constexpr int NQ = CMP ? NQC : 45;
   __shared__ float sv[3][729];
   __shared__ int s_nbr[NBR];
   __shared__ float sxr[2][2][3][8];  // [z parity][E, E8 of row 3][a][x]
@@ -1329,11 +1323,11 @@ __global__ void __launch_bounds__(64, MINB) k_hvp_col(const int* __restrict__ cb
           D[3 * a + 2] = (P1[0][0][a] - P0[0][0][a]) + (P1[1][0][a] - P0[1][0][a]) + (P1[0][1][a] - P0[0][1][a]) +
                          (P1[1][1][a] - P0[1][1][a]);
         }
-        if (C27) {
-          float c[27];
+        if (CMP) {
+          float c[NQC];
 #pragma unroll
-          for (int qq = 0; qq < 27; ++qq) c[qq] = ld_stream(Kb + qq * BV + l);
-          apply_c27(c, D, KD);
+          for (int qq = 0; qq < NQC; ++qq) c[qq] = ld_stream(Kb + qq * BV + l);
+          apply_cmp(c, D, KD);
         } else {
           float k[45];
 #pragma unroll
@@ -1444,10 +1438,10 @@ __global__ void __launch_bounds__(64, MINB) k_hvp_col(const int* __restrict__ cb
 }
 
 // [persistent-solver source: begin]
-// Shared memory of the persistent solver's HVP phase: the brick's 27-number
-// tangents (27 x 512 floats, one TMA bulk copy), the 9^3 p halo and the
+// Shared memory of the persistent solver's HVP phase: the brick's compressed
+// tangents (NQC x 512 floats, one TMA bulk copy), the 9^3 p halo and the
 // mbarrier.
-constexpr unsigned HVP_C_BYTES = 27u * BV * 4u;
+constexpr unsigned HVP_C_BYTES = (unsigned)NQC * BV * 4u;
 constexpr size_t HVP_C_SMEM = HVP_C_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
 // the column-walk phase H adds the z-exchange of the four 64-thread groups
 // (12 floats per thread) and their row 3 -> 4 partials (3 layers x 2 x 3 x 8)
@@ -1460,10 +1454,10 @@ constexpr size_t HVP_K_SMEM45 = HVP_K_BYTES45 + sizeof(float) * 3 * 729 + 16 + 1
 
 // [persistent-solver source: end]
 __device__ __forceinline__ void apply_compressed(const float* __restrict__ Cs, int l, const float D[9], float KD[9]) {
-  float c[27];
+  float c[NQC];
 #pragma unroll
-  for (int q = 0; q < 27; ++q) c[q] = Cs[q * BV + l];
-  apply_c27(c, D, KD);
+  for (int q = 0; q < NQC; ++q) c[q] = Cs[q * BV + l];
+  apply_cmp(c, D, KD);
 }
 
 
@@ -2000,14 +1994,14 @@ constexpr size_t hvp_smem_bytes() {
 // The launch shapes ("tiles") of the standalone FP32 HVP, per tangent format.
 // Entry 0 is the default before (or without) autotuning.
 const char* hvp_tile_name(int compressed, int tile) {
-  static const char* c27[HVP_TILES] = {"z-column: 64 threads, 8 cells each, 12 CTAs/SM (k_hvp_col)",
+  static const char* cmp[HVP_TILES] = {"z-column: 64 threads, 8 cells each, 12 CTAs/SM (k_hvp_col)",
                                        "brick: 256 threads, 2 cells each, 3 CTAs/SM (k_hvp_glob)",
                                        "z-column: 64 threads, 8 cells each, 8 CTAs/SM (k_hvp_col)"};
   static const char* k45[HVP_TILES] = {"z-column: 64 threads, 8 cells each, 16 CTAs/SM (k_hvp_col)",
                                        "z-column: 64 threads, 8 cells each, 12 CTAs/SM (k_hvp_col)",
                                        "brick: 256 threads, 2 cells each, 3 CTAs/SM (k_hvp_glob)"};
   if (tile < 0 || tile >= HVP_TILES) return "";
-  return compressed ? c27[tile] : k45[tile];
+  return compressed ? cmp[tile] : k45[tile];
 }
 
 static void launch_hvp_f32(mpml_ctx_s* c, int tile, const float* p, float* q, int finalize) {
@@ -2134,7 +2128,7 @@ static int ensure_cg_graph(mpml_ctx_s* c, int cg_max) {
 
 // [persistent-solver source: begin]
 // ---------------------------------------------------------------------------
-// Persistent Jacobi-PCG (FP32; 27-number compressed or 45-number packed
+// Persistent Jacobi-PCG (FP32; NQC-number compressed or 45-number packed
 // tangent): the whole CG solve in one cooperative launch.  Each iteration has
 // two phases separated by grid barriers:
 //   H: for every cell brick of this CTA, stage p_new = D^-1 r + beta p_old on
@@ -2384,10 +2378,10 @@ __device__ __forceinline__ float phase_h_col(int id, const int* s_nbr, const flo
           }
         }
       } else {
-        float c[27];
+        float c[NQC];
 #pragma unroll
-        for (int qq = 0; qq < 27; ++qq) c[qq] = GLOBAL ? ld_stream(Cs + qq * BV + l) : Cs[qq * BV + l];
-        apply_c27(c, D, KD);
+        for (int qq = 0; qq < NQC; ++qq) c[qq] = GLOBAL ? ld_stream(Cs + qq * BV + l) : Cs[qq * BV + l];
+        apply_cmp(c, D, KD);
       }
 #pragma unroll
       for (int r = 0; r < 9; ++r) pkp += D[r] * KD[r];
@@ -2487,7 +2481,7 @@ __device__ __forceinline__ float phase_h_col(int id, const int* s_nbr, const flo
 template <bool K45, bool GLOBAL = false>
 __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
   constexpr unsigned KB = GLOBAL ? 0u : (K45 ? HVP_K_BYTES45 : HVP_C_BYTES);
-  constexpr int NQ = K45 ? 45 : 27;
+  constexpr int NQ = K45 ? 45 : NQC;
   extern __shared__ __align__(128) unsigned char psm[];
   float* Cs = reinterpret_cast<float*>(psm);
   float (*sv)[729] = reinterpret_cast<float (*)[729]>(psm + KB);
@@ -2713,10 +2707,10 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
 }
 
 static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
-  // one occupancy query per tangent format (27-number compressed, 45-number packed)
+  // one occupancy query per tangent format (compressed, 45-number packed)
   static int max_blocks[4] = {-1, -1, -1, -1};
   const int k45 = c->compressed ? 0 : 1;
-  // 27-number tangent beyond a few bricks per CTA (working set well past L2): stream the
+  // compressed tangent beyond a few bricks per CTA (working set well past L2): stream the
   // tangent rows from global memory instead of one TMA copy per brick into shared memory
   // (measured 9% faster per CG iteration on the 3-8M pressed block, equal at 168^3;
   // the 45-number tangent keeps the TMA copy, which measured 2% faster on config 5)

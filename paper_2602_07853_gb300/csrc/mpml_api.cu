@@ -254,7 +254,7 @@ int mpml_create(const mpml_scene_desc* desc, const mpml_material* mats, int n_ma
   c->s = (cudaStream_t)stream;
   c->fp64 = desc->precision == MPML_FP64;
   c->esz = c->fp64 ? 8 : 4;
-  // the 27-number tangent assumes the symmetric base of the stretch step: elastic single-material FP32
+  // the compressed tangent assumes the symmetric base of the stretch step: elastic single-material FP32
   c->compressed = (!c->fp64 && n_mats == 1 && mats[0].plastic == MPML_ELASTIC) ? 1 : 0;
   for (int a = 0; a < 3; ++a) c->NB[a] = (desc->n[a] >> 3) + 1;
   c->NBT = (int64_t)c->NB[0] * c->NB[1] * c->NB[2];
@@ -620,7 +620,7 @@ int mpml_hvp_timing(mpml_ctx c, int64_t* launches, double* total_ms, double* byt
   if (bytes_per_launch) {
     // per cell brick: K (45/cell) read, p (3/node) read, m read, q (3/node) written
     const double e = (double)c->esz;
-    const double kf = c->compressed ? 27.0 : 45.0;  // tangent numbers per cell
+    const double kf = c->compressed ? (double)NQC : 45.0;  // tangent numbers per cell
     *bytes_per_launch = (double)c->ncb * BV * (kf * e + 3 * e + e + 3 * e);
   }
   return MPML_OK;

@@ -119,7 +119,7 @@ struct mpml_ctx_s {
   int nm = 1;
   cudaStream_t s = nullptr;
   int fp64 = 0;
-  int compressed = 0;  // FP32, single material: HVP on the 27-number tangent
+  int compressed = 0;  // FP32, single material: HVP on the compressed (NQC-number) tangent
   // launch shape ("tile") of the standalone FP32 HVP, an index into the table of
   // hvp_tile_name(); -1: chosen by the autotuner (or its cache) at the first solve
   int hvp_tile = -1;
@@ -319,21 +319,24 @@ __device__ __forceinline__ void quat_to_rot(T w, T x, T y, T z, T R[9]) {
   R[8] = T(1) - T(2) * (x * x + y * y);
 }
 
-// FP32 HVP of one cell on the compressed tangent (27 floats):
-// K D' = U Mt W^T with M = U^T D' W, W = S V, and Mt the clamped eigen-modes of
-// the isotropic tangent applied to M (3x3 block in the eigenbasis Qd on the
-// diagonal of M, flip / twist modes on its off-diagonal pairs).
-__device__ __forceinline__ void apply_c27(const float c[27], const float D[9], float KD[9]) {
-  float U[9], V[9], Qd[9];
+// Numbers per cell of the compressed tangent (single material, FP32):
+//   [0, 4)   unit quaternion of U
+//   [4, 13)  W = S V (row-major; S the symmetric stretch base, V the right
+//            singular vectors of the trial deformation)
+//   [13, 19) A = Q diag(lambda+) Q^T (xx, yy, zz, xy, xz, yz): the clamped 3x3
+//            block of the isotropic tangent acting on the diagonal of M
+//   [19, 22) flip moduli / 2 of the pairs (0,1), (0,2), (1,2)
+//   [22, 25) twist moduli / 2 of the same pairs
+constexpr int NQC = 25;
+
+// FP32 HVP of one cell on the compressed tangent:
+// K D' = U Mt W^T with M = U^T D' W, and Mt the clamped eigen-modes of the
+// isotropic tangent applied to M (the block A on the diagonal of M, flip /
+// twist modes on its off-diagonal pairs).
+__device__ __forceinline__ void apply_cmp(const float c[NQC], const float D[9], float KD[9]) {
+  float U[9];
   quat_to_rot<float>(c[0], c[1], c[2], c[3], U);
-  quat_to_rot<float>(c[4], c[5], c[6], c[7], V);
-  quat_to_rot<float>(c[8], c[9], c[10], c[11], Qd);
-  const float sm[9] = {c[12], c[15], c[16], c[15], c[13], c[17], c[16], c[17], c[14]};
-  float W[9];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) W[3 * a + b] = V[3 * a + b] + sm[3 * a] * V[b] + sm[3 * a + 1] * V[3 + b] + sm[3 * a + 2] * V[6 + b];
+  const float* W = c + 4;
   // M = U^T D W
   float T1[9], M[9];
 #pragma unroll
@@ -346,18 +349,16 @@ __device__ __forceinline__ void apply_c27(const float c[27], const float D[9], f
     for (int j = 0; j < 3; ++j) M[3 * i + j] = T1[3 * i] * W[j] + T1[3 * i + 1] * W[3 + j] + T1[3 * i + 2] * W[6 + j];
   float Mt[9];
   // diagonal block
-  float y[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) y[k] = c[18 + k] * (Qd[k] * M[0] + Qd[3 + k] * M[4] + Qd[6 + k] * M[8]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) Mt[4 * i] = Qd[3 * i] * y[0] + Qd[3 * i + 1] * y[1] + Qd[3 * i + 2] * y[2];
+  Mt[0] = c[13] * M[0] + c[16] * M[4] + c[17] * M[8];
+  Mt[4] = c[16] * M[0] + c[14] * M[4] + c[18] * M[8];
+  Mt[8] = c[17] * M[0] + c[18] * M[4] + c[15] * M[8];
   // pairs (0,1), (0,2), (1,2): flip (M_ij + M_ji)/sqrt2, twist (M_ij - M_ji)/sqrt2
   const int PI[3] = {0, 0, 1}, PJ[3] = {1, 2, 2};
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const int i = PI[p], j = PJ[p];
-    const float f = 0.5f * c[21 + p] * (M[3 * i + j] + M[3 * j + i]);
-    const float t = 0.5f * c[24 + p] * (M[3 * i + j] - M[3 * j + i]);
+    const float f = c[19 + p] * (M[3 * i + j] + M[3 * j + i]);
+    const float t = c[22 + p] * (M[3 * i + j] - M[3 * j + i]);
     Mt[3 * i + j] = f + t;
     Mt[3 * j + i] = f - t;
   }

@@ -1,5 +1,5 @@
 // Process-wide cache of autotuned launch shapes of the standalone FP32 HVP
-// (host code only).  Key: tangent format (27-number compressed or 45-number
+// (host code only).  Key: tangent format (25-number compressed or 45-number
 // packed) and floor(log2(active cell bricks)); value: the fastest shape and its
 // mean milliseconds.  Text form, one entry per line: "format log2_bricks tile ms".
 #include <cstdio>
@@ -30,7 +30,7 @@ int size_class(int64_t ncb) {
   return k;
 }
 
-int format_of(int compressed) { return compressed ? 27 : 45; }
+int format_of(int compressed) { return compressed ? NQC : 45; }
 
 }  // namespace
 
@@ -76,7 +76,7 @@ int tile_cache_load(const char* path) {
       if (*q != ' ' && *q != '\t' && *q != '\n' && *q != '\r') blank = false;
     if (blank) continue;
     if (std::sscanf(line, "%d %d %d %lf %n", &fmt, &cls, &tile, &ms, &used) != 4 || line[used] != '\0' ||
-        (fmt != 27 && fmt != 45) || cls < 0 || cls > 62 || tile < 0 || tile >= HVP_TILES || !(ms >= 0.0)) {
+        (fmt != NQC && fmt != 45) || cls < 0 || cls > 62 || tile < 0 || tile >= HVP_TILES || !(ms >= 0.0)) {
       bad = true;
       break;
     }

@@ -38,7 +38,7 @@ def scene(kind, seed=21, count=6000, n=24):
     return sc
 
 
-@pytest.mark.parametrize("kind", ["c27", "k45"])
+@pytest.mark.parametrize("kind", ["cmp", "k45"])
 def test_every_tile_matches_the_oracle_and_the_tuner_picks_the_fastest(kind, tmp_path):
     sc = scene(kind)
     g = GpuSim(sc, m.FP32)
@@ -71,7 +71,7 @@ def test_every_tile_matches_the_oracle_and_the_tuner_picks_the_fastest(kind, tmp
     path = tmp_path / "tiles.txt"
     m.mpml_tile_cache_save(path)
     rows = [l.split() for l in open(path)]
-    assert len(rows) == 1 and int(rows[0][0]) == (27 if kind == "c27" else 45) and int(rows[0][2]) == tile
+    assert len(rows) == 1 and int(rows[0][0]) == (25 if kind == "cmp" else 45) and int(rows[0][2]) == tile
     g.close()
 
 

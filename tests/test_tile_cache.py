@@ -27,23 +27,23 @@ def entries(path):
 
 def test_cache_round_trip(tmp_path):
     src = tmp_path / "tiles.txt"
-    src.write_text("27 10 1 0.5\n\n45 12 0 1.25\n27 3 2 0.0125\n")
+    src.write_text("25 10 1 0.5\n\n45 12 0 1.25\n25 3 2 0.0125\n")
     m.mpml_tile_cache_load(src)
     out = tmp_path / "out.txt"
     m.mpml_tile_cache_save(out)
-    assert entries(out) == [(27, 3, 2, 0.0125), (27, 10, 1, 0.5), (45, 12, 0, 1.25)]
+    assert entries(out) == [(25, 3, 2, 0.0125), (25, 10, 1, 0.5), (45, 12, 0, 1.25)]
     # loading merges: a later file overrides the same key and keeps the others
     upd = tmp_path / "upd.txt"
-    upd.write_text("27 10 0 0.4\n")
+    upd.write_text("25 10 0 0.4\n")
     m.mpml_tile_cache_load(upd)
     m.mpml_tile_cache_save(out)
-    assert entries(out) == [(27, 3, 2, 0.0125), (27, 10, 0, 0.4), (45, 12, 0, 1.25)]
+    assert entries(out) == [(25, 3, 2, 0.0125), (25, 10, 0, 0.4), (45, 12, 0, 1.25)]
 
 
-@pytest.mark.parametrize("bad", ["27 10 3 0.5\n",       # tile out of range
+@pytest.mark.parametrize("bad", ["25 10 3 0.5\n",       # tile out of range
                                  "33 10 1 0.5\n",       # unknown tangent format
-                                 "27 10 1\n",           # missing field
-                                 "27 -1 1 0.5\n",       # negative size class
+                                 "25 10 1\n",           # missing field
+                                 "25 -1 1 0.5\n",       # negative size class
                                  "45 4 1 -2\n",         # negative time
                                  "45 4 1 0.5 junk\n"])  # trailing text
 def test_malformed_cache_is_rejected_whole(tmp_path, bad):
@@ -51,7 +51,7 @@ def test_malformed_cache_is_rejected_whole(tmp_path, bad):
     good.write_text("45 7 1 0.25\n")
     m.mpml_tile_cache_load(good)
     f = tmp_path / "bad.txt"
-    f.write_text("27 5 0 0.125\n" + bad)
+    f.write_text("25 5 0 0.125\n" + bad)
     with pytest.raises(m.MPMLError) as e:
         m.mpml_tile_cache_load(f)
     assert e.value.code == m.ERR_ARG
