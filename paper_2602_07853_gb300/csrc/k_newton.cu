@@ -2157,32 +2157,38 @@ struct PcgArgs {
   float* q;
   DevScalars* sc;
   double* acc;    // [4][2] rotating accumulators of the phase sums
-  unsigned* gbar; // {arrivals, generation}
+  unsigned* gbar; // grid-barrier counter (zero at launch)
   int ncb, nnob, nb, cg_max;
   int* status;
   DevProf* pf;
 };
 
-// bounded grid barrier (all CTAs co-resident: cooperative launch)
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// bounded grid barrier (all CTAs co-resident: cooperative launch) on one
+// counter that starts at zero: CTA 0 adds 2^31 - (G - 1), every other CTA adds
+// 1, so the top bit flips exactly when the last CTA of a round arrives (no
+// proper subset of the adds crosses 2^31) and the low bits return to zero.
+// The last arrival learns it from its own add; the others poll the top bit.
 __device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = gbar + 1;
-    const unsigned g = *vgen;
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
     __threadfence();
+    const unsigned old = atomicAdd(gbar, add);
     int ok = 1;
-    if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
-      gbar[0] = 0;
-      __threadfence();
-      atomicAdd(gbar + 1, 1u);
-    } else {
+    if ((((old + add) ^ old) & 0x80000000u) == 0u) {
       unsigned spins = 0;
-      while (*vgen == g) {
+      while (((ld_acquire_gpu(gbar) ^ old) & 0x80000000u) == 0u) {
         if (++spins > (1u << 25)) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -2639,36 +2645,51 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
     const float alpha = s_coef;
     // ---------------- phase A ----------------
     float rzl = 0.f, rrl = 0.f;
-    for (int jb = blockIdx.x; jb < A.nb; jb += G) {
-      float2 d2[3], p2[3], q2[3], x2[3], r2[3];
+    // two node bricks per pass, all loads issued before the updates
+    for (int jb0 = blockIdx.x; jb0 < A.nb; jb0 += 2 * G) {
+      float2 d2[2][3], p2[2][3], q2[2][3], x2[2][3], r2[2][3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
-        d2[a] = __ldcg(reinterpret_cast<const float2*>(A.dinv + o));
-        p2[a] = __ldcg(reinterpret_cast<const float2*>(pnext + o));
-        q2[a] = __ldcg(reinterpret_cast<const float2*>(A.q + o));
-        x2[a] = __ldcg(reinterpret_cast<const float2*>(A.x + o));
-        r2[a] = __ldcg(reinterpret_cast<const float2*>(A.r + o));
+      for (int u = 0; u < 2; ++u) {
+        const int jb = jb0 + u * G;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (jb < A.nb) {
+            const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
+            d2[u][a] = __ldcg(reinterpret_cast<const float2*>(A.dinv + o));
+            p2[u][a] = __ldcg(reinterpret_cast<const float2*>(pnext + o));
+            q2[u][a] = __ldcg(reinterpret_cast<const float2*>(A.q + o));
+            x2[u][a] = __ldcg(reinterpret_cast<const float2*>(A.x + o));
+            r2[u][a] = __ldcg(reinterpret_cast<const float2*>(A.r + o));
+          } else {
+            d2[u][a] = p2[u][a] = q2[u][a] = x2[u][a] = r2[u][a] = make_float2(0.f, 0.f);
+          }
+        }
       }
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
-        if (d2[a].x > 0.f) {
-          x2[a].x += alpha * p2[a].x;
-          r2[a].x -= alpha * q2[a].x;
+      for (int u = 0; u < 2; ++u) {
+        const int jb = jb0 + u * G;
+        if (jb >= A.nb) continue;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
+          const float2 d = d2[u][a], pp = p2[u][a], qq = q2[u][a];
+          float2 xx = x2[u][a], rr = r2[u][a];
+          if (d.x > 0.f) {
+            xx.x += alpha * pp.x;
+            rr.x -= alpha * qq.x;
+          }
+          if (d.y > 0.f) {
+            xx.y += alpha * pp.y;
+            rr.y -= alpha * qq.y;
+          }
+          *reinterpret_cast<float2*>(A.x + o) = xx;
+          *reinterpret_cast<float2*>(A.r + o) = rr;
+          *reinterpret_cast<float2*>(A.q + o) = make_float2(0.f, 0.f);
+          const float srz = (d.x > 0.f ? rr.x * d.x * rr.x : 0.f) + (d.y > 0.f ? rr.y * d.y * rr.y : 0.f);
+          const float srr = (d.x > 0.f ? rr.x * rr.x : 0.f) + (d.y > 0.f ? rr.y * rr.y : 0.f);
+          rzl += srz;
+          rrl += srr;
         }
-        if (d2[a].y > 0.f) {
-          x2[a].y += alpha * p2[a].y;
-          r2[a].y -= alpha * q2[a].y;
-        }
-        *reinterpret_cast<float2*>(A.x + o) = x2[a];
-        *reinterpret_cast<float2*>(A.r + o) = r2[a];
-        *reinterpret_cast<float2*>(A.q + o) = make_float2(0.f, 0.f);
-        const float srz = (d2[a].x > 0.f ? r2[a].x * d2[a].x * r2[a].x : 0.f) +
-                          (d2[a].y > 0.f ? r2[a].y * d2[a].y * r2[a].y : 0.f);
-        const float srr = (d2[a].x > 0.f ? r2[a].x * r2[a].x : 0.f) + (d2[a].y > 0.f ? r2[a].y * r2[a].y : 0.f);
-        rzl += srz;
-        rrl += srr;
       }
     }
     double* accA = A.acc + 2 * ((2 * it + 1) & 3);
