@@ -92,34 +92,6 @@ __device__ __forceinline__ void bblock_atomic2(float a_, float b_, double* acc) 
   __syncthreads();
 }
 
-__device__ __forceinline__ bool bgrid_barrier(unsigned* gbar, int* s_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = gbar + 1;
-    const unsigned g = *vgen;
-    __threadfence();
-    int ok = 1;
-    if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
-      gbar[0] = 0;
-      __threadfence();
-      atomicAdd(gbar + 1, 1u);
-    } else {
-      unsigned spins = 0;
-      while (*vgen == g) {
-        if (++spins > (1u << 25)) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    *s_flag = ok;
-  }
-  __syncthreads();
-  return *s_flag != 0;
-}
-
 __device__ __forceinline__ unsigned bsmem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -345,7 +317,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
       }
       bblock_atomic2(pmp, 0.f, accH + 2 * s);
     }
-    if (!bgrid_barrier(A.gbar, &s_flag)) {
+    if (!grid_barrier(A.gbar, &s_flag)) {
       alive = false;
       break;
     }
@@ -393,7 +365,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
       }
       bblock_atomic2(rzl, rrl, accA + 2 * s);
     }
-    if (!bgrid_barrier(A.gbar, &s_flag)) {
+    if (!grid_barrier(A.gbar, &s_flag)) {
       alive = false;
       break;
     }

@@ -2163,41 +2163,6 @@ struct PcgArgs {
   DevProf* pf;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// bounded grid barrier (all CTAs co-resident: cooperative launch) on one
-// counter that starts at zero: CTA 0 adds 2^31 - (G - 1), every other CTA adds
-// 1, so the top bit flips exactly when the last CTA of a round arrives (no
-// proper subset of the adds crosses 2^31) and the low bits return to zero.
-// The last arrival learns it from its own add; the others poll the top bit.
-__device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
-    __threadfence();
-    const unsigned old = atomicAdd(gbar, add);
-    int ok = 1;
-    if ((((old + add) ^ old) & 0x80000000u) == 0u) {
-      unsigned spins = 0;
-      while (((ld_acquire_gpu(gbar) ^ old) & 0x80000000u) == 0u) {
-        if (++spins > (1u << 25)) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    *s_flag = ok;
-  }
-  __syncthreads();
-  return *s_flag != 0;
-}
-
 // Warp sum of FP32 values in float-float arithmetic (error-free two-sum at
 // every level, the rounding errors carried in a second float), returned as
 // a double on lane 0: FP64-grade accuracy without a chain of FP64 additions.
@@ -2492,17 +2457,39 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
   float* Cs = reinterpret_cast<float*>(psm);
   float (*sv)[729] = reinterpret_cast<float (*)[729]>(psm + KB);
   uint64_t* bar = reinterpret_cast<uint64_t*>(psm + KB + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  // the CTA's cell bricks (jc = blockIdx.x + k G) and their neighbour rows are
+  // the same in every iteration: kept in shared memory when there are at most
+  // PCG_LOCAL of them, else read per brick
+  constexpr int PCG_LOCAL = 8;
   __shared__ int s_nbr[NBR];
+  __shared__ int s_ids[PCG_LOCAL];
+  __shared__ int s_nbrs[PCG_LOCAL][NBR];
   __shared__ int s_flag;
   __shared__ float s_coef;  // alpha or beta, formed in FP64 by thread 0
   __shared__ int s_stop;    // breakdown / convergence decided by thread 0
   DevScalars* sc = A.sc;
+  const int nloc = (int)blockIdx.x < A.ncb ? (A.ncb - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const bool cached = nloc <= PCG_LOCAL;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
+  if (cached) {
+    for (int k = 0; k < nloc; ++k) {
+      const int id = A.cblist[(int)blockIdx.x + k * (int)gridDim.x];
+      if (threadIdx.x == 0) s_ids[k] = id;
+      if (threadIdx.x < NBR) s_nbrs[k][threadIdx.x] = A.nbr[id * NBR + threadIdx.x];
+    }
+  }
   __syncthreads();
   unsigned tma_phase = 0;
+  // compressed tangent staged by TMA: which local brick's tangent is in Cs (or on
+  // its way), and whether a copy is in flight; the tangent does not change during
+  // the solve, so a CTA with one brick copies it once, and a CTA with more starts
+  // the copy of its first brick at the end of phase H for the next iteration
+  constexpr bool KEEP = !K45 && !GLOBAL;
+  int cs_k = -1;
+  bool inflight = false;
   // FP64 scalar state of the recurrences: thread 0 only, in shared memory
   __shared__ double s_rz, s_rr_last, s_tol2;
   if (threadIdx.x == 0) {
@@ -2521,15 +2508,27 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
     const unsigned long long t_h0 = (A.pf && blockIdx.x == 0 && threadIdx.x == 0) ? gtimer() : 0ull;
     // ---------------- phase H ----------------
     float pmp = 0.f, pkp = 0.f;  // per-thread FP32 partials, summed in FP64 below
-    for (int jc = blockIdx.x; jc < A.ncb; jc += G) {
-      const int id = A.cblist[jc];
-      if (threadIdx.x < NBR) s_nbr[threadIdx.x] = A.nbr[id * NBR + threadIdx.x];
-      __syncthreads();
-      if (!GLOBAL && threadIdx.x == 0) {
-        // order the previous brick's generic accesses to Cs before the async copy
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(bar, KB);
-        tma_load_1d(Cs, A.C + (int64_t)id * NQ * BV, KB, bar);
+    for (int kl = 0, jc = blockIdx.x; jc < A.ncb; ++kl, jc += G) {
+      int id;
+      const int* nb_row;
+      if (cached) {
+        id = s_ids[kl];
+        nb_row = s_nbrs[kl];
+      } else {
+        id = A.cblist[jc];
+        if (threadIdx.x < NBR) s_nbr[threadIdx.x] = A.nbr[id * NBR + threadIdx.x];
+        __syncthreads();
+        nb_row = s_nbr;
+      }
+      if (!GLOBAL && !(KEEP && cached && cs_k == kl)) {
+        if (threadIdx.x == 0) {
+          // order the previous brick's generic accesses to Cs before the async copy
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive_expect_tx(bar, KB);
+          tma_load_1d(Cs, A.C + (int64_t)id * NQ * BV, KB, bar);
+        }
+        inflight = true;
+        cs_k = kl;
       }
       {
         // every thread owns at most 3 of the 729 halo slots: issue all loads first
@@ -2545,7 +2544,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
           for (int a = 0; a < 3; ++a) dv[k][a] = rv[k][a] = pv[k][a] = 0.f;
           if (i < 729) {
             const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
-            const int t = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+            const int t = (nx < 8 && ny < 8 && nz < 8) ? id : nb_row[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
             const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
             tt[k] = t;
             ll[k] = l;
@@ -2582,10 +2581,14 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       }
       __syncthreads();
       bool ok = true;
-      if (!GLOBAL) {
+      if (!GLOBAL && inflight) {
         ok = mbar_wait_bounded(bar, tma_phase);
         tma_phase ^= 1u;
-        if (!ok && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+        inflight = false;
+        if (!ok) {
+          cs_k = -1;
+          if (threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+        }
       }
       {
         // GLOBAL: the tangent is streamed from global memory; the exchange buffers
@@ -2593,9 +2596,20 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
         float* Xs = GLOBAL ? reinterpret_cast<float*>(psm + sizeof(float) * 3 * 729 + 16 + 16)
                            : (K45 ? Cs : reinterpret_cast<float*>(psm + HVP_C_SMEM));
         const float* Ksrc = GLOBAL ? A.C + (int64_t)id * NQ * BV : Cs;
-        pkp += phase_h_col<K45, GLOBAL>(id, s_nbr, sv, Ksrc, A.cflag, A.m, A.q, Xs, Xs + HVP_X_FLOATS, ok);
+        pkp += phase_h_col<K45, GLOBAL>(id, nb_row, sv, Ksrc, A.cflag, A.m, A.q, Xs, Xs + HVP_X_FLOATS, ok);
         __syncthreads();  // Cs / sv / s_nbr / exchange buffers are reused by the next brick
       }
+    }
+    if (KEEP && cached && nloc > 1) {
+      // the first brick's tangent for the next iteration (Cs is free: the last
+      // brick's walk ended at the barrier above)
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, KB);
+        tma_load_1d(Cs, A.C + (int64_t)s_ids[0] * NQ * BV, KB, bar);
+      }
+      inflight = true;
+      cs_k = 0;
     }
     // bricks with DOF nodes but no cells: p_new and the mass term
     for (int jn = blockIdx.x; jn < A.nnob; jn += G) {
@@ -2719,6 +2733,8 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
     pnext = tmp;
   }
   if (!alive && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+  // a prefetched tangent copy still in flight completes before the CTA exits
+  if (!GLOBAL && inflight && !mbar_wait_bounded(bar, tma_phase) && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     sc->iters = it;
     sc->rr_last = s_rr_last;

@@ -305,6 +305,41 @@ __device__ void jacobi3(const T Ain[9], T ev[3], T Q[9]) {
 }
 
 // [persistent-solver source: begin]
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// bounded grid barrier (all CTAs co-resident: cooperative launch) on one
+// counter that starts at zero: CTA 0 adds 2^31 - (G - 1), every other CTA adds
+// 1, so the top bit flips exactly when the last CTA of a round arrives (no
+// proper subset of the adds crosses 2^31) and the low bits return to zero.
+// The last arrival learns it from its own add; the others poll the top bit.
+__device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
+    __threadfence();
+    const unsigned old = atomicAdd(gbar, add);
+    int ok = 1;
+    if ((((old + add) ^ old) & 0x80000000u) == 0u) {
+      unsigned spins = 0;
+      while (((ld_acquire_gpu(gbar) ^ old) & 0x80000000u) == 0u) {
+        if (++spins > (1u << 25)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
 // rotation matrix (row-major) of a unit quaternion (w, x, y, z)
 template <typename T>
 __device__ __forceinline__ void quat_to_rot(T w, T x, T y, T z, T R[9]) {
