@@ -126,20 +126,22 @@ __global__ void k_init_faces(const T* __restrict__ p, const T* __restrict__ m, T
 // ---------------------------------------------------------------------------
 // stretch reconstruction (FP64)
 // ---------------------------------------------------------------------------
-__device__ bool fc_sigma(double mu, double lam, const double t[3], double J, double s[3]) {
+// fixed-corotated principal stretches for a given J: 2 mu s (s - 1) = t - lam J (J - 1)
+// (i2mu = 1 / (2 mu))
+__device__ bool fc_sigma(double i2mu, double lam, const double t[3], double J, double s[3]) {
   double c = lam * J * (J - 1);
   bool ok = true;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    double disc = 0.25 + (t[i] - c) / (2 * mu);
+    double disc = 0.25 + (t[i] - c) * i2mu;
     if (disc < -1e-12) ok = false;
     s[i] = 0.5 + sqrt(disc > 0 ? disc : 0);
   }
   return ok;
 }
-__device__ double fc_h(double mu, double lam, const double t[3], double J) {
+__device__ double fc_h(double i2mu, double lam, const double t[3], double J) {
   double s[3];
-  fc_sigma(mu, lam, t, J, s);
+  fc_sigma(i2mu, lam, t, J, s);
   return s[0] * s[1] * s[2] - J;
 }
 __device__ double cbrt_signed(double z) { return z >= 0 ? cbrt(z) : -cbrt(-z); }
@@ -200,37 +202,67 @@ __device__ bool invert_principal(int model, double mu, double lam, const double 
     return true;
   }
   if (model == MPML_FIXED_COROTATED) {
-    // library's inverse: unique root of prod_i s_i(J) = J on J >= 1/2 (bisection)
+    // library's inverse: unique root of prod_i s_i(J) = J on J >= 1/2
     if (!(mu > 0) || lam < 0) return false;
-    if (lam == 0) return fc_sigma(mu, lam, t, 1.0, s);
+    const double i2mu = 0.5 / mu;
+    if (lam == 0) return fc_sigma(i2mu, lam, t, 1.0, s);
     double tmin = fmin(t[0], fmin(t[1], t[2]));
     double d = 0.25 + (tmin + 0.5 * mu) / lam;
     if (d < 0) return false;
     double lo = 0.5, hi = 0.5 + sqrt(d);
-    if (fc_h(mu, lam, t, lo) < 0 || fc_h(mu, lam, t, hi) > 0) return false;
-    // safeguarded Newton on h(J) = prod s_i(J) - J (decreasing on the bracket):
-    // a Newton step that leaves the bracket is replaced by bisection
-    double J = exp((t[0] + t[1] + t[2]) / (2 * mu + 3 * lam));
-    if (!(J > lo && J < hi)) J = 0.5 * (lo + hi);
+    if (fc_h(i2mu, lam, t, lo) < 0 || fc_h(i2mu, lam, t, hi) > 0) return false;
+    // starting point: Newton on h(J) = prod s_i(J) - J in FP32 (GB300's FP64 pipe
+    // is slow), kept inside the bracket; the FP64 iteration below then needs a
+    // couple of steps
+    double J;
+    {
+      const float fl = (float)lam, fi = (float)i2mu, flo = (float)lo, fhi = (float)hi;
+      const float ft[3] = {(float)t[0], (float)t[1], (float)t[2]};
+      float Jf = __expf((ft[0] + ft[1] + ft[2]) / (float)(2 * mu + 3 * lam));
+      if (!(Jf > flo && Jf < fhi)) Jf = 0.5f * (flo + fhi);
+      for (int it = 0; it < 8; ++it) {
+        const float cJ = fl * Jf * (Jf - 1.f), dc = fl * (2.f * Jf - 1.f);
+        float sv[3], ir[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float disc = fmaxf(0.25f + (ft[i] - cJ) * fi, 1e-30f);
+          ir[i] = rsqrtf(disc);
+          sv[i] = 0.5f + disc * ir[i];
+        }
+        const float h = sv[0] * sv[1] * sv[2] - Jf;
+        // d s_i / dJ = -dc i2mu / (2 sqrt(disc_i))
+        const float dh = -0.5f * dc * fi * (ir[0] * sv[1] * sv[2] + ir[1] * sv[0] * sv[2] + ir[2] * sv[0] * sv[1]) - 1.f;
+        if (!(dh < 0.f)) break;
+        const float Jn = Jf - h / dh;
+        if (!(Jn > flo && Jn < fhi)) break;
+        const bool small = fabsf(Jn - Jf) <= 2e-6f * Jf;
+        Jf = Jn;
+        if (small) break;
+      }
+      J = (double)Jf;
+      if (!(J > lo && J < hi)) J = 0.5 * (lo + hi);
+    }
+    // safeguarded Newton in FP64 (decreasing h on the bracket): a step that
+    // leaves the bracket is replaced by bisection
     for (int it = 0; it < 100; ++it) {
       const double cJ = lam * J * (J - 1), dc = lam * (2 * J - 1);
-      double sv[3], prod = 1, dprod = 0;
+      double sv[3], ir[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const double disc = 0.25 + (t[i] - cJ) / (2 * mu);
-        sv[i] = 0.5 + sqrt(disc > 0 ? disc : 0);
+        const double disc = 0.25 + (t[i] - cJ) * i2mu;
+        if (disc > 0) {
+          ir[i] = rsqrt(disc);
+          sv[i] = 0.5 + disc * ir[i];
+        } else {
+          ir[i] = 0;
+          sv[i] = 0.5;
+        }
       }
-      prod = sv[0] * sv[1] * sv[2];
+      const double prod = sv[0] * sv[1] * sv[2];
       const double h = prod - J;
       if (h > 0) lo = J; else hi = J;
       if (h == 0) break;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double r = sv[i] - 0.5;  // sqrt(disc)
-        const double ds = r > 0 ? -dc / (4 * mu * r) : 0;
-        dprod += ds * (prod / sv[i]);
-      }
-      const double dh = dprod - 1;
+      const double dh = -0.5 * dc * i2mu * (ir[0] * sv[1] * sv[2] + ir[1] * sv[0] * sv[2] + ir[2] * sv[0] * sv[1]) - 1;
       double Jn = (dh < 0) ? J - h / dh : 0.5 * (lo + hi);
       if (!(Jn > lo && Jn < hi)) Jn = 0.5 * (lo + hi);
       if (fabs(Jn - J) <= 4e-16 * J || hi - lo <= 2e-16 * hi) {
@@ -239,7 +271,7 @@ __device__ bool invert_principal(int model, double mu, double lam, const double 
       }
       J = Jn;
     }
-    return fc_sigma(mu, lam, t, J, s);
+    return fc_sigma(i2mu, lam, t, J, s);
   }
   return false;
 }
@@ -277,7 +309,7 @@ __global__ void __launch_bounds__(256) k_stretch(const int* __restrict__ cblist,
         tau[3 * ra[q] + rb[q]] = tau[3 * rb[q] + ra[q]] = tq;
       }
       double ev[3], Q[9], s[3];
-      jacobi3<double>(tau, ev, Q);
+      jacobi3_mixed(tau, ev, Q);
       if (!invert_principal(si.mat[k].model, si.mat[k].mu, si.mat[k].lam, ev, s)) {
         atomicOr(status, ST_STRETCH);
 #pragma unroll

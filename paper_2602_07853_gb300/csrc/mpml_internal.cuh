@@ -304,6 +304,123 @@ __device__ void jacobi3(const T Ain[9], T ev[3], T Q[9]) {
   ev[2] = A[8];
 }
 
+// Eigen-decomposition of a symmetric 3x3 to FP64 accuracy with most of the
+// work off the (slow) FP64 pipe: cyclic Jacobi in FP32 on the matrix scaled
+// by a power of two, the FP32 eigenvectors made orthonormal in FP64 by two
+// Newton-Schulz steps Q <- Q (3I - Q^T Q) / 2, then Jacobi sweeps in FP64 on
+// Q^T A Q with rotation angles formed in FP32 and cosines refined to FP64 by
+// two Newton steps of 1/sqrt(1 + t^2) (every rotation orthogonal to FP64
+// rounding; an inexact angle only slows the annihilation to a factor ~1e-7
+// per sweep).  Same output convention as jacobi3; FP64 divisions: none.
+__device__ inline void jacobi3_mixed(const double Ain[9], double ev[3], double Q[9]) {
+  double amax = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) amax = fmax(amax, fabs(Ain[i]));
+  if (!(amax > 0.0) || !(amax < 1e300)) {  // zero or non-finite: the plain FP64 sweeps
+    jacobi3<double>(Ain, ev, Q);
+    return;
+  }
+  const int ex = ilogb(amax);
+  const double sc = scalbn(1.0, -ex), isc = scalbn(1.0, ex);
+  double A[9];
+  float Af[9], evf[3], Qf[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    A[i] = Ain[i] * sc;
+    Af[i] = (float)A[i];
+  }
+  jacobi3<float>(Af, evf, Qf);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Q[i] = (double)Qf[i];
+#pragma unroll
+  for (int ns = 0; ns < 2; ++ns) {
+    double X[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) X[3 * a + b] = Q[a] * Q[b] + Q[3 + a] * Q[3 + b] + Q[6 + a] * Q[6 + b];
+    double Y[9];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        double acc = 1.5 * Q[3 * a + b];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc -= 0.5 * Q[3 * a + k] * X[3 * k + b];
+        Y[3 * a + b] = acc;
+      }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Q[i] = Y[i];
+  }
+  // B = Q^T A Q (symmetric: upper part, mirrored)
+  double AQ[9], B[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) AQ[3 * a + b] = A[3 * a] * Q[b] + A[3 * a + 1] * Q[3 + b] + A[3 * a + 2] * Q[6 + b];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      const double v = Q[a] * AQ[b] + Q[3 + a] * AQ[3 + b] + Q[6 + a] * AQ[6 + b];
+      B[3 * a + b] = v;
+      B[3 * b + a] = v;
+    }
+  double fro = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) fro += B[i] * B[i];
+  const double tol = 4.930380657631324e-32 * fro * 1e-2;  // eps^2 fro / 100, as jacobi3
+  for (int sweep = 0; sweep < 8; ++sweep) {
+    const double off = B[1] * B[1] + B[2] * B[2] + B[5] * B[5];
+    if (!(off > tol)) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      const float apq = (float)B[3 * p + q];
+      if (apq == 0.f) continue;
+      const float theta = (float)(B[3 * q + q] - B[3 * p + p]) / (2.f * apq);
+      const float tf = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+      const double t = (double)tf, x = 1.0 + t * t;
+      double y = (double)rsqrtf((float)x);
+      y = y * (1.5 - 0.5 * x * y * y);
+      y = y * (1.5 - 0.5 * x * y * y);
+      const double cc = y, ss = t * y;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double bkp = B[3 * k + p], bkq = B[3 * k + q];
+        B[3 * k + p] = cc * bkp - ss * bkq;
+        B[3 * k + q] = ss * bkp + cc * bkq;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double bpk = B[3 * p + k], bqk = B[3 * q + k];
+        B[3 * p + k] = cc * bpk - ss * bqk;
+        B[3 * q + k] = ss * bpk + cc * bqk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double vkp = Q[3 * k + p], vkq = Q[3 * k + q];
+        Q[3 * k + p] = cc * vkp - ss * vkq;
+        Q[3 * k + q] = ss * vkp + cc * vkq;
+      }
+    }
+  }
+  ev[0] = B[0] * isc;
+  ev[1] = B[4] * isc;
+  ev[2] = B[8] * isc;
+}
+
+// jacobi3 in the type's precision; FP64 through jacobi3_mixed
+template <typename T>
+__device__ __forceinline__ void jacobi3_fast(const T A[9], T ev[3], T Q[9]) {
+  jacobi3<T>(A, ev, Q);
+}
+template <>
+__device__ __forceinline__ void jacobi3_fast<double>(const double A[9], double ev[3], double Q[9]) {
+  jacobi3_mixed(A, ev, Q);
+}
+
 // [persistent-solver source: begin]
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
   unsigned v;
@@ -425,7 +542,7 @@ __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1)
       E[3 * a + b] = acc;
     }
   T lam[3], W[9];
-  jacobi3(E, lam, W);
+  jacobi3_fast<T>(E, lam, W);
   int i0 = 0, i1 = 1, i2 = 2;
   if (lam[i1] > lam[i0]) { int t = i0; i0 = i1; i1 = t; }
   if (lam[i2] > lam[i0]) { int t = i0; i0 = i2; i2 = t; }
