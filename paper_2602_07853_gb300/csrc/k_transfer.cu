@@ -141,7 +141,14 @@ __global__ void __launch_bounds__(256) k_p2q(const int* __restrict__ cblist, con
     mats[k].lam = (T)xi.mat[k].lam;
   }
   const T dx = (T)xi.dx;
-  for (int p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+  // the brick's particles are sorted by cell: lane l of a warp takes particle
+  // l * ceil(n / 32) + j of the brick, so the lanes of one warp add into cells
+  // far apart instead of contending for the same shared-memory words
+  const int n = p1 - p0, qn = (n + 31) >> 5, lane = threadIdx.x & 31;
+  for (int j = threadIdx.x >> 5; j < qn; j += blockDim.x >> 5) {
+    const int pl = lane * qn + j;
+    if (pl >= n) continue;
+    const int p = p0 + pl;
     double xa[3] = {(double)x[3 * p], (double)x[3 * p + 1], (double)x[3 * p + 2]};
     int b[3];
     double f[3];
@@ -160,17 +167,24 @@ __global__ void __launch_bounds__(256) k_p2q(const int* __restrict__ cblist, con
     T tau[6];
     kirchhoff(mats[k], Fp, tau);
     const int lb[3] = {b[0] & 7, b[1] & 7, b[2] & 7};
+    // the base index and the 1-D factors f, 1 - f are formed in FP64, the weights
+    // from them in the context precision: a factor rounds to zero only when it is
+    // zero (a nonzero factor of a stored FP32 position is far above the FP32
+    // underflow), so the zero pattern of the weights is the FP64 one
+    T w1[3], w0[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      w1[a] = (T)f[a];
+      w0[a] = (T)(1.0 - f[a]);
+    }
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
       const int oa[3] = {o & 1, (o >> 1) & 1, (o >> 2) & 1};
-      double wd = 1.0;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) wd *= oa[a] ? f[a] : 1.0 - f[a];
-      if (wd == 0.0) continue;
-      const T w = (T)wd;
+      const T w = (oa[0] ? w1[0] : w0[0]) * (oa[1] ? w1[1] : w0[1]) * (oa[2] ? w1[2] : w0[2]);
+      if (w == T(0)) continue;
       T d[3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) d[a] = (T)(((double)oa[a] - f[a]) * xi.dx);
+      for (int a = 0; a < 3; ++a) d[a] = (oa[a] ? w0[a] : -w1[a]) * dx;
       const int cell = ((lb[2] + oa[2]) * 9 + (lb[1] + oa[1])) * 9 + (lb[0] + oa[0]);
       const T wm = w * mp;
       sh_add(&sh[0 * 729 + cell], wm);
@@ -185,7 +199,6 @@ __global__ void __launch_bounds__(256) k_p2q(const int* __restrict__ cblist, con
       for (int q = 0; q < 6; ++q) sh_add(&sh[(acc_tau(k) + q) * 729 + cell], wV * tau[q]);
     }
   }
-  (void)dx;
   __syncthreads();
   // write out the 9x9x9 block
   for (int cell = threadIdx.x; cell < 729; cell += blockDim.x) {
@@ -317,14 +330,18 @@ __global__ void __launch_bounds__(256) k_g2p(int64_t np, const T* __restrict__ x
   double f[3];
   base_of(xa, xi.inv_dx, b, f);
   T vp[3] = {0, 0, 0}, Gp[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // weights from FP64 factors in the context precision (zero pattern as in P2Q)
+  T w1[3], w0[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    w1[a] = (T)f[a];
+    w0[a] = (T)(1.0 - f[a]);
+  }
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
     const int oa[3] = {o & 1, (o >> 1) & 1, (o >> 2) & 1};
-    double wd = 1.0;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) wd *= oa[a] ? f[a] : 1.0 - f[a];
-    if (wd == 0.0) continue;
-    const T w = (T)wd;
+    const T w = (oa[0] ? w1[0] : w0[0]) * (oa[1] ? w1[1] : w0[1]) * (oa[2] ? w1[2] : w0[2]);
+    if (w == T(0)) continue;
     const int c[3] = {b[0] + oa[0], b[1] + oa[1], b[2] + oa[2]};
     const int t = bmap[((int64_t)(c[2] >> 3) * NB1 + (c[1] >> 3)) * NB0 + (c[0] >> 3)];
     const T* src = cnew + (int64_t)t * 12 * BV + ((c[2] & 7) * 64 + (c[1] & 7) * 8 + (c[0] & 7));
