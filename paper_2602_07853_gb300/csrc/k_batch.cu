@@ -47,8 +47,9 @@ struct BScene {
 };
 
 constexpr int BATCH_MAX = MPML_BATCH_MAX;
-constexpr unsigned BC_BYTES = (unsigned)NQC * BV * 4u;  // compressed tangents of one brick
-constexpr size_t BC_SMEM = BC_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
+// dynamic shared memory: the 9^3 p halo of a brick and the column walk's
+// exchange buffers (the compressed tangent is streamed from global memory)
+constexpr size_t BC_SMEM = sizeof(float) * (3 * 729 + HVP_X_FLOATS + HVP_R_FLOATS);
 
 // warp sum of FP32 values in float-float arithmetic (error-free two-sum at every
 // level, the rounding errors carried in lo); FP64 only where lane 0 converts the pair
@@ -92,42 +93,6 @@ __device__ __forceinline__ void bblock_atomic2(float a_, float b_, double* acc) 
   __syncthreads();
 }
 
-__device__ __forceinline__ unsigned bsmem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool bmbar_wait(uint64_t* bar, unsigned phase) {
-  const unsigned a = bsmem_u32(bar);
-  for (unsigned it = 0; it < (1u << 24); ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(phase)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-// D' = sum_o p_o (x) sgn_o over the 8 corners of local cell l
-__device__ __forceinline__ void bgather_D(int l, const float (*sv)[729], float D[9]) {
-#pragma unroll
-  for (int q = 0; q < 9; ++q) D[q] = 0.f;
-  const int lx = l & 7, ly = (l >> 3) & 7, lz = l >> 6;
-#pragma unroll
-  for (int o = 0; o < 8; ++o) {
-    const int i = ((lz + ((o >> 2) & 1)) * 9 + (ly + ((o >> 1) & 1))) * 9 + (lx + (o & 1));
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float pa = sv[a][i];
-      D[3 * a + 0] += (o & 1) ? pa : -pa;
-      D[3 * a + 1] += (o & 2) ? pa : -pa;
-      D[3 * a + 2] += (o & 4) ? pa : -pa;
-    }
-  }
-}
-
 struct BatchArgs {
   const BScene* scenes;
   const int2* cw;  // (scene, cell brick index) work items
@@ -142,9 +107,8 @@ struct BatchArgs {
 
 __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
   extern __shared__ __align__(128) unsigned char psm[];
-  float* Cs = reinterpret_cast<float*>(psm);
-  float (*sv)[729] = reinterpret_cast<float (*)[729]>(psm + BC_BYTES);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(psm + BC_BYTES + sizeof(float) * 3 * 729 + 8 - (sizeof(float) * 3 * 729) % 8);
+  float (*sv)[729] = reinterpret_cast<float (*)[729]>(psm);
+  float* Xs = reinterpret_cast<float*>(psm + sizeof(float) * 3 * 729);
   __shared__ int s_nbr[NBR];
   __shared__ int s_flag, s_alldone;
   __shared__ double s_rz[BATCH_MAX], s_tol2[BATCH_MAX], s_rr[BATCH_MAX];
@@ -163,12 +127,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
     s_beta[s] = 0.f;
     s_flip[s] = 0;
   }
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bsmem_u32(bar)), "r"(1) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
   __syncthreads();
-  unsigned tma_phase = 0;
   bool alive = true;
   int round = 0;
   while (alive) {
@@ -197,100 +156,61 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
       const int id = B.cblist[item.y];
       if (threadIdx.x < NBR) s_nbr[threadIdx.x] = B.nbr[id * NBR + threadIdx.x];
       __syncthreads();
-      if (threadIdx.x == 0) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bsmem_u32(bar)), "r"(BC_BYTES)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                bsmem_u32(Cs)),
-            "l"(B.C + (int64_t)id * NQC * BV), "r"(BC_BYTES), "r"(bsmem_u32(bar))
-            : "memory");
-      }
-      float pmp = 0.f, pkp = 0.f;
-      for (int i = threadIdx.x; i < 729; i += blockDim.x) {
-        const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
-        const int t = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
-        const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
-        float v[3] = {0.f, 0.f, 0.f};
-        if (t >= 0) {
-          const int64_t o = (int64_t)t * 3 * BV + l;
+      float pmp = 0.f;
+      {
+        // every thread owns at most 3 of the 729 halo slots: issue all loads first
+        int tt[3], ll[3];
+        float dv[3][3], rv[3][3], pv[3][3], mv[3];
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            const float di = __ldcg(B.dinv + o + a * BV);
-            v[a] = di > 0.f ? di * __ldcg(B.r + o + a * BV) + beta * __ldcg(pold + o + a * BV) : 0.f;
-          }
-          if (t == id) {
+        for (int k = 0; k < 3; ++k) {
+          const int i = threadIdx.x + k * 256;
+          tt[k] = -1;
+          ll[k] = 0;
+          mv[k] = 0.f;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) pnext[o + a * BV] = v[a];
-            pmp += __ldcg(B.m + (int64_t)id * BV + l) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          for (int a = 0; a < 3; ++a) dv[k][a] = rv[k][a] = pv[k][a] = 0.f;
+          if (i < 729) {
+            const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+            const int t = (nx < 8 && ny < 8 && nz < 8) ? id : s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+            const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+            tt[k] = t;
+            ll[k] = l;
+            if (t >= 0) {
+              const int64_t o = (int64_t)t * 3 * BV + l;
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                dv[k][a] = __ldcg(B.dinv + o + a * BV);
+                rv[k][a] = __ldcg(B.r + o + a * BV);
+                pv[k][a] = __ldcg(pold + o + a * BV);
+              }
+              if (t == id) mv[k] = __ldcg(B.m + (int64_t)id * BV + l);
+            }
           }
         }
-        sv[0][i] = v[0];
-        sv[1][i] = v[1];
-        sv[2][i] = v[2];
-      }
-      __syncthreads();
-      const bool ok = bmbar_wait(bar, tma_phase);
-      tma_phase ^= 1u;
-      if (!ok && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
-      float KD[2][9];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int l = threadIdx.x + h * 256;
+        for (int k = 0; k < 3; ++k) {
+          const int i = threadIdx.x + k * 256;
+          if (i >= 729) continue;
+          float v[3];
 #pragma unroll
-        for (int rr = 0; rr < 9; ++rr) KD[h][rr] = 0.f;
-        if (ok && B.cflag[(int64_t)id * BV + l]) {
-          float D[9], c[NQC];
-          bgather_D(l, sv, D);
-#pragma unroll
-          for (int q = 0; q < NQC; ++q) c[q] = Cs[q * BV + l];
-          apply_cmp(c, D, KD[h]);
-#pragma unroll
-          for (int rr = 0; rr < 9; ++rr) pkp += D[rr] * KD[h][rr];
+          for (int a = 0; a < 3; ++a) v[a] = dv[k][a] > 0.f ? dv[k][a] * rv[k][a] + beta * pv[k][a] : 0.f;
+          if (tt[k] == id) {
+            const int64_t o = (int64_t)id * 3 * BV + ll[k];
+            pnext[o] = v[0];
+            pnext[o + BV] = v[1];
+            pnext[o + 2 * BV] = v[2];
+            pmp += mv[k] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          }
+          sv[0][i] = v[0];
+          sv[1][i] = v[1];
+          sv[2][i] = v[2];
         }
       }
       __syncthreads();
-      float (*skd)[BV] = reinterpret_cast<float (*)[BV]>(Cs);
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int rr = 0; rr < 9; ++rr) skd[rr][threadIdx.x + h * 256] = KD[h][rr];
-      __syncthreads();
-      for (int i = threadIdx.x; i < 729; i += blockDim.x) {
-        const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
-        float y[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-          const int cx = nx - (o & 1), cy = ny - ((o >> 1) & 1), cz = nz - ((o >> 2) & 1);
-          if (cx < 0 || cy < 0 || cz < 0 || cx > 7 || cy > 7 || cz > 7) continue;
-          const int cc = (cz * 8 + cy) * 8 + cx;
-          const float s0 = (o & 1) ? 1.f : -1.f, s1 = (o & 2) ? 1.f : -1.f, s2 = (o & 4) ? 1.f : -1.f;
-#pragma unroll
-          for (int a = 0; a < 3; ++a) y[a] += skd[3 * a][cc] * s0 + skd[3 * a + 1][cc] * s1 + skd[3 * a + 2][cc] * s2;
-        }
-        const bool own = nx < 8 && ny < 8 && nz < 8;
-        const bool excl = nx >= 1 && nx <= 7 && ny >= 1 && ny <= 7 && nz >= 1 && nz <= 7;
-        if (own) {
-          const int l = nz * 64 + ny * 8 + nx;
-          const float mi = B.m[(int64_t)id * BV + l];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            float* dst = B.q + (int64_t)id * 3 * BV + a * BV + l;
-            const float val = y[a] + mi * sv[a][i];
-            if (excl) *dst = val;
-            else if (val != 0.f) atomicAdd(dst, val);
-          }
-        } else {
-          const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
-          if (t < 0) continue;
-          const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-            if (y[a] != 0.f) atomicAdd(B.q + (int64_t)t * 3 * BV + a * BV + l, y[a]);
-        }
-      }
-      bblock_atomic2(pmp, pkp, accH + 2 * s);  // ends with a barrier: Cs / sv / s_nbr free
+      // the column walk of the single-scene persistent solver, tangent rows streamed
+      const float pkp = phase_h_col<false, true>(id, s_nbr, sv, B.C + (int64_t)id * NQC * BV, B.cflag, B.m, B.q, Xs,
+                                                 Xs + HVP_X_FLOATS, true);
+      bblock_atomic2(pmp, pkp, accH + 2 * s);  // ends with a barrier: sv / s_nbr / exchange buffers free
     }
     // node-only bricks: p_new and the mass term
     for (int w = blockIdx.x; w < A.nnw; w += G) {

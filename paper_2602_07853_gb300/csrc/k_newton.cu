@@ -1113,13 +1113,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
 }
 
 // [persistent-solver source: end]
-// streamed read-only load: no L1 allocation, L2 fetches in 256-byte sectors
-// (the tangent block is read once per launch, in 128-byte rows per warp)
-__device__ __forceinline__ float ld_stream(const float* p) {
-  float v;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
-  return v;
-}
 
 // Standalone FP32 HVP of one cell brick per CTA on the compressed tangent (the
 // 45-number form runs in k_hvp_col), read straight from global memory (read-only during the kernel, coalesced per tangent entry; measured faster
@@ -1242,9 +1235,6 @@ __global__ void __launch_bounds__(256, 3) k_hvp_glob(const int* __restrict__ cbl
 // D' is formed from the p halo in shared memory, reusing the upper node layer
 // of cell z as the lower layer of cell z + 1.
 // ---------------------------------------------------------------------------
-// [persistent-solver source: begin]
-__device__ __forceinline__ int hidx(int nx, int ny, int nz) { return (nz * 9 + ny) * 9 + nx; }
-// [persistent-solver source: end]
 
 // node (nx, ny, nz) of the 9^3 halo of brick id receives the in-brick sum y[3]:
 // a plain store (with the mass term) where only this brick contributes, an
@@ -1475,9 +1465,6 @@ __global__ void __launch_bounds__(64, MINB) k_hvp_col(const int* __restrict__ cb
 // mbarrier.
 constexpr unsigned HVP_C_BYTES = (unsigned)NQC * BV * 4u;
 constexpr size_t HVP_C_SMEM = HVP_C_BYTES + sizeof(float) * 3 * 729 + 16 + 16;
-// the column-walk phase H adds the z-exchange of the four 64-thread groups
-// (12 floats per thread) and their row 3 -> 4 partials (3 layers x 2 x 3 x 8)
-constexpr size_t HVP_X_FLOATS = 4 * 12 * 64, HVP_R_FLOATS = 4 * 3 * 2 * 3 * 8;
 constexpr size_t HVP_C_SMEM_COL = HVP_C_SMEM + sizeof(float) * (HVP_X_FLOATS + HVP_R_FLOATS);
 // 45-number tangent in the persistent solver: the brick's 45 x 512 floats by one
 // bulk copy; the exchange buffers overlay the tangent block once it is used
@@ -2271,215 +2258,6 @@ __device__ __forceinline__ float pnew_at(const PcgArgs& A, int64_t o, float beta
   return di > 0.f ? di * A.r[o] + beta * pold[o] : 0.f;
 }
 
-// node (nx, ny, nz) of the 9^3 halo of brick id receives y[3] inside the
-// persistent solver, where q starts at zero: own nodes take the mass term too
-// (plain store where only this brick contributes, atomic add elsewhere).
-__device__ __forceinline__ void col_emit_m(int id, const int* s_nbr, const float (*sv)[729],
-                                          const float* __restrict__ m, float* q, int nx, int ny, int nz,
-                                          const float y[3]) {
-  if (nx < 8 && ny < 8 && nz < 8) {
-    const int l = (nz * 8 + ny) * 8 + nx;
-    float* dst = q + (int64_t)id * 3 * BV + l;
-    const float mi = __ldcg(m + (int64_t)id * BV + l);
-    const int i = hidx(nx, ny, nz);
-    if (nx >= 1 && ny >= 1 && nz >= 1) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) dst[a * BV] = y[a] + mi * sv[a][i];
-    } else {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float val = y[a] + mi * sv[a][i];
-        if (val != 0.f) atomicAdd(dst + a * BV, val);
-      }
-    }
-  } else {
-    const int t = s_nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
-    if (t < 0) return;
-    const int l = ((nz & 7) * 8 + (ny & 7)) * 8 + (nx & 7);
-    float* dst = q + (int64_t)t * 3 * BV + l;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (y[a] != 0.f) atomicAdd(dst + a * BV, y[a]);
-  }
-}
-
-// corner contributions of one cell: lower-z corners into N (added), upper-z
-// corners returned in U; node (x + ox, y + oy, z + oz) gets
-// (2ox-1) X + (2oy-1) Y + (2oz-1) Z of the cell's K D' rows (X, Y, Z)
-__device__ __forceinline__ void col_corners(const float KD[9], float N[2][2][3], float U[2][2][3]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float X = KD[3 * a], Yv = KD[3 * a + 1], Z = KD[3 * a + 2];
-    const float Ap = X + Yv, B = X - Yv;
-    N[1][1][a] += Ap - Z;
-    N[0][0][a] -= Ap + Z;
-    N[1][0][a] += B - Z;
-    N[0][1][a] -= B + Z;
-    U[1][1][a] = Ap + Z;
-    U[0][0][a] = Z - Ap;
-    U[1][0][a] = B + Z;
-    U[0][1][a] = Z - B;
-  }
-}
-
-// D' = sum_o p_o (x) sgn_o from the lower (P0) and upper (P1) node layers of a cell
-__device__ __forceinline__ void col_D(const float P0[2][2][3], const float P1[2][2][3], float D[9]) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float s00 = P0[0][0][a] + P1[0][0][a], s10 = P0[1][0][a] + P1[1][0][a];
-    const float s01 = P0[0][1][a] + P1[0][1][a], s11 = P0[1][1][a] + P1[1][1][a];
-    D[3 * a + 0] = (s10 + s11) - (s00 + s01);
-    D[3 * a + 1] = (s01 + s11) - (s00 + s10);
-    D[3 * a + 2] = (P1[0][0][a] - P0[0][0][a]) + (P1[1][0][a] - P0[1][0][a]) + (P1[0][1][a] - P0[0][1][a]) +
-                   (P1[1][1][a] - P0[1][1][a]);
-  }
-}
-
-// Phase H of one brick in the column walk: the CTA's four 64-thread groups take
-// two z-layers of cells each (group g: cells z = 2g, 2g + 1 of column (x, y));
-// node layers are summed along z in registers, across groups through shared
-// memory (layer 2g gets group g-1's upper corners), along x by warp shuffles and
-// along y by shuffles of eight lanes (rows 3 -> 4 through shared memory).
-// Returns the thread's sum of D' . K D'.
-template <bool K45, bool GLOBAL = false>
-__device__ __forceinline__ float phase_h_col(int id, const int* s_nbr, const float (*sv)[729], const float* Cs,
-                                             const uint8_t* __restrict__ cflag, const float* __restrict__ m, float* q,
-                                             float* X, float* R, bool ok) {
-  constexpr unsigned FULL = 0xffffffffu;
-  const int t = threadIdx.x, g = t >> 6, x = t & 7, y = (t >> 3) & 7, row = y & 3, c64 = t & 63;
-  float pkp = 0.f;
-  float Pa[2][2][3], Pb[2][2][3];
-  float Na[2][2][3], Nb[2][2][3], Nc[2][2][3];
-#pragma unroll
-  for (int ox = 0; ox < 2; ++ox)
-#pragma unroll
-    for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        Pa[ox][oy][a] = sv[a][hidx(x + ox, y + oy, 2 * g)];
-        Pb[ox][oy][a] = sv[a][hidx(x + ox, y + oy, 2 * g + 1)];
-        Na[ox][oy][a] = 0.f;
-      }
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int l = (2 * g + h) * 64 + c64;
-    float KD[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) KD[r] = 0.f;
-    if (ok && cflag[(int64_t)id * BV + l]) {
-      float D[9];
-      col_D(Pa, Pb, D);
-      if (K45) {
-#pragma unroll
-        for (int r = 0; r < 9; ++r) {
-          KD[r] += (GLOBAL ? ld_stream(Cs + k45(r, r) * BV + l) : Cs[k45(r, r) * BV + l]) * D[r];
-#pragma unroll
-          for (int cc = r + 1; cc < 9; ++cc) {
-            const float kv = GLOBAL ? ld_stream(Cs + k45(r, cc) * BV + l) : Cs[k45(r, cc) * BV + l];
-            KD[r] += kv * D[cc];
-            KD[cc] += kv * D[r];
-          }
-        }
-      } else {
-        float c[NQC];
-#pragma unroll
-        for (int qq = 0; qq < NQC; ++qq) c[qq] = GLOBAL ? ld_stream(Cs + qq * BV + l) : Cs[qq * BV + l];
-        apply_cmp(c, D, KD);
-      }
-#pragma unroll
-      for (int r = 0; r < 9; ++r) pkp += D[r] * KD[r];
-    }
-    if (h == 0) {
-      col_corners(KD, Na, Nb);  // Nb <- upper corners of cell 2g (lower of cell 2g+1 added next)
-#pragma unroll
-      for (int ox = 0; ox < 2; ++ox)
-#pragma unroll
-        for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            Pa[ox][oy][a] = Pb[ox][oy][a];
-            Pb[ox][oy][a] = sv[a][hidx(x + ox, y + oy, 2 * g + 2)];
-          }
-    } else {
-      col_corners(KD, Nb, Nc);
-    }
-  }
-  // across groups: node layer 2g + 2 = this group's Nc + group g+1's Na
-  if (K45 && !GLOBAL) __syncthreads();  // X overlays the tangent block: every cell has been applied
-  if (g < 3) {
-    float* Xg = X + g * 12 * 64;
-#pragma unroll
-    for (int ox = 0; ox < 2; ++ox)
-#pragma unroll
-      for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) Xg[((ox * 2 + oy) * 3 + a) * 64 + c64] = Nc[ox][oy][a];
-  }
-  __syncthreads();
-  if (g > 0) {
-    const float* Xg = X + (g - 1) * 12 * 64;
-#pragma unroll
-    for (int ox = 0; ox < 2; ++ox)
-#pragma unroll
-      for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) Na[ox][oy][a] += Xg[((ox * 2 + oy) * 3 + a) * 64 + c64];
-  }
-  // along x (shuffles), then the row-3 partials of every layer into shared memory
-  const int nl = g == 3 ? 3 : 2;
-  float E[3][2][3], E8[3][2][3];
-#pragma unroll
-  for (int L = 0; L < 3; ++L) {
-    if (L == 2 && nl < 3) break;
-#pragma unroll
-    for (int oy = 0; oy < 2; ++oy)
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float n0 = L == 0 ? Na[0][oy][a] : (L == 1 ? Nb[0][oy][a] : Nc[0][oy][a]);
-        const float n1 = L == 0 ? Na[1][oy][a] : (L == 1 ? Nb[1][oy][a] : Nc[1][oy][a]);
-        const float left = __shfl_up_sync(FULL, n1, 1);
-        E[L][oy][a] = n0 + (x > 0 ? left : 0.f);
-        E8[L][oy][a] = n1;
-      }
-    if (y == 3) {
-      float* Rg = R + (g * 3 + L) * 48;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        Rg[a * 8 + x] = E[L][1][a];
-        Rg[24 + a * 8 + x] = E8[L][1][a];
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int L = 0; L < 3; ++L) {
-    if (L == 2 && nl < 3) break;
-    const int nz = L == 2 ? 8 : 2 * g + L;
-    const float* Rg = R + (g * 3 + L) * 48;
-    float T[3], T8[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float up = __shfl_up_sync(FULL, E[L][1][a], 8), up8 = __shfl_up_sync(FULL, E8[L][1][a], 8);
-      float prev = 0.f, prev8 = 0.f;
-      if (row > 0) {
-        prev = up;
-        prev8 = up8;
-      } else if (y == 4) {
-        prev = Rg[a * 8 + x];
-        prev8 = Rg[24 + a * 8 + x];
-      }
-      T[a] = E[L][0][a] + prev;
-      T8[a] = E8[L][0][a] + prev8;
-    }
-    col_emit_m(id, s_nbr, sv, m, q, x, y, nz, T);
-    if (x == 7) col_emit_m(id, s_nbr, sv, m, q, 8, y, nz, T8);
-    if (y == 7) {
-      col_emit_m(id, s_nbr, sv, m, q, x, 8, nz, E[L][1]);
-      if (x == 7) col_emit_m(id, s_nbr, sv, m, q, 8, 8, nz, E8[L][1]);
-    }
-  }
-  return pkp;
-}
 
 template <bool K45, bool GLOBAL = false>
 __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
