@@ -106,6 +106,52 @@ def test_stretch_energy_gradient_hvp(precision):
     g.close()
 
 
+def _rotation(rng):
+    q = rng.standard_normal(4)
+    w, x, y, z = q / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+                     [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+                     [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)]])
+
+
+@pytest.mark.parametrize("precision", [m.FP32, m.FP64])
+@pytest.mark.parametrize("kind", ["rest", "isotropic", "double", "near_double"])
+@pytest.mark.parametrize("model", [scenes.FIXED_COROTATED, scenes.NEO_HOOKEAN, scenes.HENCKY])
+def test_stretch_degenerate_stress(precision, kind, model):
+    """Stretch reconstruction where the cell-averaged Kirchhoff stress has repeated or
+    nearly repeated eigenvalues (and zero stress at rest): the symmetric eigen-solve must
+    still reach the oracle's FP64 stretch (Sec. 4.2)."""
+    n = 16
+    rng = np.random.default_rng(11)
+    count = 3000
+    sc = scenes.Scene("degenerate", (n, n, n), 1.0 / n, float(n), 1e-3, (0.0, -9.8, 0.0),
+                      [scenes.Material(model, 1e5, 0.3)])
+    sc.x = rng.uniform(1.6 / n, 1 - 1.6 / n, (count, 3))
+    sc.v = rng.standard_normal((count, 3))
+    sc.G = np.zeros((count, 3, 3))
+    R = _rotation(rng)
+    diag = {"rest": (1.0, 1.0, 1.0), "isotropic": (1.01, 1.01, 1.01), "double": (1.01, 1.01, 0.98),
+            "near_double": (1.01, 1.01 + 1e-9, 0.98)}[kind]
+    F = R @ np.diag(diag) @ R.T
+    sc.F = np.broadcast_to(F, (count, 3, 3)).copy()
+    sc.Vp = np.full(count, sc.dx ** 3 / 8)
+    sc.mat = np.zeros(count, np.int32)
+    sc.mp = 1000.0 * sc.Vp
+    g, o, _ = both(sc, precision)
+    assert o.stretch() == 0
+    m.mpml_stretch(g.ctx)
+    S_g, S_o = g.field(m.F_CELL_STRETCH), o.field("S_ck")
+    mask = o.field("V_ck") > 0
+    ref = S_o[mask] - np.eye(3)
+    err = np.linalg.norm(S_g[mask] - S_o[mask]) / max(np.linalg.norm(ref), 1e-30)
+    if kind == "rest":
+        # S = I: the absolute error in units of the FP32 / FP64 rounding of S
+        assert np.max(np.abs(S_g[mask] - np.eye(3))) <= {m.FP32: 1e-6, m.FP64: 1e-14}[precision]
+    else:
+        assert err <= TOL[precision], err
+    g.close()
+
+
 def node_only_brick_scene(seed=9):
     """Particles filling cells 8..15 on every axis of a 32^3 grid: the DOF nodes of
     layer 16 live in bricks that contain no active cell (node-only bricks)."""
