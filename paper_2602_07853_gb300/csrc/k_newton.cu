@@ -2421,8 +2421,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       inflight = true;
       cs_k = 0;
     }
-    // bricks with DOF nodes but no cells: p_new and the mass term
-    for (int jn = blockIdx.x; jn < A.nnob; jn += G) {
+    // bricks with DOF nodes but no cells: p_new and the mass term, dealt from the
+    // last CTA down (the CTAs with the fewest cell bricks)
+    for (int jn = G - 1 - (int)blockIdx.x; jn < A.nnob; jn += G) {
       const int id = A.nolist[jn];
       for (int l = threadIdx.x; l < BV; l += blockDim.x) {
         const int64_t o = (int64_t)id * 3 * BV + l;
