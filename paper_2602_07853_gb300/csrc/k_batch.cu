@@ -212,8 +212,9 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
                                                  Xs + HVP_X_FLOATS, true);
       bblock_atomic2(pmp, pkp, accH + 2 * s);  // ends with a barrier: sv / s_nbr / exchange buffers free
     }
-    // node-only bricks: p_new and the mass term
-    for (int w = blockIdx.x; w < A.nnw; w += G) {
+    // node-only bricks: p_new and the mass term, dealt from the last CTA down (the
+    // CTAs with the fewest cell work items)
+    for (int w = G - 1 - (int)blockIdx.x; w < A.nnw; w += G) {
       const int2 item = A.nw[w];
       const int s = item.x;
       if (s_done[s]) continue;
