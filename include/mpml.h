@@ -303,8 +303,8 @@ int64_t mpml_kernel_launches(mpml_ctx ctx);
  * automatic choice); mpml_get_hvp_tile returns the shape in use (-1: not yet
  * chosen) and a one-line description (static storage).
  * mpml_tile_cache_save / _load write and read the cache as text, one line
- * "format log2_bricks tile mean_ms" per entry (format 25: compressed tangent, 45: packed); loading merges
- * into the cache (malformed lines: MPML_ERR_ARG, nothing merged; unreadable or
+ * "format log2_bricks tile mean_ms" per entry (format 25: compressed tangent,
+ * 45: packed); loading merges into the cache (malformed lines: MPML_ERR_ARG, nothing merged; unreadable or
  * unwritable file: MPML_ERR_ARG).  Host-only, thread-safe. */
 #define MPML_HVP_TILES 3
 int mpml_autotune_hvp(mpml_ctx ctx, int reps, int* tile, float* ms);

@@ -679,8 +679,8 @@ __device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[
   T ev[3], Qd[9];
   jacobi3<T>(d2, ev, Qd);
   {
-    // compressed record (valid for single-material cells; bm is the stretch
-    // step's symmetric base S - I)
+    // compressed record (valid for single-material cells; bm = B - I, the
+    // stretch step's base S - I in elastic contexts)
     double Ud[9], q[4];
 #pragma unroll
     for (int i = 0; i < 9; ++i) Ud[i] = (double)Ut[i];

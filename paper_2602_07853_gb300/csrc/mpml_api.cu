@@ -254,7 +254,8 @@ int mpml_create(const mpml_scene_desc* desc, const mpml_material* mats, int n_ma
   c->s = (cudaStream_t)stream;
   c->fp64 = desc->precision == MPML_FP64;
   c->esz = c->fp64 ? 8 : 4;
-  // the compressed tangent assumes the symmetric base of the stretch step: elastic single-material FP32
+  // the compressed tangent serves elastic single-material FP32 contexts (plastic ones, whose
+  // fixed-point solve may change the base, keep the 45-number form)
   c->compressed = (!c->fp64 && n_mats == 1 && mats[0].plastic == MPML_ELASTIC) ? 1 : 0;
   for (int a = 0; a < 3; ++a) c->NB[a] = (desc->n[a] >> 3) + 1;
   c->NBT = (int64_t)c->NB[0] * c->NB[1] * c->NB[2];
