@@ -274,7 +274,9 @@ int mpml_hvp_bench(mpml_ctx ctx, int iters, double* mean_ms);
 /* With profiling enabled: the persistent cooperative PCG kernel (use_graph = 2)
  * is bracketed by CUDA events on the context stream; returns its launches
  * since profiling was enabled, the CG iterations they ran and their total
- * milliseconds.  Host-side only (no synchronisation). */
+ * milliseconds.  With profiling enabled on the first context of a batch, the
+ * batched solver's launches are counted there (CG iterations: the largest
+ * count among the launch's scenes).  Host-side only (no synchronisation). */
 int mpml_pcg_timing(mpml_ctx ctx, int64_t* launches, int64_t* cg_iters, double* total_ms);
 /* Number of kernel launches issued on the context stream since creation. */
 int64_t mpml_kernel_launches(mpml_ctx ctx);
@@ -313,6 +315,55 @@ int mpml_get_hvp_tile(mpml_ctx ctx, int* tile, const char** description);
 int mpml_tile_cache_save(const char* path);
 int mpml_tile_cache_load(const char* path);
 void mpml_tile_cache_clear(void);
+
+/* Persistent-solver launch controls -------------------------------------
+ * Not in the paper.  The persistent Jacobi-PCG kernel (use_graph = 2) brings
+ * each cell brick's tangent block in one of two ways:
+ *   MPML_PCG_STAGED    one bulk copy of the whole block into shared memory per
+ *                      brick (kept there for the solve when a CTA owns one brick)
+ *   MPML_PCG_STREAMED  the rows are read from global memory as the column walk
+ *                      needs them (no shared-memory block)
+ *   MPML_PCG_AUTO      the shape mpml_autotune_pcg chose for this tangent format
+ *                      and size class, else a fixed rule (streamed for the
+ *                      compressed tangent above 8 bricks per SM, staged otherwise)
+ * ctas_per_sm: CTAs per SM of the cooperative launch (0 = as many as fit; a
+ *   value above what fits is MPML_ERR_ARG at the next solve).
+ * barrier_spins: bound on the polls of one grid-barrier wait (0 = the default
+ *   2^25 polls of 32 ns, about a second).  A wait that runs out ends the solve:
+ *   mpml_newton_step returns MPML_ERR_TIMEOUT; the next mpml_resample clears the
+ *   latched status and the context is usable again.  A bound of a few polls
+ *   makes the waits run out on purpose (how the tests exercise that path).
+ * The configuration applies to every later solve of the context (also the
+ * learned solver's Jacobi fallback).  mpml_get_pcg_config returns it, and in
+ * last_staging / last_ctas_per_sm (either may be NULL) the shape the last
+ * persistent launch used (0 before the first). */
+enum { MPML_PCG_AUTO = 0, MPML_PCG_STAGED = 1, MPML_PCG_STREAMED = 2 };
+typedef struct {
+  int tangent_staging;
+  int ctas_per_sm;
+  unsigned barrier_spins;
+} mpml_pcg_config;
+int mpml_set_pcg_config(mpml_ctx ctx, const mpml_pcg_config* cfg);
+int mpml_get_pcg_config(mpml_ctx ctx, mpml_pcg_config* cfg, int* last_staging, int* last_ctas_per_sm);
+
+/* Persistent-solver autotuner: times MPML_PCG_SHAPES shapes of the persistent
+ * solve (staged or streamed tangent x 1 or 2 CTAs per SM; shapes that do not
+ * fit are skipped, their time reported as -1) on the current Newton system:
+ * each runs `iters` Jacobi-PCG iterations from the same start (the solver's
+ * state is restored afterwards), CUDA events on the context stream, best of
+ * `reps`.  The fastest becomes the context's shape under MPML_PCG_AUTO and is
+ * recorded in the process-wide tile cache under format 125 (compressed) or
+ * 145 (45 numbers) and log2 of the cell bricks.  Shape index =
+ * (staging - 1) * 2 + (ctas_per_sm - 1).  FP32 contexts after a linearisation
+ * (mpml_linearize or mpml_newton_step), MPML_ERR_ARG otherwise.  Synchronising. */
+#define MPML_PCG_SHAPES 4
+int mpml_autotune_pcg(mpml_ctx ctx, int iters, int reps, int* shape, float* ms);
+
+/* Lame parameters of an isotropic material from Young's modulus E > 0 and
+ * Poisson's ratio -1 < nu < 1/2: mu = E / (2 (1 + nu)),
+ * lambda = E nu / ((1 + nu)(1 - 2 nu)) (the standard relations; the paper
+ * quotes E and nu).  MPML_ERR_ARG outside that range. */
+int mpml_lame_parameters(double E, double nu, double* mu, double* lambda);
 
 /* Learned preconditioner ------------------------------------------------
  * Not in the paper: the workload asks for a small 3D convolutional network
@@ -384,11 +435,16 @@ int mpml_nn_train(mpml_ctx ctx, const mpml_train_opts* opts, mpml_train_stats* s
  * GPU that loads this library holds until the process exits): a grid with
  * NB_x*NB_y*NB_z*512 > MPML_NOALLOC_MAX_SLOTS (e.g. more than 127 cells per
  * axis of a cube) is rejected with MPML_ERR_TOO_LARGE, n_particles above
- * INT32_MAX with MPML_ERR_ARG.  The first call on a device looks up the
- * array's device address (the device must be current); make that first call
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU (other streams, other threads) race.  Synchronises
- * the stream; returns MPML_ERR_OUT_OF_DOMAIN / MPML_ERR_NONFINITE for bad
+ * INT32_MAX with MPML_ERR_ARG.  The CUDA runtime loads the library's device
+ * code, and with it places the array, on a device at the first use of the
+ * library there -- possibly this call: make that first call (the device
+ * current) before an arena claims the device's memory and before any stream
+ * capture.  Every call looks up the array's address on the current device.
+ * All calls share the array: calls whose work overlaps on the GPU (other
+ * streams, other threads) race.  Cost: linear in the particles, plus a
+ * quadratic term per centre in the particles of that centre (cheap up to a
+ * few thousand per centre; typical scenes hold 8-24).  Synchronises the
+ * stream; returns MPML_ERR_OUT_OF_DOMAIN / MPML_ERR_NONFINITE for bad
  * particles (perm is then incomplete). */
 #define MPML_NOALLOC_MAX_SLOTS (1 << 21)
 int mpml_sort_particles_noalloc(const int n[3], double inv_dx, int precision, const void* x,

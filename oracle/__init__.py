@@ -14,8 +14,8 @@ marshals numpy arrays and gives the steps the paper's names:
 * :meth:`Oracle.newton`   Algorithm 3, minimise the incremental potential
 * :meth:`Oracle.load`     Algorithm 4
 
-Parity status of each function is listed in the repository's DESIGN.md;
-every function here is pinned by a ``-m "not gpu"`` test except the
+Every function here is pinned by a ``-m "not gpu"`` test (finite
+differences, closed forms, brute force, conservation laws) except the
 long-horizon trajectories of contact scenes (parity unpinned: compared as
 statistics only).
 """

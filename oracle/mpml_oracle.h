@@ -18,8 +18,8 @@
  *   - Algorithm 4 (Load): Sec. 3.3 node-to-centre sampling, Sec. 3.1
  *     centre-to-particle interpolation, advection and F update.
  *
- * Readings of passages the paper leaves open are listed in the design doc of
- * the repository and repeated at the function that uses them.
+ * Where the paper leaves a passage open, the reading taken is stated at the
+ * function that uses it.
  */
 #ifndef MPML_ORACLE_H
 #define MPML_ORACLE_H

@@ -102,6 +102,7 @@ struct BatchArgs {
   double* acc;     // [4][nsc][2] rotating per-scene accumulators
   unsigned* gbar;
   int cg_max;
+  unsigned spins;  // bound on the polls of one grid-barrier wait
   int* status;
 };
 
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
       }
       bblock_atomic2(pmp, 0.f, accH + 2 * s);
     }
-    if (!grid_barrier(A.gbar, &s_flag)) {
+    if (!grid_barrier(A.gbar, &s_flag, A.spins)) {
       alive = false;
       break;
     }
@@ -286,7 +287,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_batch(BatchArgs A) {
       }
       bblock_atomic2(rzl, rrl, accA + 2 * s);
     }
-    if (!grid_barrier(A.gbar, &s_flag)) {
+    if (!grid_barrier(A.gbar, &s_flag, A.spins)) {
       alive = false;
       break;
     }
@@ -342,16 +343,13 @@ int ensure_event(mpml_ctx_s* c) {
 }
 
 int pcg_batch(mpml_ctx_s* owner, const std::vector<mpml_ctx_s*>& cs, int cg_max) {
-  static int max_blocks = -1;
-  if (max_blocks < 0) {
-    cudaFuncSetAttribute(k_pcg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BC_SMEM);
-    int per_sm = 0, nsm = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batch, 256, BC_SMEM) != cudaSuccess) per_sm = 0;
-    max_blocks = per_sm * nsm;
-  }
-  if (max_blocks <= 0) return MPML_ERR_CUDA;
+  // CTAs per SM: the first context's mpml_pcg_config, else as many as fit
+  int nsm = 0;
+  const int fit = launch_fit((const void*)k_pcg_batch, 256, BC_SMEM, LS_BATCH, &nsm);
+  if (fit <= 0) return MPML_ERR_CUDA;
+  const int per_sm = owner->pcg_cfg.ctas_per_sm > 0 ? owner->pcg_cfg.ctas_per_sm : fit;
+  if (per_sm > fit) return MPML_ERR_ARG;
+  const int max_blocks = per_sm * nsm;
   const int S = (int)cs.size();
   std::vector<BScene> sc(S);
   std::vector<int2> cw, nw, aw;
@@ -422,10 +420,16 @@ int pcg_batch(mpml_ctx_s* owner, const std::vector<mpml_ctx_s*>& cs, int cg_max)
   a.acc = reinterpret_cast<double*>(base + off_acc);
   a.gbar = reinterpret_cast<unsigned*>(base + off_bar);
   a.cg_max = cg_max;
+  a.spins = owner->pcg_cfg.barrier_spins ? owner->pcg_cfg.barrier_spins : BARRIER_SPINS_DEFAULT;
   a.status = (int*)owner->status.p;
   void* args[] = {&a};
+  // with profiling enabled on the first context: CUDA events around the launch (mpml_pcg_timing)
+  const bool timed = owner->profiling && owner->pcg_ev[0] && owner->pcg_ev[1];
+  if (timed) cudaEventRecord(owner->pcg_ev[0], s);
   rc = cuda_status(cudaLaunchCooperativeKernel((const void*)k_pcg_batch, dim3(max_blocks), dim3(256), args, BC_SMEM, s));
+  if (timed) cudaEventRecord(owner->pcg_ev[1], s);
   owner->launches++;
+  owner->pcg_last_ctas = per_sm;
   if (rc) return rc;
   // every scene's stream continues after the shared launch
   cudaEventRecord(owner->bev, s);
@@ -487,6 +491,19 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
     // one cooperative launch for every active scene's Jacobi-PCG solve
     if ((rc = pcg_batch(owner, cs, o->cg_max))) return rc;
     if ((rc = read_all(cs))) return rc;
+    if (owner->profiling && owner->pcg_ev[0] && owner->pcg_ev[1]) {
+      // the launch's time, and as its CG iterations the largest count of its scenes
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, owner->pcg_ev[0], owner->pcg_ev[1]) == cudaSuccess) {
+        int mx = 0;
+        for (mpml_ctx_s* c : cs) mx = std::max(mx, c->hscal->iters);
+        owner->pcg_ms += ms;
+        owner->pcg_launches += 1;
+        owner->pcg_iters += mx;
+      } else {
+        cudaGetLastError();
+      }
+    }
     for (int i : idx) {
       mpml_ctx_s* c = ctxs[i];
       const int k = it[i];

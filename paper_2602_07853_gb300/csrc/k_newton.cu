@@ -2046,11 +2046,7 @@ static void launch_hvp(mpml_ctx_s* c, const T* p, T* q, int finalize) {
   if (sizeof(T) == 4) {
     launch_hvp_f32(c, c->hvp_tile >= 0 ? c->hvp_tile : 0, (const float*)p, (float*)q, finalize);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_hvp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hvp_smem_bytes<T>());
-      attr = true;
-    }
+    launch_fit((const void*)k_hvp<T>, 256, hvp_smem_bytes<T>(), LS_HVP64, nullptr);
     k_hvp<T><<<(unsigned)c->ncb, 256, hvp_smem_bytes<T>(), c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
                                                                  (const uint8_t*)c->cflag.p, (const T*)c->cK.p, p,
                                                                  (const T*)c->nmass.p, q, dscal(c), finalize, pf,
@@ -2178,6 +2174,7 @@ struct PcgArgs {
   double* acc;    // [4][2] rotating accumulators of the phase sums
   unsigned* gbar; // grid-barrier counter (zero at launch)
   int ncb, nnob, nb, cg_max;
+  unsigned spins;  // bound on the polls of one grid-barrier wait
   int* status;
   DevProf* pf;
 };
@@ -2448,7 +2445,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       z[1] = 0.0;
     }
     block_atomic2(pmp, pkp, accH);
-    if (!grid_barrier(A.gbar, &s_flag)) {
+    if (!grid_barrier(A.gbar, &s_flag, A.spins)) {
       alive = false;
       break;
     }
@@ -2524,7 +2521,7 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
       z[1] = 0.0;
     }
     block_atomic2(rzl, rrl, accA);
-    if (!grid_barrier(A.gbar, &s_flag)) {
+    if (!grid_barrier(A.gbar, &s_flag, A.spins)) {
       alive = false;
       break;
     }
@@ -2554,32 +2551,62 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
   }
 }
 
-static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
-  // one occupancy query per tangent format (compressed, 45-number packed)
-  static int max_blocks[4] = {-1, -1, -1, -1};
+// The four kernels of the persistent solver: tangent format x staging.
+static const void* pcg_kernel(int k45, int streamed) {
+  return k45 ? (streamed ? (const void*)k_pcg_persistent<true, true> : (const void*)k_pcg_persistent<true>)
+             : (streamed ? (const void*)k_pcg_persistent<false, true> : (const void*)k_pcg_persistent<false>);
+}
+
+static size_t pcg_smem(int k45, int streamed) {
+  return streamed ? sizeof(float) * (3 * 729 + HVP_X_FLOATS + HVP_R_FLOATS) + 32 : (k45 ? HVP_K_SMEM45 : HVP_C_SMEM_COL);
+}
+
+// tile-cache format keys of the persistent solver's shapes (the standalone HVP uses 25 and 45)
+static int pcg_cache_format(int k45) { return k45 ? 145 : 125; }
+
+// The shape (staging, CTAs per SM) of the next persistent launch: the context's
+// explicit configuration, else the autotuned shape cached for this format and
+// size class, else the fixed rule -- the compressed tangent is streamed from
+// global memory beyond eight cell bricks per SM (measured 9% faster per CG
+// iteration on the 3-8M pressed block, equal at 168^3; the 45-number tangent
+// keeps the shared-memory copy, 2% faster on the 256^3 slab on sand), and as
+// many CTAs per SM as fit.
+static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
   const int k45 = c->compressed ? 0 : 1;
-  // compressed tangent beyond a few bricks per CTA (working set well past L2): stream the
-  // tangent rows from global memory instead of one TMA copy per brick into shared memory
-  // (measured 9% faster per CG iteration on the 3-8M pressed block, equal at 168^3;
-  // the 45-number tangent keeps the TMA copy, which measured 2% faster on config 5)
-  static int nsm_g = 0;
-  if (!nsm_g) cudaDeviceGetAttribute(&nsm_g, cudaDevAttrMultiProcessorCount, 0);
-  const int use_global = (!k45 && c->ncb > 4 * 2 * (int64_t)nsm_g) ? 1 : 0;
-  const void* kfn = k45 ? (use_global ? (const void*)k_pcg_persistent<true, true> : (const void*)k_pcg_persistent<true>)
-                        : (use_global ? (const void*)k_pcg_persistent<false, true> : (const void*)k_pcg_persistent<false>);
-  const size_t smem = use_global ? sizeof(float) * (3 * 729 + HVP_X_FLOATS + HVP_R_FLOATS) + 32
-                               : (k45 ? HVP_K_SMEM45 : HVP_C_SMEM_COL);
-  const int vi = k45 + 2 * use_global;
-  if (max_blocks[vi] < 0) {
-    cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0, nsm = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem) != cudaSuccess) per_sm = 0;
-    max_blocks[vi] = per_sm * nsm;
+  int st = c->pcg_cfg.tangent_staging, cp = c->pcg_cfg.ctas_per_sm;
+  if (st == MPML_PCG_AUTO || cp == 0) {
+    const int cached = tile_cache_lookup_fmt(pcg_cache_format(k45), c->ncb);
+    if (cached >= 0) {
+      if (st == MPML_PCG_AUTO) st = cached / 2 + 1;
+      if (cp == 0) cp = cached % 2 + 1;
+    }
   }
-  if (max_blocks[vi] <= 0) return MPML_ERR_CUDA;
-  const int G = max_blocks[vi];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return MPML_ERR_CUDA;
+  }
+  if (st == MPML_PCG_AUTO) st = (!k45 && c->ncb > 4 * 2 * (int64_t)n) ? MPML_PCG_STREAMED : MPML_PCG_STAGED;
+  const int streamed = st == MPML_PCG_STREAMED;
+  const int fit = launch_fit(pcg_kernel(k45, streamed), 256, pcg_smem(k45, streamed), LS_PCG + k45 + 2 * streamed,
+                             nullptr);
+  if (fit <= 0) return MPML_ERR_CUDA;
+  if (cp == 0) cp = fit;
+  if (cp > fit) return MPML_ERR_ARG;
+  *staging = st;
+  *ctas = cp;
+  *nsm = n;
+  return MPML_OK;
+}
+
+// One cooperative launch of the persistent solver with the given shape;
+// ev0 / ev1 (optional) are recorded around it on the context stream.
+static int pcg_launch(mpml_ctx_s* c, int cg_max, int staging, int ctas, int nsm, cudaEvent_t ev0, cudaEvent_t ev1) {
+  const int k45 = c->compressed ? 0 : 1;
+  const int streamed = staging == MPML_PCG_STREAMED;
+  const void* kfn = pcg_kernel(k45, streamed);
+  const size_t smem = pcg_smem(k45, streamed);
+  const int G = ctas * nsm;
   int rc;
   // barrier words (2 unsigned) followed by the 4 x 2 rotating accumulators
   if ((rc = ensure(c->gbar, 16 + 8 * sizeof(double))) || (rc = ensure(c->np2, sizeof(float) * 3 * c->nb * BV)))
@@ -2604,18 +2631,108 @@ static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
   a.ncb = (int)c->ncb;
   a.nnob = (int)c->nnob;
   a.nb = (int)c->nb;
-  a.cg_max = o->cg_max;
+  a.cg_max = cg_max;
+  a.spins = c->pcg_cfg.barrier_spins ? c->pcg_cfg.barrier_spins : BARRIER_SPINS_DEFAULT;
   a.status = (int*)c->status.p;
   a.pf = c->profiling ? (DevProf*)c->prof.p : nullptr;
   // q starts at zero (the phase-A kernel zeroes it after each use)
   cudaMemsetAsync(c->nq.p, 0, sizeof(float) * 3 * c->nb * BV, c->s);
   void* args[] = {&a};
-  const bool timed = c->profiling && c->pcg_ev[0] && c->pcg_ev[1];
-  if (timed) cudaEventRecord(c->pcg_ev[0], c->s);
+  if (ev0) cudaEventRecord(ev0, c->s);
   rc = cuda_status(cudaLaunchCooperativeKernel(kfn, dim3(G), dim3(256), args, smem, c->s));
-  if (timed) cudaEventRecord(c->pcg_ev[1], c->s);
+  if (ev1) cudaEventRecord(ev1, c->s);
   c->launches++;
+  c->pcg_last_staging = staging;
+  c->pcg_last_ctas = ctas;
   return rc;
+}
+
+static int pcg_persistent(mpml_ctx_s* c, const mpml_solver_opts* o) {
+  int staging = 0, ctas = 0, nsm = 0, rc;
+  if ((rc = pcg_shape(c, &staging, &ctas, &nsm))) return rc;
+  const bool timed = c->profiling && c->pcg_ev[0] && c->pcg_ev[1];
+  return pcg_launch(c, o->cg_max, staging, ctas, nsm, timed ? c->pcg_ev[0] : nullptr, timed ? c->pcg_ev[1] : nullptr);
+}
+
+// Persistent-solver autotuner (mpml_autotune_pcg): linearises at the current
+// iterate, then every shape runs `iters` CG iterations of that system from the
+// same start (x, r, p and the
+// scalars are saved before and restored after each run, with the stopping
+// tolerance cleared so that every shape runs all iterations); best of reps.
+int pcg_autotune(mpml_ctx_s* c, int iters, int reps, int* choice, float* ms) {
+  if (c->fp64 || !c->have_lin) return MPML_ERR_ARG;
+  if (iters < 1) iters = 1;
+  if (reps < 1) reps = 1;
+  for (int k = 0; k < MPML_PCG_SHAPES; ++k)
+    if (ms) ms[k] = -1.f;
+  if (c->ncb == 0) {
+    if (choice) *choice = 0;
+    return MPML_OK;
+  }
+  const int k45 = c->compressed ? 0 : 1;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || nsm <= 0) {
+    cudaGetLastError();
+    return MPML_ERR_CUDA;
+  }
+  const size_t vb = sizeof(float) * 3 * c->nb * BV;
+  int rc;
+  // the Newton system at the current iterate, with a fresh CG start (x = 0, r = -g)
+  if ((rc = prep_t<float>(c, 1, 1, 1e-6, iters))) return rc;
+  if ((rc = ensure(c->tuneq, 3 * vb + sizeof(DevScalars)))) return rc;
+  char* save = (char*)c->tuneq.p;
+  DevScalars* sv = (DevScalars*)(save + 3 * vb);
+  cudaMemcpyAsync(save, c->nx.p, vb, cudaMemcpyDeviceToDevice, c->s);
+  cudaMemcpyAsync(save + vb, c->nr.p, vb, cudaMemcpyDeviceToDevice, c->s);
+  cudaMemcpyAsync(save + 2 * vb, c->np.p, vb, cudaMemcpyDeviceToDevice, c->s);
+  cudaMemcpyAsync(sv, c->scal.p, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c->s);
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return MPML_ERR_CUDA;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return MPML_ERR_CUDA;
+  }
+  auto restore = [&]() {
+    cudaMemcpyAsync(c->nx.p, save, vb, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(c->nr.p, save + vb, vb, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(c->np.p, save + 2 * vb, vb, cudaMemcpyDeviceToDevice, c->s);
+    cudaMemcpyAsync(c->scal.p, sv, sizeof(DevScalars), cudaMemcpyDeviceToDevice, c->s);
+  };
+  float best = 0.f;
+  int arg = -1;
+  for (int shape = 0; shape < MPML_PCG_SHAPES && !rc; ++shape) {
+    const int staging = shape / 2 + 1, ctas = shape % 2 + 1, streamed = staging == MPML_PCG_STREAMED;
+    const int fit = launch_fit(pcg_kernel(k45, streamed), 256, pcg_smem(k45, streamed), LS_PCG + k45 + 2 * streamed,
+                               nullptr);
+    if (fit < ctas) continue;
+    float tbest = -1.f;
+    for (int i = 0; i <= reps && !rc; ++i) {
+      restore();
+      cudaMemsetAsync(&((DevScalars*)c->scal.p)->tol2, 0, sizeof(double), c->s);
+      cudaMemsetAsync(&((DevScalars*)c->scal.p)->done, 0, sizeof(int), c->s);
+      if ((rc = pcg_launch(c, iters, staging, ctas, nsm, a, b))) break;
+      if ((rc = cuda_status(cudaEventSynchronize(b)))) break;
+      float e = 0.f;
+      cudaEventElapsedTime(&e, a, b);
+      if (i > 0 && (tbest < 0.f || e < tbest)) tbest = e;  // the first run is a warm-up
+    }
+    if (rc) break;
+    if (ms) ms[shape] = tbest;
+    if (arg < 0 || tbest < best) {
+      best = tbest;
+      arg = shape;
+    }
+  }
+  restore();
+  const int rc2 = cuda_status(cudaStreamSynchronize(c->s));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if (arg < 0) return MPML_ERR_CUDA;
+  if (choice) *choice = arg;
+  tile_cache_store_fmt(pcg_cache_format(k45), c->ncb, arg, best);
+  return MPML_OK;
 }
 
 // after the solve has been read back: add the launch's event time and iterations

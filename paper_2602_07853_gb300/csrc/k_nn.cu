@@ -328,14 +328,12 @@ int nn_ensure(mpml_ctx_s* c) {
   return MPML_OK;
 }
 
+// shared-memory limits of the convolution kernels, once per device
 static void set_conv_attrs() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_conv<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, HALO_BYTES + W_BYTES);
-  cudaFuncSetAttribute(k_conv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, HALO_BYTES + W_BYTES);
-  cudaFuncSetAttribute(k_conv<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, HALO_BYTES + W_BYTES);
-  cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, HALO_BYTES + BV * 32);
-  done = true;
+  launch_fit((const void*)k_conv<0>, 256, HALO_BYTES + W_BYTES, LS_CONV + 0, nullptr);
+  launch_fit((const void*)k_conv<1>, 256, HALO_BYTES + W_BYTES, LS_CONV + 1, nullptr);
+  launch_fit((const void*)k_conv<2>, 256, HALO_BYTES + W_BYTES, LS_CONV + 2, nullptr);
+  launch_fit((const void*)k_conv_wgrad, 256, HALO_BYTES + BV * 32, LS_CONV + 3, nullptr);
 }
 
 int nn_refresh_weights(mpml_ctx_s* c) {

@@ -18,21 +18,25 @@
 //
 // Scratch: one file-scope device array of MPML_NOALLOC_MAX_SLOTS counters,
 // as many start offsets, the scan's block sums and a status word (about
-// 16 MiB).  The CUDA runtime places it in every device's memory when the
-// library's code is loaded there, and it stays until the process exits.  The
-// host never dereferences the symbol: on the first call on a device (with
-// that device current) cudaGetSymbolAddress gives its device address, which
-// is cached per device and passed to the kernels.  Every call clears the
-// counters and the status word it uses, so a call never sees a previous
-// call's data; but all calls on one device share the array, so two calls
-// whose kernels overlap on the GPU (different streams, or different host
-// threads) race and give wrong results.
+// 16 MiB).  The CUDA runtime places it in a device's memory when it loads the
+// library's code there -- by default lazily, at the first use of the library
+// on that device, which may be this entry point's first call -- and it stays
+// until the process exits.  So the first call on a device (or any earlier
+// library call there) must come before an arena claims the device's memory
+// and before any stream capture.  The host never dereferences the symbol:
+// every call asks cudaGetSymbolAddress (a host-side lookup that allocates
+// nothing once the code is loaded) for its address on the current device and
+// passes that to the kernels, so the address stays right after a
+// cudaDeviceReset reloads the code.  Every call clears the counters and the
+// status word it uses, so a call never sees a previous call's data; but all
+// calls on one device share the array, so two calls whose kernels overlap on
+// the GPU (different streams, or different host threads) race and give wrong
+// results.
 #include <cuda_runtime.h>
 
 #include <climits>
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 
 #include "mpml.h"
 
@@ -54,7 +58,6 @@ constexpr int64_t NA_INTS = NA_OFF_STATUS + 64;
 
 constexpr int NA_ST_OUT_OF_DOMAIN = 1;
 constexpr int NA_ST_NONFINITE = 2;
-constexpr int NA_MAX_DEVICES = 64;
 
 static __device__ __align__(256) int na_scratch[NA_INTS];
 
@@ -173,48 +176,84 @@ __global__ void k_na_scatter(int64_t np, const T* __restrict__ x, NaGrid g, int*
   if (k >= 0) perm[atomicAdd(&cursor[k], 1)] = (int32_t)p;
 }
 
-// Within one centre the scatter order is arbitrary: restore input order
-// (insertion sort; a centre holds a handful of particles).
-__global__ void k_na_order_segments(int64_t nslots, const int* start, int32_t* perm, int64_t* keys) {
+// Within one centre the scatter order is arbitrary: restore input order.
+// A thread sorts the segment of its centre in place when it is short (at most
+// NA_SEG_SHORT particles, insertion sort); longer segments are queued in shared
+// memory and sorted by the whole block: up to NA_SEG_SMEM particles are staged
+// in shared memory and each goes to its rank (the indices in a segment are
+// distinct), O(k^2 / 256) per block; a segment longer than that (compressed
+// material with thousands of particles in one centre) falls back to one
+// thread's insertion sort, O(k^2).
+constexpr int NA_SEG_SHORT = 32;
+constexpr int NA_SEG_SMEM = 4096;
+
+__global__ void __launch_bounds__(256) k_na_order_segments(int64_t nslots, const int* start, int32_t* perm,
+                                                           int64_t* keys) {
+  __shared__ int64_t s_queue[256];
+  __shared__ int s_nq;
+  __shared__ int32_t s_seg[NA_SEG_SMEM];
+  if (threadIdx.x == 0) s_nq = 0;
+  __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nslots) return;
-  const int s = start[k], e = start[k + 1];
-  for (int i = s + 1; i < e; ++i) {
-    const int32_t v = perm[i];
-    int j = i - 1;
-    while (j >= s && perm[j] > v) {
-      perm[j + 1] = perm[j];
-      --j;
+  if (k < nslots) {
+    const int s = start[k], e = start[k + 1];
+    if (e - s <= NA_SEG_SHORT) {
+      for (int i = s + 1; i < e; ++i) {
+        const int32_t v = perm[i];
+        int j = i - 1;
+        while (j >= s && perm[j] > v) {
+          perm[j + 1] = perm[j];
+          --j;
+        }
+        perm[j + 1] = v;
+      }
+      if (keys)
+        for (int i = s; i < e; ++i) keys[i] = k;
+    } else {
+      s_queue[atomicAdd(&s_nq, 1)] = k;
     }
-    perm[j + 1] = v;
   }
-  if (keys)
-    for (int i = s; i < e; ++i) keys[i] = k;
+  __syncthreads();
+  const int nq = s_nq;
+  for (int qi = 0; qi < nq; ++qi) {
+    const int64_t kk = s_queue[qi];
+    const int s = start[kk], e = start[kk + 1], len = e - s;
+    if (len <= NA_SEG_SMEM) {
+      for (int i = threadIdx.x; i < len; i += blockDim.x) s_seg[i] = perm[s + i];
+      __syncthreads();
+      for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int32_t v = s_seg[i];
+        int r = 0;
+        for (int j = 0; j < len; ++j) r += s_seg[j] < v ? 1 : 0;
+        perm[s + r] = v;
+      }
+      __syncthreads();  // s_seg is reused by the next queued segment
+    } else if (threadIdx.x == 0) {
+      for (int i = s + 1; i < e; ++i) {
+        const int32_t v = perm[i];
+        int j = i - 1;
+        while (j >= s && perm[j] > v) {
+          perm[j + 1] = perm[j];
+          --j;
+        }
+        perm[j + 1] = v;
+      }
+    }
+    if (keys)
+      for (int i = s + (int)threadIdx.x; i < e; i += blockDim.x) keys[i] = kk;
+  }
 }
 
-std::mutex g_na_mutex;
-int* g_na_base[NA_MAX_DEVICES] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device.
+// Device address of the scratch array on the current device (looked up on
+// every call: cheap, allocation-free once the code is loaded, and never stale).
 int na_scratch_base(int** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  int* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress((void**)&p, na_scratch);
+  if (e != cudaSuccess || !p) {
     cudaGetLastError();
     return MPML_ERR_CUDA;
   }
-  if (dev < 0 || dev >= NA_MAX_DEVICES) return MPML_ERR_ARG;
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_base[dev]) {
-    int* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress((void**)&p, na_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return MPML_ERR_CUDA;
-    }
-    g_na_base[dev] = p;
-  }
-  *out = g_na_base[dev];
+  *out = p;
   return MPML_OK;
 }
 

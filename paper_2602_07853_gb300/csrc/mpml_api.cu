@@ -4,10 +4,55 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 
 #include "mpml_internal.cuh"
 
 using namespace mpml;
+
+namespace mpml {
+
+namespace {
+constexpr int LF_MAX_DEVICES = 64;
+std::mutex g_lf_mu;
+int g_lf_fit[LF_MAX_DEVICES][LS_COUNT];
+bool g_lf_init = false;
+}  // namespace
+
+int launch_fit(const void* fn, int threads, size_t smem, int slot, int* nsm) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || slot < 0 || slot >= LS_COUNT) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (nsm) {
+    *nsm = 0;
+    if (cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+  }
+  if (dev < 0 || dev >= LF_MAX_DEVICES) return 0;
+  std::lock_guard<std::mutex> lk(g_lf_mu);
+  if (!g_lf_init) {
+    for (auto& row : g_lf_fit)
+      for (int& v : row) v = -1;
+    g_lf_init = true;
+  }
+  int& fit = g_lf_fit[dev][slot];
+  if (fit < 0) {
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
+    fit = per_sm;
+  }
+  return fit;
+}
+
+}  // namespace mpml
 
 namespace {
 
@@ -650,6 +695,34 @@ int mpml_get_hvp_tile(mpml_ctx c, int* tile, const char** description) {
   if (!c || c->fp64) return MPML_ERR_ARG;
   if (tile) *tile = c->hvp_tile;
   if (description) *description = c->hvp_tile >= 0 ? hvp_tile_name(c->compressed, c->hvp_tile) : "";
+  return MPML_OK;
+}
+
+int mpml_set_pcg_config(mpml_ctx c, const mpml_pcg_config* cfg) {
+  if (!c || !cfg) return MPML_ERR_ARG;
+  if (cfg->tangent_staging < MPML_PCG_AUTO || cfg->tangent_staging > MPML_PCG_STREAMED) return MPML_ERR_ARG;
+  if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 2) return MPML_ERR_ARG;
+  c->pcg_cfg = *cfg;
+  return MPML_OK;
+}
+
+int mpml_get_pcg_config(mpml_ctx c, mpml_pcg_config* cfg, int* last_staging, int* last_ctas_per_sm) {
+  if (!c || !cfg) return MPML_ERR_ARG;
+  *cfg = c->pcg_cfg;
+  if (last_staging) *last_staging = c->pcg_last_staging;
+  if (last_ctas_per_sm) *last_ctas_per_sm = c->pcg_last_ctas;
+  return MPML_OK;
+}
+
+int mpml_autotune_pcg(mpml_ctx c, int iters, int reps, int* shape, float* ms) {
+  if (!c || c->stage < 2) return MPML_ERR_ARG;
+  return pcg_autotune(c, iters, reps, shape, ms);
+}
+
+int mpml_lame_parameters(double E, double nu, double* mu, double* lambda) {
+  if (!mu || !lambda || !(E > 0) || !(nu > -1.0 && nu < 0.5)) return MPML_ERR_ARG;
+  *mu = E / (2.0 * (1.0 + nu));
+  *lambda = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
   return MPML_OK;
 }
 

@@ -178,6 +178,10 @@ struct mpml_ctx_s {
   cudaEvent_t pcg_ev[2] = {nullptr, nullptr};
   int64_t pcg_launches = 0, pcg_iters = 0;
   double pcg_ms = 0.0;
+  // persistent-solver launch controls (mpml_set_pcg_config) and the shape the
+  // last launch used (staging 1 = shared-memory block, 2 = streamed rows)
+  mpml_pcg_config pcg_cfg = {0, 0, 0u};
+  int pcg_last_staging = 0, pcg_last_ctas = 0;
 };
 
 namespace mpml {
@@ -213,6 +217,10 @@ int hvp_autotune(mpml_ctx_s* c, int reps, int* choice, float* ms);
 // process-wide cache of autotuned tiles, keyed by tangent format and brick count
 int tile_cache_lookup(int compressed, int64_t ncb);
 void tile_cache_store(int compressed, int64_t ncb, int tile, float ms);
+int tile_cache_lookup_fmt(int fmt, int64_t ncb);
+void tile_cache_store_fmt(int fmt, int64_t ncb, int tile, float ms);
+// persistent-solver autotuner (mpml_autotune_pcg)
+int pcg_autotune(mpml_ctx_s* c, int iters, int reps, int* choice, float* ms);
 int tile_cache_save(const char* path);
 int tile_cache_load(const char* path);
 void tile_cache_clear();
@@ -236,6 +244,19 @@ int nn_collect(mpml_ctx_s* c, int nsamples, double rtol, int cg_max);
 int nn_train(mpml_ctx_s* c, int epochs, int batch, float lr, double* loss_first, double* loss_last);
 
 inline unsigned div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Per-device launch facts, looked up once per (current device, slot): the
+// first call sets fn's dynamic shared-memory limit to smem on that device and
+// queries how many CTAs of `threads` threads fit on one SM; returns that count
+// (0 when the query fails) and, if nsm is not null, the device's SM count.
+enum LaunchSlot : int {
+  LS_PCG = 0,       // 4 persistent-solver variants: + K45 + 2 * streamed
+  LS_BATCH = 4,
+  LS_HVP64 = 5,
+  LS_CONV = 6,      // 4 convolution kernels of the learned preconditioner
+  LS_COUNT = 10
+};
+int launch_fit(const void* fn, int threads, size_t smem, int slot, int* nsm);
 
 // ---------------------------------------------------------------------------
 // Device math
@@ -433,7 +454,9 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 // 1, so the top bit flips exactly when the last CTA of a round arrives (no
 // proper subset of the adds crosses 2^31) and the low bits return to zero.
 // The last arrival learns it from its own add; the others poll the top bit.
-__device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag) {
+// `limit` bounds the polls of one wait (each after a 32 ns sleep).
+constexpr unsigned BARRIER_SPINS_DEFAULT = 1u << 25;
+__device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag, unsigned limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned add = blockIdx.x == 0 ? 0x80000000u - (gridDim.x - 1u) : 1u;
@@ -443,7 +466,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* gbar, int* s_flag) {
     if ((((old + add) ^ old) & 0x80000000u) == 0u) {
       unsigned spins = 0;
       while (((ld_acquire_gpu(gbar) ^ old) & 0x80000000u) == 0u) {
-        if (++spins > (1u << 25)) {
+        if (++spins > limit) {
           ok = 0;
           break;
         }

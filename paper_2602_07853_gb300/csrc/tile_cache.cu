@@ -1,7 +1,9 @@
-// Process-wide cache of autotuned launch shapes of the standalone FP32 HVP
-// (host code only).  Key: tangent format (25-number compressed or 45-number
-// packed) and floor(log2(active cell bricks)); value: the fastest shape and its
-// mean milliseconds.  Text form, one entry per line: "format log2_bricks tile ms".
+// Process-wide cache of autotuned launch shapes (host code only).  Key: format
+// and floor(log2(active cell bricks)); value: the fastest shape and its
+// milliseconds.  Formats 25 / 45: the standalone FP32 HVP on the compressed /
+// 45-number tangent (shapes 0 .. HVP_TILES-1); 125 / 145: the persistent solver
+// on the same two tangents (shapes 0 .. MPML_PCG_SHAPES-1).  Text form, one
+// entry per line: "format log2_bricks tile ms".
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -32,17 +34,29 @@ int size_class(int64_t ncb) {
 
 int format_of(int compressed) { return compressed ? NQC : 45; }
 
+bool shape_ok(int fmt, int tile) {
+  if (fmt == NQC || fmt == 45) return tile >= 0 && tile < HVP_TILES;
+  if (fmt == 100 + NQC || fmt == 145) return tile >= 0 && tile < MPML_PCG_SHAPES;
+  return false;
+}
+
 }  // namespace
 
-int tile_cache_lookup(int compressed, int64_t ncb) {
+int tile_cache_lookup_fmt(int fmt, int64_t ncb) {
   std::lock_guard<std::mutex> lk(g_mu);
-  auto it = g_cache.find({format_of(compressed), size_class(ncb)});
+  auto it = g_cache.find({fmt, size_class(ncb)});
   return it == g_cache.end() ? -1 : it->second.tile;
 }
 
-void tile_cache_store(int compressed, int64_t ncb, int tile, float ms) {
+void tile_cache_store_fmt(int fmt, int64_t ncb, int tile, float ms) {
   std::lock_guard<std::mutex> lk(g_mu);
-  g_cache[{format_of(compressed), size_class(ncb)}] = Entry{tile, ms};
+  g_cache[{fmt, size_class(ncb)}] = Entry{tile, ms};
+}
+
+int tile_cache_lookup(int compressed, int64_t ncb) { return tile_cache_lookup_fmt(format_of(compressed), ncb); }
+
+void tile_cache_store(int compressed, int64_t ncb, int tile, float ms) {
+  tile_cache_store_fmt(format_of(compressed), ncb, tile, ms);
 }
 
 void tile_cache_clear() {
@@ -76,7 +90,7 @@ int tile_cache_load(const char* path) {
       if (*q != ' ' && *q != '\t' && *q != '\n' && *q != '\r') blank = false;
     if (blank) continue;
     if (std::sscanf(line, "%d %d %d %lf %n", &fmt, &cls, &tile, &ms, &used) != 4 || line[used] != '\0' ||
-        (fmt != NQC && fmt != 45) || cls < 0 || cls > 62 || tile < 0 || tile >= HVP_TILES || !(ms >= 0.0)) {
+        !shape_ok(fmt, tile) || cls < 0 || cls > 62 || !(ms >= 0.0)) {
       bad = true;
       break;
     }

@@ -25,6 +25,8 @@ ELASTIC, VON_MISES, DRUCKER_PRAGER = 0, 1, 2
 FP32, FP64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
+PCG_AUTO, PCG_STAGED, PCG_STREAMED = 0, 1, 2
+PCG_SHAPES = 4  # MPML_PCG_SHAPES
 KEYS_PARTICLES, KEYS_CELLS, KEYS_NODES = 0, 1, 2
 F_CELL_MASS, F_CELL_VEL, F_CELL_VGRAD, F_CELL_VOL, F_CELL_TAU, F_CELL_STRETCH = 0, 1, 2, 3, 4, 5
 F_CELL_VEL_NEW, F_CELL_VGRAD_NEW = 6, 7
@@ -62,6 +64,10 @@ class mpml_solve_stats(C.Structure):
                 ("g0_norm", C.c_double), ("g_norm", C.c_double), ("phi0", C.c_double), ("phi", C.c_double),
                 ("n_particles", C.c_int64), ("n_cells", C.c_int64), ("n_nodes", C.c_int64),
                 ("n_bricks", C.c_int64), ("fcg_fallbacks", C.c_int), ("plastic_projections", C.c_int)]
+
+
+class mpml_pcg_config(C.Structure):
+    _fields_ = [("tangent_staging", C.c_int), ("ctas_per_sm", C.c_int), ("barrier_spins", C.c_uint)]
 
 
 class mpml_train_opts(C.Structure):
@@ -120,6 +126,11 @@ EXPORTS = {
     "mpml_tile_cache_save": (C.c_int, [C.c_char_p]),
     "mpml_tile_cache_load": (C.c_int, [C.c_char_p]),
     "mpml_tile_cache_clear": (None, []),
+    "mpml_set_pcg_config": (C.c_int, [C.c_void_p, C.POINTER(mpml_pcg_config)]),
+    "mpml_get_pcg_config": (C.c_int, [C.c_void_p, C.POINTER(mpml_pcg_config), C.POINTER(C.c_int),
+                                      C.POINTER(C.c_int)]),
+    "mpml_autotune_pcg": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+    "mpml_lame_parameters": (C.c_int, [C.c_double, C.c_double, _D, _D]),
 }
 
 
@@ -328,6 +339,27 @@ def mpml_get_hvp_tile(ctx):
     return tile.value, (desc.value or b"").decode()
 
 
+def mpml_set_pcg_config(ctx, tangent_staging=PCG_AUTO, ctas_per_sm=0, barrier_spins=0):
+    cfg = mpml_pcg_config()
+    cfg.tangent_staging, cfg.ctas_per_sm, cfg.barrier_spins = int(tangent_staging), int(ctas_per_sm), int(barrier_spins)
+    return _check(load().mpml_set_pcg_config(ctx, C.byref(cfg)), "mpml_set_pcg_config")
+
+
+def mpml_get_pcg_config(ctx):
+    """(config dict, staging of the last persistent launch, its CTAs per SM)."""
+    cfg, st, cp = mpml_pcg_config(), C.c_int(), C.c_int()
+    _check(load().mpml_get_pcg_config(ctx, C.byref(cfg), C.byref(st), C.byref(cp)), "mpml_get_pcg_config")
+    return (dict(tangent_staging=cfg.tangent_staging, ctas_per_sm=cfg.ctas_per_sm, barrier_spins=cfg.barrier_spins),
+            st.value, cp.value)
+
+
+def mpml_autotune_pcg(ctx, iters=20, reps=2):
+    """(chosen shape, [ms of each of the PCG_SHAPES shapes, -1 where it does not fit])."""
+    shape, ms = C.c_int(), (C.c_float * PCG_SHAPES)()
+    _check(load().mpml_autotune_pcg(ctx, int(iters), int(reps), C.byref(shape), ms), "mpml_autotune_pcg")
+    return shape.value, [float(v) for v in ms]
+
+
 def mpml_tile_cache_save(path):
     _check(load().mpml_tile_cache_save(os.fsencode(path)), "mpml_tile_cache_save")
 
@@ -394,9 +426,14 @@ def particles_from_tensors(x, v, F, G, mass, volume, mat, perm=None):
     return p
 
 
-def lame_parameters(E, nu):
-    """(mu, lambda) from Young's modulus and Poisson's ratio."""
-    return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+def mpml_lame_parameters(E, nu):
+    """(mu, lambda) from Young's modulus and Poisson's ratio (computed by the library)."""
+    mu, lam = C.c_double(), C.c_double()
+    _check(load().mpml_lame_parameters(float(E), float(nu), C.byref(mu), C.byref(lam)), "mpml_lame_parameters")
+    return mu.value, lam.value
+
+
+lame_parameters = mpml_lame_parameters
 
 
 # ---------------------------------------------------------------------------

@@ -173,12 +173,17 @@ def pressed_block(n: int = 128, seed: int = 3, ppc: int = 8) -> Scene:
     return _finish(sc, x, np.zeros_like(x), np.zeros(len(x), np.int64), ppc)
 
 
-def slab_on_sand(n: int = 256, seed: int = 5, ppc: int = 8, dt: float = 2e-3) -> Scene:
+def slab_on_sand(n: int = 256, seed: int = 5, ppc: int = 8, dt: float = 2e-3, impact: bool = False) -> Scene:
     """A von Mises slab dropped onto a Drucker-Prager sand box (Hencky elasticity).
     Slab 0.6 x 0.1 x 0.6 at x, z in [0.35, 0.95], y in [0.5, 0.6] (E = 5e5, nu = 0.3,
     yield stress 2e3, rho = 1000); sand box 0.55 x 0.35 x 0.55 at x, z in [0.05, 0.6],
     y in [1/256, 0.35 + 1/256] (E = 1e6, nu = 0.3, friction angle 30 degrees, rho = 2000).
-    Box edges are snapped to the voxel grid of size 1/n."""
+    Box edges are snapped to the voxel grid of size 1/n.
+
+    ``impact=True`` starts at the moment of impact instead: the slab's lowest voxel row is
+    one empty row above the sand's top row (so the trilinear stencils of both share a row of
+    cells: mixed cells from the first step) and the slab moves down at the speed of a free
+    fall from its original height, sqrt(2 g dh); the sand is at rest, F = I."""
     dx = 1.0 / n
     sc = Scene(f"slab_on_sand_{n}", (n, n, n), dx, float(n), dt, (0.0, -9.8, 0.0),
                [Material(HENCKY, 5e5, 0.3, 1000.0, VON_MISES, 2e3, 0.0),
@@ -193,20 +198,30 @@ def slab_on_sand(n: int = 256, seed: int = 5, ppc: int = 8, dt: float = 2e-3) ->
     y0 = 1.0 / 256
     slab = box((0.35, 0.5, 0.35), (0.95, 0.6, 0.95))
     sand = box((0.05, max(y0, 1.0 / n), 0.05), (0.6, 0.35 + y0, 0.6))
+    v_slab = 0.0
+    if impact:
+        drop = int(slab[:, 1].min() - (sand[:, 1].max() + 2))  # voxel rows the slab falls
+        slab = slab - np.array([0, drop, 0])
+        v_slab = -float(np.sqrt(2.0 * 9.8 * drop * dx))
     xs = seed_voxels(slab, dx, ppc, rng)
     xb = seed_voxels(sand, dx, ppc, rng)
     x = np.concatenate([xs, xb])
     mat = np.concatenate([np.zeros(len(xs), np.int64), np.ones(len(xb), np.int64)])
-    return _finish(sc, x, np.zeros_like(x), mat, ppc)
+    v = np.zeros_like(x)
+    v[:len(xs), 1] = v_slab
+    if impact:
+        sc.name += "_impact"
+    return _finish(sc, x, v, mat, ppc)
 
 
 def batch_scene(index: int, n: int = 64, ppc: int = 8, dt: float = 1e-3,
-                extent: Optional[int] = None) -> Scene:
+                extent: Optional[int] = None, row: int = 2) -> Scene:
     """Scene ``index`` of the many-scene batch: its own n^3 unit domain, one fixed-corotated
     shape dropped onto the floor at 1 m/s.  Seeded with 4 + index: extent e ~ U{8..48} voxels
     (or ``extent``), shape box (e^3) / sphere (diameter e) / torus (R = 0.3 e, r = 0.15 e),
     E log-uniform in [1e4, 1e7] Pa, nu uniform in [0.2, 0.45]; the shape is centred in x, z
-    with its lowest voxel in row 2, so that it reaches the sticky floor within about 8 steps."""
+    with its lowest voxel in row ``row``: row 2 reaches the sticky floor after a short fall,
+    row 1 touches it from the first step (the cells of that row reach node layer 0)."""
     rng = np.random.Generator(np.random.PCG64(4 + index))
     e = int(rng.integers(8, 49)) if extent is None else int(extent)
     shape = int(rng.integers(0, 3))
@@ -215,7 +230,7 @@ def batch_scene(index: int, n: int = 64, ppc: int = 8, dt: float = 1e-3,
     dx = 1.0 / n
     sc = Scene(f"batch_{index}_{['box', 'sphere', 'torus'][shape]}{e}", (n, n, n), dx, float(n), dt,
                (0.0, -9.8, 0.0), [Material(FIXED_COROTATED, E, nu)])
-    lo = np.array([(n - e) // 2, 2, (n - e) // 2])
+    lo = np.array([(n - e) // 2, row, (n - e) // 2])
     g = _grid_voxels(lo, lo + e)
     c = (g + 0.5 - lo - e / 2.0)  # voxel centres relative to the shape centre, in voxels
     if shape == 1:

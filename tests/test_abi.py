@@ -61,8 +61,8 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "mpml.h"
 int main(void){
- printf("%zu %zu %zu %zu %zu\n", sizeof(mpml_scene_desc), sizeof(mpml_material), sizeof(mpml_particles),
-        sizeof(mpml_solver_opts), sizeof(mpml_solve_stats));
+ printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mpml_scene_desc), sizeof(mpml_material), sizeof(mpml_particles),
+        sizeof(mpml_solver_opts), sizeof(mpml_solve_stats), sizeof(mpml_pcg_config));
  printf("%zu %zu %zu %zu\n", offsetof(mpml_scene_desc, plate_vel), offsetof(mpml_particles, perm),
         offsetof(mpml_solve_stats, g0_norm), offsetof(mpml_solve_stats, n_bricks));
  return 0;}
@@ -73,7 +73,7 @@ int main(void){
     sizes = [int(v) for v in lines[0].split()]
     offs = [int(v) for v in lines[1].split()]
     assert sizes == [ctypes.sizeof(t) for t in (m.mpml_scene_desc, m.mpml_material, m.mpml_particles,
-                                                 m.mpml_solver_opts, m.mpml_solve_stats)]
+                                                 m.mpml_solver_opts, m.mpml_solve_stats, m.mpml_pcg_config)]
     assert offs == [m.mpml_scene_desc.plate_vel.offset, m.mpml_particles.perm.offset,
                     m.mpml_solve_stats.g0_norm.offset, m.mpml_solve_stats.n_bricks.offset]
 
@@ -94,3 +94,27 @@ def test_noalloc_sort_rejects_on_the_host(lib_path):
     assert f(n_ok, 128.0, m.FP32, dummy, 1 << 31, dummy, None, None) == m.ERR_ARG
     assert f((ctypes.c_int * 3)(1, 8, 8), 128.0, m.FP32, dummy, 10, dummy, None, None) == m.ERR_ARG
     assert lib.mpml_status_str(m.ERR_TOO_LARGE).decode().startswith("size above")
+
+
+def test_lame_parameters_in_the_library(lib_path):
+    """mpml_lame_parameters (host code): the pair it returns gives back E and nu through the
+    inverse relations E = mu (3 lambda + 2 mu) / (lambda + mu), nu = lambda / (2 (lambda + mu));
+    invalid moduli are rejected."""
+    import paper_2602_07853_gb300.mpml as m
+    for E, nu in ((1e5, 0.3), (1e8, 0.33), (5e5, 0.0), (1e6, 0.45), (2e3, -0.2)):
+        mu, lam = m.mpml_lame_parameters(E, nu)
+        assert abs(mu * (3 * lam + 2 * mu) / (lam + mu) - E) <= 1e-12 * E
+        assert abs(lam / (2 * (lam + mu)) - nu) <= 1e-12
+    for E, nu in ((0.0, 0.3), (1e5, 0.5), (1e5, -1.0), (float("nan"), 0.3)):
+        with pytest.raises(m.MPMLError) as e:
+            m.mpml_lame_parameters(E, nu)
+        assert e.value.code == m.ERR_ARG
+
+
+def test_pcg_config_rejects_on_the_host(lib_path):
+    import paper_2602_07853_gb300.mpml as m
+    lib = m.load()
+    cfg = m.mpml_pcg_config()
+    assert lib.mpml_set_pcg_config(None, ctypes.byref(cfg)) == m.ERR_ARG
+    assert lib.mpml_get_pcg_config(None, ctypes.byref(cfg), None, None) == m.ERR_ARG
+    assert lib.mpml_autotune_pcg(None, 10, 1, None, None) == m.ERR_ARG

@@ -26,8 +26,11 @@ def test_reference_arm_line():
     assert d["impl"] == "reference"
     assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["unit"] == "steps/s" and d["higher_is_better"] is True
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) <= 1e-6 * d["ms_per_step"]
+    # ms_per_step: wall time of one timed sample (what ran); value: the sample scaled to a full step
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert abs(d["extrapolated_ms_per_step"] - 1e3 / d["value"]) <= 1e-6 * d["extrapolated_ms_per_step"]
     assert isinstance(d["config"], dict) and "workload" in d["config"]
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert cb["host"]["nproc"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

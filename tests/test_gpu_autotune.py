@@ -10,7 +10,7 @@ import torch
 import paper_2602_07853_gb300.mpml as m
 from paper_2602_07853_gb300 import scenes
 from tests._util import make_oracle
-from tests._gpu import GpuSim, rel_err
+from tests._gpu import GpuSim, check
 
 pytestmark = pytest.mark.gpu
 
@@ -60,14 +60,14 @@ def test_every_tile_matches_the_oracle_and_the_tuner_picks_the_fastest(kind, tmp
         m.mpml_set_hvp_tile(g.ctx, t)
         tile, desc = m.mpml_get_hvp_tile(g.ctx)
         assert tile == t and desc
-        assert rel_err(m.mpml_hvp(g.ctx, p), want) <= 1e-5, (t, desc)
+        check(m.mpml_hvp(g.ctx, p), want, 1e-5, (t, desc))
     m.mpml_set_hvp_tile(g.ctx, -1)
     tile, ms = m.mpml_autotune_hvp(g.ctx, 3)
     assert 0 <= tile < m.HVP_TILES
     assert all(t > 0 for t in ms) and ms[tile] == min(ms)
     assert m.mpml_get_hvp_tile(g.ctx)[0] == tile
     # the autotuner leaves the linearisation and the solver vectors usable
-    assert rel_err(m.mpml_hvp(g.ctx, p), want) <= 1e-5
+    check(m.mpml_hvp(g.ctx, p), want, 1e-5, 'hvp')
     path = tmp_path / "tiles.txt"
     m.mpml_tile_cache_save(path)
     rows = [l.split() for l in open(path)]
@@ -89,7 +89,7 @@ def test_graph_solve_autotunes_and_matches_the_persistent_solver():
     assert 0 <= tile < m.HVP_TILES  # chosen on the first graph-driven solve
     va, vb = a.field(m.F_NODE_VNEW), b.field(m.F_NODE_VNEW)
     vhat = a.field(m.F_NODE_VHAT)
-    assert rel_err(va - vhat, vb - vhat) <= 1e-4
+    check(va - vhat, vb - vhat, 1e-4, 'v_new - vhat')
     # a second context of the same format and size takes the cached choice
     c = GpuSim(sc, m.FP32)
     c.set_particles()

@@ -17,7 +17,7 @@ import torch
 import paper_2602_07853_gb300.mpml as m
 from paper_2602_07853_gb300 import scenes
 from tests._util import make_oracle
-from tests._gpu import GpuSim, rel_err
+from tests._gpu import GpuSim, OracleSim, check
 
 pytestmark = pytest.mark.gpu
 
@@ -69,7 +69,7 @@ def test_batch_matches_single_scene_solves():
             assert sb.g_norm <= max(1e-6 * sb.g0_norm, 1e-11)
         for g, gr in zip(sims, ref):
             v_b, v_1 = g.field(m.F_NODE_VNEW), gr.field(m.F_NODE_VNEW)
-            assert rel_err(v_b, v_1) <= 1e-4
+            check(v_b, v_1, 1e-4, 'v_new batch vs single')
             g.g2p()
             gr.g2p()
     # the shapes reached the sticky floor: some scene needed Newton iterations with contact
@@ -84,12 +84,10 @@ def test_batch_scene_against_oracle():
     g, h = GpuSim(sc, m.FP32), GpuSim(other, m.FP32)
     g.set_particles()
     h.set_particles()
-    o = make_oracle(sc)
-    p_o = g.inputs()
+    o = OracleSim(make_oracle(sc), g.inputs())
     for step in range(3):
         t = step * sc.dt
-        o.set_time(t)
-        rc, p_o, _ = o.step(p_o)
+        rc, _ = o.step(t)
         assert rc >= 0
         for s in (g, h):
             m.mpml_set_time(s.ctx, t)
@@ -98,7 +96,7 @@ def test_batch_scene_against_oracle():
         assert rc >= 0
         g.g2p()
         h.g2p()
-    err = np.abs(g.particles()["x"] - p_o["x"]).max()
+    err = np.abs(g.particles_by_identity()["x"] - o.particles_by_identity()["x"]).max()
     assert err <= 1e-4 * sc.dx, err
     g.close()
     h.close()

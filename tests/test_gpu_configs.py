@@ -12,7 +12,7 @@ import torch
 import paper_2602_07853_gb300.mpml as m
 from paper_2602_07853_gb300 import scenes
 from tests._util import make_oracle
-from tests._gpu import GpuSim, rel_err
+from tests._gpu import GpuSim, OracleSim, check
 
 pytestmark = pytest.mark.gpu
 
@@ -25,21 +25,20 @@ def _cuda():
 
 
 def run_steps(sc, precision, steps):
+    """Both sides step the scene; particles returned by identity (see by_identity)."""
     g = GpuSim(sc, precision)
     g.set_particles()
-    o = make_oracle(sc)
-    p_o = g.inputs()
+    o = OracleSim(make_oracle(sc), g.inputs())
     newton = []
     for s in range(steps):
-        o.set_time(s * sc.dt)
-        rc, p_o, st_o = o.step(p_o)
+        rc, st_o = o.step(s * sc.dt)
         assert rc >= 0
         rc_g, st_g = g.step(s * sc.dt)
         assert rc_g >= 0
         newton.append((st_g.newton_iters, st_o.newton_iters))
-    got = g.particles()
+    got = g.particles_by_identity()
     g.close()
-    return got, p_o, newton
+    return got, o.particles_by_identity(), newton
 
 
 @pytest.mark.parametrize("precision", [m.FP64, m.FP32])
@@ -81,7 +80,7 @@ def test_two_spheres_fp32_against_fp64_path():
         g.close()
     p64, v64, st64 = out[m.FP64]
     p32, v32, st32 = out[m.FP32]
-    assert rel_err(v32, v64) <= 1e-4  # both Newton solves stop at 1e-6
+    check(v32, v64, 1e-4, 'v_new fp32 vs fp64')  # both Newton solves stop at 1e-6
     assert np.abs(p32["x"] - p64["x"]).max() <= 1e-4 * sc.dx
     assert abs(st32.newton_iters - st64.newton_iters) <= 1
 

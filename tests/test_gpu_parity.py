@@ -1,9 +1,12 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (derived in the design doc):
+Tolerances:
   - integer work (keys, sort order, active cells, DOF nodes): bit-exact;
-  - FP32 transfers / stretch / energy / gradient / HVP: norm-relative error
-    <= 1e-5 per field (the gradient/HVP bound of the workload statement);
+  - FP32 transfers / stretch / energy / gradient / HVP: <= 1e-5 per field, both
+    norm-relative and as the largest element error relative to the field's
+    largest element (FP32 sums of at most 64 weighted terms round to about
+    64 * 2^-24 = 4e-6 of their largest term; 1e-5 is also the workload's
+    gradient / HVP bound);
   - FP64 path: <= 1e-10;
   - positions after 10 steps: <= 1e-4 dx.
 """
@@ -15,7 +18,7 @@ import oracle
 import paper_2602_07853_gb300.mpml as m
 from paper_2602_07853_gb300 import scenes
 from tests._util import make_oracle
-from tests._gpu import GpuSim, rel_err
+from tests._gpu import GpuSim, OracleSim, check, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -75,8 +78,7 @@ def test_unload_fields(precision):
     pairs = [(m.F_CELL_MASS, "m_c"), (m.F_CELL_VEL, "v_c"), (m.F_CELL_VGRAD, "G_c"), (m.F_CELL_VOL, "V_ck"),
              (m.F_CELL_TAU, "tau_ck"), (m.F_NODE_MASS, "m_i"), (m.F_NODE_VEL, "v_i"), (m.F_NODE_VHAT, "vhat")]
     for f, name in pairs:
-        e = rel_err(g.field(f), o.field(name))
-        assert e <= tol, (name, e)
+        check(g.field(f), o.field(name), tol, name)
     g.close()
 
 
@@ -91,7 +93,7 @@ def test_stretch_energy_gradient_hvp(precision):
     S_g, S_o = g.field(m.F_CELL_STRETCH), o.field("S_ck")
     V = o.field("V_ck")
     mask = V > 0
-    assert rel_err(S_g[mask] - np.eye(3), S_o[mask] - np.eye(3)) <= tol
+    check(S_g[mask] - np.eye(3), S_o[mask] - np.eye(3), tol, 'S - I')
     nn = o.count("nodes")
     rng = np.random.default_rng(5)
     v = o.field("vhat") + 0.05 * rng.standard_normal((nn, 3))
@@ -99,10 +101,10 @@ def test_stretch_energy_gradient_hvp(precision):
     phi_o, g_o = o.eval(v)
     phi_g, g_g = m.mpml_eval(g.ctx, v)
     assert abs(phi_g - phi_o) <= tol * abs(phi_o)
-    assert rel_err(g_g, g_o) <= tol
+    check(g_g, g_o, tol, 'gradient')
     o.linearize(v, project=True)
     p = rng.standard_normal((nn, 3)).astype(g.npdt).astype(np.float64)
-    assert rel_err(m.mpml_hvp(g.ctx, p), o.hvp(p)) <= tol
+    check(m.mpml_hvp(g.ctx, p), o.hvp(p), tol, 'hvp')
     g.close()
 
 
@@ -179,7 +181,7 @@ def test_hvp_and_solve_with_node_only_bricks(precision):
     o.linearize(v)
     m.mpml_linearize(g.ctx, v)
     p = np.random.default_rng(1).standard_normal((nn, 3)).astype(g.npdt).astype(np.float64)
-    assert rel_err(m.mpml_hvp(g.ctx, p), o.hvp(p)) <= TOL[precision]
+    check(m.mpml_hvp(g.ctx, p), o.hvp(p), TOL[precision], 'hvp')
     rc_o, st_o = o.newton(oracle.default_solver())
     rc, st = g.newton(m.solver_opts())
     assert rc == 0 and rc_o == 0
@@ -199,7 +201,7 @@ def test_newton_step_solution(precision):
     assert st.newton_iters >= 1
     v_g, v_o = g.field(m.F_NODE_VNEW), o.field("v_new")
     # both solves stop at relative residual 1e-6: the solutions agree to that order
-    assert rel_err(v_g - o.field("vhat"), v_o - o.field("vhat")) <= 1e-4
+    check(v_g - o.field("vhat"), v_o - o.field("vhat"), 1e-4, 'v_new - vhat')
     g.close()
 
 
@@ -215,10 +217,10 @@ def test_load_given_same_node_velocity(precision):
     g.g2p()
     got = g.particles()
     tol = TOL[precision]
-    assert rel_err(g.field(m.F_CELL_VEL_NEW), o.field("v_c_new")) <= tol
-    assert rel_err(g.field(m.F_CELL_VGRAD_NEW), o.field("G_c_new")) <= tol
+    check(g.field(m.F_CELL_VEL_NEW), o.field("v_c_new"), tol, 'v_c_new')
+    check(g.field(m.F_CELL_VGRAD_NEW), o.field("G_c_new"), tol, 'G_c_new')
     for k in ("v", "G", "F"):
-        assert rel_err(got[k], out[k]) <= tol, k
+        check(got[k], out[k], tol, k)
     assert np.abs(got["x"] - out["x"]).max() <= (1e-6 if precision == m.FP32 else 1e-14)
     assert np.array_equal(got["mat"], out["mat"])
     g.close()
@@ -232,16 +234,14 @@ def test_ten_steps_positions(variant, precision):
     sc = scenes.elastic_cube(variant)
     g = GpuSim(sc, precision)
     g.set_particles()
-    o = make_oracle(sc)
-    p_o = g.inputs()
+    o = OracleSim(make_oracle(sc), g.inputs())
     for s in range(10):
-        o.set_time(s * sc.dt)
-        rc, p_o, st_o = o.step(p_o)
+        rc, st_o = o.step(s * sc.dt)
         assert rc >= 0
         rc_g, st_g = g.step(s * sc.dt)
         assert rc_g >= 0
-    got = g.particles()
-    err = np.abs(got["x"] - p_o["x"]).max()
+    got, ref = g.particles_by_identity(), o.particles_by_identity()
+    err = np.abs(got["x"] - ref["x"]).max()
     assert err <= 1e-4 * sc.dx, err
     g.close()
 
@@ -301,17 +301,17 @@ def test_full_size_two_spheres():
     assert np.array_equal(g.keys(m.KEYS_CELLS), o.cell_keys())
     assert np.array_equal(g.keys(m.KEYS_NODES), o.node_keys())
     for f, name in ((m.F_CELL_MASS, "m_c"), (m.F_NODE_MASS, "m_i"), (m.F_NODE_VEL, "v_i")):
-        assert rel_err(g.field(f), o.field(name)) <= 1e-5
+        check(g.field(f), o.field(name), 1e-5, name)
     assert o.stretch() == 0
     m.mpml_stretch(g.ctx)
     # operator parity at full size, linearised at vhat
     vhat = o.field("vhat")
     phi_o, g_o = o.eval(vhat)
     phi_g, g_g = m.mpml_eval(g.ctx, vhat)
-    assert rel_err(g_g, g_o) <= 1e-5
+    check(g_g, g_o, 1e-5, 'gradient')
     o.linearize(vhat)
     p = np.random.default_rng(3).standard_normal(vhat.shape).astype(np.float32).astype(np.float64)
-    assert rel_err(m.mpml_hvp(g.ctx, p), o.hvp(p)) <= 1e-5
+    check(m.mpml_hvp(g.ctx, p), o.hvp(p), 1e-5, 'hvp')
     rc, st = g.newton(m.solver_opts())
     assert rc == 0, (rc, st.newton_iters, list(st.cg_iters[:st.newton_iters]))
     v_g = g.field(m.F_NODE_VNEW)
@@ -347,24 +347,24 @@ def test_material_mixtures_up_to_the_slot_limit(precision, nmat):
     g, o, _ = both(sc, precision)
     tol = TOL[precision]
     for f, name in [(m.F_CELL_VOL, "V_ck"), (m.F_CELL_TAU, "tau_ck"), (m.F_NODE_MASS, "m_i"), (m.F_NODE_VEL, "v_i")]:
-        assert rel_err(g.field(f), o.field(name)) <= tol, name
+        check(g.field(f), o.field(name), tol, name)
     assert o.stretch() == 0
     m.mpml_stretch(g.ctx)
     V = o.field("V_ck")
     mask = V > 0
     assert (mask.sum(axis=1) >= 3).any()  # cells that hold three or more materials
     S_g, S_o = g.field(m.F_CELL_STRETCH), o.field("S_ck")
-    assert rel_err(S_g[mask] - np.eye(3), S_o[mask] - np.eye(3)) <= tol
+    check(S_g[mask] - np.eye(3), S_o[mask] - np.eye(3), tol, 'S - I')
     nn = o.count("nodes")
     rng = np.random.default_rng(12)
     v = (o.field("vhat") + 0.05 * rng.standard_normal((nn, 3))).astype(g.npdt).astype(np.float64)
     phi_o, g_o = o.eval(v)
     phi_g, g_g = m.mpml_eval(g.ctx, v)
     assert abs(phi_g - phi_o) <= tol * abs(phi_o)
-    assert rel_err(g_g, g_o) <= tol
+    check(g_g, g_o, tol, 'gradient')
     o.linearize(v, project=True)
     p = rng.standard_normal((nn, 3)).astype(g.npdt).astype(np.float64)
-    assert rel_err(m.mpml_hvp(g.ctx, p), o.hvp(p)) <= tol
+    check(m.mpml_hvp(g.ctx, p), o.hvp(p), tol, 'hvp')
     g.close()
 
 

@@ -1,0 +1,232 @@
+"""The solver paths the large workloads run, and the solver's failure reports, on the GPU.
+
+- Every launch shape of the persistent Jacobi-PCG kernel (tangent block staged in shared
+  memory or streamed from global memory, one or two CTAs per SM), forced through
+  mpml_set_pcg_config, on both tangent formats, against the FP64 oracle's Newton solution
+  (both stop at relative residual 1e-6: compared at 1e-4 on v - vhat, element by element).
+- Full-size solves of the 3-8M pressed block (1,051,200 active cells, about 2,100 cell bricks:
+  the streamed kernel) and of the 256^3 slab on sand at impact (19.2M particles, 2.5M cells:
+  the staged 45-number kernel, 16+ bricks per CTA): the oracle's own FP64 gradient at the GPU
+  solution is within the Newton tolerance of its gradient at the start.
+- The slab on sand at impact, reduced to 64^3 (mixed slab / sand cells from the first step,
+  plastic flow in both materials), stepped through the impact against the oracle.
+- A batch of 16 scenes of uneven size in one lockstep solve against per-scene oracle steps.
+- Failure reports (Algorithm 3's solve must report them): a grid-barrier wait that runs out
+  (MPML_ERR_TIMEOUT, context usable afterwards), a stress that no stretch can produce
+  (MPML_ERR_STRETCH, as the oracle reports), a Newton cap that is too small
+  (MPML_WARN_NOT_CONVERGED).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2602_07853_gb300.mpml as m
+from paper_2602_07853_gb300 import scenes
+from tests._util import make_oracle
+from tests._gpu import GpuSim, OracleSim, check
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(m.PCG_STAGED, 1), (m.PCG_STAGED, 2), (m.PCG_STREAMED, 1), (m.PCG_STREAMED, 2)]
+
+
+@pytest.fixture(autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def oracle_solution(sc):
+    o = make_oracle(sc)
+    inp = {k: (v.astype(np.float64) if k != "mat" else v) for k, v in sc.particles(np.float32).items()}
+    assert o.unload(**inp) == 0
+    assert o.stretch() == 0
+    rc, st = o.newton(oracle.default_solver())
+    assert rc == 0
+    return o, st
+
+
+@pytest.mark.parametrize("name", ["pressed_block_32", "stretched_cube", "slab_on_sand_32_impact"])
+def test_every_persistent_shape_matches_the_oracle(name):
+    sc = {"pressed_block_32": lambda: scenes.pressed_block(32),
+          "stretched_cube": lambda: scenes.elastic_cube("stretched"),
+          "slab_on_sand_32_impact": lambda: scenes.slab_on_sand(32, impact=True)}[name]()
+    o, st_o = oracle_solution(sc)
+    assert st_o.newton_iters >= 1
+    vhat, v_o = o.field("vhat"), o.field("v_new")
+    for staging, ctas in SHAPES:
+        g = GpuSim(sc, m.FP32)
+        g.set_particles()
+        m.mpml_set_pcg_config(g.ctx, staging, ctas)
+        g.resample()
+        rc, st = g.newton()
+        assert rc == 0, (staging, ctas, rc)
+        _, last_staging, last_ctas = m.mpml_get_pcg_config(g.ctx)
+        assert (last_staging, last_ctas) == (staging, ctas)
+        check(g.field(m.F_NODE_VNEW) - vhat, v_o - vhat, 1e-4, f"v_new - vhat ({name}, staging {staging}, {ctas}/SM)")
+        g.close()
+
+
+def full_size_gradient_check(sc, expect_staging):
+    """GPU Newton solve at full size; the oracle's FP64 gradient at the GPU solution."""
+    g = GpuSim(sc, m.FP32)
+    g.set_particles()
+    o = make_oracle(sc)
+    assert o.unload(**g.inputs()) == 0
+    g.resample()
+    assert np.array_equal(g.keys(m.KEYS_CELLS), o.cell_keys())
+    assert o.stretch() == 0
+    # the oracle's gradient norm at the Newton start v0 (vhat with the Dirichlet values imposed)
+    _, st0 = o.newton(oracle.default_solver(newton_max=0))
+    g0 = st0.g0_norm
+    assert g0 > 0
+    rc, st = g.newton()
+    assert rc == 0, (rc, st.newton_iters, list(st.cg_iters[:st.newton_iters]))
+    assert st.newton_iters >= 1
+    _, last_staging, _ = m.mpml_get_pcg_config(g.ctx)
+    assert last_staging == expect_staging
+    v_g = g.field(m.F_NODE_VNEW)
+    g.close()
+    _, g1 = o.eval(v_g)
+    ratio = np.linalg.norm(g1) / g0
+    assert ratio <= 2e-6, ratio
+    return st
+
+
+def test_full_size_pressed_block_236_streamed_solver():
+    """Config 3 at dx = 1/236 (7.9M particles): above eight cell bricks per SM the compressed
+    tangent is streamed (the automatic rule), a path smaller scenes reach only when forced."""
+    full_size_gradient_check(scenes.pressed_block(236), m.PCG_STREAMED)
+
+
+def test_full_size_slab_on_sand_256_at_impact():
+    """Config 5 (256^3, 19.2M particles, two plastic materials) at impact: the staged 45-number
+    persistent solver with many bricks per CTA."""
+    full_size_gradient_check(scenes.slab_on_sand(256, impact=True), m.PCG_STAGED)
+
+
+@pytest.mark.parametrize("precision", [m.FP32, m.FP64])
+def test_slab_on_sand_through_the_impact(precision):
+    """Config 5 reduced to 64^3 (288,608 particles) from the moment of impact: 4 steps with
+    mixed slab / sand cells, Newton with line search, and the von Mises / Drucker-Prager
+    return maps in G2P; positions within 1e-4 dx of the oracle and F element by element."""
+    sc = scenes.slab_on_sand(64, impact=True)
+    g = GpuSim(sc, precision)
+    g.set_particles()
+    o = OracleSim(make_oracle(sc), g.inputs())
+    newton = 0
+    for s in range(4):
+        rc, st_o = o.step(s * sc.dt)
+        assert rc >= 0
+        rc_g, st_g = g.step(s * sc.dt)
+        assert rc_g == 0
+        assert st_g.newton_iters == st_o.newton_iters
+        newton += st_g.newton_iters
+    assert newton >= 4
+    V = o.o.field("V_ck")
+    assert ((V > 0).sum(axis=1) == 2).any()  # mixed slab / sand cells
+    got, ref = g.particles_by_identity(), o.particles_by_identity()
+    err = np.abs(got["x"] - ref["x"]).max()
+    assert err <= 1e-4 * sc.dx, err
+    check(got["F"] - np.eye(3), ref["F"] - np.eye(3), 1e-4 if precision == m.FP32 else 1e-9, "F - I after 4 steps")
+    check(got["v"], ref["v"], 1e-4 if precision == m.FP32 else 1e-9, "v after 4 steps")
+    g.close()
+
+
+def test_batch_of_16_uneven_scenes_against_the_oracle():
+    """16 scenes of extents 6..21 voxels (boxes, spheres, tori; ~200 to ~80k particles) on their
+    own 32^3 grids with seeded random velocity, velocity gradient and deformation (so every
+    scene solves a nonlinear system from the first step), two lockstep batched steps against
+    each scene's oracle steps."""
+    scs = [scenes.random_state(scenes.batch_scene(i, n=32, extent=6 + i), 100 + i, v_scale=0.05, G_scale=0.5,
+                               F_scale=0.01) for i in range(16)]
+    sims = [GpuSim(sc, m.FP32) for sc in scs]
+    for g in sims:
+        g.set_particles()
+    orcs = [OracleSim(make_oracle(sc), g.inputs()) for sc, g in zip(scs, sims)]
+    for step in range(2):
+        for o, sc in zip(orcs, scs):
+            rc, _ = o.step(step * sc.dt)
+            assert rc >= 0
+        for g in sims:
+            m.mpml_set_time(g.ctx, step * g.sc.dt)
+            g.resample()
+        rc, stats = m.mpml_newton_step_batch([g.ctx for g in sims])
+        assert rc == 0
+        assert all(s.newton_iters >= 1 for s in stats)
+        for g in sims:
+            g.g2p()
+    for g, o, sc in zip(sims, orcs, scs):
+        got, p = g.particles_by_identity(), o.particles_by_identity()
+        err = np.abs(got["x"] - p["x"]).max()
+        assert err <= 1e-4 * sc.dx, (sc.name, err)
+        check(got["v"], p["v"], 1e-4, f"v ({sc.name})")
+        g.close()
+
+
+def test_grid_barrier_timeout_is_reported_and_the_context_recovers():
+    """A bound of one poll per grid-barrier wait: CTAs give up waiting for the others, the
+    persistent solve ends early, and mpml_newton_step reports MPML_ERR_TIMEOUT.  After the next
+    resample (which clears the latched status) the default bound solves normally."""
+    sc = scenes.two_spheres(64, gap=1.0 / 64)
+    g = GpuSim(sc, m.FP32)
+    g.set_particles()
+    g.resample()
+    m.mpml_set_pcg_config(g.ctx, barrier_spins=1)
+    with pytest.raises(m.MPMLError) as e:
+        g.newton()
+    assert e.value.code == m.ERR_TIMEOUT
+    m.mpml_set_pcg_config(g.ctx)
+    g.resample()
+    rc, st = g.newton()
+    assert rc == 0 and st.newton_iters >= 1
+    g.close()
+
+
+def test_batched_grid_barrier_timeout_is_reported():
+    scs = [scenes.random_state(scenes.batch_scene(i, n=32, extent=6 + i), 200 + i, v_scale=0.05) for i in range(3)]
+    sims = [GpuSim(sc, m.FP32) for sc in scs]
+    for g in sims:
+        g.set_particles()
+        g.resample()
+    m.mpml_set_pcg_config(sims[0].ctx, barrier_spins=1)
+    with pytest.raises(m.MPMLError) as e:
+        m.mpml_newton_step_batch([g.ctx for g in sims])
+    assert e.value.code == m.ERR_TIMEOUT
+    for g in sims:
+        g.close()
+
+
+@pytest.mark.parametrize("precision", [m.FP32, m.FP64])
+def test_unrecoverable_compression_reports_stretch_error(precision):
+    """Fixed-corotated particles compressed to F = 0.6 I (J = 0.216): the cell stress has no
+    stretch on the admissible branch (J >= 1/2).  The device latches the error and
+    mpml_newton_step returns MPML_ERR_STRETCH, as the oracle's stretch reconstruction does."""
+    sc = scenes.elastic_cube("fall")
+    sc.F = np.tile(0.6 * np.eye(3), (sc.num_particles, 1, 1))
+    o = make_oracle(sc)
+    assert o.unload(**{k: (v.astype(np.float64) if k != "mat" else v)
+                       for k, v in sc.particles(np.float32).items()}) == 0
+    assert o.stretch() == m.ERR_STRETCH
+    g = GpuSim(sc, precision)
+    g.set_particles()
+    g.resample()
+    with pytest.raises(m.MPMLError) as e:
+        g.newton()
+    assert e.value.code == m.ERR_STRETCH
+    g.close()
+
+
+def test_newton_cap_reports_not_converged():
+    """The pressed block needs more than one Newton iteration per step: with newton_max = 1
+    the step returns MPML_WARN_NOT_CONVERGED (a warning: the iterate is still usable)."""
+    sc = scenes.pressed_block(32)
+    g = GpuSim(sc, m.FP32)
+    g.set_particles()
+    g.resample()
+    rc, st = g.newton(m.solver_opts(newton_max=1))
+    assert rc == m.WARN_NOT_CONVERGED
+    assert st.newton_iters == 1 and st.g_norm > 1e-6 * st.g0_norm
+    g.close()
