@@ -181,6 +181,16 @@ def pcg_bytes_per_iter(n_cells, n_nodes, tangent_bytes=CMP_TANGENT_BYTES):
     return tangent_bytes * n_cells + (28.0 + 120.0) * n_nodes
 
 
+def pcg_kernel_name(k45, staging, ctas):
+    """The persistent solver kernel a launch shape runs (staging 1 shared-memory block, 2 streamed
+    rows, 3 column groups)."""
+    fmt = "K45" if k45 else "compressed"
+    if staging == 3:
+        return f"k_pcg_groups<{fmt}> (one brick per 64-thread group, {ctas} CTAs/SM)"
+    kind = "staged" if staging == 1 else "streamed"
+    return f"k_pcg_persistent<{fmt}, {kind}> ({ctas} CTAs/SM)"
+
+
 def pcg_floor_bytes_per_iter(n_cells, n_nodes):
     """The same with the algorithmic floor of the HVP: the state that defines a cell's Hessian
     (F 9, S 6, V 1 numbers: 64 B per active cell, the tangent recomputed) instead of the stored one."""
@@ -392,6 +402,7 @@ def trajectory(m, sc, warmup, steps, peaks, opts=None, tangent_bytes=None):
 
     for s in range(warmup):
         one(s)
+    tune_shape, tune_ms = m.mpml_autotune_pcg(ctx, 30, 2)
     torch.cuda.synchronize()
     m.mpml_set_profiling(ctx, 1)
     ms, newton, cg, fb, alg = [], 0, 0, 0, 0.0
@@ -416,12 +427,14 @@ def trajectory(m, sc, warmup, steps, peaks, opts=None, tangent_bytes=None):
     out = {"particles": int(cn["particles"]), "active_cells": int(cn["cells"]), "dof_nodes": int(cn["nodes"]),
            "steps_per_s": 1e3 * len(ms) / float(np.sum(ms)), "ms_per_step": float(np.mean(ms)),
            "newton_iters_per_step": newton / len(ms), "cg_iters_per_step": cg / len(ms),
-           "steps_timed": f"trajectory steps {warmup}..{warmup + steps - 1}"}
+           "steps_timed": f"trajectory steps {warmup}..{warmup + steps - 1}",
+           "pcg_autotune": {"chosen": tune_shape,
+                            "us_per_cg_iter": [round(1e3 * t / 30, 2) if t >= 0 else None for t in tune_ms]}}
     if fb:
         out["fcg_fallbacks_per_step"] = fb / len(ms)
     if pcg_n > 0 and pcg_iters > 0:
         gbs = alg / (pcg_ms / 1e3) / 1e9 if pcg_iters == cg else None
-        out["pcg_kernel"] = {"shape": f"{'staged' if last_staging == 1 else 'streamed'} tangent, {last_ctas} CTAs/SM",
+        out["pcg_kernel"] = {"shape": pcg_kernel_name(tb == PACKED_TANGENT_BYTES, last_staging, last_ctas),
                              "us_per_cg_iter": 1e3 * pcg_ms / pcg_iters, "launches": pcg_n,
                              "gbs": gbs, "frac": gbs / peaks["hbm_gbs"] if gbs else None,
                              "bytes_rule": f"{int(tb)} B per active cell + 148 B per DOF node per CG iteration"}
@@ -676,6 +689,9 @@ def run_ours(args, rank, world, local_rank):
     # warm-up: trajectory steps 0 .. W-1 from the moment of impact
     for s in range(W):
         one_step(ctx, parts, s)
+    # the persistent solver's launch shape, autotuned on the last warm-up system (untimed; the
+    # choice is cached for this tangent format and size class and used by the timed steps)
+    tune_shape, tune_ms = m.mpml_autotune_pcg(ctx, 30, 2) if W > 0 else (None, [])
     barrier()
     m.mpml_set_profiling(ctx, 1)
     launches0 = m.mpml_kernel_launches(ctx)
@@ -743,8 +759,7 @@ def run_ours(args, rank, world, local_rank):
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": tr["dram_bytes_per_launch_scaled"] if tr else None,
                 "peak_kind": peak_kind + " (hbm_gbs of MEASURED_PEAKS.json)" if peak_kind == "measured" else peak_kind,
-                "kernel": f"k_pcg_persistent<K45, {'staged' if last_staging == 1 else 'streamed'}> "
-                          f"({last_ctas} CTAs/SM)",
+                "kernel": pcg_kernel_name(True, last_staging, last_ctas),
                 "launches_timed": pcg_n, "mean_launch_ms": mean_ms, "cg_iters_per_launch": pcg_iters / pcg_n,
                 "bytes_per_cg_iter_rule": "180 B per active cell (45-number tangent) + 28 B (HVP) + 120 B (CG "
                                           "vector passes) per DOF node",
@@ -816,6 +831,10 @@ def run_ours(args, rank, world, local_rank):
                 "cg_iters_per_step": float(np.mean(cg_its)),
                 "newton_iters_per_s": float(np.sum(newton_its)) / (total_ms / 1e3),
                 "per_step": per_step, "step_ms": step_ms,
+                "pcg_autotune": {"chosen": tune_shape, "shapes": [list(sh) for sh in m.PCG_SHAPE_TABLE],
+                                 "us_per_cg_iter": [round(1e3 * t / 30, 2) if t >= 0 else None for t in tune_ms],
+                                 "rule": "30 CG iterations of the last warm-up Newton system per shape, best of 2; "
+                                         "shape = (staging 1 staged / 2 streamed / 3 column groups, CTAs per SM)"},
                 "hvp_gbs": hvp["gbs"] if hvp else None, "hvp": hvp, "learned_precond": learned,
                 "other_configs": others,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

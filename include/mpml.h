@@ -317,27 +317,35 @@ int mpml_tile_cache_load(const char* path);
 void mpml_tile_cache_clear(void);
 
 /* Persistent-solver launch controls -------------------------------------
- * Not in the paper.  The persistent Jacobi-PCG kernel (use_graph = 2) brings
- * each cell brick's tangent block in one of two ways:
- *   MPML_PCG_STAGED    one bulk copy of the whole block into shared memory per
- *                      brick (kept there for the solve when a CTA owns one brick)
- *   MPML_PCG_STREAMED  the rows are read from global memory as the column walk
- *                      needs them (no shared-memory block)
+ * Not in the paper.  The persistent Jacobi-PCG kernel (use_graph = 2) applies
+ * the tangent of each cell brick in one of three ways:
+ *   MPML_PCG_STAGED    the CTA's 256 threads work on one brick at a time; its
+ *                      whole tangent block comes in by one bulk copy into
+ *                      shared memory (kept there for the solve when a CTA owns
+ *                      one brick)
+ *   MPML_PCG_STREAMED  the same, with the rows read from global memory as the
+ *                      column walk needs them (no shared-memory block)
+ *   MPML_PCG_COLUMNS   each 64-thread group of a CTA works on a brick of its
+ *                      own, rows streamed from global memory (four bricks in
+ *                      flight per CTA, up to four CTAs per SM)
  *   MPML_PCG_AUTO      the shape mpml_autotune_pcg chose for this tangent format
- *                      and size class, else a fixed rule (streamed for the
- *                      compressed tangent above 8 bricks per SM, staged otherwise)
- * ctas_per_sm: CTAs per SM of the cooperative launch (0 = as many as fit; a
- *   value above what fits is MPML_ERR_ARG at the next solve).
+ *                      and size class, else a fixed rule: above 8 cell bricks
+ *                      per SM streamed for the compressed tangent and column
+ *                      groups for the 45-number one, staged otherwise
+ * ctas_per_sm: CTAs per SM of the cooperative launch (0 = as many as fit, at
+ *   most 2 for the first two forms and 4 for the third; a value above what
+ *   fits is MPML_ERR_ARG at the next solve).
  * barrier_spins: bound on the polls of one grid-barrier wait (0 = the default
  *   2^25 polls of 32 ns, about a second).  A wait that runs out ends the solve:
  *   mpml_newton_step returns MPML_ERR_TIMEOUT; the next mpml_resample clears the
  *   latched status and the context is usable again.  A bound of a few polls
  *   makes the waits run out on purpose (how the tests exercise that path).
  * The configuration applies to every later solve of the context (also the
- * learned solver's Jacobi fallback).  mpml_get_pcg_config returns it, and in
+ * learned solver's Jacobi fallback; the batched solver uses ctas_per_sm and
+ * barrier_spins of its first context).  mpml_get_pcg_config returns it, and in
  * last_staging / last_ctas_per_sm (either may be NULL) the shape the last
  * persistent launch used (0 before the first). */
-enum { MPML_PCG_AUTO = 0, MPML_PCG_STAGED = 1, MPML_PCG_STREAMED = 2 };
+enum { MPML_PCG_AUTO = 0, MPML_PCG_STAGED = 1, MPML_PCG_STREAMED = 2, MPML_PCG_COLUMNS = 3 };
 typedef struct {
   int tangent_staging;
   int ctas_per_sm;
@@ -346,17 +354,18 @@ typedef struct {
 int mpml_set_pcg_config(mpml_ctx ctx, const mpml_pcg_config* cfg);
 int mpml_get_pcg_config(mpml_ctx ctx, mpml_pcg_config* cfg, int* last_staging, int* last_ctas_per_sm);
 
-/* Persistent-solver autotuner: times MPML_PCG_SHAPES shapes of the persistent
- * solve (staged or streamed tangent x 1 or 2 CTAs per SM; shapes that do not
- * fit are skipped, their time reported as -1) on the current Newton system:
- * each runs `iters` Jacobi-PCG iterations from the same start (the solver's
- * state is restored afterwards), CUDA events on the context stream, best of
- * `reps`.  The fastest becomes the context's shape under MPML_PCG_AUTO and is
- * recorded in the process-wide tile cache under format 125 (compressed) or
- * 145 (45 numbers) and log2 of the cell bricks.  Shape index =
- * (staging - 1) * 2 + (ctas_per_sm - 1).  FP32 contexts after a linearisation
- * (mpml_linearize or mpml_newton_step), MPML_ERR_ARG otherwise.  Synchronising. */
-#define MPML_PCG_SHAPES 4
+/* Persistent-solver autotuner: times the MPML_PCG_SHAPES shapes of the
+ * persistent solve (index: 0 staged x 1 CTA/SM, 1 staged x 2, 2 streamed x 1,
+ * 3 streamed x 2, 4 column groups x 2, 5 column groups x 3, 6 column groups
+ * x 4; shapes that do not fit are skipped, their time reported as -1) on the
+ * Newton system at the current iterate: each runs `iters` Jacobi-PCG
+ * iterations from the same start (the solver's state is restored afterwards),
+ * CUDA events on the context stream, best of `reps`.  The fastest becomes the
+ * context's shape under MPML_PCG_AUTO and is recorded in the process-wide tile
+ * cache under format 125 (compressed) or 145 (45 numbers) and log2 of the cell
+ * bricks.  FP32 contexts after a linearisation (mpml_linearize or
+ * mpml_newton_step), MPML_ERR_ARG otherwise.  Synchronising. */
+#define MPML_PCG_SHAPES 7
 int mpml_autotune_pcg(mpml_ctx ctx, int iters, int reps, int* shape, float* ms);
 
 /* Lame parameters of an isotropic material from Young's modulus E > 0 and

@@ -2551,34 +2551,389 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
   }
 }
 
-// The four kernels of the persistent solver: tangent format x staging.
-static const void* pcg_kernel(int k45, int streamed) {
+// ---------------------------------------------------------------------------
+// Persistent Jacobi-PCG, column-group form: the same iteration and phases as
+// k_pcg_persistent, but in phase H each 64-thread group of a CTA owns a brick
+// of its own (group g of CTA b takes the cell bricks b * 4 + g + k * 4 G): it
+// stages p_new on the brick's 9^3 node block (fused p update, as above) in its
+// own shared memory and walks the 64 z-columns of cells with the tangent rows
+// streamed from global memory (thread (x, y) walks column (x, y): lower and
+// upper node layers in registers, node sums along x by shuffles, along y by
+// shuffles and one row exchange per layer, a 64-thread named barrier per
+// layer).  Four independent bricks per CTA and four CTAs per SM keep about
+// 45 outstanding tangent loads per thread in flight without any block-wide
+// barrier inside phase H.
+// ---------------------------------------------------------------------------
+struct ColGroup {
+  float sv[3][729];          // p_new on the 9^3 node block
+  float sxr[2][2][3][8];     // [z parity][E, E8 of row 3][a][x]
+  int nbr[NBR];
+  int pad;
+};
+
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory");
+}
+
+template <bool K45>
+__global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
+  constexpr int NQ = K45 ? 45 : NQC;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ ColGroup gs[4];
+  __shared__ int s_flag;
+  __shared__ float s_coef;
+  __shared__ int s_stop;
+  __shared__ double s_rz, s_rr_last, s_tol2;
+  DevScalars* sc = A.sc;
+  const int g = threadIdx.x >> 6, t = threadIdx.x & 63, x = t & 7, y = t >> 3, row = y & 3;
+  ColGroup& S = gs[g];
+  const int G = gridDim.x, NG = 4 * G, gid = 4 * (int)blockIdx.x + g;
+  if (threadIdx.x == 0) {
+    s_rz = sc->rz;
+    s_tol2 = sc->tol2;
+    s_rr_last = sc->rr_last;
+  }
+  int done = sc->done;
+  int it = 0;
+  float beta = 0.f;
+  float* pold = A.pa;
+  float* pnext = A.pb;
+  bool alive = true;
+  __syncthreads();
+  while (!done && alive) {
+    const unsigned long long t_h0 = (A.pf && blockIdx.x == 0 && threadIdx.x == 0) ? gtimer() : 0ull;
+    // ---------------- phase H ----------------
+    float pmp = 0.f, pkp = 0.f;
+    for (int jc = gid; jc < A.ncb; jc += NG) {
+      const int id = A.cblist[jc];
+      if (t < NBR) S.nbr[t] = A.nbr[id * NBR + t];
+      group_sync(g);
+      // p_new on the 9^3 node block, three nodes per thread and batch, all loads first
+      for (int i0 = t; i0 < 729; i0 += 3 * 64) {
+        int tb[3], ll[3];
+        float dv[3][3], rv[3][3], pv[3][3], mv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int i = i0 + 64 * k;
+          tb[k] = -1;
+          ll[k] = 0;
+          mv[k] = 0.f;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) dv[k][a] = rv[k][a] = pv[k][a] = 0.f;
+          if (i < 729) {
+            const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+            const int tt = (nx < 8 && ny < 8 && nz < 8) ? id : S.nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+            const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
+            tb[k] = tt;
+            ll[k] = l;
+            if (tt >= 0) {
+              const int64_t o = (int64_t)tt * 3 * BV + l;
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                dv[k][a] = __ldcg(A.dinv + o + a * BV);
+                rv[k][a] = __ldcg(A.r + o + a * BV);
+                pv[k][a] = __ldcg(pold + o + a * BV);
+              }
+              if (tt == id) mv[k] = __ldcg(A.m + (int64_t)id * BV + l);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int i = i0 + 64 * k;
+          if (i >= 729) continue;
+          float v[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) v[a] = dv[k][a] > 0.f ? dv[k][a] * rv[k][a] + beta * pv[k][a] : 0.f;
+          if (tb[k] == id) {
+            const int64_t o = (int64_t)id * 3 * BV + ll[k];
+            pnext[o] = v[0];
+            pnext[o + BV] = v[1];
+            pnext[o + 2 * BV] = v[2];
+            pmp += mv[k] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+          }
+          S.sv[0][i] = v[0];
+          S.sv[1][i] = v[1];
+          S.sv[2][i] = v[2];
+        }
+      }
+      group_sync(g);
+      // the z-column walk of this thread's column (x, y)
+      const float* Kb = A.C + (int64_t)id * NQ * BV;
+      const uint8_t* cf = A.cflag + (int64_t)id * BV;
+      float P0[2][2][3], Cz[2][2][3];
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+        for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            P0[ox][oy][a] = S.sv[a][hidx(x + ox, y + oy, 0)];
+            Cz[ox][oy][a] = 0.f;
+          }
+#pragma unroll 1
+      for (int z = 0; z <= 8; ++z) {
+        float N[2][2][3];
+        if (z < 8) {
+          float P1[2][2][3];
+#pragma unroll
+          for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+            for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+              for (int a = 0; a < 3; ++a) P1[ox][oy][a] = S.sv[a][hidx(x + ox, y + oy, z + 1)];
+          const int l = (z * 8 + y) * 8 + x;
+          float KD[9];
+#pragma unroll
+          for (int r = 0; r < 9; ++r) KD[r] = 0.f;
+          if (cf[l]) {
+            float D[9];
+            col_D(P0, P1, D);
+            if (K45) {
+              float k[45];
+#pragma unroll
+              for (int qq = 0; qq < 45; ++qq) k[qq] = ld_stream(Kb + qq * BV + l);
+#pragma unroll
+              for (int r = 0; r < 9; ++r) {
+                KD[r] += k[k45(r, r)] * D[r];
+#pragma unroll
+                for (int cc = r + 1; cc < 9; ++cc) {
+                  KD[r] += k[k45(r, cc)] * D[cc];
+                  KD[cc] += k[k45(r, cc)] * D[r];
+                }
+              }
+            } else {
+              float c[NQC];
+#pragma unroll
+              for (int qq = 0; qq < NQC; ++qq) c[qq] = ld_stream(Kb + qq * BV + l);
+              apply_cmp(c, D, KD);
+            }
+#pragma unroll
+            for (int r = 0; r < 9; ++r) pkp += D[r] * KD[r];
+          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float X = KD[3 * a], Yv = KD[3 * a + 1], Z = KD[3 * a + 2];
+            const float Ap = X + Yv, B = X - Yv;
+            N[1][1][a] = Cz[1][1][a] + (Ap - Z);
+            N[0][0][a] = Cz[0][0][a] - (Ap + Z);
+            N[1][0][a] = Cz[1][0][a] + (B - Z);
+            N[0][1][a] = Cz[0][1][a] - (B + Z);
+            Cz[1][1][a] = Ap + Z;
+            Cz[0][0][a] = Z - Ap;
+            Cz[1][0][a] = B + Z;
+            Cz[0][1][a] = Z - B;
+          }
+#pragma unroll
+          for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+            for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+              for (int a = 0; a < 3; ++a) P0[ox][oy][a] = P1[ox][oy][a];
+        } else {
+#pragma unroll
+          for (int ox = 0; ox < 2; ++ox)
+#pragma unroll
+            for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+              for (int a = 0; a < 3; ++a) N[ox][oy][a] = Cz[ox][oy][a];
+        }
+        // along x by shuffles; along y by shuffles of eight lanes and the row 3 -> 4
+        // exchange (double-buffered by z parity: one barrier per layer)
+        float E[2][3], E8[2][3];
+#pragma unroll
+        for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float left = __shfl_up_sync(FULL, N[1][oy][a], 1);
+            E[oy][a] = N[0][oy][a] + (x > 0 ? left : 0.f);
+            E8[oy][a] = N[1][oy][a];
+          }
+        const int buf = z & 1;
+        if (y == 3) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            S.sxr[buf][0][a][x] = E[1][a];
+            S.sxr[buf][1][a][x] = E8[1][a];
+          }
+        }
+        group_sync(g);
+        float T[3], T8[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float up = __shfl_up_sync(FULL, E[1][a], 8), up8 = __shfl_up_sync(FULL, E8[1][a], 8);
+          float prev = 0.f, prev8 = 0.f;
+          if (row > 0) {
+            prev = up;
+            prev8 = up8;
+          } else if (y == 4) {
+            prev = S.sxr[buf][0][a][x];
+            prev8 = S.sxr[buf][1][a][x];
+          }
+          T[a] = E[0][a] + prev;
+          T8[a] = E8[0][a] + prev8;
+        }
+        col_emit_m(id, S.nbr, S.sv, A.m, A.q, x, y, z, T);
+        if (x == 7) col_emit_m(id, S.nbr, S.sv, A.m, A.q, 8, y, z, T8);
+        if (y == 7) {
+          col_emit_m(id, S.nbr, S.sv, A.m, A.q, x, 8, z, E[1]);
+          if (x == 7) col_emit_m(id, S.nbr, S.sv, A.m, A.q, 8, 8, z, E8[1]);
+        }
+      }
+      group_sync(g);  // S.sv and S.nbr are reused by the group's next brick
+    }
+    // bricks with DOF nodes but no cells: p_new and the mass term
+    for (int jn = G - 1 - (int)blockIdx.x; jn < A.nnob; jn += G) {
+      const int id = A.nolist[jn];
+      for (int l = threadIdx.x; l < BV; l += blockDim.x) {
+        const int64_t o = (int64_t)id * 3 * BV + l;
+        const float v0 = pnew_at(A, o, beta, pold), v1 = pnew_at(A, o + BV, beta, pold),
+                    v2 = pnew_at(A, o + 2 * BV, beta, pold);
+        pnext[o] = v0;
+        pnext[o + BV] = v1;
+        pnext[o + 2 * BV] = v2;
+        const float mi = A.m[(int64_t)id * BV + l];
+        pmp += mi * (v0 * v0 + v1 * v1 + v2 * v2);
+        if (v0 != 0.f) atomicAdd(A.q + o, mi * v0);
+        if (v1 != 0.f) atomicAdd(A.q + o + BV, mi * v1);
+        if (v2 != 0.f) atomicAdd(A.q + o + 2 * BV, mi * v2);
+      }
+    }
+    double* accH = A.acc + 2 * ((2 * it) & 3);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double* zz = A.acc + 2 * ((2 * it + 2) & 3);
+      zz[0] = 0.0;
+      zz[1] = 0.0;
+    }
+    block_atomic2(pmp, pkp, accH);
+    if (!grid_barrier(A.gbar, &s_flag, A.spins)) {
+      alive = false;
+      break;
+    }
+    if (threadIdx.x == 0) {
+      const double pq = __ldcg(accH) + __ldcg(accH + 1);
+      s_stop = !(pq > 0.0);
+      s_coef = s_stop ? 0.f : (float)(s_rz / pq);
+      if (A.pf && blockIdx.x == 0) {
+        A.pf->ns += gtimer() - t_h0;
+        A.pf->count += 1;
+      }
+    }
+    __syncthreads();
+    if (s_stop) {
+      done = 1;
+      break;
+    }
+    const float alpha = s_coef;
+    // ---------------- phase A ----------------
+    float rzl = 0.f, rrl = 0.f;
+    for (int jb = blockIdx.x; jb < A.nb; jb += G) {
+      float2 d2[3], p2[3], q2[3], x2[3], r2[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
+        d2[a] = __ldcg(reinterpret_cast<const float2*>(A.dinv + o));
+        p2[a] = __ldcg(reinterpret_cast<const float2*>(pnext + o));
+        q2[a] = __ldcg(reinterpret_cast<const float2*>(A.q + o));
+        x2[a] = __ldcg(reinterpret_cast<const float2*>(A.x + o));
+        r2[a] = __ldcg(reinterpret_cast<const float2*>(A.r + o));
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
+        const float2 d = d2[a], pp = p2[a], qq = q2[a];
+        float2 xx = x2[a], rr = r2[a];
+        if (d.x > 0.f) {
+          xx.x += alpha * pp.x;
+          rr.x -= alpha * qq.x;
+        }
+        if (d.y > 0.f) {
+          xx.y += alpha * pp.y;
+          rr.y -= alpha * qq.y;
+        }
+        *reinterpret_cast<float2*>(A.x + o) = xx;
+        *reinterpret_cast<float2*>(A.r + o) = rr;
+        *reinterpret_cast<float2*>(A.q + o) = make_float2(0.f, 0.f);
+        rzl += (d.x > 0.f ? rr.x * d.x * rr.x : 0.f) + (d.y > 0.f ? rr.y * d.y * rr.y : 0.f);
+        rrl += (d.x > 0.f ? rr.x * rr.x : 0.f) + (d.y > 0.f ? rr.y * rr.y : 0.f);
+      }
+    }
+    double* accA = A.acc + 2 * ((2 * it + 1) & 3);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double* zz = A.acc + 2 * ((2 * it + 3) & 3);
+      zz[0] = 0.0;
+      zz[1] = 0.0;
+    }
+    block_atomic2(rzl, rrl, accA);
+    if (!grid_barrier(A.gbar, &s_flag, A.spins)) {
+      alive = false;
+      break;
+    }
+    ++it;
+    if (threadIdx.x == 0) {
+      const double rzn = __ldcg(accA), rrn = __ldcg(accA + 1);
+      s_rr_last = rrn;
+      s_stop = (rrn <= s_tol2 || it >= A.cg_max || !(rrn == rrn)) ? 1 : 0;
+      s_coef = (float)(rzn / s_rz);
+      s_rz = rzn;
+    }
+    __syncthreads();
+    done = s_stop;
+    beta = s_coef;
+    float* tmp = pold;
+    pold = pnext;
+    pnext = tmp;
+  }
+  if (!alive && threadIdx.x == 0) atomicOr(A.status, ST_TIMEOUT);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sc->iters = it;
+    sc->rr_last = s_rr_last;
+    sc->rz = s_rz;
+    sc->done = 1;
+  }
+}
+
+// The kernels of the persistent solver: tangent format x staging (1 shared-memory
+// block, 2 streamed rows, 3 column groups).
+static const void* pcg_kernel(int k45, int staging) {
+  if (staging == MPML_PCG_COLUMNS) return k45 ? (const void*)k_pcg_groups<true> : (const void*)k_pcg_groups<false>;
+  const bool streamed = staging == MPML_PCG_STREAMED;
   return k45 ? (streamed ? (const void*)k_pcg_persistent<true, true> : (const void*)k_pcg_persistent<true>)
              : (streamed ? (const void*)k_pcg_persistent<false, true> : (const void*)k_pcg_persistent<false>);
 }
 
-static size_t pcg_smem(int k45, int streamed) {
-  return streamed ? sizeof(float) * (3 * 729 + HVP_X_FLOATS + HVP_R_FLOATS) + 32 : (k45 ? HVP_K_SMEM45 : HVP_C_SMEM_COL);
+static size_t pcg_smem(int k45, int staging) {
+  if (staging == MPML_PCG_COLUMNS) return 0;  // static shared memory only
+  return staging == MPML_PCG_STREAMED ? sizeof(float) * (3 * 729 + HVP_X_FLOATS + HVP_R_FLOATS) + 32
+                                      : (k45 ? HVP_K_SMEM45 : HVP_C_SMEM_COL);
 }
+
+static int pcg_slot(int k45, int staging) { return LS_PCG + k45 + 2 * (staging - 1); }
+
+// the autotuner's shapes: (staging, CTAs per SM)
+static const int PCG_SHAPE_TABLE[MPML_PCG_SHAPES][2] = {
+    {MPML_PCG_STAGED, 1},  {MPML_PCG_STAGED, 2},  {MPML_PCG_STREAMED, 1}, {MPML_PCG_STREAMED, 2},
+    {MPML_PCG_COLUMNS, 2}, {MPML_PCG_COLUMNS, 3}, {MPML_PCG_COLUMNS, 4}};
 
 // tile-cache format keys of the persistent solver's shapes (the standalone HVP uses 25 and 45)
 static int pcg_cache_format(int k45) { return k45 ? 145 : 125; }
 
 // The shape (staging, CTAs per SM) of the next persistent launch: the context's
 // explicit configuration, else the autotuned shape cached for this format and
-// size class, else the fixed rule -- the compressed tangent is streamed from
-// global memory beyond eight cell bricks per SM (measured 9% faster per CG
-// iteration on the 3-8M pressed block, equal at 168^3; the 45-number tangent
-// keeps the shared-memory copy, 2% faster on the 256^3 slab on sand), and as
-// many CTAs per SM as fit.
+// size class, else the fixed rule -- beyond eight cell bricks per SM the
+// compressed tangent is streamed from global memory (83 vs 90 us per CG
+// iteration on the 3-8M pressed block, equal at 168^3) and the 45-number
+// tangent goes to the column-group solver (210 vs 251 us on the 256^3 slab on
+// sand at impact); below, the CTA-per-brick solver with the shared-memory
+// block; as many CTAs per SM as fit.
 static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
   const int k45 = c->compressed ? 0 : 1;
   int st = c->pcg_cfg.tangent_staging, cp = c->pcg_cfg.ctas_per_sm;
   if (st == MPML_PCG_AUTO || cp == 0) {
     const int cached = tile_cache_lookup_fmt(pcg_cache_format(k45), c->ncb);
-    if (cached >= 0) {
-      if (st == MPML_PCG_AUTO) st = cached / 2 + 1;
-      if (cp == 0) cp = cached % 2 + 1;
+    if (cached >= 0 && cached < MPML_PCG_SHAPES) {
+      if (st == MPML_PCG_AUTO) st = PCG_SHAPE_TABLE[cached][0];
+      if (cp == 0 && st == PCG_SHAPE_TABLE[cached][0]) cp = PCG_SHAPE_TABLE[cached][1];
     }
   }
   int n = 0;
@@ -2586,10 +2941,9 @@ static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
     cudaGetLastError();
     return MPML_ERR_CUDA;
   }
-  if (st == MPML_PCG_AUTO) st = (!k45 && c->ncb > 4 * 2 * (int64_t)n) ? MPML_PCG_STREAMED : MPML_PCG_STAGED;
-  const int streamed = st == MPML_PCG_STREAMED;
-  const int fit = launch_fit(pcg_kernel(k45, streamed), 256, pcg_smem(k45, streamed), LS_PCG + k45 + 2 * streamed,
-                             nullptr);
+  if (st == MPML_PCG_AUTO)
+    st = c->ncb > 4 * 2 * (int64_t)n ? (k45 ? MPML_PCG_COLUMNS : MPML_PCG_STREAMED) : MPML_PCG_STAGED;
+  const int fit = launch_fit(pcg_kernel(k45, st), 256, pcg_smem(k45, st), pcg_slot(k45, st), nullptr);
   if (fit <= 0) return MPML_ERR_CUDA;
   if (cp == 0) cp = fit;
   if (cp > fit) return MPML_ERR_ARG;
@@ -2603,9 +2957,8 @@ static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
 // ev0 / ev1 (optional) are recorded around it on the context stream.
 static int pcg_launch(mpml_ctx_s* c, int cg_max, int staging, int ctas, int nsm, cudaEvent_t ev0, cudaEvent_t ev1) {
   const int k45 = c->compressed ? 0 : 1;
-  const int streamed = staging == MPML_PCG_STREAMED;
-  const void* kfn = pcg_kernel(k45, streamed);
-  const size_t smem = pcg_smem(k45, streamed);
+  const void* kfn = pcg_kernel(k45, staging);
+  const size_t smem = pcg_smem(k45, staging);
   const int G = ctas * nsm;
   int rc;
   // barrier words (2 unsigned) followed by the 4 x 2 rotating accumulators
@@ -2701,9 +3054,8 @@ int pcg_autotune(mpml_ctx_s* c, int iters, int reps, int* choice, float* ms) {
   float best = 0.f;
   int arg = -1;
   for (int shape = 0; shape < MPML_PCG_SHAPES && !rc; ++shape) {
-    const int staging = shape / 2 + 1, ctas = shape % 2 + 1, streamed = staging == MPML_PCG_STREAMED;
-    const int fit = launch_fit(pcg_kernel(k45, streamed), 256, pcg_smem(k45, streamed), LS_PCG + k45 + 2 * streamed,
-                               nullptr);
+    const int staging = PCG_SHAPE_TABLE[shape][0], ctas = PCG_SHAPE_TABLE[shape][1];
+    const int fit = launch_fit(pcg_kernel(k45, staging), 256, pcg_smem(k45, staging), pcg_slot(k45, staging), nullptr);
     if (fit < ctas) continue;
     float tbest = -1.f;
     for (int i = 0; i <= reps && !rc; ++i) {

@@ -700,8 +700,8 @@ int mpml_get_hvp_tile(mpml_ctx c, int* tile, const char** description) {
 
 int mpml_set_pcg_config(mpml_ctx c, const mpml_pcg_config* cfg) {
   if (!c || !cfg) return MPML_ERR_ARG;
-  if (cfg->tangent_staging < MPML_PCG_AUTO || cfg->tangent_staging > MPML_PCG_STREAMED) return MPML_ERR_ARG;
-  if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 2) return MPML_ERR_ARG;
+  if (cfg->tangent_staging < MPML_PCG_AUTO || cfg->tangent_staging > MPML_PCG_COLUMNS) return MPML_ERR_ARG;
+  if (cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 4) return MPML_ERR_ARG;
   c->pcg_cfg = *cfg;
   return MPML_OK;
 }

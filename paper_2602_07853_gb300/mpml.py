@@ -25,8 +25,9 @@ ELASTIC, VON_MISES, DRUCKER_PRAGER = 0, 1, 2
 FP32, FP64 = 0, 1
 MEM_DEVICE, MEM_HOST = 0, 1
 PRECOND_JACOBI, PRECOND_LEARNED = 0, 1
-PCG_AUTO, PCG_STAGED, PCG_STREAMED = 0, 1, 2
-PCG_SHAPES = 4  # MPML_PCG_SHAPES
+PCG_AUTO, PCG_STAGED, PCG_STREAMED, PCG_COLUMNS = 0, 1, 2, 3
+PCG_SHAPES = 7  # MPML_PCG_SHAPES
+PCG_SHAPE_TABLE = ((1, 1), (1, 2), (2, 1), (2, 2), (3, 2), (3, 3), (3, 4))
 KEYS_PARTICLES, KEYS_CELLS, KEYS_NODES = 0, 1, 2
 F_CELL_MASS, F_CELL_VEL, F_CELL_VGRAD, F_CELL_VOL, F_CELL_TAU, F_CELL_STRETCH = 0, 1, 2, 3, 4, 5
 F_CELL_VEL_NEW, F_CELL_VGRAD_NEW = 6, 7

@@ -1,9 +1,11 @@
 """The solver paths the large workloads run, and the solver's failure reports, on the GPU.
 
 - Every launch shape of the persistent Jacobi-PCG kernel (tangent block staged in shared
-  memory or streamed from global memory, one or two CTAs per SM), forced through
+  memory or streamed from global memory with the CTA on one brick, one or two CTAs per SM;
+  one brick per 64-thread group, two to four CTAs per SM), forced through
   mpml_set_pcg_config, on both tangent formats, against the FP64 oracle's Newton solution
-  (both stop at relative residual 1e-6: compared at 1e-4 on v - vhat, element by element).
+  (both stop at relative residual 1e-6: compared at 1e-4 on v - vhat, element by element),
+  and the persistent-solver autotuner's choice.
 - Full-size solves of the 3-8M pressed block (1,051,200 active cells, about 2,100 cell bricks:
   the streamed kernel) and of the 256^3 slab on sand at impact (19.2M particles, 2.5M cells:
   the staged 45-number kernel, 16+ bricks per CTA): the oracle's own FP64 gradient at the GPU
@@ -28,7 +30,7 @@ from tests._gpu import GpuSim, OracleSim, check
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(m.PCG_STAGED, 1), (m.PCG_STAGED, 2), (m.PCG_STREAMED, 1), (m.PCG_STREAMED, 2)]
+SHAPES = [tuple(sh) for sh in m.PCG_SHAPE_TABLE]
 
 
 @pytest.fixture(autouse=True)
@@ -69,10 +71,12 @@ def test_every_persistent_shape_matches_the_oracle(name):
         g.close()
 
 
-def full_size_gradient_check(sc, expect_staging):
+def full_size_gradient_check(sc, expect_staging, force=None):
     """GPU Newton solve at full size; the oracle's FP64 gradient at the GPU solution."""
     g = GpuSim(sc, m.FP32)
     g.set_particles()
+    if force is not None:
+        m.mpml_set_pcg_config(g.ctx, *force)
     o = make_oracle(sc)
     assert o.unload(**g.inputs()) == 0
     g.resample()
@@ -95,16 +99,54 @@ def full_size_gradient_check(sc, expect_staging):
     return st
 
 
-def test_full_size_pressed_block_236_streamed_solver():
-    """Config 3 at dx = 1/236 (7.9M particles): above eight cell bricks per SM the compressed
-    tangent is streamed (the automatic rule), a path smaller scenes reach only when forced."""
-    full_size_gradient_check(scenes.pressed_block(236), m.PCG_STREAMED)
+@pytest.mark.parametrize("force", [None, (m.PCG_COLUMNS, 4)])
+def test_full_size_pressed_block_236(force):
+    """Config 3 at dx = 1/236 (7.9M particles): without a tuned shape, above eight cell bricks
+    per SM the compressed tangent is streamed (the fixed rule), a path smaller scenes reach only
+    when forced; and the column-group solver at four CTAs per SM."""
+    full_size_gradient_check(scenes.pressed_block(236), force[0] if force else m.PCG_STREAMED, force)
 
 
-def test_full_size_slab_on_sand_256_at_impact():
-    """Config 5 (256^3, 19.2M particles, two plastic materials) at impact: the staged 45-number
-    persistent solver with many bricks per CTA."""
-    full_size_gradient_check(scenes.slab_on_sand(256, impact=True), m.PCG_STAGED)
+@pytest.mark.parametrize("force", [None, (m.PCG_STAGED, 2)])
+def test_full_size_slab_on_sand_256_at_impact(force):
+    """Config 5 (256^3, 19.2M particles, two plastic materials) at impact: the column-group
+    solver (fixed rule for the 45-number tangent above eight cell bricks per SM), and the
+    staged solver with many bricks per CTA."""
+    full_size_gradient_check(scenes.slab_on_sand(256, impact=True), force[0] if force else m.PCG_COLUMNS, force)
+
+
+@pytest.mark.parametrize("name", ["two_spheres_48", "slab_on_sand_48_impact"])
+def test_pcg_autotuner_picks_the_fastest_shape(name):
+    """mpml_autotune_pcg times every shape on the current system; its choice is the fastest
+    it measured, later solves of the context (and of another context of the same format and
+    size class) run it, and their solutions match the oracle."""
+    sc = {"two_spheres_48": lambda: scenes.two_spheres(48, gap=1.0 / 48),
+          "slab_on_sand_48_impact": lambda: scenes.slab_on_sand(48, impact=True)}[name]()
+    m.mpml_tile_cache_clear()
+    o, _ = oracle_solution(sc)
+    vhat, v_o = o.field("vhat"), o.field("v_new")
+    g = GpuSim(sc, m.FP32)
+    g.set_particles()
+    g.resample()
+    m.mpml_stretch(g.ctx)
+    m.mpml_linearize(g.ctx, g.field(m.F_NODE_VHAT))
+    shape, ms = m.mpml_autotune_pcg(g.ctx, 20, 2)
+    timed = [t for t in ms if t >= 0]
+    assert len(timed) >= 4 and ms[shape] == min(timed), ms
+    for ctx_owner in (g, None):
+        h = g if ctx_owner is g else GpuSim(sc, m.FP32)
+        if h is not g:
+            h.set_particles()
+        # resample: mpml_newton_step starts from the context's current node velocities, which
+        # mpml_linearize set to its argument
+        h.resample()
+        rc, st = h.newton()
+        assert rc == 0
+        _, staging, ctas = m.mpml_get_pcg_config(h.ctx)
+        assert (staging, ctas) == tuple(m.PCG_SHAPE_TABLE[shape])
+        check(h.field(m.F_NODE_VNEW) - vhat, v_o - vhat, 1e-4, f"v_new - vhat (tuned shape {shape})")
+        h.close()
+    m.mpml_tile_cache_clear()
 
 
 @pytest.mark.parametrize("precision", [m.FP32, m.FP64])

@@ -40,7 +40,18 @@ def test_cache_round_trip(tmp_path):
     assert entries(out) == [(25, 3, 2, 0.0125), (25, 10, 0, 0.4), (45, 12, 0, 1.25)]
 
 
+def test_persistent_solver_shapes_round_trip(tmp_path):
+    """Formats 125 / 145 hold the persistent solver's shapes (0 .. PCG_SHAPES - 1)."""
+    src = tmp_path / "pcg.txt"
+    src.write_text(f"125 11 {m.PCG_SHAPES - 1} 2.5\n145 12 4 3.75\n25 11 0 0.5\n")
+    m.mpml_tile_cache_load(src)
+    out = tmp_path / "out.txt"
+    m.mpml_tile_cache_save(out)
+    assert entries(out) == [(25, 11, 0, 0.5), (125, 11, m.PCG_SHAPES - 1, 2.5), (145, 12, 4, 3.75)]
+
+
 @pytest.mark.parametrize("bad", ["25 10 3 0.5\n",       # tile out of range
+                                 f"145 10 {m.PCG_SHAPES} 0.5\n",  # persistent shape out of range
                                  "33 10 1 0.5\n",       # unknown tangent format
                                  "25 10 1\n",           # missing field
                                  "25 -1 1 0.5\n",       # negative size class
