@@ -672,13 +672,15 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
 // The projected tangent of one cell in the storage precision T from the signed
 // SVD (U, V, W = S V) and the isotropic eigen-data of psi: the 45-number
 // packed form and the NQC-number compressed form (layout at apply_cmp).
+// want_k: 1 the packed 45-number form, 2 also the compressed form (the packed one
+// gives the Jacobi diagonal in both cases).
 template <typename T>
 __device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[9], const T pp[3], const T pm[3], T kv,
-                              const double bm[9], CellOut<T>& out) {
+                              const double bm[9], int want_k, CellOut<T>& out) {
   // diagonal block: eigen-decomposition of d2, clamp
   T ev[3], Qd[9];
   jacobi3<T>(d2, ev, Qd);
-  {
+  if (want_k == 2) {
     // compressed record (valid for single-material cells; bm = B - I, the
     // stretch step's base S - I in elastic contexts)
     double Ud[9], q[4];
@@ -760,7 +762,7 @@ __device__ void build_tangent(const T Ut[9], const T Vt[9], const T Wt[9], T d2[
 
 template <typename T>
 __device__ void cell_material(const MatParams<double>& M, double V, const double Gd[9] /* dt*G */,
-                              const double bm[9] /* B - I */, double kq, double kk, bool want_k, CellOut<T>& out,
+                              const double bm[9] /* B - I */, double kq, double kk, int want_k, CellOut<T>& out,
                               bool want_psi = true) {
   double sm[9], H[9];
   trial_h(Gd, bm, sm, H);
@@ -810,14 +812,17 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
           for (int k = 0; k < 3; ++k) acc += (float)sm[3 * a + k] * Vf[3 * k + b];
           Wf[3 * a + b] = acc;
         }
-      build_tangent<T>(Uf, Vf, Wf, spf.d2, spf.pp, spf.pm, (float)(kk * V), bm, out);
+      build_tangent<T>(Uf, Vf, Wf, spf.d2, spf.pp, spf.pm, (float)(kk * V), bm, want_k, out);
       return;
     }
   }
   double U[9], s[3], e[3], Vv[9], Jm1;
   svd_from_h<double>(H, U, s, e, Vv, Jm1);
+  // the energy and the principal stresses in FP64 (the gradient); in FP32 contexts the
+  // tangent moduli, stored in FP32, are evaluated in FP32 (FP64 divisions and logarithms
+  // are the expensive part of this kernel on this part)
   Spec<double> sp;
-  if (!spectral<double>(M, s, e, Jm1, sp)) {
+  if (!spectral<double, sizeof(T) == 4 ? 1 : 3>(M, s, e, Jm1, sp)) {
     out.ok = false;
     return;
   }
@@ -859,15 +864,36 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
     Ut[i] = (T)U[i];
     Wt[i] = (T)W[i];
     Vt[i] = (T)Vv[i];
-    d2[i] = (T)sp.d2[i];
   }
   T pp[3], pm[3];
+  if constexpr (sizeof(T) == 4) {
+    MatParams<float> Mf;
+    Mf.model = M.model;
+    Mf.mu = (float)M.mu;
+    Mf.lam = (float)M.lam;
+    const float sf[3] = {(float)s[0], (float)s[1], (float)s[2]}, ef[3] = {(float)e[0], (float)e[1], (float)e[2]};
+    Spec<float> spf;
+    if (!spectral<float, 2>(Mf, sf, ef, (float)Jm1, spf)) {
+      out.ok = false;
+      return;
+    }
 #pragma unroll
-  for (int p = 0; p < 3; ++p) {
-    pp[p] = (T)sp.pp[p];
-    pm[p] = (T)sp.pm[p];
+    for (int i = 0; i < 9; ++i) d2[i] = spf.d2[i];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      pp[p] = spf.pp[p];
+      pm[p] = spf.pm[p];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) d2[i] = (T)sp.d2[i];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      pp[p] = (T)sp.pp[p];
+      pm[p] = (T)sp.pm[p];
+    }
   }
-  build_tangent<T>(Ut, Vt, Wt, d2, pp, pm, (T)(kk * V), bm, out);
+  build_tangent<T>(Ut, Vt, Wt, d2, pp, pm, (T)(kk * V), bm, want_k, out);
 }
 
 // node init: g = m (v - vhat) (FP64), diag = m, inertia energy (all bricks, 512 thr)
@@ -941,7 +967,7 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
       if (V == 0.0) continue;
       double bm[9];
       load_base(cs, si.b9, id, si.nm, k, l, bm);
-      cell_material<T>(si.mat[k], V, Gd, bm, kq, kk, want_k != 0, co, want_psi != 0);
+      cell_material<T>(si.mat[k], V, Gd, bm, kq, kk, want_k, co, want_psi != 0);
     }
     if (!co.ok) {
       bad = 1;
@@ -1892,7 +1918,7 @@ __global__ void __launch_bounds__(256) k_energy_cells(const int* __restrict__ cb
         double U[9], s[3], e[3], Vv[9], Jm1;
         svd_from_h<double>(H, U, s, e, Vv, Jm1);
         Spec<double> sp;
-        if (!spectral<double>(si.mat[k], s, e, Jm1, sp)) {
+        if (!spectral<double, 1>(si.mat[k], s, e, Jm1, sp)) {  // the energy only
           bad = 1;
           continue;
         }

@@ -101,7 +101,7 @@ __device__ void kirchhoff(const MatParams<T>& M, const T F[9], T tau[6]) {
   T U[9], s[3], e[3], V[9], Jm1;
   svd_from_h(H, U, s, e, V, Jm1);
   Spec<T> sp;
-  spectral(M, s, e, Jm1, sp);
+  spectral<T, 1>(M, s, e, Jm1, sp);  // the principal stresses only
   T t[3] = {s[0] * sp.d1[0], s[1] * sp.d1[1], s[2] * sp.d1[2]};
   const int ra[6] = {0, 1, 2, 0, 0, 1}, rb[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll

@@ -828,8 +828,9 @@ __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1)
   T u0[3], u1[3], u2[3];
   T n0 = dsqrt(b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2]);
   if (n0 > T(1e-30)) {
+    const T in0 = T(1) / n0;  // one division, three products (divisions are costly in FP64)
 #pragma unroll
-    for (int r = 0; r < 3; ++r) u0[r] = b[0][r] / n0;
+    for (int r = 0; r < 3; ++r) u0[r] = b[0][r] * in0;
   } else {
     u0[0] = 1; u0[1] = 0; u0[2] = 0;
   }
@@ -838,8 +839,9 @@ __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1)
   for (int r = 0; r < 3; ++r) u1[r] = b[1][r] - dd * u0[r];
   T n1 = dsqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
   if (n1 > T(1e-30)) {
+    const T in1 = T(1) / n1;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) u1[r] /= n1;
+    for (int r = 0; r < 3; ++r) u1[r] *= in1;
   } else {
     T a0 = fabs(u0[0]) > T(0.9) ? T(0) : T(1), a1 = fabs(u0[0]) > T(0.9) ? T(1) : T(0);
     T ee = a0 * u0[0] + a1 * u0[1];
@@ -981,24 +983,31 @@ __device__ __forceinline__ int pair_j(int p) { return p == 0 ? 1 : 2; }
 __device__ __forceinline__ int pair_k(int p) { return 2 - p; }
 
 // returns false where the energy is undefined (J <= 0 for NH / Hencky)
-template <typename T>
+// The isotropic eigen-data of psi at the signed singular values s (e = s - 1,
+// Jm1 = J - 1): PARTS bit 1 the energy and the principal stresses d1 (what the
+// gradient needs), bit 2 the projected-tangent moduli d2 (3x3 block), pp (flip)
+// and pm (twist).  The two parts can be evaluated in different precisions.
+template <typename T, int PARTS = 3>
 __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm1, Spec<T>& o) {
+  constexpr bool P1 = (PARTS & 1) != 0, P2 = (PARTS & 2) != 0;
   const T mu = M.mu, lam = M.lam;
   const T J = T(1) + Jm1;
   if (M.model == MPML_FIXED_COROTATED) {
-    o.psi = mu * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) + T(0.5) * lam * Jm1 * Jm1;
+    if (P1) o.psi = mu * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) + T(0.5) * lam * Jm1 * Jm1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int j = (i + 1) % 3, k = (i + 2) % 3;
-      o.d1[i] = T(2) * mu * e[i] + lam * Jm1 * s[j] * s[k];
-      o.d2[4 * i] = T(2) * mu + lam * (s[j] * s[k]) * (s[j] * s[k]);
+      if (P1) o.d1[i] = T(2) * mu * e[i] + lam * Jm1 * s[j] * s[k];
+      if (P2) o.d2[4 * i] = T(2) * mu + lam * (s[j] * s[k]) * (s[j] * s[k]);
     }
+    if (P2) {
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const int i = pair_i(p), j = pair_j(p), k = pair_k(p);
-      o.d2[3 * i + j] = o.d2[3 * j + i] = lam * s[k] * (T(2) * J - T(1));
-      o.pp[p] = T(2) * mu - lam * Jm1 * s[k];
-      o.pm[p] = T(2) * mu * (e[i] + e[j]) / (s[i] + s[j]) + lam * Jm1 * s[k];
+      for (int p = 0; p < 3; ++p) {
+        const int i = pair_i(p), j = pair_j(p), k = pair_k(p);
+        o.d2[3 * i + j] = o.d2[3 * j + i] = lam * s[k] * (T(2) * J - T(1));
+        o.pp[p] = T(2) * mu - lam * Jm1 * s[k];
+        o.pm[p] = T(2) * mu * (e[i] + e[j]) / (s[i] + s[j]) + lam * Jm1 * s[k];
+      }
     }
     return true;
   }
@@ -1010,29 +1019,36 @@ __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm
     const T I1m3 = e[0] * (T(2) + e[0]) + e[1] * (T(2) + e[1]) + e[2] * (T(2) + e[2]);
     const T I1 = T(3) + I1m3;
     const T J2m1 = Jm1 * (T(2) + Jm1);
-    // I1 - 3 - 2 (J - 1) = sum e_i^2 - 2 (e0 e1 + e0 e2 + e1 e2) - 2 e0 e1 e2
-    const T b2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] - T(2) * (e[0] * e[1] + e[0] * e[2] + e[1] * e[2]) -
-                 T(2) * e[0] * e[1] * e[2];
-    o.psi = nh_psi(mu, kap, Jm1, I1m3, b2);
+    if (P1) {
+      // I1 - 3 - 2 (J - 1) = sum e_i^2 - 2 (e0 e1 + e0 e2 + e1 e2) - 2 e0 e1 e2
+      const T b2 = e[0] * e[0] + e[1] * e[1] + e[2] * e[2] - T(2) * (e[0] * e[1] + e[0] * e[2] + e[1] * e[2]) -
+                   T(2) * e[0] * e[1] * e[2];
+      o.psi = nh_psi(mu, kap, Jm1, I1m3, b2);
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int j = (i + 1) % 3, k = (i + 2) % 3;
-      // s_i - I1/(3 s_i) = ((s_i^2 - s_j^2) + (s_i^2 - s_k^2)) / (3 s_i)
-      const T dij = (e[i] - e[j]) * (T(2) + e[i] + e[j]);
-      const T dik = (e[i] - e[k]) * (T(2) + e[i] + e[k]);
-      o.d1[i] = mu * c * (dij + dik) / (T(3) * s[i]) + T(0.5) * kap * J2m1 / s[i];
-      o.d2[4 * i] = mu * c * (T(-1) / T(3) + T(5) * I1 / (T(9) * s[i] * s[i])) +
-                    T(0.5) * kap * (J * J + T(1)) / (s[i] * s[i]);
+      if (P1) {
+        // s_i - I1/(3 s_i) = ((s_i^2 - s_j^2) + (s_i^2 - s_k^2)) / (3 s_i)
+        const T dij = (e[i] - e[j]) * (T(2) + e[i] + e[j]);
+        const T dik = (e[i] - e[k]) * (T(2) + e[i] + e[k]);
+        o.d1[i] = mu * c * (dij + dik) / (T(3) * s[i]) + T(0.5) * kap * J2m1 / s[i];
+      }
+      if (P2)
+        o.d2[4 * i] = mu * c * (T(-1) / T(3) + T(5) * I1 / (T(9) * s[i] * s[i])) +
+                      T(0.5) * kap * (J * J + T(1)) / (s[i] * s[i]);
     }
+    if (P2) {
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const int i = pair_i(p), j = pair_j(p);
-      const T sij = s[i] * s[j];
-      o.d2[3 * i + j] = o.d2[3 * j + i] =
-          mu * c / sij * (T(-2) / T(3) * s[i] * s[i] - T(2) / T(3) * s[j] * s[j] + T(2) / T(9) * I1) +
-          kap * J * J / sij;
-      o.pp[p] = mu * c * (T(1) + I1 / (T(3) * sij)) - T(0.5) * kap * J2m1 / sij;
-      o.pm[p] = mu * c * (T(1) - I1 / (T(3) * sij)) + T(0.5) * kap * J2m1 / sij;
+      for (int p = 0; p < 3; ++p) {
+        const int i = pair_i(p), j = pair_j(p);
+        const T sij = s[i] * s[j];
+        o.d2[3 * i + j] = o.d2[3 * j + i] =
+            mu * c / sij * (T(-2) / T(3) * s[i] * s[i] - T(2) / T(3) * s[j] * s[j] + T(2) / T(9) * I1) +
+            kap * J * J / sij;
+        o.pp[p] = mu * c * (T(1) + I1 / (T(3) * sij)) - T(0.5) * kap * J2m1 / sij;
+        o.pm[p] = mu * c * (T(1) - I1 / (T(3) * sij)) + T(0.5) * kap * J2m1 / sij;
+      }
     }
     return true;
   }
@@ -1040,19 +1056,21 @@ __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm
     // Sec. "Water": psi = kappa/2 (J - 1)^2, kappa = lam + 2/3 mu; no inverted fluid
     if (!(J > T(0))) return false;
     const T kap = lam + T(2) / T(3) * mu;
-    o.psi = T(0.5) * kap * Jm1 * Jm1;
+    if (P1) o.psi = T(0.5) * kap * Jm1 * Jm1;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const int j = (i + 1) % 3, k = (i + 2) % 3;
-      o.d1[i] = kap * Jm1 * s[j] * s[k];
-      o.d2[4 * i] = kap * (s[j] * s[k]) * (s[j] * s[k]);
+      if (P1) o.d1[i] = kap * Jm1 * s[j] * s[k];
+      if (P2) o.d2[4 * i] = kap * (s[j] * s[k]) * (s[j] * s[k]);
     }
+    if (P2) {
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const int i = pair_i(p), j = pair_j(p), k = pair_k(p);
-      o.d2[3 * i + j] = o.d2[3 * j + i] = kap * s[k] * (T(2) * J - T(1));
-      o.pp[p] = -kap * Jm1 * s[k];
-      o.pm[p] = kap * Jm1 * s[k];
+      for (int p = 0; p < 3; ++p) {
+        const int i = pair_i(p), j = pair_j(p), k = pair_k(p);
+        o.d2[3 * i + j] = o.d2[3 * j + i] = kap * s[k] * (T(2) * J - T(1));
+        o.pp[p] = -kap * Jm1 * s[k];
+        o.pm[p] = kap * Jm1 * s[k];
+      }
     }
     return true;
   }
@@ -1060,22 +1078,24 @@ __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm
     if (!(s[0] > T(0) && s[1] > T(0) && s[2] > T(0))) return false;
     const T l[3] = {log1p_t(e[0]), log1p_t(e[1]), log1p_t(e[2])};
     const T tr = l[0] + l[1] + l[2];
-    o.psi = mu * (l[0] * l[0] + l[1] * l[1] + l[2] * l[2]) + T(0.5) * lam * tr * tr;
+    if (P1) o.psi = mu * (l[0] * l[0] + l[1] * l[1] + l[2] * l[2]) + T(0.5) * lam * tr * tr;
     T t[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       t[i] = T(2) * mu * l[i] + lam * tr;
-      o.d1[i] = t[i] / s[i];
-      o.d2[4 * i] = (T(2) * mu + lam - t[i]) / (s[i] * s[i]);
+      if (P1) o.d1[i] = t[i] / s[i];
+      if (P2) o.d2[4 * i] = (T(2) * mu + lam - t[i]) / (s[i] * s[i]);
     }
+    if (P2) {
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const int i = pair_i(p), j = pair_j(p);
-      o.d2[3 * i + j] = o.d2[3 * j + i] = lam / (s[i] * s[j]);
-      const T z = (s[i] - s[j]) / s[j];
-      const T L = fabs(z) < T(1e-4) ? T(1) - T(0.5) * z + z * z / T(3) : log1p_t(z) / z;
-      o.pp[p] = (T(2) * mu * (L - l[j]) - lam * tr) / (s[i] * s[j]);
-      o.pm[p] = (t[i] * s[j] + t[j] * s[i]) / (s[i] * s[j] * (s[i] + s[j]));
+      for (int p = 0; p < 3; ++p) {
+        const int i = pair_i(p), j = pair_j(p);
+        o.d2[3 * i + j] = o.d2[3 * j + i] = lam / (s[i] * s[j]);
+        const T z = (s[i] - s[j]) / s[j];
+        const T L = fabs(z) < T(1e-4) ? T(1) - T(0.5) * z + z * z / T(3) : log1p_t(z) / z;
+        o.pp[p] = (T(2) * mu * (L - l[j]) - lam * tr) / (s[i] * s[j]);
+        o.pm[p] = (t[i] * s[j] + t[j] * s[i]) / (s[i] * s[j] * (s[i] + s[j]));
+      }
     }
     return true;
   }
