@@ -186,7 +186,7 @@ def pcg_kernel_name(k45, staging, ctas):
     rows, 3 column groups)."""
     fmt = "K45" if k45 else "compressed"
     if staging == 3:
-        return f"k_pcg_groups<{fmt}> (one brick per 64-thread group, {ctas} CTAs/SM)"
+        return f"k_pcg_groups<{fmt}> (half a brick per 64-thread group, {ctas} CTAs/SM)"
     kind = "staged" if staging == 1 else "streamed"
     return f"k_pcg_persistent<{fmt}, {kind}> ({ctas} CTAs/SM)"
 

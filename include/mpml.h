@@ -325,13 +325,15 @@ void mpml_tile_cache_clear(void);
  *                      one brick)
  *   MPML_PCG_STREAMED  the same, with the rows read from global memory as the
  *                      column walk needs them (no shared-memory block)
- *   MPML_PCG_COLUMNS   each 64-thread group of a CTA works on a brick of its
- *                      own, rows streamed from global memory (four bricks in
- *                      flight per CTA, up to four CTAs per SM)
+ *   MPML_PCG_COLUMNS   each 64-thread group of a CTA works on half a brick
+ *                      (four z-layers of cells) of its own, rows streamed from
+ *                      global memory (four half-bricks in flight per CTA; builds
+ *                      for 2, 3 and 4 CTAs per SM, the 2-CTA one loading each
+ *                      layer's rows one layer ahead)
  *   MPML_PCG_AUTO      the shape mpml_autotune_pcg chose for this tangent format
  *                      and size class, else a fixed rule: above 8 cell bricks
- *                      per SM streamed for the compressed tangent and column
- *                      groups for the 45-number one, staged otherwise
+ *                      per SM column groups (4 CTAs per SM for the 45-number
+ *                      tangent, 3 for the compressed one), staged otherwise
  * ctas_per_sm: CTAs per SM of the cooperative launch (0 = as many as fit, at
  *   most 2 for the first two forms and 4 for the third; a value above what
  *   fits is MPML_ERR_ARG at the next solve).

@@ -2579,31 +2579,103 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
 
 // ---------------------------------------------------------------------------
 // Persistent Jacobi-PCG, column-group form: the same iteration and phases as
-// k_pcg_persistent, but in phase H each 64-thread group of a CTA owns a brick
-// of its own (group g of CTA b takes the cell bricks b * 4 + g + k * 4 G): it
-// stages p_new on the brick's 9^3 node block (fused p update, as above) in its
-// own shared memory and walks the 64 z-columns of cells with the tangent rows
-// streamed from global memory (thread (x, y) walks column (x, y): lower and
-// upper node layers in registers, node sums along x by shuffles, along y by
-// shuffles and one row exchange per layer, a 64-thread named barrier per
-// layer).  Four independent bricks per CTA and four CTAs per SM keep about
-// 45 outstanding tangent loads per thread in flight without any block-wide
-// barrier inside phase H.
+// k_pcg_persistent, but in phase H each 64-thread group of a CTA owns a work
+// unit of its own -- half a cell brick, four z-layers of cells (group g of CTA
+// b takes the units b * 4 + g + k * 4 G, unit u = half u & 1 of cell brick
+// u >> 1; halves balance the groups' work to within one unit) -- stages p_new on
+// the unit's 9 x 9 x 5 node block (fused p update, as above) and the unit's cell
+// flags and node masses in its own shared memory, and walks the 64 z-columns of
+// cells with the tangent rows streamed from global memory (thread (x, y) walks
+// column (x, y): lower and upper node layers in registers, node sums along x by
+// shuffles, along y by shuffles and one row exchange per layer, a 64-thread
+// named barrier per layer).  Four independent units per CTA and two to four
+// CTAs per SM keep up to 45 outstanding tangent loads per thread in flight
+// without any block-wide barrier inside phase H.
 // ---------------------------------------------------------------------------
 struct ColGroup {
   float sv[3][729];          // p_new on the 9^3 node block
   float sxr[2][2][3][8];     // [z parity][E, E8 of row 3][a][x]
+  float m[BV];               // the brick's node masses
   int nbr[NBR];
-  int pad;
+  uint8_t cf[BV];            // the brick's active-cell flags
 };
+
+// node (nx, ny, nz) of the group's brick block receives y[3] (as col_emit_m, with
+// the brick's masses from shared memory)
+__device__ __forceinline__ void col_emit_g(int id, const ColGroup& S, float* q, int nx, int ny, int nz,
+                                          const float y[3]) {
+  if (nx < 8 && ny < 8 && nz < 8) {
+    const int l = (nz * 8 + ny) * 8 + nx;
+    float* dst = q + (int64_t)id * 3 * BV + l;
+    const float mi = S.m[l];
+    const int i = hidx(nx, ny, nz);
+    if (nx >= 1 && ny >= 1 && nz >= 1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dst[a * BV] = y[a] + mi * S.sv[a][i];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float val = y[a] + mi * S.sv[a][i];
+        if (val != 0.f) atomicAdd(dst + a * BV, val);
+      }
+    }
+  } else {
+    const int t = S.nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+    if (t < 0) return;
+    const int l = ((nz & 7) * 8 + (ny & 7)) * 8 + (nx & 7);
+    float* dst = q + (int64_t)t * 3 * BV + l;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (y[a] != 0.f) atomicAdd(dst + a * BV, y[a]);
+  }
+}
 
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory");
 }
 
-template <bool K45>
-__global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
+// MINB: CTAs per SM the build is for (4: 64 registers; 3: 85; 2: 128 registers, and
+// then each thread loads the next layer's tangent rows while it applies the current
+// layer's, so that one layer's memory latency overlaps the previous layer's work).
+// Half-brick work units: unit (brick, hz) holds the brick's cell layers 4hz .. 4hz+3
+// and its node layers 4hz .. 4hz+4 (local layers 0 .. 4); it owns (writes p_new and
+// adds the mass term for) the node layers 4hz .. 4hz+3 of the brick.  Node (nx, ny,
+// local nzl) receives y[3]: plain store where only this unit contributes (owned,
+// nx, ny >= 1 and 1 <= nzl <= 3), atomic add elsewhere.
+__device__ __forceinline__ void col_emit_h(int id, const ColGroup& S, float* q, int nx, int ny, int nzl, int hz,
+                                          const float y[3]) {
+  const int nz = 4 * hz + nzl;
+  if (nx < 8 && ny < 8 && nz < 8) {
+    const int l = (nz * 8 + ny) * 8 + nx;
+    float* dst = q + (int64_t)id * 3 * BV + l;
+    const bool owned = nzl < 4;
+    const float mi = owned ? S.m[l] : 0.f;
+    const int i = hidx(nx, ny, nzl);
+    if (owned && nx >= 1 && ny >= 1 && nzl >= 1) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) dst[a * BV] = y[a] + mi * S.sv[a][i];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float val = y[a] + mi * S.sv[a][i];
+        if (val != 0.f) atomicAdd(dst + a * BV, val);
+      }
+    }
+  } else {
+    const int t = S.nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
+    if (t < 0) return;
+    const int l = ((nz & 7) * 8 + (ny & 7)) * 8 + (nx & 7);
+    float* dst = q + (int64_t)t * 3 * BV + l;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (y[a] != 0.f) atomicAdd(dst + a * BV, y[a]);
+  }
+}
+
+template <bool K45, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
   constexpr int NQ = K45 ? 45 : NQC;
+  constexpr bool PF = MINB <= 2;
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ ColGroup gs[4];
   __shared__ int s_flag;
@@ -2630,12 +2702,16 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
     const unsigned long long t_h0 = (A.pf && blockIdx.x == 0 && threadIdx.x == 0) ? gtimer() : 0ull;
     // ---------------- phase H ----------------
     float pmp = 0.f, pkp = 0.f;
-    for (int jc = gid; jc < A.ncb; jc += NG) {
-      const int id = A.cblist[jc];
+    for (int u = gid; u < 2 * A.ncb; u += NG) {
+      const int id = A.cblist[u >> 1], hz = u & 1;
       if (t < NBR) S.nbr[t] = A.nbr[id * NBR + t];
+      // the unit's active-cell flags (read by the walk from shared memory)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) S.cf[t + 64 * k] = A.cflag[(int64_t)id * BV + 256 * hz + t + 64 * k];
       group_sync(g);
-      // p_new on the 9^3 node block, three nodes per thread and batch, all loads first
-      for (int i0 = t; i0 < 729; i0 += 3 * 64) {
+      // p_new on the unit's 9 x 9 x 5 node block, three nodes per thread and batch, all
+      // loads first; the owned nodes' p_new and masses are written
+      for (int i0 = t; i0 < 405; i0 += 3 * 64) {
         int tb[3], ll[3];
         float dv[3][3], rv[3][3], pv[3][3], mv[3];
 #pragma unroll
@@ -2646,8 +2722,8 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
           mv[k] = 0.f;
 #pragma unroll
           for (int a = 0; a < 3; ++a) dv[k][a] = rv[k][a] = pv[k][a] = 0.f;
-          if (i < 729) {
-            const int nx = i % 9, ny = (i / 9) % 9, nz = i / 81;
+          if (i < 405) {
+            const int nx = i % 9, ny = (i / 9) % 9, nz = 4 * hz + i / 81;
             const int tt = (nx < 8 && ny < 8 && nz < 8) ? id : S.nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
             const int l = (nz & 7) * 64 + (ny & 7) * 8 + (nx & 7);
             tb[k] = tt;
@@ -2660,23 +2736,24 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
                 rv[k][a] = __ldcg(A.r + o + a * BV);
                 pv[k][a] = __ldcg(pold + o + a * BV);
               }
-              if (tt == id) mv[k] = __ldcg(A.m + (int64_t)id * BV + l);
+              if (tt == id && i < 324) mv[k] = __ldcg(A.m + (int64_t)id * BV + l);
             }
           }
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const int i = i0 + 64 * k;
-          if (i >= 729) continue;
+          if (i >= 405) continue;
           float v[3];
 #pragma unroll
           for (int a = 0; a < 3; ++a) v[a] = dv[k][a] > 0.f ? dv[k][a] * rv[k][a] + beta * pv[k][a] : 0.f;
-          if (tb[k] == id) {
+          if (tb[k] == id && i < 324) {  // owned: own brick, local layers 0 .. 3
             const int64_t o = (int64_t)id * 3 * BV + ll[k];
             pnext[o] = v[0];
             pnext[o + BV] = v[1];
             pnext[o + 2 * BV] = v[2];
             pmp += mv[k] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            S.m[ll[k]] = mv[k];
           }
           S.sv[0][i] = v[0];
           S.sv[1][i] = v[1];
@@ -2684,9 +2761,8 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
         }
       }
       group_sync(g);
-      // the z-column walk of this thread's column (x, y)
+      // the z-column walk of this thread's column (x, y) over the unit's four cell layers
       const float* Kb = A.C + (int64_t)id * NQ * BV;
-      const uint8_t* cf = A.cflag + (int64_t)id * BV;
       float P0[2][2][3], Cz[2][2][3];
 #pragma unroll
       for (int ox = 0; ox < 2; ++ox)
@@ -2697,10 +2773,20 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
             P0[ox][oy][a] = S.sv[a][hidx(x + ox, y + oy, 0)];
             Cz[ox][oy][a] = 0.f;
           }
+      // prefetched tangent rows of the next layer's cell (PF builds)
+      float kn[PF ? NQ : 1];
+      int fn = 0;
+      if (PF) {
+        fn = S.cf[y * 8 + x];
+        if (fn) {
+#pragma unroll
+          for (int qq = 0; qq < NQ; ++qq) kn[qq] = ld_stream(Kb + qq * BV + 256 * hz + y * 8 + x);
+        }
+      }
 #pragma unroll 1
-      for (int z = 0; z <= 8; ++z) {
+      for (int z = 0; z <= 4; ++z) {
         float N[2][2][3];
-        if (z < 8) {
+        if (z < 4) {
           float P1[2][2][3];
 #pragma unroll
           for (int ox = 0; ox < 2; ++ox)
@@ -2708,17 +2794,31 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
             for (int oy = 0; oy < 2; ++oy)
 #pragma unroll
               for (int a = 0; a < 3; ++a) P1[ox][oy][a] = S.sv[a][hidx(x + ox, y + oy, z + 1)];
-          const int l = (z * 8 + y) * 8 + x;
+          const int lu = (z * 8 + y) * 8 + x, l = 256 * hz + lu;  // cell in the unit and in the brick
           float KD[9];
 #pragma unroll
           for (int r = 0; r < 9; ++r) KD[r] = 0.f;
-          if (cf[l]) {
+          int fc;
+          float kc[PF ? NQ : 1];
+          if (PF) {
+            fc = fn;
+#pragma unroll
+            for (int qq = 0; qq < (PF ? NQ : 1); ++qq) kc[qq] = kn[qq];
+            fn = z < 3 ? S.cf[lu + 64] : 0;
+            if (fn) {
+#pragma unroll
+              for (int qq = 0; qq < (PF ? NQ : 1); ++qq) kn[qq] = ld_stream(Kb + qq * BV + l + 64);
+            }
+          } else {
+            fc = S.cf[lu];
+          }
+          if (fc) {
             float D[9];
             col_D(P0, P1, D);
             if (K45) {
               float k[45];
 #pragma unroll
-              for (int qq = 0; qq < 45; ++qq) k[qq] = ld_stream(Kb + qq * BV + l);
+              for (int qq = 0; qq < 45; ++qq) k[qq] = PF ? kc[qq < (PF ? NQ : 1) ? qq : 0] : ld_stream(Kb + qq * BV + l);
 #pragma unroll
               for (int r = 0; r < 9; ++r) {
                 KD[r] += k[k45(r, r)] * D[r];
@@ -2731,7 +2831,7 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
             } else {
               float c[NQC];
 #pragma unroll
-              for (int qq = 0; qq < NQC; ++qq) c[qq] = ld_stream(Kb + qq * BV + l);
+              for (int qq = 0; qq < NQC; ++qq) c[qq] = PF ? kc[qq < (PF ? NQ : 1) ? qq : 0] : ld_stream(Kb + qq * BV + l);
               apply_cmp(c, D, KD);
             }
 #pragma unroll
@@ -2799,14 +2899,14 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
           T[a] = E[0][a] + prev;
           T8[a] = E8[0][a] + prev8;
         }
-        col_emit_m(id, S.nbr, S.sv, A.m, A.q, x, y, z, T);
-        if (x == 7) col_emit_m(id, S.nbr, S.sv, A.m, A.q, 8, y, z, T8);
+        col_emit_h(id, S, A.q, x, y, z, hz, T);
+        if (x == 7) col_emit_h(id, S, A.q, 8, y, z, hz, T8);
         if (y == 7) {
-          col_emit_m(id, S.nbr, S.sv, A.m, A.q, x, 8, z, E[1]);
-          if (x == 7) col_emit_m(id, S.nbr, S.sv, A.m, A.q, 8, 8, z, E8[1]);
+          col_emit_h(id, S, A.q, x, 8, z, hz, E[1]);
+          if (x == 7) col_emit_h(id, S, A.q, 8, 8, z, hz, E8[1]);
         }
       }
-      group_sync(g);  // S.sv and S.nbr are reused by the group's next brick
+      group_sync(g);  // S.sv, S.m, S.cf and S.nbr are reused by the group's next unit
     }
     // bricks with DOF nodes but no cells: p_new and the mass term
     for (int jn = G - 1 - (int)blockIdx.x; jn < A.nnob; jn += G) {
@@ -2921,8 +3021,12 @@ __global__ void __launch_bounds__(256, 4) k_pcg_groups(PcgArgs A) {
 
 // The kernels of the persistent solver: tangent format x staging (1 shared-memory
 // block, 2 streamed rows, 3 column groups).
-static const void* pcg_kernel(int k45, int staging) {
-  if (staging == MPML_PCG_COLUMNS) return k45 ? (const void*)k_pcg_groups<true> : (const void*)k_pcg_groups<false>;
+static const void* pcg_kernel(int k45, int staging, int ctas) {
+  if (staging == MPML_PCG_COLUMNS) {
+    if (ctas <= 2) return k45 ? (const void*)k_pcg_groups<true, 2> : (const void*)k_pcg_groups<false, 2>;
+    if (ctas == 3) return k45 ? (const void*)k_pcg_groups<true, 3> : (const void*)k_pcg_groups<false, 3>;
+    return k45 ? (const void*)k_pcg_groups<true, 4> : (const void*)k_pcg_groups<false, 4>;
+  }
   const bool streamed = staging == MPML_PCG_STREAMED;
   return k45 ? (streamed ? (const void*)k_pcg_persistent<true, true> : (const void*)k_pcg_persistent<true>)
              : (streamed ? (const void*)k_pcg_persistent<false, true> : (const void*)k_pcg_persistent<false>);
@@ -2934,7 +3038,11 @@ static size_t pcg_smem(int k45, int staging) {
                                       : (k45 ? HVP_K_SMEM45 : HVP_C_SMEM_COL);
 }
 
-static int pcg_slot(int k45, int staging) { return LS_PCG + k45 + 2 * (staging - 1); }
+// launch_fit slots: CTA-per-brick forms k45 + 2 (staging - 1); column groups by their build
+static int pcg_slot(int k45, int staging, int ctas) {
+  if (staging == MPML_PCG_COLUMNS) return LS_PCG + 4 + 3 * k45 + (ctas <= 2 ? 0 : ctas - 2);
+  return LS_PCG + k45 + 2 * (staging - 1);
+}
 
 // the autotuner's shapes: (staging, CTAs per SM)
 static const int PCG_SHAPE_TABLE[MPML_PCG_SHAPES][2] = {
@@ -2947,11 +3055,11 @@ static int pcg_cache_format(int k45) { return k45 ? 145 : 125; }
 // The shape (staging, CTAs per SM) of the next persistent launch: the context's
 // explicit configuration, else the autotuned shape cached for this format and
 // size class, else the fixed rule -- beyond eight cell bricks per SM the
-// compressed tangent is streamed from global memory (83 vs 90 us per CG
-// iteration on the 3-8M pressed block, equal at 168^3) and the 45-number
-// tangent goes to the column-group solver (210 vs 251 us on the 256^3 slab on
-// sand at impact); below, the CTA-per-brick solver with the shared-memory
-// block; as many CTAs per SM as fit.
+// column-group solver (256^3 slab on sand at impact, 45 numbers: 197 us per CG
+// iteration at four CTAs per SM against 248 us for the shared-memory block;
+// 3-8M pressed block, compressed: 76 us at three CTAs per SM against 82 us
+// streamed), below it the CTA-per-brick solver with the shared-memory block
+// (two CTAs per SM).
 static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
   const int k45 = c->compressed ? 0 : 1;
   int st = c->pcg_cfg.tangent_staging, cp = c->pcg_cfg.ctas_per_sm;
@@ -2967,11 +3075,13 @@ static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
     cudaGetLastError();
     return MPML_ERR_CUDA;
   }
-  if (st == MPML_PCG_AUTO)
-    st = c->ncb > 4 * 2 * (int64_t)n ? (k45 ? MPML_PCG_COLUMNS : MPML_PCG_STREAMED) : MPML_PCG_STAGED;
-  const int fit = launch_fit(pcg_kernel(k45, st), 256, pcg_smem(k45, st), pcg_slot(k45, st), nullptr);
+  if (st == MPML_PCG_AUTO) st = c->ncb > 4 * 2 * (int64_t)n ? MPML_PCG_COLUMNS : MPML_PCG_STAGED;
+  // the column-group form has a build per CTA count; without a choice, four CTAs per SM
+  // for the 45-number tangent and three (85 registers) for the compressed one
+  const int want = cp > 0 ? cp : (st == MPML_PCG_COLUMNS ? (k45 ? 4 : 3) : 2);
+  const int fit = launch_fit(pcg_kernel(k45, st, want), 256, pcg_smem(k45, st), pcg_slot(k45, st, want), nullptr);
   if (fit <= 0) return MPML_ERR_CUDA;
-  if (cp == 0) cp = fit;
+  if (cp == 0) cp = fit < want ? fit : want;
   if (cp > fit) return MPML_ERR_ARG;
   *staging = st;
   *ctas = cp;
@@ -2983,7 +3093,7 @@ static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
 // ev0 / ev1 (optional) are recorded around it on the context stream.
 static int pcg_launch(mpml_ctx_s* c, int cg_max, int staging, int ctas, int nsm, cudaEvent_t ev0, cudaEvent_t ev1) {
   const int k45 = c->compressed ? 0 : 1;
-  const void* kfn = pcg_kernel(k45, staging);
+  const void* kfn = pcg_kernel(k45, staging, ctas);
   const size_t smem = pcg_smem(k45, staging);
   const int G = ctas * nsm;
   int rc;
@@ -3081,7 +3191,8 @@ int pcg_autotune(mpml_ctx_s* c, int iters, int reps, int* choice, float* ms) {
   int arg = -1;
   for (int shape = 0; shape < MPML_PCG_SHAPES && !rc; ++shape) {
     const int staging = PCG_SHAPE_TABLE[shape][0], ctas = PCG_SHAPE_TABLE[shape][1];
-    const int fit = launch_fit(pcg_kernel(k45, staging), 256, pcg_smem(k45, staging), pcg_slot(k45, staging), nullptr);
+    const int fit = launch_fit(pcg_kernel(k45, staging, ctas), 256, pcg_smem(k45, staging),
+                               pcg_slot(k45, staging, ctas), nullptr);
     if (fit < ctas) continue;
     float tbest = -1.f;
     for (int i = 0; i <= reps && !rc; ++i) {

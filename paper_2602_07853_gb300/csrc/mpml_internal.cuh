@@ -250,11 +250,11 @@ inline unsigned div_up(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b
 // queries how many CTAs of `threads` threads fit on one SM; returns that count
 // (0 when the query fails) and, if nsm is not null, the device's SM count.
 enum LaunchSlot : int {
-  LS_PCG = 0,       // 6 persistent-solver variants: + K45 + 2 * (staging - 1)
-  LS_BATCH = 6,
-  LS_HVP64 = 7,
-  LS_CONV = 8,      // 4 convolution kernels of the learned preconditioner
-  LS_COUNT = 12
+  LS_PCG = 0,       // 10 persistent-solver builds (tangent format x form x CTAs per SM)
+  LS_BATCH = 10,
+  LS_HVP64 = 11,
+  LS_CONV = 12,     // 4 convolution kernels of the learned preconditioner
+  LS_COUNT = 16
 };
 int launch_fit(const void* fn, int threads, size_t smem, int slot, int* nsm);
 

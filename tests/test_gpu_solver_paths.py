@@ -7,9 +7,10 @@
   (both stop at relative residual 1e-6: compared at 1e-4 on v - vhat, element by element),
   and the persistent-solver autotuner's choice.
 - Full-size solves of the 3-8M pressed block (1,051,200 active cells, about 2,100 cell bricks:
-  the streamed kernel) and of the 256^3 slab on sand at impact (19.2M particles, 2.5M cells:
-  the staged 45-number kernel, 16+ bricks per CTA): the oracle's own FP64 gradient at the GPU
-  solution is within the Newton tolerance of its gradient at the start.
+  the column-group and streamed kernels) and of the 256^3 slab on sand at impact (19.2M
+  particles, 2.5M cells: the column-group kernel and the staged 45-number kernel with 16+ bricks
+  per CTA): the oracle's own FP64 gradient at the GPU solution is within the Newton tolerance of
+  its gradient at the start.
 - The slab on sand at impact, reduced to 64^3 (mixed slab / sand cells from the first step,
   plastic flow in both materials), stepped through the impact against the oracle.
 - A batch of 16 scenes of uneven size in one lockstep solve against per-scene oracle steps.
@@ -99,12 +100,12 @@ def full_size_gradient_check(sc, expect_staging, force=None):
     return st
 
 
-@pytest.mark.parametrize("force", [None, (m.PCG_COLUMNS, 4)])
+@pytest.mark.parametrize("force", [None, (m.PCG_STREAMED, 2)])
 def test_full_size_pressed_block_236(force):
-    """Config 3 at dx = 1/236 (7.9M particles): without a tuned shape, above eight cell bricks
-    per SM the compressed tangent is streamed (the fixed rule), a path smaller scenes reach only
-    when forced; and the column-group solver at four CTAs per SM."""
-    full_size_gradient_check(scenes.pressed_block(236), force[0] if force else m.PCG_STREAMED, force)
+    """Config 3 at dx = 1/236 (7.9M particles, about 2,100 cell bricks): without a tuned shape,
+    above eight cell bricks per SM the column-group solver runs the compressed tangent (the fixed
+    rule); and the CTA-per-brick solver with streamed rows and many bricks per CTA."""
+    full_size_gradient_check(scenes.pressed_block(236), force[0] if force else m.PCG_COLUMNS, force)
 
 
 @pytest.mark.parametrize("force", [None, (m.PCG_STAGED, 2)])
