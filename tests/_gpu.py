@@ -28,6 +28,13 @@ def max_err(a, b):
 REPORT = []
 
 
+def record(name, value, tol):
+    """A scalar error measured by a test (e.g. positions in units of dx) into the report."""
+    import os
+    REPORT.append((os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], str(name), float(value), float(value), tol))
+    assert value <= tol, f"{name}: {value:.3e} > {tol}"
+
+
 def check(got, want, tol, name="", elem_tol=None):
     """Element-by-element parity of a floating-point field: the norm-relative error
     ||a - b|| / ||b|| and the largest element error max|a - b| / max|b| are both within tol
