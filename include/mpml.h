@@ -332,11 +332,12 @@ void mpml_tile_cache_clear(void);
  *                      layer's rows one layer ahead)
  *   MPML_PCG_AUTO      the shape mpml_autotune_pcg chose for this tangent format
  *                      and size class, else a fixed rule: above 8 cell bricks
- *                      per SM column groups (4 CTAs per SM for the 45-number
- *                      tangent, 3 for the compressed one), staged otherwise
- * ctas_per_sm: CTAs per SM of the cooperative launch (0 = as many as fit, at
- *   most 2 for the first two forms and 4 for the third; a value above what
- *   fits is MPML_ERR_ARG at the next solve).
+ *                      per SM column groups at 3 CTAs per SM, staged at 2
+ *                      otherwise
+ * ctas_per_sm: CTAs per SM of the cooperative launch (0 = the autotuned or
+ *   fixed-rule count, capped at what fits; at most 2 for the first two forms
+ *   and 4 for the third; a value above what fits is MPML_ERR_ARG at the next
+ *   solve).
  * barrier_spins: bound on the polls of one grid-barrier wait (0 = the default
  *   2^25 polls of 32 ns, about a second).  A wait that runs out ends the solve:
  *   mpml_newton_step returns MPML_ERR_TIMEOUT; the next mpml_resample clears the

@@ -2593,50 +2593,17 @@ __global__ void __launch_bounds__(256, 2) k_pcg_persistent(PcgArgs A) {
 // without any block-wide barrier inside phase H.
 // ---------------------------------------------------------------------------
 struct ColGroup {
-  float sv[3][729];          // p_new on the 9^3 node block
+  float sv[3][405];          // p_new on the unit's 9 x 9 x 5 node block
   float sxr[2][2][3][8];     // [z parity][E, E8 of row 3][a][x]
-  float m[BV];               // the brick's node masses
+  float m[256];              // the masses of the unit's owned nodes
   int nbr[NBR];
-  uint8_t cf[BV];            // the brick's active-cell flags
+  uint8_t cf[256];           // the unit's active-cell flags
 };
-
-// node (nx, ny, nz) of the group's brick block receives y[3] (as col_emit_m, with
-// the brick's masses from shared memory)
-__device__ __forceinline__ void col_emit_g(int id, const ColGroup& S, float* q, int nx, int ny, int nz,
-                                          const float y[3]) {
-  if (nx < 8 && ny < 8 && nz < 8) {
-    const int l = (nz * 8 + ny) * 8 + nx;
-    float* dst = q + (int64_t)id * 3 * BV + l;
-    const float mi = S.m[l];
-    const int i = hidx(nx, ny, nz);
-    if (nx >= 1 && ny >= 1 && nz >= 1) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) dst[a * BV] = y[a] + mi * S.sv[a][i];
-    } else {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const float val = y[a] + mi * S.sv[a][i];
-        if (val != 0.f) atomicAdd(dst + a * BV, val);
-      }
-    }
-  } else {
-    const int t = S.nbr[nbr_index(nx >> 3, ny >> 3, nz >> 3)];
-    if (t < 0) return;
-    const int l = ((nz & 7) * 8 + (ny & 7)) * 8 + (nx & 7);
-    float* dst = q + (int64_t)t * 3 * BV + l;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (y[a] != 0.f) atomicAdd(dst + a * BV, y[a]);
-  }
-}
 
 __device__ __forceinline__ void group_sync(int g) {
   asm volatile("bar.sync %0, 64;" ::"r"(g + 1) : "memory");
 }
 
-// MINB: CTAs per SM the build is for (4: 64 registers; 3: 85; 2: 128 registers, and
-// then each thread loads the next layer's tangent rows while it applies the current
-// layer's, so that one layer's memory latency overlaps the previous layer's work).
 // Half-brick work units: unit (brick, hz) holds the brick's cell layers 4hz .. 4hz+3
 // and its node layers 4hz .. 4hz+4 (local layers 0 .. 4); it owns (writes p_new and
 // adds the mass term for) the node layers 4hz .. 4hz+3 of the brick.  Node (nx, ny,
@@ -2649,7 +2616,7 @@ __device__ __forceinline__ void col_emit_h(int id, const ColGroup& S, float* q, 
     const int l = (nz * 8 + ny) * 8 + nx;
     float* dst = q + (int64_t)id * 3 * BV + l;
     const bool owned = nzl < 4;
-    const float mi = owned ? S.m[l] : 0.f;
+    const float mi = owned ? S.m[l - 256 * hz] : 0.f;
     const int i = hidx(nx, ny, nzl);
     if (owned && nx >= 1 && ny >= 1 && nzl >= 1) {
 #pragma unroll
@@ -2676,6 +2643,7 @@ template <bool K45, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
   constexpr int NQ = K45 ? 45 : NQC;
   constexpr bool PF = MINB <= 2;
+  constexpr int SB = 3;  // halo nodes per thread and load batch
   constexpr unsigned FULL = 0xffffffffu;
   __shared__ ColGroup gs[4];
   __shared__ int s_flag;
@@ -2691,6 +2659,7 @@ __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
     s_tol2 = sc->tol2;
     s_rr_last = sc->rr_last;
   }
+
   int done = sc->done;
   int it = 0;
   float beta = 0.f;
@@ -2711,11 +2680,11 @@ __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
       group_sync(g);
       // p_new on the unit's 9 x 9 x 5 node block, three nodes per thread and batch, all
       // loads first; the owned nodes' p_new and masses are written
-      for (int i0 = t; i0 < 405; i0 += 3 * 64) {
-        int tb[3], ll[3];
-        float dv[3][3], rv[3][3], pv[3][3], mv[3];
+      for (int i0 = t; i0 < 405; i0 += SB * 64) {
+        int tb[SB], ll[SB];
+        float dv[SB][3], rv[SB][3], pv[SB][3], mv[SB];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < SB; ++k) {
           const int i = i0 + 64 * k;
           tb[k] = -1;
           ll[k] = 0;
@@ -2741,7 +2710,7 @@ __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
           }
         }
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < SB; ++k) {
           const int i = i0 + 64 * k;
           if (i >= 405) continue;
           float v[3];
@@ -2753,7 +2722,7 @@ __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
             pnext[o + BV] = v[1];
             pnext[o + 2 * BV] = v[2];
             pmp += mv[k] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            S.m[ll[k]] = mv[k];
+            S.m[ll[k] - 256 * hz] = mv[k];
           }
           S.sv[0][i] = v[0];
           S.sv[1][i] = v[1];
@@ -2818,7 +2787,8 @@ __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
             if (K45) {
               float k[45];
 #pragma unroll
-              for (int qq = 0; qq < 45; ++qq) k[qq] = PF ? kc[qq < (PF ? NQ : 1) ? qq : 0] : ld_stream(Kb + qq * BV + l);
+              for (int qq = 0; qq < 45; ++qq)
+                k[qq] = PF ? kc[qq < (PF ? NQ : 1) ? qq : 0] : ld_stream(Kb + qq * BV + l);
 #pragma unroll
               for (int r = 0; r < 9; ++r) {
                 KD[r] += k[k45(r, r)] * D[r];
@@ -2831,7 +2801,8 @@ __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
             } else {
               float c[NQC];
 #pragma unroll
-              for (int qq = 0; qq < NQC; ++qq) c[qq] = PF ? kc[qq < (PF ? NQ : 1) ? qq : 0] : ld_stream(Kb + qq * BV + l);
+              for (int qq = 0; qq < NQC; ++qq)
+                c[qq] = PF ? kc[qq < (PF ? NQ : 1) ? qq : 0] : ld_stream(Kb + qq * BV + l);
               apply_cmp(c, D, KD);
             }
 #pragma unroll
@@ -2953,22 +2924,31 @@ __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
     const float alpha = s_coef;
     // ---------------- phase A ----------------
     float rzl = 0.f, rrl = 0.f;
-    for (int jb = blockIdx.x; jb < A.nb; jb += G) {
-      float2 d2[3], p2[3], q2[3], x2[3], r2[3];
+    constexpr int PA = 1;  // node bricks per phase-A pass
+    for (int jb0 = blockIdx.x; jb0 < A.nb; jb0 += PA * G) {
+      // PA node bricks per pass, all loads issued first
+      float2 d2[PA * 3], p2[PA * 3], q2[PA * 3], x2[PA * 3], r2[PA * 3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
-        d2[a] = __ldcg(reinterpret_cast<const float2*>(A.dinv + o));
-        p2[a] = __ldcg(reinterpret_cast<const float2*>(pnext + o));
-        q2[a] = __ldcg(reinterpret_cast<const float2*>(A.q + o));
-        x2[a] = __ldcg(reinterpret_cast<const float2*>(A.x + o));
-        r2[a] = __ldcg(reinterpret_cast<const float2*>(A.r + o));
+      for (int e = 0; e < PA * 3; ++e) {
+        const int jb = jb0 + (e / 3) * G, a = e % 3;
+        if (jb < A.nb) {
+          const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
+          d2[e] = __ldcg(reinterpret_cast<const float2*>(A.dinv + o));
+          p2[e] = __ldcg(reinterpret_cast<const float2*>(pnext + o));
+          q2[e] = __ldcg(reinterpret_cast<const float2*>(A.q + o));
+          x2[e] = __ldcg(reinterpret_cast<const float2*>(A.x + o));
+          r2[e] = __ldcg(reinterpret_cast<const float2*>(A.r + o));
+        } else {
+          d2[e] = p2[e] = q2[e] = x2[e] = r2[e] = make_float2(0.f, 0.f);
+        }
       }
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
+      for (int e = 0; e < PA * 3; ++e) {
+        const int jb = jb0 + (e / 3) * G, a = e % 3;
+        if (jb >= A.nb) continue;
         const int64_t o = ((int64_t)jb * 3 + a) * BV + 2 * threadIdx.x;
-        const float2 d = d2[a], pp = p2[a], qq = q2[a];
-        float2 xx = x2[a], rr = r2[a];
+        const float2 d = d2[e], pp = p2[e], qq = q2[e];
+        float2 xx = x2[e], rr = r2[e];
         if (d.x > 0.f) {
           xx.x += alpha * pp.x;
           rr.x -= alpha * qq.x;
@@ -3032,7 +3012,7 @@ static const void* pcg_kernel(int k45, int staging, int ctas) {
              : (streamed ? (const void*)k_pcg_persistent<false, true> : (const void*)k_pcg_persistent<false>);
 }
 
-static size_t pcg_smem(int k45, int staging) {
+static size_t pcg_smem(int k45, int staging, int ctas) {
   if (staging == MPML_PCG_COLUMNS) return 0;  // static shared memory only
   return staging == MPML_PCG_STREAMED ? sizeof(float) * (3 * 729 + HVP_X_FLOATS + HVP_R_FLOATS) + 32
                                       : (k45 ? HVP_K_SMEM45 : HVP_C_SMEM_COL);
@@ -3055,11 +3035,11 @@ static int pcg_cache_format(int k45) { return k45 ? 145 : 125; }
 // The shape (staging, CTAs per SM) of the next persistent launch: the context's
 // explicit configuration, else the autotuned shape cached for this format and
 // size class, else the fixed rule -- beyond eight cell bricks per SM the
-// column-group solver (256^3 slab on sand at impact, 45 numbers: 197 us per CG
-// iteration at four CTAs per SM against 248 us for the shared-memory block;
-// 3-8M pressed block, compressed: 76 us at three CTAs per SM against 82 us
-// streamed), below it the CTA-per-brick solver with the shared-memory block
-// (two CTAs per SM).
+// column-group solver at three CTAs per SM (256^3 slab on sand at impact, 45
+// numbers: 186 us per CG iteration against 204 us at four CTAs per SM and 248 us
+// for the shared-memory block; 3-8M pressed block, compressed: 73 us against
+// 82 us streamed), below it the CTA-per-brick solver with the shared-memory
+// block (two CTAs per SM).
 static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
   const int k45 = c->compressed ? 0 : 1;
   int st = c->pcg_cfg.tangent_staging, cp = c->pcg_cfg.ctas_per_sm;
@@ -3076,10 +3056,9 @@ static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
     return MPML_ERR_CUDA;
   }
   if (st == MPML_PCG_AUTO) st = c->ncb > 4 * 2 * (int64_t)n ? MPML_PCG_COLUMNS : MPML_PCG_STAGED;
-  // the column-group form has a build per CTA count; without a choice, four CTAs per SM
-  // for the 45-number tangent and three (85 registers) for the compressed one
-  const int want = cp > 0 ? cp : (st == MPML_PCG_COLUMNS ? (k45 ? 4 : 3) : 2);
-  const int fit = launch_fit(pcg_kernel(k45, st, want), 256, pcg_smem(k45, st), pcg_slot(k45, st, want), nullptr);
+  // the column-group form has a build per CTA count (2, 3, 4); without a choice, three
+  const int want = cp > 0 ? cp : (st == MPML_PCG_COLUMNS ? 3 : 2);
+  const int fit = launch_fit(pcg_kernel(k45, st, want), 256, pcg_smem(k45, st, want), pcg_slot(k45, st, want), nullptr);
   if (fit <= 0) return MPML_ERR_CUDA;
   if (cp == 0) cp = fit < want ? fit : want;
   if (cp > fit) return MPML_ERR_ARG;
@@ -3094,7 +3073,7 @@ static int pcg_shape(mpml_ctx_s* c, int* staging, int* ctas, int* nsm) {
 static int pcg_launch(mpml_ctx_s* c, int cg_max, int staging, int ctas, int nsm, cudaEvent_t ev0, cudaEvent_t ev1) {
   const int k45 = c->compressed ? 0 : 1;
   const void* kfn = pcg_kernel(k45, staging, ctas);
-  const size_t smem = pcg_smem(k45, staging);
+  const size_t smem = pcg_smem(k45, staging, ctas);
   const int G = ctas * nsm;
   int rc;
   // barrier words (2 unsigned) followed by the 4 x 2 rotating accumulators
@@ -3191,7 +3170,7 @@ int pcg_autotune(mpml_ctx_s* c, int iters, int reps, int* choice, float* ms) {
   int arg = -1;
   for (int shape = 0; shape < MPML_PCG_SHAPES && !rc; ++shape) {
     const int staging = PCG_SHAPE_TABLE[shape][0], ctas = PCG_SHAPE_TABLE[shape][1];
-    const int fit = launch_fit(pcg_kernel(k45, staging, ctas), 256, pcg_smem(k45, staging),
+    const int fit = launch_fit(pcg_kernel(k45, staging, ctas), 256, pcg_smem(k45, staging, ctas),
                                pcg_slot(k45, staging, ctas), nullptr);
     if (fit < ctas) continue;
     float tbest = -1.f;
