@@ -755,6 +755,8 @@ def run_ours(args, rank, world, local_rank):
         mean_ms = pcg_ms / pcg_n
         achieved = alg_bytes / (pcg_ms / 1e3) / 1e9
         tr = ncu_traffic(f"slab_on_sand_{args.n}_impact") if last_staging == 3 else None
+        if tr and tr.get("ctas_per_sm") != last_ctas:
+            tr = None  # captured with another CTA count
         traffic = None
         if tr:
             # the captured smaller case's DRAM bytes per CG iteration, scaled by the active cells
