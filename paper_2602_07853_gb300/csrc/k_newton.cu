@@ -816,13 +816,14 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
       return;
     }
   }
+  // FP32 contexts: the FP64 stress and energy to about 1e-14 (LITE: jacobi3_lite, Newton-
+  // refined reciprocals, series logarithms; the FP64 pipe bounds this kernel), the tangent
+  // moduli, stored in FP32, evaluated in FP32
+  constexpr bool LITE = sizeof(T) == 4;
   double U[9], s[3], e[3], Vv[9], Jm1;
-  svd_from_h<double>(H, U, s, e, Vv, Jm1);
-  // the energy and the principal stresses in FP64 (the gradient); in FP32 contexts the
-  // tangent moduli, stored in FP32, are evaluated in FP32 (FP64 divisions and logarithms
-  // are the expensive part of this kernel on this part)
+  svd_from_h<double, LITE>(H, U, s, e, Vv, Jm1);
   Spec<double> sp;
-  if (!spectral<double, sizeof(T) == 4 ? 1 : 3>(M, s, e, Jm1, sp)) {
+  if (!spectral<double, LITE ? 5 : 3>(M, s, e, Jm1, sp)) {
     out.ok = false;
     return;
   }
@@ -1915,10 +1916,11 @@ __global__ void __launch_bounds__(256) k_energy_cells(const int* __restrict__ cb
         continue;
       }
       if (need_svd) {
+        // FP32 contexts: the same LITE evaluation as the Newton prep's energy
         double U[9], s[3], e[3], Vv[9], Jm1;
-        svd_from_h<double>(H, U, s, e, Vv, Jm1);
+        svd_from_h<double, sizeof(T) == 4>(H, U, s, e, Vv, Jm1);
         Spec<double> sp;
-        if (!spectral<double, 1>(si.mat[k], s, e, Jm1, sp)) {  // the energy only
+        if (!spectral<double, sizeof(T) == 4 ? 5 : 1>(si.mat[k], s, e, Jm1, sp)) {  // the energy only
           bad = 1;
           continue;
         }

@@ -432,14 +432,126 @@ __device__ inline void jacobi3_mixed(const double Ain[9], double ev[3], double Q
   ev[2] = B[8] * isc;
 }
 
-// jacobi3 in the type's precision; FP64 through jacobi3_mixed
-template <typename T>
-__device__ __forceinline__ void jacobi3_fast(const T A[9], T ev[3], T Q[9]) {
-  jacobi3<T>(A, ev, Q);
+// 1/sqrt(x) and 1/x (x > 0, finite, within the FP32 range) from the FP32 rsqrt
+// approximation refined by Newton-Raphson steps in FP64: y <- y (3 - x y^2) / 2 for
+// the reciprocal square root, y <- y (2 - x y) for the reciprocal (each step squares
+// the relative error: 1e-7 -> 1e-14 -> rounding).  A few FP64 multiply-adds in place
+// of the longer FP64 division and square-root sequences.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);
+  return y * (1.5 - 0.5 * x * y * y);
 }
-template <>
-__device__ __forceinline__ void jacobi3_fast<double>(const double A[9], double ev[3], double Q[9]) {
-  jacobi3_mixed(A, ev, Q);
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double r = (double)rsqrtf((float)x);
+  double y = r * r;
+  y = y + y * (1.0 - x * y);
+  return y + y * (1.0 - x * y);
+}
+
+// Eigen-decomposition of a symmetric 3x3 to about 1e-14 of its norm (eigenvalues)
+// with the least FP64 work, for the FP64 stress, gradient and energy of FP32
+// contexts: cyclic Jacobi in FP32 on the matrix scaled by a power of two; the
+// first two FP32 eigenvectors made orthonormal in FP64 by Gram-Schmidt, the third
+// their cross product; B = Q^T A Q in FP64; then one FP64 Jacobi sweep on B with
+// FP32-formed angles and the symmetric update (b_pp -= t b_pq, b_qq += t b_pq,
+// b_pq := 0).  After the FP32 stage the off-diagonal of B is ~1e-7 of the norm;
+// the sweep's angles are good to FP32 rounding, so what it leaves is ~1e-14 of
+// the norm, and the eigenvalues (diagonal of B) carry its square over the gap.
+// Same output convention as jacobi3.
+__device__ inline void jacobi3_lite(const double Ain[9], double ev[3], double Q[9]) {
+  double amax = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) amax = fmax(amax, fabs(Ain[i]));
+  if (!(amax > 0.0) || !(amax < 1e300)) {  // zero or non-finite: the plain FP64 sweeps
+    jacobi3<double>(Ain, ev, Q);
+    return;
+  }
+  const int ex = ilogb(amax);
+  const double sc = scalbn(1.0, -ex), isc = scalbn(1.0, ex);
+  double A[9];
+  float Af[9], evf[3], Qf[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    A[i] = Ain[i] * sc;
+    Af[i] = (float)A[i];
+  }
+  jacobi3<float>(Af, evf, Qf);
+  // Gram-Schmidt on columns 0 and 1, column 2 = column 0 x column 1
+  double q0[3] = {(double)Qf[0], (double)Qf[3], (double)Qf[6]};
+  double q1[3] = {(double)Qf[1], (double)Qf[4], (double)Qf[7]};
+  const double i0 = rsqrt_nr(q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) q0[r] *= i0;
+  const double d01 = q0[0] * q1[0] + q0[1] * q1[1] + q0[2] * q1[2];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) q1[r] -= d01 * q0[r];
+  const double i1 = rsqrt_nr(q1[0] * q1[0] + q1[1] * q1[1] + q1[2] * q1[2]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) q1[r] *= i1;
+  const double q2[3] = {q0[1] * q1[2] - q0[2] * q1[1], q0[2] * q1[0] - q0[0] * q1[2], q0[0] * q1[1] - q0[1] * q1[0]};
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    Q[3 * r] = q0[r];
+    Q[3 * r + 1] = q1[r];
+    Q[3 * r + 2] = q2[r];
+  }
+  // B = Q^T A Q (upper part, mirrored)
+  double AQ[9], B[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) AQ[3 * a + b] = A[3 * a] * Q[b] + A[3 * a + 1] * Q[3 + b] + A[3 * a + 2] * Q[6 + b];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = a; b < 3; ++b) {
+      const double v = Q[a] * AQ[b] + Q[3 + a] * AQ[3 + b] + Q[6 + a] * AQ[6 + b];
+      B[3 * a + b] = v;
+      B[3 * b + a] = v;
+    }
+#pragma unroll
+  for (int pq = 0; pq < 3; ++pq) {
+    const int p = pq == 2 ? 1 : 0;
+    const int q = pq == 0 ? 1 : 2;
+    const int r = 3 - p - q;
+    const double bpq = B[3 * p + q];
+    const float apq = (float)bpq;
+    if (apq == 0.f) continue;
+    const float theta = (float)(B[3 * q + q] - B[3 * p + p]) / (2.f * apq);
+    const float tf = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+    const double t = (double)tf;
+    const double cc = rsqrt_nr(1.0 + t * t), ss = t * cc;
+    B[3 * p + p] -= t * bpq;
+    B[3 * q + q] += t * bpq;
+    B[3 * p + q] = B[3 * q + p] = 0.0;
+    const double brp = B[3 * r + p], brq = B[3 * r + q];
+    B[3 * r + p] = B[3 * p + r] = cc * brp - ss * brq;
+    B[3 * r + q] = B[3 * q + r] = ss * brp + cc * brq;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double vkp = Q[3 * k + p], vkq = Q[3 * k + q];
+      Q[3 * k + p] = cc * vkp - ss * vkq;
+      Q[3 * k + q] = ss * vkp + cc * vkq;
+    }
+  }
+  ev[0] = B[0] * isc;
+  ev[1] = B[4] * isc;
+  ev[2] = B[8] * isc;
+}
+
+// jacobi3 in the type's precision; FP64 through jacobi3_mixed (to FP64 rounding) or
+// jacobi3_lite (to about 1e-14)
+template <typename T, bool LITE = false>
+__device__ __forceinline__ void jacobi3_fast(const T A[9], T ev[3], T Q[9]) {
+  if constexpr (sizeof(T) == 8) {
+    if constexpr (LITE)
+      jacobi3_lite(A, ev, Q);
+    else
+      jacobi3_mixed(A, ev, Q);
+  } else {
+    jacobi3<T>(A, ev, Q);
+  }
 }
 
 // [persistent-solver source: begin]
@@ -774,10 +886,21 @@ __device__ __forceinline__ float phase_h_col(int id, const int* s_nbr, const flo
 
 // [persistent-solver source: end]
 
+// 1 / sqrt(nn): FP64 LITE builds take rsqrt_nr within the FP32 range
+template <typename T, bool LITE>
+__device__ __forceinline__ T inv_sqrt_t(T nn) {
+  if constexpr (LITE && sizeof(T) == 8) {
+    if (nn > T(1e-36) && nn < T(1e36)) return rsqrt_nr(nn);
+  }
+  return T(1) / dsqrt(nn);
+}
+
 // Signed SVD of F = I + H from the eigen-decomposition of F^T F - I =
 // H + H^T + H^T H, returning s = singular values (s0 >= s1 >= |s2|, s2 < 0
 // when det F < 0), e = s - 1 computed without cancellation, J - 1 likewise.
-template <typename T>
+// LITE (FP64): the eigen-decomposition by jacobi3_lite and the square roots and
+// reciprocals by rsqrt_nr / rcp_nr -- results to about 1e-14 instead of FP64 rounding.
+template <typename T, bool LITE = false>
 __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1) {
   T E[9];
 #pragma unroll
@@ -790,7 +913,7 @@ __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1)
       E[3 * a + b] = acc;
     }
   T lam[3], W[9];
-  jacobi3_fast<T>(E, lam, W);
+  jacobi3_fast<T, LITE>(E, lam, W);
   int i0 = 0, i1 = 1, i2 = 2;
   if (lam[i1] > lam[i0]) { int t = i0; i0 = i1; i1 = t; }
   if (lam[i2] > lam[i0]) { int t = i0; i0 = i2; i2 = t; }
@@ -811,7 +934,15 @@ __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1)
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     T li = l[i] > T(-1) ? l[i] : T(-1);
-    s[i] = dsqrt(T(1) + li);
+    const T x = T(1) + li;
+    if constexpr (LITE && sizeof(T) == 8) {
+      if (x > T(1e-30) && x < T(1e30)) {
+        s[i] = x * rsqrt_nr(x);
+        e[i] = li * rcp_nr(T(1) + s[i]);
+        continue;
+      }
+    }
+    s[i] = dsqrt(x);
     e[i] = li / (T(1) + s[i]);
   }
   // b_j = F v_j
@@ -826,9 +957,9 @@ __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1)
       b[j][r] = acc;
     }
   T u0[3], u1[3], u2[3];
-  T n0 = dsqrt(b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2]);
-  if (n0 > T(1e-30)) {
-    const T in0 = T(1) / n0;  // one division, three products (divisions are costly in FP64)
+  const T nn0 = b[0][0] * b[0][0] + b[0][1] * b[0][1] + b[0][2] * b[0][2];
+  if (nn0 > T(1e-60)) {
+    const T in0 = inv_sqrt_t<T, LITE>(nn0);  // three products (divisions are costly in FP64)
 #pragma unroll
     for (int r = 0; r < 3; ++r) u0[r] = b[0][r] * in0;
   } else {
@@ -837,9 +968,9 @@ __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1)
   T dd = u0[0] * b[1][0] + u0[1] * b[1][1] + u0[2] * b[1][2];
 #pragma unroll
   for (int r = 0; r < 3; ++r) u1[r] = b[1][r] - dd * u0[r];
-  T n1 = dsqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
-  if (n1 > T(1e-30)) {
-    const T in1 = T(1) / n1;
+  const T nn1 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
+  if (nn1 > T(1e-60)) {
+    const T in1 = inv_sqrt_t<T, LITE>(nn1);
 #pragma unroll
     for (int r = 0; r < 3; ++r) u1[r] *= in1;
   } else {
@@ -982,14 +1113,24 @@ __device__ __forceinline__ int pair_i(int p) { return p == 2 ? 1 : 0; }
 __device__ __forceinline__ int pair_j(int p) { return p == 0 ? 1 : 2; }
 __device__ __forceinline__ int pair_k(int p) { return 2 - p; }
 
+// log(1 + x): for |x| < 0.05 as x minus the series of x - log(1 + x) (about one
+// rounding error, multiply-adds only), otherwise the library function
+template <typename T>
+__device__ __forceinline__ T log1p_series(T x) {
+  return fabs(x) < T(0.05) ? x - x_minus_log1p(x) : log1p_t(x);
+}
+
 // returns false where the energy is undefined (J <= 0 for NH / Hencky)
 // The isotropic eigen-data of psi at the signed singular values s (e = s - 1,
 // Jm1 = J - 1): PARTS bit 1 the energy and the principal stresses d1 (what the
 // gradient needs), bit 2 the projected-tangent moduli d2 (3x3 block), pp (flip)
 // and pm (twist).  The two parts can be evaluated in different precisions.
+// Bit 4 (with the FP64 energy and stresses of FP32 contexts): the Hencky
+// logarithms by log1p_series and the reciprocals of s by rcp_nr.
 template <typename T, int PARTS = 3>
 __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm1, Spec<T>& o) {
   constexpr bool P1 = (PARTS & 1) != 0, P2 = (PARTS & 2) != 0;
+  constexpr bool LITE = (PARTS & 4) != 0 && sizeof(T) == 8;
   const T mu = M.mu, lam = M.lam;
   const T J = T(1) + Jm1;
   if (M.model == MPML_FIXED_COROTATED) {
@@ -1076,14 +1217,22 @@ __device__ bool spectral(const MatParams<T>& M, const T s[3], const T e[3], T Jm
   }
   if (M.model == MPML_HENCKY) {
     if (!(s[0] > T(0) && s[1] > T(0) && s[2] > T(0))) return false;
-    const T l[3] = {log1p_t(e[0]), log1p_t(e[1]), log1p_t(e[2])};
+    T l[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) l[i] = LITE ? log1p_series(e[i]) : log1p_t(e[i]);
     const T tr = l[0] + l[1] + l[2];
     if (P1) o.psi = mu * (l[0] * l[0] + l[1] * l[1] + l[2] * l[2]) + T(0.5) * lam * tr * tr;
     T t[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       t[i] = T(2) * mu * l[i] + lam * tr;
-      if (P1) o.d1[i] = t[i] / s[i];
+      if (P1) {
+        if constexpr (LITE) {
+          o.d1[i] = (s[i] > T(1e-30) && s[i] < T(1e30)) ? t[i] * rcp_nr(s[i]) : t[i] / s[i];
+        } else {
+          o.d1[i] = t[i] / s[i];
+        }
+      }
       if (P2) o.d2[4 * i] = (T(2) * mu + lam - t[i]) / (s[i] * s[i]);
     }
     if (P2) {
