@@ -58,6 +58,9 @@ def parse():
                     help="only build this workload at --n, take --warmup steps, then one solve (for profilers)")
     ap.add_argument("--no-other-configs", action="store_true",
                     help="skip the extra measurements of the other workloads (batch, two spheres, large block)")
+    ap.add_argument("--cg-forcing", type=float, default=0.3,
+                    help="inexact-Newton forcing cap of the trajectory workloads' solves (solver option cg_forcing; "
+                         "0: every CG solve to cg_rtol); Newton stops at 1e-6 of the initial FP64 gradient either way")
     return ap.parse_args()
 
 
@@ -427,7 +430,7 @@ def trajectory(m, sc, warmup, steps, peaks, opts=None, tangent_bytes=None):
     out = {"particles": int(cn["particles"]), "active_cells": int(cn["cells"]), "dof_nodes": int(cn["nodes"]),
            "steps_per_s": 1e3 * len(ms) / float(np.sum(ms)), "ms_per_step": float(np.mean(ms)),
            "newton_iters_per_step": newton / len(ms), "cg_iters_per_step": cg / len(ms),
-           "steps_timed": f"trajectory steps {warmup}..{warmup + steps - 1}",
+           "steps_timed": f"trajectory steps {warmup}..{warmup + steps - 1}", "cg_forcing": opts.cg_forcing,
            "pcg_autotune": {"chosen": tune_shape,
                             "us_per_cg_iter": [round(1e3 * t / 30, 2) if t >= 0 else None for t in tune_ms]}}
     if fb:
@@ -509,12 +512,13 @@ def other_configs(m, args, peaks):
     torch.cuda.empty_cache()
 
     # config 2b: the two-sphere collision at 168^3 along its trajectory from contact
+    fo = m.solver_opts(cg_forcing=args.cg_forcing)
     out["two_spheres_168"] = trajectory(m, scenes.two_spheres(168, gap=1.0 / 168), 3, max(4, min(args.steps, 10)),
-                                        peaks)
+                                        peaks, fo)
     out["two_spheres_168"]["workload"] = ("two Neo-Hookean spheres (E=1e6, nu=0.4, r=0.15) colliding at 2 m/s on a "
                                           "168^3 grid, dt=2e-3, from contact")
     # config 3-8M: the pressed block at dx = 1/236
-    out["pressed_block_236"] = trajectory(m, scenes.pressed_block(236), 2, max(3, min(args.steps, 5)), peaks)
+    out["pressed_block_236"] = trajectory(m, scenes.pressed_block(236), 2, max(3, min(args.steps, 5)), peaks, fo)
     out["pressed_block_236"]["workload"] = ("fixed-corotated block (E=1e8, nu=0.33) pressed by a plate at 0.1 m/s, "
                                             "dx=1/236, dt=1e-3")
 
@@ -576,7 +580,7 @@ def other_configs(m, args, peaks):
     out["ppc_independence_two_spheres_128"] = ppc_rows
 
     # water (Sec. "Water"): dam break with a solid cube in the flow, 128^3, implicit steps
-    out["dam_break_water_128"] = trajectory(m, scenes.dam_break(128), 1, 3, peaks)
+    out["dam_break_water_128"] = trajectory(m, scenes.dam_break(128), 1, 3, peaks, fo)
     out["dam_break_water_128"]["workload"] = ("water column (bulk modulus 3.3e5 Pa) collapsing onto a fixed-corotated "
                                               "cube, steps 1-3 from rest")
     return out
@@ -675,14 +679,14 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     ctx, cur, parts = make_ctx(m, sc, stream)
     init = {k: v.clone() for k, v in cur.items()}
-    opts = m.solver_opts()
+    opts = m.solver_opts(cg_forcing=args.cg_forcing)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     W, K = args.warmup, args.steps
 
-    def one_step(c, pp, s):
+    def one_step(c, pp, s, o=None):
         m.mpml_set_time(c, s * sc.dt)
         m.mpml_resample(c, pp)
-        rc, st = m.mpml_newton_step(c, opts)
+        rc, st = m.mpml_newton_step(c, o if o is not None else opts)
         m.mpml_g2p(c, pp)
         return st
 
@@ -714,7 +718,9 @@ def run_ours(args, rank, world, local_rank):
         alg_bytes += pcg_bytes_per_iter(cn["cells"], cn["nodes"], PACKED_TANGENT_BYTES) * st.cg_iters_total
         floor_bytes += pcg_floor_bytes_per_iter(cn["cells"], cn["nodes"]) * st.cg_iters_total
         per_step.append({"step": W + i, "newton": st.newton_iters, "cg": st.cg_iters_total, "cells": cn["cells"],
-                         "nodes": cn["nodes"]})
+                         "nodes": cn["nodes"], "status": st.status,
+                         "g_rel": st.g_norm / st.g0_norm if st.g0_norm > 0 else 0.0,
+                         "cg_per_newton": [int(st.cg_iters[k]) for k in range(min(st.newton_iters, 64))]})
     barrier()
     clk = clocks.stop()
     launches = m.mpml_kernel_launches(ctx) - launches0
@@ -726,6 +732,27 @@ def run_ours(args, rank, world, local_rank):
     m.mpml_set_profiling(ctx, 0)
     counts = m.mpml_counts(ctx)
     value = job_throughput(world, K, total_ms / 1e3)
+
+    # for comparison: the trajectory continued for three steps with every CG solve to cg_rtol
+    exact = None
+    if args.cg_forcing > 0:
+        o0 = m.solver_opts()
+        ms0, nw0, cg0, gr0 = [], [], [], []
+        for i in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = one_step(ctx, parts, W + K + i, o0)
+            e1.record(stream)
+            e1.synchronize()
+            ms0.append(e0.elapsed_time(e1))
+            nw0.append(st.newton_iters)
+            cg0.append(st.cg_iters_total)
+            gr0.append(st.g_norm / st.g0_norm if st.g0_norm > 0 else 0.0)
+        exact = {"cg_forcing": 0.0, "steps": f"trajectory steps {W + K}..{W + K + 2}",
+                 "steps_per_s": 3e3 / float(np.sum(ms0)), "ms_per_step": float(np.mean(ms0)),
+                 "newton_iters_per_step": float(np.mean(nw0)), "cg_iters_per_step": float(np.mean(cg0)),
+                 "g_rel_max": float(np.max(gr0))}
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region): the same
     # trajectory steps W .. W+K-1 after W untimed warm-up steps from the moment of impact
@@ -831,6 +858,7 @@ def run_ours(args, rank, world, local_rank):
                            "materials": "2 (von Mises slab, Drucker-Prager sand; mixed cells)",
                            "precision": "fp32 storage and arithmetic, fp64 reductions and Newton iterate",
                            "preconditioner": "jacobi", "cg_rtol": 1e-6, "newton_rtol": 1e-6,
+                           "cg_forcing": args.cg_forcing,
                            "steps_timed": f"trajectory steps {W}..{W + K - 1} after impact",
                            "l2": "inputs (2.1 GB of particles) larger than L2, and a 256 MB L2 flush between "
                                  "timed steps",
@@ -838,7 +866,7 @@ def run_ours(args, rank, world, local_rank):
                 "newton_iters_per_step": float(np.mean(newton_its)),
                 "cg_iters_per_step": float(np.mean(cg_its)),
                 "newton_iters_per_s": float(np.sum(newton_its)) / (total_ms / 1e3),
-                "per_step": per_step, "step_ms": step_ms,
+                "per_step": per_step, "step_ms": step_ms, "without_forcing": exact,
                 "pcg_autotune": {"chosen": tune_shape, "shapes": [list(sh) for sh in m.PCG_SHAPE_TABLE],
                                  "us_per_cg_iter": [round(1e3 * t / 30, 2) if t >= 0 else None for t in tune_ms],
                                  "rule": "30 CG iterations of the last warm-up Newton system per shape, best of 2; "

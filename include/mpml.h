@@ -154,6 +154,18 @@ typedef struct {
                           solve), so the converged grid state satisfies the yield condition;
                           the linear solves see elasticity only.  Single-scene solver only
                           (mpml_newton_step_batch rejects it with MPML_ERR_ARG). */
+  double cg_forcing;   /* Not in the paper (which leaves the CG tolerance open).  0 (default):
+                          every CG solve stops at cg_rtol ||g_k||.  In (0, 0.5]: inexact
+                          Newton -- the CG of Newton iteration k stops at eta_k ||g_k|| with
+                          eta_0 = cg_forcing and eta_k = min(cg_forcing, 0.9 (||g_k|| /
+                          ||g_{k-1}||)^2) (Eisenstat and Walker's second forcing choice, with
+                          their safeguard max(eta_k, 0.9 eta_{k-1}^2) when the latter exceeds
+                          0.1), never below cg_rtol nor below half of what the Newton target
+                          still needs (0.5 max(newton_rtol ||g_0||, newton_atol) / ||g_k||),
+                          capped at 0.5.  Newton's own test (newton_rtol on the FP64 gradient)
+                          is unchanged.  Single-scene solver only (mpml_newton_step_batch
+                          rejects a nonzero value with MPML_ERR_ARG); other values are
+                          MPML_ERR_ARG. */
 } mpml_solver_opts;
 
 typedef struct {

@@ -3755,6 +3755,28 @@ static int plastic_project(mpml_ctx_s* c, int* changed) {
   return MPML_OK;
 }
 
+// the CG stopping threshold |r|^2 <= tol2 of the next solve (inexact Newton)
+__global__ void k_set_tol2(DevScalars* sc, double tol2) { sc->tol2 = tol2; }
+
+// Forcing term of Newton iteration k (opts.cg_forcing > 0): Eisenstat and Walker's
+// second choice eta_k = 0.9 (|g_k| / |g_{k-1}|)^2 with their safeguard, capped at
+// cg_forcing, floored at cg_rtol and at half of the reduction the Newton target still
+// needs, and at most 0.5.
+static double newton_forcing(const mpml_solver_opts* o, int k, double gn, double gprev, double eta_prev,
+                             double target) {
+  double eta = o->cg_forcing;
+  if (k > 0 && gprev > 0.0) {
+    const double q = gn / gprev;
+    eta = 0.9 * q * q;
+    const double sg = 0.9 * eta_prev * eta_prev;
+    if (sg > 0.1 && sg > eta) eta = sg;
+    if (eta > o->cg_forcing) eta = o->cg_forcing;
+  }
+  if (eta < o->cg_rtol) eta = o->cg_rtol;
+  if (gn > 0.0 && eta < 0.5 * target / gn) eta = 0.5 * target / gn;
+  return eta < 0.5 ? eta : 0.5;
+}
+
 template <typename T>
 static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st) {
   int rc = alloc_solver<T>(c);
@@ -3791,12 +3813,21 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
   st->g0_norm = g0;
   st->phi0 = phi;
   int status = MPML_OK, it = 0;
+  double gprev = 0.0, eta = 0.0;
+  const double target = fmax(o->newton_rtol * g0, o->newton_atol);
   while (true) {
     if (gn <= o->newton_rtol * g0 || gn <= o->newton_atol || gn <= gfloor) break;
     if (it >= o->newton_max) {
       status = MPML_WARN_NOT_CONVERGED;
       break;
     }
+    if (o->cg_forcing > 0.0) {
+      // inexact Newton: this solve stops at eta |g_k| (the prep set cg_rtol |g_k|)
+      eta = newton_forcing(o, it, gn, gprev, eta, target);
+      k_set_tol2<<<1, 1, 0, c->s>>>(dscal(c), eta * eta * gn * gn);
+      c->launches++;
+    }
+    gprev = gn;
     int cgit = 0;
     double rel = 0;
     c->last_fcg_fallback = 0;

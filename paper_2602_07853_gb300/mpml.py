@@ -56,7 +56,7 @@ class mpml_solver_opts(C.Structure):
     _fields_ = [("cg_rtol", C.c_double), ("cg_max", C.c_int), ("newton_rtol", C.c_double),
                 ("newton_atol", C.c_double), ("newton_max", C.c_int), ("ls_c1", C.c_double),
                 ("ls_max", C.c_int), ("precond", C.c_int), ("check_every", C.c_int), ("use_graph", C.c_int),
-                ("plastic_fixed_point", C.c_int)]
+                ("plastic_fixed_point", C.c_int), ("cg_forcing", C.c_double)]
 
 
 class mpml_solve_stats(C.Structure):
@@ -401,11 +401,13 @@ def material(model, mu, lam, plastic=ELASTIC, yield_stress=0.0, friction_angle=0
 
 
 def solver_opts(cg_rtol=1e-6, cg_max=10000, newton_rtol=1e-6, newton_atol=0.0, newton_max=50, ls_c1=1e-4,
-                ls_max=30, precond=PRECOND_JACOBI, check_every=16, use_graph=2, plastic_fixed_point=0):
+                ls_max=30, precond=PRECOND_JACOBI, check_every=16, use_graph=2, plastic_fixed_point=0,
+                cg_forcing=0.0):
     o = mpml_solver_opts()
     o.cg_rtol, o.cg_max, o.newton_rtol, o.newton_atol, o.newton_max = cg_rtol, cg_max, newton_rtol, newton_atol, newton_max
     o.ls_c1, o.ls_max, o.precond, o.check_every, o.use_graph = ls_c1, ls_max, precond, check_every, use_graph
     o.plastic_fixed_point = int(plastic_fixed_point)
+    o.cg_forcing = float(cg_forcing)
     return o
 
 
