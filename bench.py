@@ -473,7 +473,7 @@ def other_configs(m, args, peaks):
             for c in ctxs:
                 m.mpml_set_time(c, s * scs[0].dt)
             m.mpml_resample_batch(ctxs, parts)
-            rc, st = m.mpml_newton_step_batch(ctxs)
+            rc, st = m.mpml_newton_step_batch(ctxs, m.solver_opts(cg_forcing=args.cg_forcing))
             for c, pp in zip(ctxs, parts):
                 m.mpml_g2p(c, pp)
             torch.cuda.synchronize()
@@ -505,7 +505,8 @@ def other_configs(m, args, peaks):
                                      "bytes_rule": "sum over scenes of (100 B per active cell + 148 B per DOF "
                                                    "node) x that scene's CG iterations, over the launches' time"},
                       "solver": "mpml_resample_batch + mpml_newton_step_batch (one persistent PCG launch per "
-                                "Newton round over all scenes), one stream per scene"}
+                                "Newton round over all scenes), one stream per scene",
+                      "cg_forcing": args.cg_forcing}
     for c in ctxs:
         m.mpml_destroy(c)
     del made

@@ -163,9 +163,8 @@ typedef struct {
                           0.1), never below cg_rtol nor below half of what the Newton target
                           still needs (0.5 max(newton_rtol ||g_0||, newton_atol) / ||g_k||),
                           capped at 0.5.  Newton's own test (newton_rtol on the FP64 gradient)
-                          is unchanged.  Single-scene solver only (mpml_newton_step_batch
-                          rejects a nonzero value with MPML_ERR_ARG); other values are
-                          MPML_ERR_ARG. */
+                          is unchanged.  The batched solver applies it per scene.  Other
+                          values are MPML_ERR_ARG. */
 } mpml_solver_opts;
 
 typedef struct {

@@ -445,6 +445,7 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
   std::vector<mpml_ctx_s*> all(ctxs, ctxs + n);
   std::vector<int> it(n, 0), status(n, MPML_OK), active(n, 0);
   std::vector<double> g0(n, 0.0), gn(n, 0.0), phi(n, 0.0), phi_el(n, 0.0), gfloor(n, 0.0);
+  std::vector<double> gprev(n, 0.0), eta(n, 0.0);  // inexact Newton (opts.cg_forcing > 0)
   mpml_ctx_s* owner = ctxs[0];
   std::vector<mpml_ctx_s*> work;
   for (int i = 0; i < n; ++i) {
@@ -488,6 +489,14 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
     if (idx.empty()) break;
     std::vector<mpml_ctx_s*> cs;
     for (int i : idx) cs.push_back(ctxs[i]);
+    if (o->cg_forcing > 0.0) {
+      // each scene's solve stops at its own forcing term (written on the launch's stream)
+      for (int i : idx) {
+        eta[i] = newton_forcing(o, it[i], gn[i], gprev[i], eta[i], fmax(o->newton_rtol * g0[i], o->newton_atol));
+        gprev[i] = gn[i];
+        if ((rc = set_cg_tol2(ctxs[i], owner->s, eta[i] * eta[i] * gn[i] * gn[i]))) return rc;
+      }
+    }
     // one cooperative launch for every active scene's Jacobi-PCG solve
     if ((rc = pcg_batch(owner, cs, o->cg_max))) return rc;
     if ((rc = read_all(cs))) return rc;

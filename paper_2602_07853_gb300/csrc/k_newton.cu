@@ -3758,12 +3758,17 @@ static int plastic_project(mpml_ctx_s* c, int* changed) {
 // the CG stopping threshold |r|^2 <= tol2 of the next solve (inexact Newton)
 __global__ void k_set_tol2(DevScalars* sc, double tol2) { sc->tol2 = tol2; }
 
+int set_cg_tol2(mpml_ctx_s* c, cudaStream_t s, double tol2) {
+  k_set_tol2<<<1, 1, 0, s>>>(dscal(c), tol2);
+  c->launches++;
+  return cuda_status(cudaGetLastError());
+}
+
 // Forcing term of Newton iteration k (opts.cg_forcing > 0): Eisenstat and Walker's
 // second choice eta_k = 0.9 (|g_k| / |g_{k-1}|)^2 with their safeguard, capped at
 // cg_forcing, floored at cg_rtol and at half of the reduction the Newton target still
 // needs, and at most 0.5.
-static double newton_forcing(const mpml_solver_opts* o, int k, double gn, double gprev, double eta_prev,
-                             double target) {
+double newton_forcing(const mpml_solver_opts* o, int k, double gn, double gprev, double eta_prev, double target) {
   double eta = o->cg_forcing;
   if (k > 0 && gprev > 0.0) {
     const double q = gn / gprev;
@@ -3824,8 +3829,7 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     if (o->cg_forcing > 0.0) {
       // inexact Newton: this solve stops at eta |g_k| (the prep set cg_rtol |g_k|)
       eta = newton_forcing(o, it, gn, gprev, eta, target);
-      k_set_tol2<<<1, 1, 0, c->s>>>(dscal(c), eta * eta * gn * gn);
-      c->launches++;
+      if ((rc = set_cg_tol2(c, c->s, eta * eta * gn * gn))) return rc;
     }
     gprev = gn;
     int cgit = 0;

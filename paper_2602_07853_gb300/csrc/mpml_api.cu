@@ -490,7 +490,8 @@ int mpml_newton_step_batch(mpml_ctx* ctxs, int n, const mpml_solver_opts* o, mpm
   }
   mpml_solver_opts def = {1e-6, 10000, 1e-6, 0.0, 50, 1e-4, 30, MPML_PRECOND_JACOBI, 16, 2, 0, 0.0};
   if (!o) o = &def;
-  if (o->plastic_fixed_point || o->cg_forcing != 0.0) return MPML_ERR_ARG;  // single-scene solver only
+  if (o->plastic_fixed_point) return MPML_ERR_ARG;  // single-scene solver only
+  if (!(o->cg_forcing >= 0.0 && o->cg_forcing <= 0.5)) return MPML_ERR_ARG;
   std::vector<mpml_solve_stats> local;
   if (!stats) {
     local.resize(n);

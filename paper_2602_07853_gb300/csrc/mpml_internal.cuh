@@ -201,6 +201,10 @@ int resample_device_end(mpml_ctx_s* c, const void* x, const void* v, const void*
 int p2q_q2n(mpml_ctx_s* c);
 int stretch_all(mpml_ctx_s* c);
 int newton_solve(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* st);
+// inexact Newton (opts.cg_forcing > 0): the forcing term of Newton iteration k, and the
+// device write of the next CG solve's threshold |r|^2 <= tol2 on stream s
+double newton_forcing(const mpml_solver_opts* o, int k, double gn, double gprev, double eta_prev, double target);
+int set_cg_tol2(mpml_ctx_s* c, cudaStream_t s, double tol2);
 int explicit_solve(mpml_ctx_s* c);
 int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve_stats* st);
 int g2p_device(mpml_ctx_s* c, void* x, void* v, void* F, void* G, void* m, void* V, int32_t* mat);

@@ -194,7 +194,8 @@ def test_slab_on_sand_impact_inexact_newton_against_the_oracle(precision):
 
 
 def test_cg_forcing_out_of_range_is_rejected():
-    """cg_forcing outside [0, 0.5] (or NaN) is MPML_ERR_ARG; the batched solver takes none."""
+    """cg_forcing outside [0, 0.5] (or NaN) is MPML_ERR_ARG, for the single-scene and the batched
+    solver; in range, both converge to Newton's tolerance."""
     sc = scenes.elastic_cube("stretched")
     g = GpuSim(sc, m.FP32)
     g.set_particles()
@@ -205,15 +206,20 @@ def test_cg_forcing_out_of_range_is_rejected():
     rc, _ = g.newton(m.solver_opts(cg_forcing=0.5))
     assert rc == 0
     g.close()
-    scs = [scenes.batch_scene(i, n=32, extent=8) for i in range(2)]
+    scs = [scenes.random_state(scenes.batch_scene(i, n=32, extent=6 + i), 100 + i, v_scale=0.05, G_scale=0.5,
+                               F_scale=0.01) for i in range(2)]
     sims = [GpuSim(s, m.FP32) for s in scs]
     for s in sims:
         s.set_particles()
         s.resample()
     ptrs = [s.ctx.value if isinstance(s.ctx, m.C.c_void_p) else s.ctx for s in sims]
     rc = m.load().mpml_newton_step_batch((m.C.c_void_p * 2)(*ptrs), 2,
-                                         m.C.byref(m.solver_opts(cg_forcing=0.3)), None)
+                                         m.C.byref(m.solver_opts(cg_forcing=0.7)), None)
     assert rc == m.ERR_ARG
+    rc, stats = m.mpml_newton_step_batch([s.ctx for s in sims], m.solver_opts(cg_forcing=0.3))
+    assert rc == 0
+    for st in stats:
+        assert st.newton_iters >= 1 and st.g_norm <= 1e-6 * st.g0_norm
     for s in sims:
         s.close()
 
