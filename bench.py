@@ -721,7 +721,8 @@ def run_ours(args, rank, world, local_rank):
         per_step.append({"step": W + i, "newton": st.newton_iters, "cg": st.cg_iters_total, "cells": cn["cells"],
                          "nodes": cn["nodes"], "status": st.status,
                          "g_rel": st.g_norm / st.g0_norm if st.g0_norm > 0 else 0.0,
-                         "cg_per_newton": [int(st.cg_iters[k]) for k in range(min(st.newton_iters, 64))]})
+                         "cg_per_newton": [int(st.cg_iters[k]) for k in range(min(st.newton_iters, 64))],
+                         "alpha": [float(st.alpha[k]) for k in range(min(st.newton_iters, 64))]})
     barrier()
     clk = clocks.stop()
     launches = m.mpml_kernel_launches(ctx) - launches0

@@ -21,6 +21,8 @@
 // each kernel (no host round trip inside an iteration).
 #include "mpml_internal.cuh"
 
+#include <utility>
+
 namespace mpml {
 
 // ---------------------------------------------------------------------------
@@ -936,7 +938,7 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
                                                  const uint8_t* __restrict__ cflag, const T* __restrict__ acc,
                                                  const double* __restrict__ cs, const double* __restrict__ v,
                                                  SolveInfo si, int want_k, T* __restrict__ K, double* g, T* diag,
-                                                 DevScalars* sc, int* status, int want_psi) {
+                                                 DevScalars* sc, int* status, int want_psi, int trial) {
   __shared__ double sv[3][729];
   const int id = cblist[blockIdx.x];
   stage_nodes<double, double, double>(id, nbr, v, nullptr, 0.0, sv);
@@ -1010,7 +1012,14 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
       }
     }
   }
-  if (bad) atomicOr(status, ST_NONFINITE);
+  // a trial iterate of the line search reports cells where the energy is undefined as
+  // infeasible (the step is rejected); elsewhere they are an error
+  if (bad) {
+    if (trial)
+      atomicAdd(&sc->infeasible, 1);
+    else
+      atomicOr(status, ST_NONFINITE);
+  }
   double vals[1] = {esum};
   double* const dst[1] = {&sc->phi_el};
   block_add<1>(vals, dst);
@@ -1018,9 +1027,11 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
 
 // finalize the gradient (mask), Jacobi inverse, |g|^2 and the CG start:
 // x = 0, r = -g, z = D^-1 r, p = z, q(face) = 0.
+// mode 0: mask, inverse and |g|^2 only; 1: all; 2: the CG start only (g masked and the
+// diagonal inverted by an earlier mode-0 launch).
 template <typename T>
 __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
-                                                  double* g, T* diag_dinv, T* x, T* r, T* p, T* q, int init_cg,
+                                                  double* g, T* diag_dinv, T* x, T* r, T* p, T* q, int mode,
                                                   double rtol2, int cg_max, DevScalars* sc, double* part) {
   const int id = blockIdx.x, l = threadIdx.x;
   const int64_t slot = (int64_t)id * BV + l;
@@ -1034,11 +1045,16 @@ __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nf
   for (int a = 0; a < 3; ++a) {
     const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
     double gv = free_ ? g[o] : 0.0;
-    g[o] = gv;
-    T di = free_ ? T(1) / diag_dinv[o] : T(0);
-    diag_dinv[o] = di;
+    T di;
+    if (mode == 2) {
+      di = free_ ? diag_dinv[o] : T(0);
+    } else {
+      g[o] = gv;
+      di = free_ ? T(1) / diag_dinv[o] : T(0);
+      diag_dinv[o] = di;
+    }
     gg += gv * gv;
-    if (init_cg) {
+    if (mode != 0) {
       T rv = (T)(-gv), zv = di * rv;
       x[o] = T(0);
       r[o] = rv;
@@ -1947,6 +1963,19 @@ __global__ void __launch_bounds__(512) k_axpy(const T* __restrict__ dinv, const 
   }
 }
 
+// v_out = v + alpha x on free DOFs, v elsewhere (the line search's trial iterate)
+template <typename T>
+__global__ void __launch_bounds__(512) k_axpy_out(const T* __restrict__ dinv, const T* __restrict__ x, double alpha,
+                                                  const double* __restrict__ v, double* vout) {
+  const int id = blockIdx.x, l = threadIdx.x;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+    const double vo = v[o];
+    vout[o] = dinv[o] > T(0) ? vo + alpha * (double)x[o] : vo;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1978,7 +2007,8 @@ static int alloc_solver(mpml_ctx_s* c) {
   if ((rc = ensure(c->cs, sizeof(double) * 6 * c->nm * ns)) || (rc = ensure(c->cK, es * 45 * ns)) ||
       (rc = ensure(c->ng, sizeof(double) * 3 * ns)) || (rc = ensure(c->ndinv, es * 3 * ns)) || (rc = ensure(c->nx, es * 3 * ns)) ||
       (rc = ensure(c->nr, es * 3 * ns)) || (rc = ensure(c->np, es * 3 * ns)) || (rc = ensure(c->nq, es * 3 * ns)) ||
-      (rc = ensure(c->part, sizeof(double) * 10 * (c->nb ? c->nb : 1))))
+      (rc = ensure(c->part, sizeof(double) * 10 * (c->nb ? c->nb : 1))) ||
+      (rc = ensure(c->nvtry, sizeof(double) * 3 * ns)))
     return rc;
   return MPML_OK;
 }
@@ -2013,7 +2043,8 @@ static int read_scalars(mpml_ctx_s* c) {
 
 // prep at the current iterate (c->nvnew): gradient, energy, K (optional), CG start
 template <typename T>
-static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg_max, int want_psi = 1) {
+static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg_max, int want_psi = 1,
+                  int trial = 0) {
   SolveInfo si = solve_info(c);
   cudaMemsetAsync(c->scal.p, 0, sizeof(DevScalars), c->s);
   const unsigned nb = (unsigned)c->nb, ncb = (unsigned)c->ncb;
@@ -2025,11 +2056,23 @@ static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg
                                     (const T*)c->cacc.p, (const double*)(c->fp_active ? c->cB.p : c->cs.p), (const double*)c->nvnew.p, si,
                                     want_k ? (c->compressed ? 2 : 1) : 0, (T*)c->cK.p, (double*)c->ng.p,
                                     (T*)c->ndinv.p, dscal(c),
-                                    (int*)c->status.p, want_psi);
+                                    (int*)c->status.p, want_psi, trial);
   k_finalize<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (double*)c->ng.p,
-                                    (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p, (T*)c->np.p, (T*)c->nq.p, init_cg,
-                                    cg_rtol * cg_rtol, cg_max, dscal(c), part_fin(c));
+                                    (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p, (T*)c->np.p, (T*)c->nq.p,
+                                    init_cg ? 1 : 0, cg_rtol * cg_rtol, cg_max, dscal(c), part_fin(c));
   c->launches += ncb > 0 ? 3 : 2;
+  return cuda_status(cudaGetLastError());
+}
+
+// the CG start (x = 0, r = -g, ...) after a prep without it
+template <typename T>
+static int cg_start_t(mpml_ctx_s* c, double cg_rtol, int cg_max) {
+  if (c->nb == 0) return MPML_OK;
+  k_finalize<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
+                                                 (double*)c->ng.p, (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p,
+                                                 (T*)c->np.p, (T*)c->nq.p, 2, cg_rtol * cg_rtol, cg_max, dscal(c),
+                                                 part_fin(c));
+  c->launches++;
   return cuda_status(cudaGetLastError());
 }
 
@@ -3852,8 +3895,32 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     if ((rc = read_scalars(c))) return rc;
     const double slope = c->hscal->slope, lsA = c->hscal->ls_a, lsB = c->hscal->ls_b;
     double alpha = 1.0, phit = 0, phit_el = 0;
-    bool accepted = false;
-    for (int ls = 0; ls <= o->ls_max; ++ls) {
+    bool accepted = false, linearised = false;
+    int ls0 = 0;
+    if (!fp) {
+      // the full step first, by the prep at the trial iterate v + dx (without the CG start,
+      // so that dx survives a rejection): its energy decides the Armijo test and, accepted,
+      // it is the next iteration's linearisation (no separate line-search energy)
+      k_axpy_out<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nx.p, 1.0,
+                                                     (const double*)c->nvnew.p, (double*)c->nvtry.p);
+      c->launches++;
+      std::swap(c->nvnew, c->nvtry);
+      if ((rc = prep_t<T>(c, 1, 0, o->cg_rtol, o->cg_max, 1, 1)) || (rc = read_scalars(c))) return rc;
+      const double pel = c->hscal->phi_el, pin = c->hscal->phi_in, gg = c->hscal->gg;
+      const double dphi = lsA + 0.5 * lsB + (pel - phi_el);
+      if (c->hscal->infeasible == 0 && dphi <= o->ls_c1 * slope && gg == gg) {
+        if ((rc = cg_start_t<T>(c, o->cg_rtol, o->cg_max))) return rc;
+        accepted = linearised = true;
+        phit = pin + pel;
+        phit_el = pel;
+        gn = sqrt(gg);
+      } else {
+        std::swap(c->nvnew, c->nvtry);  // back to v; dx is intact
+        alpha = 0.5;
+        ls0 = 1;
+      }
+    }
+    for (int ls = ls0; !accepted && ls <= o->ls_max; ++ls) {
       int inf = 0;
       if ((rc = energy_t<T>(c, alpha, &phit, &inf))) return rc;
       phit_el = c->hscal->phi_el;
@@ -3871,6 +3938,11 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     if (!accepted) {
       status = MPML_WARN_NOT_CONVERGED;
       break;
+    }
+    if (linearised) {
+      phi = phit;
+      phi_el = phit_el;
+      continue;
     }
     k_axpy<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const T*)c->ndinv.p, (const T*)c->nx.p, alpha, (double*)c->nvnew.p);
     c->launches++;

@@ -335,7 +335,7 @@ int mpml_destroy(mpml_ctx c) {
                  &c->pG, &c->pm, &c->pV, &c->pmat, &c->pperm, &c->pkey, &c->prank, &c->pbase, &c->ux, &c->uv,
                  &c->uF, &c->uG, &c->um, &c->uV, &c->umat, &c->cnt, &c->start, &c->scan_tmp, &c->cflag,
                  &c->cacc, &c->cs, &c->cK, &c->cnew, &c->nflag, &c->nmass, &c->nv, &c->nvhat, &c->nvfix,
-                 &c->nvnew, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->bbatch, &c->nolist,
+                 &c->nvnew, &c->nvtry, &c->ng, &c->ndinv, &c->nx, &c->nr, &c->np, &c->nq, &c->np2, &c->scal, &c->status, &c->prof, &c->part, &c->gbar, &c->bbatch, &c->nolist,
                  &c->nnw, &c->nnact, &c->nny, &c->nnpart, &c->nz, &c->nns_r, &c->nns_e, &c->nnhd, &c->tuneq, &c->cB};
   for (Buf* b : bufs) free_buf(*b);
   if (c->hscal) cudaFreeHost(c->hscal);

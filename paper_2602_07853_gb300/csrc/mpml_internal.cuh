@@ -147,6 +147,7 @@ struct mpml_ctx_s {
   mpml::Buf cflag, cacc, cs, cK, cnew;
   // nodes
   mpml::Buf nflag, nmass, nv, nvhat, nvfix, nvnew, ng, ndinv, nx, nr, np, np2, nq;
+  mpml::Buf nvtry;  // the line search's trial iterate v + x (swapped with nvnew when accepted)
   // scalars and status
   mpml::Buf scal, status, prof, part, gbar;
   mpml::Buf bbatch;  // batched solver: scene table, work lists, accumulators (first context of a batch)
