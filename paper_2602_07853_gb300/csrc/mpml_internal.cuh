@@ -907,15 +907,16 @@ __device__ __forceinline__ T inv_sqrt_t(T nn) {
 // reciprocals by rsqrt_nr / rcp_nr -- results to about 1e-14 instead of FP64 rounding.
 template <typename T, bool LITE = false>
 __device__ void svd_from_h(const T H[9], T U[9], T s[3], T e[3], T V[9], T& Jm1) {
-  T E[9];
+  T E[9];  // symmetric: the upper triangle, mirrored
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
+    for (int b = a; b < 3; ++b) {
       T acc = H[3 * a + b] + H[3 * b + a];
 #pragma unroll
       for (int k = 0; k < 3; ++k) acc += H[3 * k + a] * H[3 * k + b];
       E[3 * a + b] = acc;
+      E[3 * b + a] = acc;
     }
   T lam[3], W[9];
   jacobi3_fast<T, LITE>(E, lam, W);
