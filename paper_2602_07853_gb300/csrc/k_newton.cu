@@ -517,6 +517,98 @@ __device__ __forceinline__ double jm1_of_h(const double H[9]) {
   return trH + 0.5 * (trH * trH - trH2) + detH;
 }
 
+// Symmetric 3x3 as (xx, yy, zz, xy, xz, yz); the product of two that commute (so that
+// the product is symmetric again)
+struct Sym3 {
+  double xx, yy, zz, xy, xz, yz;
+};
+__device__ __forceinline__ Sym3 sym_mul(const Sym3& A, const Sym3& B) {
+  return {A.xx * B.xx + A.xy * B.xy + A.xz * B.xz, A.xy * B.xy + A.yy * B.yy + A.yz * B.yz,
+          A.xz * B.xz + A.yz * B.yz + A.zz * B.zz, A.xx * B.xy + A.xy * B.yy + A.xz * B.yz,
+          A.xx * B.xz + A.xy * B.yz + A.xz * B.zz, A.xy * B.xz + A.yy * B.yz + A.yz * B.zz};
+}
+
+// L = log(b) of b = F F^T = I + E, E = H + H^T + H H^T, without an eigen-decomposition:
+// log(I + E) = 2 atanh(Z) with Z = E (2I + E)^-1 (symmetric; commutes with E), summed as
+// the odd series 2 (Z + Z^3/3 + ... + Z^11/11) in Horner form in Z^2.  Only where every
+// |E_ij| <= 0.03 (|Z| <= 0.047, so the first omitted term is below 1e-16 of |Z|): returns
+// false elsewhere (the caller takes the eigen-decomposition).  Multiply-adds and one
+// Newton-refined reciprocal: no FP64 transcendental or division.
+__device__ bool hencky_log_b(const double H[9], Sym3& L) {
+  Sym3 E;
+  {
+    double e[6];
+    const int I[6] = {0, 1, 2, 0, 0, 1}, Jx[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int a = I[q], b = Jx[q];
+      double acc = H[3 * a + b] + H[3 * b + a];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += H[3 * a + k] * H[3 * b + k];
+      e[q] = acc;
+    }
+    E = {e[0], e[1], e[2], e[3], e[4], e[5]};
+  }
+  const double mx = fmax(fmax(fmax(fabs(E.xx), fabs(E.yy)), fmax(fabs(E.zz), fabs(E.xy))), fmax(fabs(E.xz), fabs(E.yz)));
+  if (!(mx <= 0.03)) return false;
+  // (2I + E)^-1 by cofactors (symmetric); its determinant is within [6.2, 10]
+  const double a00 = 2.0 + E.xx, a11 = 2.0 + E.yy, a22 = 2.0 + E.zz;
+  const double c00 = a11 * a22 - E.yz * E.yz, c11 = a00 * a22 - E.xz * E.xz, c22 = a00 * a11 - E.xy * E.xy;
+  const double c01 = E.xz * E.yz - E.xy * a22, c02 = E.xy * E.yz - E.xz * a11, c12 = E.xy * E.xz - a00 * E.yz;
+  const double id = rcp_nr(a00 * c00 + E.xy * c01 + E.xz * c02);
+  const Sym3 Ai = {c00 * id, c11 * id, c22 * id, c01 * id, c02 * id, c12 * id};
+  const Sym3 Z = sym_mul(E, Ai), Y = sym_mul(Z, Z);
+  // S = 1 + Y/3 + Y^2/5 + ... + Y^5/11
+  Sym3 S = {Y.xx * (1.0 / 11) + 1.0 / 9, Y.yy * (1.0 / 11) + 1.0 / 9, Y.zz * (1.0 / 11) + 1.0 / 9,
+            Y.xy * (1.0 / 11), Y.xz * (1.0 / 11), Y.yz * (1.0 / 11)};
+  const double cs[4] = {1.0 / 7, 1.0 / 5, 1.0 / 3, 1.0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    S = sym_mul(Y, S);
+    S.xx += cs[k];
+    S.yy += cs[k];
+    S.zz += cs[k];
+  }
+  const Sym3 T = sym_mul(Z, S);
+  L = {2.0 * T.xx, 2.0 * T.yy, 2.0 * T.zz, 2.0 * T.xy, 2.0 * T.xz, 2.0 * T.yz};
+  return true;
+}
+
+// Hencky energy from L = log(F F^T): mu/4 tr(L^2) + lam/8 (tr L)^2 (= mu |log s|^2 +
+// lam/2 (sum log s)^2 over the singular values s)
+__device__ __forceinline__ double hencky_psi(const MatParams<double>& M, const Sym3& L) {
+  const double tr = L.xx + L.yy + L.zz;
+  const double tr2 = L.xx * L.xx + L.yy * L.yy + L.zz * L.zz + 2.0 * (L.xy * L.xy + L.xz * L.xz + L.yz * L.yz);
+  return 0.25 * M.mu * tr2 + 0.125 * M.lam * tr * tr;
+}
+
+// Hencky P S^T of F = (I + dt G) B = I + H in FP64 without an SVD, at small strain:
+// the Kirchhoff stress tau = mu L + lam/2 tr(L) I with L = log(F F^T), and P S^T =
+// tau F^{-T} B^T = tau (I + dt G)^{-T}.  Returns false outside hencky_log_b's range
+// or for J <= 0; psi is the energy by hencky_psi.
+__device__ bool hencky_closed_form(const MatParams<double>& M, const double Gd[9], const double H[9], double PSt[9],
+                                   double& psi) {
+  if (!(jm1_of_h(H) > -1.0)) return false;
+  Sym3 L;
+  if (!hencky_log_b(H, L)) return false;
+  psi = hencky_psi(M, L);
+  const double hl = 0.5 * M.lam * (L.xx + L.yy + L.zz);
+  const double tau[9] = {M.mu * L.xx + hl, M.mu * L.xy, M.mu * L.xz, M.mu * L.xy, M.mu * L.yy + hl,
+                         M.mu * L.yz, M.mu * L.xz, M.mu * L.yz, M.mu * L.zz + hl};
+  const double a0 = 1.0 + Gd[0], a1 = Gd[1], a2 = Gd[2], a3 = Gd[3], a4 = 1.0 + Gd[4], a5 = Gd[5], a6 = Gd[6],
+               a7 = Gd[7], a8 = 1.0 + Gd[8];
+  const double cof[9] = {a4 * a8 - a5 * a7, a5 * a6 - a3 * a8, a3 * a7 - a4 * a6,
+                         a2 * a7 - a1 * a8, a0 * a8 - a2 * a6, a1 * a6 - a0 * a7,
+                         a1 * a5 - a2 * a4, a2 * a3 - a0 * a5, a0 * a4 - a1 * a3};
+  const double idet = rcp_nr(a0 * cof[0] + a1 * cof[1] + a2 * cof[2]);  // det(I + dt G) near 1
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      PSt[3 * a + b] = (tau[3 * a] * cof[b] + tau[3 * a + 1] * cof[3 + b] + tau[3 * a + 2] * cof[6 + b]) * idet;
+  return true;
+}
+
 // Split Neo-Hookean P S^T of F = (I + dt G)(I + s) = I + H in FP64 without an
 // SVD: tau = mu J^{-2/3} dev(b) + kappa/2 (J^2 - 1) I with b - I = H + H^T +
 // H H^T, and P S^T = tau (I + dt G)^{-T}.  Returns false for J <= 0.
@@ -644,6 +736,13 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
     psi = 0.5 * (M.lam + 2.0 / 3.0 * M.mu) * Jm1 * Jm1;
     return true;
   }
+  if (M.model == MPML_HENCKY && Jm1 > -1.0) {
+    Sym3 L;
+    if (hencky_log_b(H, L)) {  // small strain: the log series (as hencky_closed_form)
+      psi = hencky_psi(M, L);
+      return true;
+    }
+  }
   double E[9];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -770,8 +869,9 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
   double sm[9], H[9];
   trial_h(Gd, bm, sm, H);
   if constexpr (sizeof(T) == 4) {
-    double PSt[9];
-    const bool closed = (M.model == MPML_NEO_HOOKEAN && nh_closed_form(M, Gd, H, PSt)) ||
+    double PSt[9], psi_h = 0.0;
+    const bool hencky = M.model == MPML_HENCKY && hencky_closed_form(M, Gd, H, PSt, psi_h);
+    const bool closed = hencky || (M.model == MPML_NEO_HOOKEAN && nh_closed_form(M, Gd, H, PSt)) ||
                         (M.model == MPML_FIXED_COROTATED && fc_closed_form(M, Gd, H, sm, PSt));
     if (M.model == MPML_NEO_HOOKEAN && !closed) {
       out.ok = false;
@@ -782,9 +882,9 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
       // energy is skipped when the caller has it already (the accepted line-search
       // value at this iterate): its FP64 transcendentals dominate this kernel.
       if (want_psi) {
-        double psi;
+        double psi = psi_h;  // Hencky: from the same L (psi_from_h's small-strain branch)
         bool need_svd;
-        if (!psi_from_h(M, H, psi, need_svd) || need_svd) {
+        if (!hencky && (!psi_from_h(M, H, psi, need_svd) || need_svd)) {
           out.ok = false;
           return;
         }
