@@ -310,6 +310,35 @@ __global__ void __launch_bounds__(256) k_stretch(const int* __restrict__ cblist,
         double tq = (double)a[(acc_tau(k) + q) * BV] / V;
         tau[3 * ra[q] + rb[q]] = tau[3 * rb[q] + ra[q]] = tq;
       }
+      if (si.mat[k].model == MPML_HENCKY) {
+        // Hencky inverts in closed form: eps = (tau - lam tr(eps) I) / (2 mu) with
+        // tr(eps) = tr(tau) / (2 mu + 3 lam), and S - I = expm1(eps); at small strain
+        // (every |eps_ij| <= 0.03) by the series to eps^9 / 9! (remainder below 1e-16 of
+        // |eps|) instead of the eigen-decomposition
+        const double mu = si.mat[k].mu, lam = si.mat[k].lam;
+        const double i2m = 1.0 / (2.0 * mu), lt = lam * (tau[0] + tau[4] + tau[8]) / (2.0 * mu + 3.0 * lam);
+        const Sym3<double> E = {(tau[0] - lt) * i2m, (tau[4] - lt) * i2m, (tau[8] - lt) * i2m,
+                                tau[1] * i2m,        tau[2] * i2m,        tau[5] * i2m};
+        const double mx = fmax(fmax(fmax(fabs(E.xx), fabs(E.yy)), fmax(fabs(E.zz), fabs(E.xy))),
+                               fmax(fabs(E.xz), fabs(E.yz)));
+        if (mu > 0.0 && mx <= 0.03) {
+          Sym3<double> P = {1.0 + E.xx / 9.0, 1.0 + E.yy / 9.0, 1.0 + E.zz / 9.0, E.xy / 9.0, E.xz / 9.0, E.yz / 9.0};
+#pragma unroll
+          for (int kk = 8; kk >= 2; --kk) {
+            const double ik = 1.0 / kk;
+            const Sym3<double> EP = sym_mul(E, P);
+            P = {1.0 + EP.xx * ik, 1.0 + EP.yy * ik, 1.0 + EP.zz * ik, EP.xy * ik, EP.xz * ik, EP.yz * ik};
+          }
+          const Sym3<double> Sm = sym_mul(E, P);
+          so[0] = Sm.xx;
+          so[BV] = Sm.yy;
+          so[2 * BV] = Sm.zz;
+          so[3 * BV] = Sm.xy;
+          so[4 * BV] = Sm.xz;
+          so[5 * BV] = Sm.yz;
+          continue;
+        }
+      }
       double ev[3], Q[9], s[3];
       jacobi3_mixed(tau, ev, Q);
       if (!invert_principal(si.mat[k].model, si.mat[k].mu, si.mat[k].lam, ev, s)) {
@@ -517,66 +546,26 @@ __device__ __forceinline__ double jm1_of_h(const double H[9]) {
   return trH + 0.5 * (trH * trH - trH2) + detH;
 }
 
-// Symmetric 3x3 as (xx, yy, zz, xy, xz, yz); the product of two that commute (so that
-// the product is symmetric again)
-struct Sym3 {
-  double xx, yy, zz, xy, xz, yz;
-};
-__device__ __forceinline__ Sym3 sym_mul(const Sym3& A, const Sym3& B) {
-  return {A.xx * B.xx + A.xy * B.xy + A.xz * B.xz, A.xy * B.xy + A.yy * B.yy + A.yz * B.yz,
-          A.xz * B.xz + A.yz * B.yz + A.zz * B.zz, A.xx * B.xy + A.xy * B.yy + A.xz * B.yz,
-          A.xx * B.xz + A.xy * B.yz + A.xz * B.zz, A.xy * B.xz + A.yy * B.yz + A.yz * B.zz};
-}
-
-// L = log(b) of b = F F^T = I + E, E = H + H^T + H H^T, without an eigen-decomposition:
-// log(I + E) = 2 atanh(Z) with Z = E (2I + E)^-1 (symmetric; commutes with E), summed as
-// the odd series 2 (Z + Z^3/3 + ... + Z^11/11) in Horner form in Z^2.  Only where every
-// |E_ij| <= 0.03 (|Z| <= 0.047, so the first omitted term is below 1e-16 of |Z|): returns
-// false elsewhere (the caller takes the eigen-decomposition).  Multiply-adds and one
-// Newton-refined reciprocal: no FP64 transcendental or division.
-__device__ bool hencky_log_b(const double H[9], Sym3& L) {
-  Sym3 E;
-  {
-    double e[6];
-    const int I[6] = {0, 1, 2, 0, 0, 1}, Jx[6] = {0, 1, 2, 1, 2, 2};
+// L = log(b) of b = F F^T = I + E, E = H + H^T + H H^T, without an eigen-decomposition
+// (log_spd_series); false where some |E_ij| > 0.03 (the caller takes the eigen-decomposition)
+__device__ bool hencky_log_b(const double H[9], Sym3<double>& L) {
+  double e[6];
+  const int I[6] = {0, 1, 2, 0, 0, 1}, Jx[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const int a = I[q], b = Jx[q];
-      double acc = H[3 * a + b] + H[3 * b + a];
+  for (int q = 0; q < 6; ++q) {
+    const int a = I[q], b = Jx[q];
+    double acc = H[3 * a + b] + H[3 * b + a];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) acc += H[3 * a + k] * H[3 * b + k];
-      e[q] = acc;
-    }
-    E = {e[0], e[1], e[2], e[3], e[4], e[5]};
+    for (int k = 0; k < 3; ++k) acc += H[3 * a + k] * H[3 * b + k];
+    e[q] = acc;
   }
-  const double mx = fmax(fmax(fmax(fabs(E.xx), fabs(E.yy)), fmax(fabs(E.zz), fabs(E.xy))), fmax(fabs(E.xz), fabs(E.yz)));
-  if (!(mx <= 0.03)) return false;
-  // (2I + E)^-1 by cofactors (symmetric); its determinant is within [6.2, 10]
-  const double a00 = 2.0 + E.xx, a11 = 2.0 + E.yy, a22 = 2.0 + E.zz;
-  const double c00 = a11 * a22 - E.yz * E.yz, c11 = a00 * a22 - E.xz * E.xz, c22 = a00 * a11 - E.xy * E.xy;
-  const double c01 = E.xz * E.yz - E.xy * a22, c02 = E.xy * E.yz - E.xz * a11, c12 = E.xy * E.xz - a00 * E.yz;
-  const double id = rcp_nr(a00 * c00 + E.xy * c01 + E.xz * c02);
-  const Sym3 Ai = {c00 * id, c11 * id, c22 * id, c01 * id, c02 * id, c12 * id};
-  const Sym3 Z = sym_mul(E, Ai), Y = sym_mul(Z, Z);
-  // S = 1 + Y/3 + Y^2/5 + ... + Y^5/11
-  Sym3 S = {Y.xx * (1.0 / 11) + 1.0 / 9, Y.yy * (1.0 / 11) + 1.0 / 9, Y.zz * (1.0 / 11) + 1.0 / 9,
-            Y.xy * (1.0 / 11), Y.xz * (1.0 / 11), Y.yz * (1.0 / 11)};
-  const double cs[4] = {1.0 / 7, 1.0 / 5, 1.0 / 3, 1.0};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    S = sym_mul(Y, S);
-    S.xx += cs[k];
-    S.yy += cs[k];
-    S.zz += cs[k];
-  }
-  const Sym3 T = sym_mul(Z, S);
-  L = {2.0 * T.xx, 2.0 * T.yy, 2.0 * T.zz, 2.0 * T.xy, 2.0 * T.xz, 2.0 * T.yz};
-  return true;
+  const Sym3<double> E = {e[0], e[1], e[2], e[3], e[4], e[5]};
+  return log_spd_series(E, L);
 }
 
 // Hencky energy from L = log(F F^T): mu/4 tr(L^2) + lam/8 (tr L)^2 (= mu |log s|^2 +
 // lam/2 (sum log s)^2 over the singular values s)
-__device__ __forceinline__ double hencky_psi(const MatParams<double>& M, const Sym3& L) {
+__device__ __forceinline__ double hencky_psi(const MatParams<double>& M, const Sym3<double>& L) {
   const double tr = L.xx + L.yy + L.zz;
   const double tr2 = L.xx * L.xx + L.yy * L.yy + L.zz * L.zz + 2.0 * (L.xy * L.xy + L.xz * L.xz + L.yz * L.yz);
   return 0.25 * M.mu * tr2 + 0.125 * M.lam * tr * tr;
@@ -589,7 +578,7 @@ __device__ __forceinline__ double hencky_psi(const MatParams<double>& M, const S
 __device__ bool hencky_closed_form(const MatParams<double>& M, const double Gd[9], const double H[9], double PSt[9],
                                    double& psi) {
   if (!(jm1_of_h(H) > -1.0)) return false;
-  Sym3 L;
+  Sym3<double> L;
   if (!hencky_log_b(H, L)) return false;
   psi = hencky_psi(M, L);
   const double hl = 0.5 * M.lam * (L.xx + L.yy + L.zz);
@@ -737,7 +726,7 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
     return true;
   }
   if (M.model == MPML_HENCKY && Jm1 > -1.0) {
-    Sym3 L;
+    Sym3<double> L;
     if (hencky_log_b(H, L)) {  // small strain: the log series (as hencky_closed_form)
       psi = hencky_psi(M, L);
       return true;

@@ -97,6 +97,38 @@ __device__ void kirchhoff(const MatParams<T>& M, const T F[9], T tau[6]) {
     tau[5] = mc * B[5];
     return;
   }
+  if (M.model == MPML_HENCKY) {
+    // small strain: tau = mu log(b) + lam/2 tr(log b) I with b - I = H + H^T + H H^T and
+    // log(b) by its series (no eigen-decomposition); J > 0 from the invariants of H
+    T e6[6];
+    const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      T acc = H[3 * ia[q] + ib[q]] + H[3 * ib[q] + ia[q]];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) acc += H[3 * ia[q] + k] * H[3 * ib[q] + k];
+      e6[q] = acc;
+    }
+    T trH = H[0] + H[4] + H[8], trH2 = 0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) trH2 += H[3 * a + b] * H[3 * b + a];
+    const T detH = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                   H[2] * (H[3] * H[7] - H[4] * H[6]);
+    const T Jm1h = trH + T(0.5) * (trH * trH - trH2) + detH;
+    Sym3<T> L;
+    if (Jm1h > T(-1) && log_spd_series(Sym3<T>{e6[0], e6[1], e6[2], e6[3], e6[4], e6[5]}, L)) {
+      const T hl = T(0.5) * M.lam * (L.xx + L.yy + L.zz);
+      tau[0] = M.mu * L.xx + hl;
+      tau[1] = M.mu * L.yy + hl;
+      tau[2] = M.mu * L.zz + hl;
+      tau[3] = M.mu * L.xy;
+      tau[4] = M.mu * L.xz;
+      tau[5] = M.mu * L.yz;
+      return;
+    }
+  }
   // fixed-corotated and Hencky: tau = U diag(s_i dpsi/ds_i) U^T (Sec. 4.3)
   T U[9], s[3], e[3], V[9], Jm1;
   svd_from_h(H, U, s, e, V, Jm1);

@@ -1126,6 +1126,57 @@ __device__ __forceinline__ T log1p_series(T x) {
   return fabs(x) < T(0.05) ? x - x_minus_log1p(x) : log1p_t(x);
 }
 
+// Symmetric 3x3 as (xx, yy, zz, xy, xz, yz); sym_mul is the product of two that commute
+// (so that the product is symmetric again)
+template <typename T>
+struct Sym3 {
+  T xx, yy, zz, xy, xz, yz;
+};
+template <typename T>
+__device__ __forceinline__ Sym3<T> sym_mul(const Sym3<T>& A, const Sym3<T>& B) {
+  return {A.xx * B.xx + A.xy * B.xy + A.xz * B.xz, A.xy * B.xy + A.yy * B.yy + A.yz * B.yz,
+          A.xz * B.xz + A.yz * B.yz + A.zz * B.zz, A.xx * B.xy + A.xy * B.yy + A.xz * B.yz,
+          A.xx * B.xz + A.xy * B.yz + A.xz * B.zz, A.xy * B.xz + A.yy * B.yz + A.yz * B.zz};
+}
+
+// log(I + E) of a symmetric E near zero without an eigen-decomposition: 2 atanh(Z) with
+// Z = E (2I + E)^-1 (symmetric; commutes with E), as the odd series 2 (Z + Z^3/3 + ...)
+// in Horner form in Z^2 -- to Z^11 in FP64, Z^5 in FP32.  Only where every |E_ij| <= 0.03
+// (then |Z| <= 0.047 and the first omitted term is below the type's rounding of |Z|):
+// returns false elsewhere.  Multiply-adds and one reciprocal (Newton-refined in FP64).
+template <typename T>
+__device__ bool log_spd_series(const Sym3<T>& E, Sym3<T>& L) {
+  const T mx = fmax(fmax(fmax(fabs(E.xx), fabs(E.yy)), fmax(fabs(E.zz), fabs(E.xy))), fmax(fabs(E.xz), fabs(E.yz)));
+  if (!(mx <= T(0.03))) return false;
+  // (2I + E)^-1 by cofactors (symmetric); its determinant is within [6.2, 10]
+  const T a00 = T(2) + E.xx, a11 = T(2) + E.yy, a22 = T(2) + E.zz;
+  const T c00 = a11 * a22 - E.yz * E.yz, c11 = a00 * a22 - E.xz * E.xz, c22 = a00 * a11 - E.xy * E.xy;
+  const T c01 = E.xz * E.yz - E.xy * a22, c02 = E.xy * E.yz - E.xz * a11, c12 = E.xy * E.xz - a00 * E.yz;
+  const T det = a00 * c00 + E.xy * c01 + E.xz * c02;
+  T id;
+  if constexpr (sizeof(T) == 8)
+    id = rcp_nr(det);
+  else
+    id = T(1) / det;
+  const Sym3<T> Ai = {c00 * id, c11 * id, c22 * id, c01 * id, c02 * id, c12 * id};
+  const Sym3<T> Z = sym_mul(E, Ai), Y = sym_mul(Z, Z);
+  // S = 1 + Y/3 + Y^2/5 + ... (to Y^5/11 in FP64, Y^2/5 in FP32)
+  constexpr int NT = sizeof(T) == 8 ? 5 : 2;
+  const T cl = T(1) / T(2 * NT + 1), cn = T(1) / T(2 * NT - 1);
+  Sym3<T> S = {Y.xx * cl + cn, Y.yy * cl + cn, Y.zz * cl + cn, Y.xy * cl, Y.xz * cl, Y.yz * cl};
+#pragma unroll
+  for (int k = NT - 2; k >= 0; --k) {
+    const T ck = T(1) / T(2 * k + 1);
+    S = sym_mul(Y, S);
+    S.xx += ck;
+    S.yy += ck;
+    S.zz += ck;
+  }
+  const Sym3<T> Tz = sym_mul(Z, S);
+  L = {T(2) * Tz.xx, T(2) * Tz.yy, T(2) * Tz.zz, T(2) * Tz.xy, T(2) * Tz.xz, T(2) * Tz.yz};
+  return true;
+}
+
 // returns false where the energy is undefined (J <= 0 for NH / Hencky)
 // The isotropic eigen-data of psi at the signed singular values s (e = s - 1,
 // Jm1 = J - 1): PARTS bit 1 the energy and the principal stresses d1 (what the
