@@ -932,6 +932,8 @@ def pcg_probe(args):
     ctx, p, pp = make_ctx(m, sc, stream)
     launches = []
     for s in range(args.warmup + 1):
+        if s == args.warmup:
+            m.mpml_set_profiling(ctx, 1)  # the last step: solver launch and HVP-phase times
         m.mpml_set_time(ctx, s * sc.dt)
         m.mpml_resample(ctx, pp)
         rc, st = m.mpml_newton_step(ctx, m.solver_opts())
@@ -939,10 +941,13 @@ def pcg_probe(args):
         launches.append(st.newton_iters)
     cn = m.mpml_counts(ctx)
     _, staging, ctas = m.mpml_get_pcg_config(ctx)
+    hn, hms, _ = m.mpml_hvp_timing(ctx)
+    pn, pit, pms = m.mpml_pcg_timing(ctx)
     print(json.dumps({"probe": args.pcg_probe, "n": args.n, "particles": cn["particles"], "cells": cn["cells"],
                       "nodes": cn["nodes"], "newton_per_step": launches, "last_cg_iters":
                       [int(st.cg_iters[k]) for k in range(min(st.newton_iters, 64))], "staging": staging,
-                      "ctas_per_sm": ctas, "rc": rc}), flush=True)
+                      "ctas_per_sm": ctas, "us_per_cg_iter": 1e3 * pms / max(pit, 1),
+                      "us_hvp_phase": 1e3 * hms / max(hn, 1), "rc": rc}), flush=True)
     m.mpml_destroy(ctx)
     return 0
 
