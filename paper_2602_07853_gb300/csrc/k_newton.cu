@@ -2900,7 +2900,7 @@ __global__ void __launch_bounds__(256, MINB) k_pcg_groups(PcgArgs A) {
           for (int qq = 0; qq < NQ; ++qq) kn[qq] = ld_stream(Kb + qq * BV + 256 * hz + y * 8 + x);
         }
       }
-#pragma unroll 1
+#pragma unroll
       for (int z = 0; z <= 4; ++z) {
         float N[2][2][3];
         if (z < 4) {
