@@ -993,21 +993,24 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
 template <typename T>
 __global__ void __launch_bounds__(512) k_node_init(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
                                                    const double* __restrict__ v, const double* __restrict__ vhat,
-                                                   double* g, T* diag, DevScalars* sc) {
-  const int id = blockIdx.x, l = threadIdx.x;
-  const int64_t slot = (int64_t)id * BV + l;
-  const bool dof = nflag[slot] & NF_DOF;
-  const bool free_ = dof && !(nflag[slot] & NF_FIXED);
+                                                   double* g, T* diag, DevScalars* sc, int nb) {
+  const int l = threadIdx.x;
   double ein = 0, mv2 = 0;
-  const double mi = dof ? (double)m[slot] : 0.0;
+  // several bricks per block: the FP64 block sums (slow on this part) once per block
+  for (int id = blockIdx.x; id < nb; id += gridDim.x) {
+    const int64_t slot = (int64_t)id * BV + l;
+    const bool dof = nflag[slot] & NF_DOF;
+    const bool free_ = dof && !(nflag[slot] & NF_FIXED);
+    const double mi = dof ? (double)m[slot] : 0.0;
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const int64_t o = (int64_t)id * 3 * BV + r * BV + l;
-    double d = dof ? v[o] - vhat[o] : 0.0;
-    g[o] = mi * d;
-    diag[o] = (T)mi;
-    ein += 0.5 * mi * d * d;
-    if (free_) mv2 += (mi * vhat[o]) * (mi * vhat[o]);
+    for (int r = 0; r < 3; ++r) {
+      const int64_t o = (int64_t)id * 3 * BV + r * BV + l;
+      double d = dof ? v[o] - vhat[o] : 0.0;
+      g[o] = mi * d;
+      diag[o] = (T)mi;
+      ein += 0.5 * mi * d * d;
+      if (free_) mv2 += (mi * vhat[o]) * (mi * vhat[o]);
+    }
   }
   double vals[2] = {ein, mv2};
   double* const dst[2] = {&sc->phi_in, &sc->mv2};
@@ -1135,14 +1138,16 @@ __global__ void __launch_bounds__(256, 1) k_prep(const int* __restrict__ cblist,
 template <typename T>
 __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
                                                   double* g, T* diag_dinv, T* x, T* r, T* p, T* q, int mode,
-                                                  double rtol2, int cg_max, DevScalars* sc, double* part) {
-  const int id = blockIdx.x, l = threadIdx.x;
+                                                  double rtol2, int cg_max, DevScalars* sc, double* part, int nb) {
+  const int l = threadIdx.x;
+  const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
+  double gg = 0, rz = 0, rr = 0, pmp = 0, nfr = 0;
+  // several bricks per block: the FP64 block sums (slow on this part) once per block
+  for (int id = blockIdx.x; id < nb; id += gridDim.x) {
   const int64_t slot = (int64_t)id * BV + l;
   const uint8_t f = nflag[slot];
   const bool free_ = (f & NF_DOF) && !(f & NF_FIXED);
-  const bool face = (l & 7) == 0 || ((l >> 3) & 7) == 0 || (l >> 6) == 0;
-  double gg = 0, rz = 0, rr = 0, pmp = 0;
-  const double nfr = free_ ? 3.0 : 0.0;
+  nfr += free_ ? 3.0 : 0.0;
   const T mi = free_ ? m[slot] : T(0);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -1167,6 +1172,7 @@ __global__ void __launch_bounds__(512) k_finalize(const uint8_t* __restrict__ nf
       rr += (double)rv * (double)rv;
       pmp += (double)mi * (double)zv * (double)zv;
     }
+  }
   }
   double vals[5] = {gg, rz, rr, pmp, nfr};
   block_store<5>(vals, part);
@@ -1958,20 +1964,23 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_ls_setup(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
                                                   const double* __restrict__ g, const double* __restrict__ v,
                                                   const double* __restrict__ vhat, const T* __restrict__ x,
-                                                  DevScalars* sc) {
-  const int id = blockIdx.x, l = threadIdx.x;
-  const int64_t slot = (int64_t)id * BV + l;
+                                                  DevScalars* sc, int nb) {
+  const int l = threadIdx.x;
   double sl = 0, A = 0, B = 0;
-  const bool dof = (nflag[slot] & NF_DOF) != 0;
-  const double mi = (double)m[slot];
+  // several bricks per block: the FP64 block sums (slow on this part) once per block
+  for (int id = blockIdx.x; id < nb; id += gridDim.x) {
+    const int64_t slot = (int64_t)id * BV + l;
+    const bool dof = (nflag[slot] & NF_DOF) != 0;
+    const double mi = (double)m[slot];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
-    const double xv = (double)x[o];
-    sl += g[o] * xv;
-    if (dof) {
-      A += mi * (v[o] - vhat[o]) * xv;
-      B += mi * xv * xv;
+    for (int a = 0; a < 3; ++a) {
+      const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+      const double xv = (double)x[o];
+      sl += g[o] * xv;
+      if (dof) {
+        A += mi * (v[o] - vhat[o]) * xv;
+        B += mi * xv * xv;
+      }
     }
   }
   double vals[3] = {sl, A, B};
@@ -1983,17 +1992,20 @@ __global__ void __launch_bounds__(512) k_ls_setup(const uint8_t* __restrict__ nf
 template <typename T>
 __global__ void __launch_bounds__(512) k_energy_nodes(const uint8_t* __restrict__ nflag, const T* __restrict__ m,
                                                       const double* __restrict__ v, const T* __restrict__ x,
-                                                      const double* __restrict__ vhat, double alpha, DevScalars* sc) {
-  const int id = blockIdx.x, l = threadIdx.x;
-  const int64_t slot = (int64_t)id * BV + l;
+                                                      const double* __restrict__ vhat, double alpha, DevScalars* sc,
+                                                      int nb) {
+  const int l = threadIdx.x;
   double e = 0;
-  if (nflag[slot] & NF_DOF) {
-    const double mi = (double)m[slot];
+  for (int id = blockIdx.x; id < nb; id += gridDim.x) {
+    const int64_t slot = (int64_t)id * BV + l;
+    if (nflag[slot] & NF_DOF) {
+      const double mi = (double)m[slot];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
-      const double d = v[o] + alpha * (double)x[o] - vhat[o];
-      e += 0.5 * mi * d * d;
+      for (int a = 0; a < 3; ++a) {
+        const int64_t o = (int64_t)id * 3 * BV + a * BV + l;
+        const double d = v[o] + alpha * (double)x[o] - vhat[o];
+        e += 0.5 * mi * d * d;
+      }
     }
   }
   double vals[1] = {e};
@@ -2144,6 +2156,10 @@ static int read_scalars(mpml_ctx_s* c) {
   return cuda_status(cudaStreamSynchronize(c->s));
 }
 
+// blocks of the node-wise kernels: eight node bricks per block (their FP64 block sums once
+// per block)
+static unsigned node_blocks(int64_t nb) { return (unsigned)((nb + 7) / 8); }
+
 // prep at the current iterate (c->nvnew): gradient, energy, K (optional), CG start
 template <typename T>
 static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg_max, int want_psi = 1,
@@ -2152,17 +2168,17 @@ static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg
   cudaMemsetAsync(c->scal.p, 0, sizeof(DevScalars), c->s);
   const unsigned nb = (unsigned)c->nb, ncb = (unsigned)c->ncb;
   if (nb == 0) return MPML_OK;
-  k_node_init<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (const double*)c->nvnew.p,
-                                     (const double*)c->nvhat.p, (double*)c->ng.p, (T*)c->ndinv.p, dscal(c));
+  k_node_init<T><<<node_blocks(nb), BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (const double*)c->nvnew.p,
+                                     (const double*)c->nvhat.p, (double*)c->ng.p, (T*)c->ndinv.p, dscal(c), (int)nb);
   if (ncb > 0)
     k_prep<T><<<ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p, (const uint8_t*)c->cflag.p,
                                     (const T*)c->cacc.p, (const double*)(c->fp_active ? c->cB.p : c->cs.p), (const double*)c->nvnew.p, si,
                                     want_k ? (c->compressed ? 2 : 1) : 0, (T*)c->cK.p, (double*)c->ng.p,
                                     (T*)c->ndinv.p, dscal(c),
                                     (int*)c->status.p, want_psi, trial);
-  k_finalize<T><<<nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (double*)c->ng.p,
+  k_finalize<T><<<node_blocks(nb), BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p, (double*)c->ng.p,
                                     (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p, (T*)c->np.p, (T*)c->nq.p,
-                                    init_cg ? 1 : 0, cg_rtol * cg_rtol, cg_max, dscal(c), part_fin(c));
+                                    init_cg ? 1 : 0, cg_rtol * cg_rtol, cg_max, dscal(c), part_fin(c), (int)nb);
   c->launches += ncb > 0 ? 3 : 2;
   return cuda_status(cudaGetLastError());
 }
@@ -2171,10 +2187,10 @@ static int prep_t(mpml_ctx_s* c, int want_k, int init_cg, double cg_rtol, int cg
 template <typename T>
 static int cg_start_t(mpml_ctx_s* c, double cg_rtol, int cg_max) {
   if (c->nb == 0) return MPML_OK;
-  k_finalize<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
+  k_finalize<T><<<node_blocks(c->nb), BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
                                                  (double*)c->ng.p, (T*)c->ndinv.p, (T*)c->nx.p, (T*)c->nr.p,
                                                  (T*)c->np.p, (T*)c->nq.p, 2, cg_rtol * cg_rtol, cg_max, dscal(c),
-                                                 part_fin(c));
+                                                 part_fin(c), (int)c->nb);
   c->launches++;
   return cuda_status(cudaGetLastError());
 }
@@ -3791,9 +3807,9 @@ static int energy_t(mpml_ctx_s* c, double alpha, double* phi, int* infeasible) {
   cudaMemsetAsync(&d->phi_in, 0, sizeof(double), c->s);
   cudaMemsetAsync(&d->phi_el, 0, sizeof(double), c->s);
   cudaMemsetAsync(&d->infeasible, 0, sizeof(int), c->s);
-  k_energy_nodes<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
+  k_energy_nodes<T><<<node_blocks(c->nb), BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
                                                      (const double*)c->nvnew.p, (const T*)c->nx.p,
-                                                     (const double*)c->nvhat.p, alpha, d);
+                                                     (const double*)c->nvhat.p, alpha, d, (int)c->nb);
   if (c->ncb > 0)
     k_energy_cells<T><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
                                                          (const uint8_t*)c->cflag.p, (const T*)c->cacc.p,
@@ -3991,9 +4007,9 @@ static int newton_t(mpml_ctx_s* c, const mpml_solver_opts* o, mpml_solve_stats* 
     // slope g^T dx and the exact inertia change along dx
     DevScalars* d = dscal(c);
     cudaMemsetAsync(&d->slope, 0, 3 * sizeof(double), c->s);
-    k_ls_setup<T><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
+    k_ls_setup<T><<<node_blocks(c->nb), BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const T*)c->nmass.p,
                                                    (const double*)c->ng.p, (const double*)c->nvnew.p,
-                                                   (const double*)c->nvhat.p, (const T*)c->nx.p, d);
+                                                   (const double*)c->nvhat.p, (const T*)c->nx.p, d, (int)c->nb);
     c->launches++;
     if ((rc = read_scalars(c))) return rc;
     const double slope = c->hscal->slope, lsA = c->hscal->ls_a, lsB = c->hscal->ls_b;
@@ -4305,9 +4321,9 @@ int batch_prep(mpml_ctx_s* c, double cg_rtol, int cg_max) { return prep_t<float>
 void batch_slope_launch(mpml_ctx_s* c) {
   DevScalars* d = dscal(c);
   cudaMemsetAsync(&d->slope, 0, 3 * sizeof(double), c->s);
-  k_ls_setup<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const float*)c->nmass.p,
+  k_ls_setup<float><<<node_blocks(c->nb), BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const float*)c->nmass.p,
                                                      (const double*)c->ng.p, (const double*)c->nvnew.p,
-                                                     (const double*)c->nvhat.p, (const float*)c->nx.p, d);
+                                                     (const double*)c->nvhat.p, (const float*)c->nx.p, d, (int)c->nb);
   c->launches++;
 }
 
@@ -4317,9 +4333,9 @@ void batch_energy_launch(mpml_ctx_s* c, double alpha) {
   cudaMemsetAsync(&d->phi_in, 0, sizeof(double), c->s);
   cudaMemsetAsync(&d->phi_el, 0, sizeof(double), c->s);
   cudaMemsetAsync(&d->infeasible, 0, sizeof(int), c->s);
-  k_energy_nodes<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const float*)c->nmass.p,
+  k_energy_nodes<float><<<node_blocks(c->nb), BV, 0, c->s>>>((const uint8_t*)c->nflag.p, (const float*)c->nmass.p,
                                                          (const double*)c->nvnew.p, (const float*)c->nx.p,
-                                                         (const double*)c->nvhat.p, alpha, d);
+                                                         (const double*)c->nvhat.p, alpha, d, (int)c->nb);
   if (c->ncb > 0)
     k_energy_cells<float><<<(unsigned)c->ncb, 256, 0, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
                                                              (const uint8_t*)c->cflag.p, (const float*)c->cacc.p,
