@@ -152,7 +152,7 @@ __device__ __forceinline__ void sh_add(T* p, T v) {
 
 // dynamic smem: nf * 729 T
 template <typename T>
-__global__ void __launch_bounds__(256) k_p2q(const int* __restrict__ cblist, const int* __restrict__ nbr,
+__global__ void __launch_bounds__(384) k_p2q(const int* __restrict__ cblist, const int* __restrict__ nbr,
                                              const int* __restrict__ start, const T* __restrict__ x,
                                              const T* __restrict__ v, const T* __restrict__ F,
                                              const T* __restrict__ G, const T* __restrict__ m,
@@ -460,7 +460,7 @@ static int p2q_q2n_t(mpml_ctx_s* c) {
   if (c->ncb > 0) {
     size_t smem = es * xi.nf * 729;
     cudaFuncSetAttribute(k_p2q<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_p2q<T><<<(unsigned)c->ncb, 256, smem, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
+    k_p2q<T><<<(unsigned)c->ncb, 384, smem, c->s>>>((const int*)c->cblist.p, (const int*)c->nbr.p,
                                                   (const int*)c->start.p, (const T*)c->px.p, (const T*)c->pv.p,
                                                   (const T*)c->pF.p, (const T*)c->pG.p, (const T*)c->pm.p,
                                                   (const T*)c->pV.p, (const int32_t*)c->pmat.p, xi, (T*)c->cacc.p);
