@@ -28,6 +28,9 @@ int batch_prep(mpml_ctx_s* c, double cg_rtol, int cg_max);
 void batch_slope_launch(mpml_ctx_s* c);
 void batch_energy_launch(mpml_ctx_s* c, double alpha);
 void batch_axpy_launch(mpml_ctx_s* c, double alpha);
+int batch_trial_launch(mpml_ctx_s* c, double cg_rtol, int cg_max);
+void batch_trial_revert(mpml_ctx_s* c);
+int batch_cg_start(mpml_ctx_s* c, double cg_rtol, int cg_max);
 
 struct BScene {
   const int* cblist;
@@ -526,13 +529,31 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
     }
     if ((rc = read_all(cs))) return rc;
     std::vector<double> slope(n), lsA(n), lsB(n), alpha(n, 1.0), phit_el(n, 0.0);
-    std::vector<int> accepted(n, 0);
+    std::vector<int> accepted(n, 0), lin(n, 0);
     for (int i : idx) {
       slope[i] = ctxs[i]->hscal->slope;
       lsA[i] = ctxs[i]->hscal->ls_a;
       lsB[i] = ctxs[i]->hscal->ls_b;
     }
-    for (int ls = 0; ls <= o->ls_max; ++ls) {
+    // the full step first, by each scene's prep at its trial iterate (as the single-scene
+    // solver): accepted, it is the next round's linearisation (CG start added); rejected,
+    // the scene goes back to v and halves from 1/2 with the line-search energy
+    for (int i : idx)
+      if ((rc = batch_trial_launch(ctxs[i], o->cg_rtol, o->cg_max))) return rc;
+    if ((rc = read_all(cs))) return rc;
+    for (int i : idx) {
+      const mpml_ctx_s* c = ctxs[i];
+      const double pel = c->hscal->phi_el, gg = c->hscal->gg;
+      const double dphi = lsA[i] + 0.5 * lsB[i] + (pel - phi_el[i]);
+      if (c->hscal->infeasible == 0 && dphi <= o->ls_c1 * slope[i] && gg == gg) {
+        accepted[i] = lin[i] = 1;
+        if ((rc = batch_cg_start(ctxs[i], o->cg_rtol, o->cg_max))) return rc;
+      } else {
+        batch_trial_revert(ctxs[i]);
+        alpha[i] = 0.5;
+      }
+    }
+    for (int ls = 1; ls <= o->ls_max; ++ls) {
       std::vector<mpml_ctx_s*> pend;
       std::vector<int> pidx;
       for (int i : idx)
@@ -562,6 +583,10 @@ int newton_batch(mpml_ctx_s** ctxs, int n, const mpml_solver_opts* o, mpml_solve
       if (!accepted[i]) {
         status[i] = MPML_WARN_NOT_CONVERGED;
         active[i] = 0;
+        continue;
+      }
+      if (lin[i]) {  // linearised at the trial iterate already
+        upd.push_back(ctxs[i]);
         continue;
       }
       batch_axpy_launch(ctxs[i], alpha[i]);

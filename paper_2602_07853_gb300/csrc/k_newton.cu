@@ -4344,6 +4344,18 @@ void batch_energy_launch(mpml_ctx_s* c, double alpha) {
   c->launches += 2;
 }
 
+// the line search's full step (see newton_t): v + dx into the trial buffer, made current, and
+// the prep there without the CG start; batch_trial_revert makes v current again
+int batch_trial_launch(mpml_ctx_s* c, double cg_rtol, int cg_max) {
+  k_axpy_out<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const float*)c->ndinv.p, (const float*)c->nx.p, 1.0,
+                                                     (const double*)c->nvnew.p, (double*)c->nvtry.p);
+  c->launches++;
+  std::swap(c->nvnew, c->nvtry);
+  return prep_t<float>(c, 1, 0, cg_rtol, cg_max, 1, 1);
+}
+void batch_trial_revert(mpml_ctx_s* c) { std::swap(c->nvnew, c->nvtry); }
+int batch_cg_start(mpml_ctx_s* c, double cg_rtol, int cg_max) { return cg_start_t<float>(c, cg_rtol, cg_max); }
+
 void batch_axpy_launch(mpml_ctx_s* c, double alpha) {
   k_axpy<float><<<(unsigned)c->nb, BV, 0, c->s>>>((const float*)c->ndinv.p, (const float*)c->nx.p, alpha,
                                                  (double*)c->nvnew.p);
