@@ -547,8 +547,9 @@ __device__ __forceinline__ double jm1_of_h(const double H[9]) {
 }
 
 // L = log(b) of b = F F^T = I + E, E = H + H^T + H H^T, without an eigen-decomposition
-// (log_spd_series); false where some |E_ij| > 0.03 (the caller takes the eigen-decomposition)
-__device__ bool hencky_log_b(const double H[9], Sym3<double>& L) {
+// (log_spd_series; with mixed, for the FP64 stress of FP32 contexts, the split below at the
+// smallest strains); false where some |E_ij| > 0.03 (the caller takes the eigen-decomposition)
+__device__ bool hencky_log_b(const double H[9], Sym3<double>& L, bool mixed) {
   double e[6];
   const int I[6] = {0, 1, 2, 0, 0, 1}, Jx[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
@@ -560,6 +561,27 @@ __device__ bool hencky_log_b(const double H[9], Sym3<double>& L) {
     e[q] = acc;
   }
   const Sym3<double> E = {e[0], e[1], e[2], e[3], e[4], e[5]};
+  const double mx = fmax(fmax(fmax(fabs(E.xx), fabs(E.yy)), fmax(fabs(E.zz), fabs(E.xy))), fmax(fabs(E.xz), fabs(E.yz)));
+  if (mixed && mx <= 0.01) {
+    // (FP32 contexts) |E| <= 0.03: log(I + E) = E - E^2/2 + R with the first two terms in FP64 and the
+    // remainder R = E^3 (1/3 - E/4 + E^2/5 - E^3/6 + E^4/7) (next term below 1e-7 of R) in
+    // FP32: R is at most 3e-4 of the logarithm, so its FP32 rounding stays below 1e-10 of it
+    const Sym3<double> E2 = sym_mul(E, E);
+    const Sym3<float> Ef = {(float)E.xx, (float)E.yy, (float)E.zz, (float)E.xy, (float)E.xz, (float)E.yz};
+    const float cs[5] = {1.f / 3.f, -1.f / 4.f, 1.f / 5.f, -1.f / 6.f, 1.f / 7.f};
+    Sym3<float> P = {cs[4], cs[4], cs[4], 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 3; k >= 0; --k) {
+      P = sym_mul(Ef, P);
+      P.xx += cs[k];
+      P.yy += cs[k];
+      P.zz += cs[k];
+    }
+    const Sym3<float> R = sym_mul(sym_mul(sym_mul(Ef, Ef), Ef), P);
+    L = {E.xx - 0.5 * E2.xx + (double)R.xx, E.yy - 0.5 * E2.yy + (double)R.yy, E.zz - 0.5 * E2.zz + (double)R.zz,
+         E.xy - 0.5 * E2.xy + (double)R.xy, E.xz - 0.5 * E2.xz + (double)R.xz, E.yz - 0.5 * E2.yz + (double)R.yz};
+    return true;
+  }
   return log_spd_series(E, L);
 }
 
@@ -574,12 +596,12 @@ __device__ __forceinline__ double hencky_psi(const MatParams<double>& M, const S
 // Hencky P S^T of F = (I + dt G) B = I + H in FP64 without an SVD, at small strain:
 // the Kirchhoff stress tau = mu L + lam/2 tr(L) I with L = log(F F^T), and P S^T =
 // tau F^{-T} B^T = tau (I + dt G)^{-T}.  Returns false outside hencky_log_b's range
-// or for J <= 0; psi is the energy by hencky_psi.
+// or for J <= 0; psi is the energy by hencky_psi; mixed as for hencky_log_b.
 __device__ bool hencky_closed_form(const MatParams<double>& M, const double Gd[9], const double H[9], double PSt[9],
-                                   double& psi) {
+                                   double& psi, bool mixed) {
   if (!(jm1_of_h(H) > -1.0)) return false;
   Sym3<double> L;
-  if (!hencky_log_b(H, L)) return false;
+  if (!hencky_log_b(H, L, mixed)) return false;
   psi = hencky_psi(M, L);
   const double hl = 0.5 * M.lam * (L.xx + L.yy + L.zz);
   const double tau[9] = {M.mu * L.xx + hl, M.mu * L.xy, M.mu * L.xz, M.mu * L.xy, M.mu * L.yy + hl,
@@ -694,7 +716,8 @@ __device__ bool fc_closed_form(const MatParams<double>& M, const double Gd[9], c
 // Energy density of F = I + H (FP64) from the eigenvalues of F^T F - I only;
 // returns false when it is undefined.  Fixed-corotated with J <= 0 (an inverted
 // cell, where the signed SVD is needed) reports `need_svd`.
-__device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double& psi, bool& need_svd) {
+__device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double& psi, bool& need_svd,
+                           bool mixed = false) {
   need_svd = false;
   const double Jm1 = jm1_of_h(H);
   if (M.model == MPML_NEO_HOOKEAN) {
@@ -727,7 +750,7 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
   }
   if (M.model == MPML_HENCKY && Jm1 > -1.0) {
     Sym3<double> L;
-    if (hencky_log_b(H, L)) {  // small strain: the log series (as hencky_closed_form)
+    if (hencky_log_b(H, L, mixed)) {  // small strain: the log series (as hencky_closed_form)
       psi = hencky_psi(M, L);
       return true;
     }
@@ -859,7 +882,7 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
   trial_h(Gd, bm, sm, H);
   if constexpr (sizeof(T) == 4) {
     double PSt[9], psi_h = 0.0;
-    const bool hencky = M.model == MPML_HENCKY && hencky_closed_form(M, Gd, H, PSt, psi_h);
+    const bool hencky = M.model == MPML_HENCKY && hencky_closed_form(M, Gd, H, PSt, psi_h, true);
     const bool closed = hencky || (M.model == MPML_NEO_HOOKEAN && nh_closed_form(M, Gd, H, PSt)) ||
                         (M.model == MPML_FIXED_COROTATED && fc_closed_form(M, Gd, H, sm, PSt));
     if (M.model == MPML_NEO_HOOKEAN && !closed) {
@@ -873,7 +896,7 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
       if (want_psi) {
         double psi = psi_h;  // Hencky: from the same L (psi_from_h's small-strain branch)
         bool need_svd;
-        if (!hencky && (!psi_from_h(M, H, psi, need_svd) || need_svd)) {
+        if (!hencky && (!psi_from_h(M, H, psi, need_svd, true) || need_svd)) {
           out.ok = false;
           return;
         }
@@ -923,7 +946,7 @@ __device__ void cell_material(const MatParams<double>& M, double V, const double
     // the energy by the same formula as the line search (k_energy_cells)
     double psi;
     bool need_svd;
-    if (!psi_from_h(M, H, psi, need_svd)) {
+    if (!psi_from_h(M, H, psi, need_svd, sizeof(T) == 4)) {
       out.ok = false;
       return;
     }
@@ -2042,7 +2065,7 @@ __global__ void __launch_bounds__(256) k_energy_cells(const int* __restrict__ cb
       trial_h(Gd, bm, sm, H);
       double psi;
       bool need_svd;
-      if (!psi_from_h(si.mat[k], H, psi, need_svd)) {
+      if (!psi_from_h(si.mat[k], H, psi, need_svd, sizeof(T) == 4)) {
         bad = 1;
         continue;
       }
