@@ -321,6 +321,30 @@ __global__ void __launch_bounds__(256) k_stretch(const int* __restrict__ cblist,
                                 tau[1] * i2m,        tau[2] * i2m,        tau[5] * i2m};
         const double mx = fmax(fmax(fmax(fabs(E.xx), fabs(E.yy)), fmax(fabs(E.zz), fabs(E.xy))),
                                fmax(fabs(E.xz), fabs(E.yz)));
+        if (sizeof(T) == 4 && mu > 0.0 && mx <= 0.01) {
+          // FP32 contexts, |eps| <= 0.03: E + E^2/2 in FP64 and the remainder E^3 (1/6 + E/24 +
+          // E^2/120 + E^3/720 + E^4/5040) in FP32 (at most 1.5e-4 of S - I: its rounding stays
+          // near 1e-11 of it)
+          const Sym3<double> E2 = sym_mul(E, E);
+          const Sym3<float> Ef = {(float)E.xx, (float)E.yy, (float)E.zz, (float)E.xy, (float)E.xz, (float)E.yz};
+          const float cs[5] = {1.f / 6.f, 1.f / 24.f, 1.f / 120.f, 1.f / 720.f, 1.f / 5040.f};
+          Sym3<float> Pf = {cs[4], cs[4], cs[4], 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int kk = 3; kk >= 0; --kk) {
+            Pf = sym_mul(Ef, Pf);
+            Pf.xx += cs[kk];
+            Pf.yy += cs[kk];
+            Pf.zz += cs[kk];
+          }
+          const Sym3<float> R = sym_mul(sym_mul(sym_mul(Ef, Ef), Ef), Pf);
+          so[0] = E.xx + 0.5 * E2.xx + (double)R.xx;
+          so[BV] = E.yy + 0.5 * E2.yy + (double)R.yy;
+          so[2 * BV] = E.zz + 0.5 * E2.zz + (double)R.zz;
+          so[3 * BV] = E.xy + 0.5 * E2.xy + (double)R.xy;
+          so[4 * BV] = E.xz + 0.5 * E2.xz + (double)R.xz;
+          so[5 * BV] = E.yz + 0.5 * E2.yz + (double)R.yz;
+          continue;
+        }
         if (mu > 0.0 && mx <= 0.03) {
           Sym3<double> P = {1.0 + E.xx / 9.0, 1.0 + E.yy / 9.0, 1.0 + E.zz / 9.0, E.xy / 9.0, E.xz / 9.0, E.yz / 9.0};
 #pragma unroll
@@ -597,11 +621,20 @@ __device__ __forceinline__ double hencky_psi(const MatParams<double>& M, const S
 // the Kirchhoff stress tau = mu L + lam/2 tr(L) I with L = log(F F^T), and P S^T =
 // tau F^{-T} B^T = tau (I + dt G)^{-T}.  Returns false outside hencky_log_b's range
 // or for J <= 0; psi is the energy by hencky_psi; mixed as for hencky_log_b.
+// det(I + H) > 0 where hencky_log_b accepted H: there F F^T is within 0.1 of I, so |det F| is
+// near 1 and its sign is safe in FP32
+__device__ __forceinline__ bool det_positive_near_rotation(const double H[9]) {
+  float f[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) f[q] = (float)H[q] + ((q % 4 == 0) ? 1.f : 0.f);
+  return f[0] * (f[4] * f[8] - f[5] * f[7]) - f[1] * (f[3] * f[8] - f[5] * f[6]) + f[2] * (f[3] * f[7] - f[4] * f[6]) >
+         0.f;
+}
+
 __device__ bool hencky_closed_form(const MatParams<double>& M, const double Gd[9], const double H[9], double PSt[9],
                                    double& psi, bool mixed) {
-  if (!(jm1_of_h(H) > -1.0)) return false;
   Sym3<double> L;
-  if (!hencky_log_b(H, L, mixed)) return false;
+  if (!hencky_log_b(H, L, mixed) || !det_positive_near_rotation(H)) return false;
   psi = hencky_psi(M, L);
   const double hl = 0.5 * M.lam * (L.xx + L.yy + L.zz);
   const double tau[9] = {M.mu * L.xx + hl, M.mu * L.xy, M.mu * L.xz, M.mu * L.xy, M.mu * L.yy + hl,
@@ -719,6 +752,13 @@ __device__ bool fc_closed_form(const MatParams<double>& M, const double Gd[9], c
 __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double& psi, bool& need_svd,
                            bool mixed = false) {
   need_svd = false;
+  if (M.model == MPML_HENCKY) {
+    Sym3<double> L;
+    if (hencky_log_b(H, L, mixed) && det_positive_near_rotation(H)) {  // small strain (as hencky_closed_form)
+      psi = hencky_psi(M, L);
+      return true;
+    }
+  }
   const double Jm1 = jm1_of_h(H);
   if (M.model == MPML_NEO_HOOKEAN) {
     if (!(Jm1 > -1.0)) return false;
@@ -747,13 +787,6 @@ __device__ bool psi_from_h(const MatParams<double>& M, const double H[9], double
     if (!(Jm1 > -1.0)) return false;
     psi = 0.5 * (M.lam + 2.0 / 3.0 * M.mu) * Jm1 * Jm1;
     return true;
-  }
-  if (M.model == MPML_HENCKY && Jm1 > -1.0) {
-    Sym3<double> L;
-    if (hencky_log_b(H, L, mixed)) {  // small strain: the log series (as hencky_closed_form)
-      psi = hencky_psi(M, L);
-      return true;
-    }
   }
   double E[9];
 #pragma unroll
