@@ -353,7 +353,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_text(args.n), "grid": args.n, "particles": full_p, "precision": "fp64",
-                       "preconditioner": "jacobi", "cg_rtol": 1e-6, "newton_rtol": 1e-6},
+                       "preconditioner": "jacobi", "cg_rtol": 1e-6, "newton_rtol": 1e-6,
+                       "cg_forcing": 0.0},
             "extrapolated_ms_per_step": 1e3 / value,
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle", "sample": sample,
                              "host": cpu},

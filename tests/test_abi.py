@@ -63,8 +63,9 @@ def test_struct_layouts_match_header(tmp_path):
 int main(void){
  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(mpml_scene_desc), sizeof(mpml_material), sizeof(mpml_particles),
         sizeof(mpml_solver_opts), sizeof(mpml_solve_stats), sizeof(mpml_pcg_config));
- printf("%zu %zu %zu %zu\n", offsetof(mpml_scene_desc, plate_vel), offsetof(mpml_particles, perm),
-        offsetof(mpml_solve_stats, g0_norm), offsetof(mpml_solve_stats, n_bricks));
+ printf("%zu %zu %zu %zu %zu\n", offsetof(mpml_scene_desc, plate_vel), offsetof(mpml_particles, perm),
+        offsetof(mpml_solve_stats, g0_norm), offsetof(mpml_solve_stats, n_bricks),
+        offsetof(mpml_solver_opts, cg_forcing));
  return 0;}
 ''')
     exe = tmp_path / "layout"
@@ -75,7 +76,8 @@ int main(void){
     assert sizes == [ctypes.sizeof(t) for t in (m.mpml_scene_desc, m.mpml_material, m.mpml_particles,
                                                  m.mpml_solver_opts, m.mpml_solve_stats, m.mpml_pcg_config)]
     assert offs == [m.mpml_scene_desc.plate_vel.offset, m.mpml_particles.perm.offset,
-                    m.mpml_solve_stats.g0_norm.offset, m.mpml_solve_stats.n_bricks.offset]
+                    m.mpml_solve_stats.g0_norm.offset, m.mpml_solve_stats.n_bricks.offset,
+                    m.mpml_solver_opts.cg_forcing.offset]
 
 
 def test_noalloc_sort_rejects_on_the_host(lib_path):

@@ -30,6 +30,7 @@ def test_reference_arm_line():
     assert d["value"] > 0 and d["ms_per_step"] > 0
     assert abs(d["extrapolated_ms_per_step"] - 1e3 / d["value"]) <= 1e-6 * d["extrapolated_ms_per_step"]
     assert isinstance(d["config"], dict) and "workload" in d["config"]
+    assert d["config"]["cg_forcing"] == 0.0  # the oracle solves every CG system to cg_rtol
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert cb["host"]["nproc"] >= 1
